@@ -1,0 +1,496 @@
+/*
+ * vr_oracle.c -- plain, slow, FP64 CPU ray caster for noisy spectral cubes.
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark load this library.  It shares no code, header, table
+ * or helper with the CUDA path; it reads the cube in its plain linear layout
+ * (x fastest, then y, then z) and knows nothing of bricks.
+ *
+ * What it computes (paper §3.1, process item 3: every output pixel becomes
+ * one ray, and the ray is mapped to RGBA by a pre-selected transfer
+ * function; the abstract's emphasis on low signal-to-noise data motivates
+ * the clip).  The paper prints no formulas, so each step below is the
+ * reading this project fixes, evaluated in double precision on the stored
+ * voxel values:
+ *
+ *   camera -> ray   u = px + 1/2 - w/2, v = py + 1/2 - h/2;
+ *                   ortho: o = eye + u du + v dv, d = fwd / |fwd|;
+ *                   persp: o = eye, d = (fwd + u du + v dv) / |...|.
+ *   ray / box       box = [0, n-1] per axis (between the first and last voxel
+ *                   centres).  Slab test; an axis with d_i == 0 passes iff
+ *                   0 <= o_i <= n_i - 1 (no division).  t_entry = max(0,
+ *                   max t_near), t_exit = min t_far, hit iff t_exit >= t_entry.
+ *   samples         K = floor((t_exit - t_entry) / step) + 1 if hit, else 0;
+ *                   t_k = t_entry + k step from the integer k; p_k = o + t_k d
+ *                   clamped to the box.
+ *   trilinear       i0 = min(floor(p), n - 2), f = p - i0 per axis; the eight
+ *                   corners are interpolated along x, then y, then z with
+ *                   lerp(a, b, f) = a + f (b - a).
+ *   transfer fn.    s < clip: fully transparent (skipped).  Otherwise
+ *                   x = clamp((s - v_lo) / (v_hi - v_lo), 0, 1) (N - 1),
+ *                   i = min(floor(x), N - 2), RGBA = lerp(L'[i], L'[i+1], x - i)
+ *                   where L' is the table with alpha' = 1 - (1 - alpha)^step
+ *                   (opacity per unit voxel length corrected to the step).
+ *   composite       front to back: C += (1 - A) alpha rgb, A += (1 - A) alpha;
+ *                   after each composited sample the ray stops once
+ *                   A >= term_alpha.  Output premultiplied (C, A); K = 0 -> 0.
+ *   MIP             max_k s_k (raw value); K = 0 -> -infinity.
+ *   SUM             sum_k s_k * step (an additive mode used only by tests).
+ *
+ * Storage types: float32 values; IEEE binary16 bit patterns (decoded here
+ * from the format's definition); int8 codes q with a per-frequency-plane
+ * scale and offset, value = q * scale[z] + offset[z] evaluated in double.
+ *
+ * Acceptance sets.  Three places turn an arbitrarily small perturbation of
+ * the arithmetic into a finite change of the result: the sample count K, the
+ * clip test, and the termination test.  A single-precision implementation can
+ * legitimately land on the other side of each.  For every pixel the oracle
+ * therefore returns the primary double-precision result plus the results of
+ * the alternative decisions whose deciding quantity lies within a stated band
+ * of its threshold (bands are inputs; the tests state them):
+ *   K band      (t_exit - t_entry)/step within band_k of an integer (this also
+ *               covers near-miss / grazing rays, K = 0 <-> 1, and rays lying
+ *               within band_pos of a face plane they are parallel to);
+ *   clip band   |s - clip| <= band_clip * max(1, |s|) where the table's alpha
+ *               at the clip level is non-zero (the sample's decision is
+ *               flipped alone);
+ *   term band   every composited sample from the first with A >= ta - band_a
+ *               up to the first with A >= ta + band_a is a possible stop.
+ * Flags: bit 0 K tie, bit 1 clip tie, bit 2 termination tie, bit 3 the
+ * alternative list was truncated at VRO_MAXALT.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define VRO_MAXALT 8
+#define VRO_MAXCLIP 2
+
+enum { VRO_F32 = 0, VRO_F16 = 1, VRO_I8 = 2 };
+enum { VRO_MIP = 0, VRO_COMPOSITE = 1, VRO_SUM = 2 };
+enum { VRO_ORTHO = 0, VRO_PERSP = 1 };
+
+/* One camera record as laid out in memory by the callers (64 bytes). */
+typedef struct {
+    int32_t proj;
+    float eye[3], fwd[3], du[3], dv[3], pad[3];
+} vro_camera;
+
+typedef struct {
+    int64_t n[3];          /* nx, ny, nz */
+    int32_t dtype;         /* VRO_F32 / VRO_F16 / VRO_I8 */
+    const void* data;      /* n[0]*n[1]*n[2] elements, x fastest */
+    const float* scale;    /* int8 only: per z plane */
+    const float* offset;   /* int8 only: per z plane */
+} vro_volume;
+
+typedef struct {
+    const float* lut;      /* n_lut x 4 (r, g, b, alpha per unit length) */
+    int32_t n_lut;
+    double v_lo, v_hi, clip, term_alpha;
+} vro_tf;
+
+typedef struct {
+    double band_k, band_pos, band_clip, band_a;
+} vro_bands;
+
+/* ------------------------------------------------------------------ */
+/* storage decoding                                                     */
+/* ------------------------------------------------------------------ */
+
+/* IEEE 754 binary16: 1 sign bit, 5 exponent bits (bias 15), 10 fraction bits. */
+static double half_to_double(uint16_t h)
+{
+    int sign = (h >> 15) & 1;
+    int e = (h >> 10) & 0x1f;
+    int m = h & 0x3ff;
+    double v;
+    if (e == 0)
+        v = ldexp((double)m, -24);                 /* zero / subnormal */
+    else if (e == 31)
+        v = (m == 0) ? INFINITY : NAN;
+    else
+        v = ldexp((double)(1024 + m), e - 25);     /* (1 + m/1024) 2^(e-15) */
+    return sign ? -v : v;
+}
+
+static double voxel(const vro_volume* vol, int64_t i, int64_t j, int64_t k)
+{
+    int64_t idx = (k * vol->n[1] + j) * vol->n[0] + i;
+    switch (vol->dtype) {
+    case VRO_F32:
+        return (double)((const float*)vol->data)[idx];
+    case VRO_F16:
+        return half_to_double(((const uint16_t*)vol->data)[idx]);
+    default:
+        return (double)((const int8_t*)vol->data)[idx] * (double)vol->scale[k]
+               + (double)vol->offset[k];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* geometry                                                             */
+/* ------------------------------------------------------------------ */
+
+static void make_ray(const vro_camera* c, int w, int h, int px, int py,
+                     double o[3], double d[3])
+{
+    double u = px + 0.5 - w / 2.0;
+    double v = py + 0.5 - h / 2.0;
+    double nrm = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (c->proj == VRO_ORTHO) {
+            o[a] = (double)c->eye[a] + u * (double)c->du[a] + v * (double)c->dv[a];
+            d[a] = (double)c->fwd[a];
+        } else {
+            o[a] = (double)c->eye[a];
+            d[a] = (double)c->fwd[a] + u * (double)c->du[a] + v * (double)c->dv[a];
+        }
+        nrm += d[a] * d[a];
+    }
+    nrm = sqrt(nrm);
+    for (int a = 0; a < 3; ++a) d[a] /= nrm;
+}
+
+/* Slab test over the axes the ray is not parallel to: t_near/t_far (t_near
+ * unclamped).  For the parallel axes (d_i == 0, no division) it reports
+ * *miss_dist, how far outside [0, n_i - 1] the worst excluded coordinate lies
+ * (0 when none is excluded), and *face_dist, the smallest distance of an
+ * included coordinate to one of its two face planes (infinity if none).   */
+static void slab(const double o[3], const double d[3], const int64_t n[3],
+                 double* t_near, double* t_far, double* miss_dist, double* face_dist)
+{
+    double tn = -INFINITY, tf = INFINITY;
+    *miss_dist = 0.0;
+    *face_dist = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        double hi = (double)(n[a] - 1);
+        if (d[a] != 0.0) {
+            double ta = (0.0 - o[a]) / d[a];
+            double tb = (hi - o[a]) / d[a];
+            double lo_t = ta < tb ? ta : tb;
+            double hi_t = ta < tb ? tb : ta;
+            if (lo_t > tn) tn = lo_t;
+            if (hi_t < tf) tf = hi_t;
+        } else if (o[a] < 0.0 || o[a] > hi) {
+            double md = o[a] < 0.0 ? -o[a] : o[a] - hi;
+            if (md > *miss_dist) *miss_dist = md;
+        } else {
+            double fd = fmin(o[a], hi - o[a]);
+            if (fd < *face_dist) *face_dist = fd;
+        }
+    }
+    *t_near = tn;
+    *t_far = tf;
+}
+
+static double lerp(double a, double b, double f) { return a + f * (b - a); }
+
+static double sample(const vro_volume* vol, const double o[3], const double d[3],
+                     double t)
+{
+    double p[3], f[3];
+    int64_t i0[3];
+    for (int a = 0; a < 3; ++a) {
+        double hi = (double)(vol->n[a] - 1);
+        p[a] = o[a] + t * d[a];
+        if (p[a] < 0.0) p[a] = 0.0;
+        if (p[a] > hi) p[a] = hi;
+        int64_t fl = (int64_t)floor(p[a]);
+        if (fl > vol->n[a] - 2) fl = vol->n[a] - 2;
+        i0[a] = fl;
+        f[a] = p[a] - (double)fl;
+    }
+    double c[2][2][2];
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx)
+                c[cz][cy][cx] = voxel(vol, i0[0] + cx, i0[1] + cy, i0[2] + cz);
+    double y0z0 = lerp(c[0][0][0], c[0][0][1], f[0]);
+    double y1z0 = lerp(c[0][1][0], c[0][1][1], f[0]);
+    double y0z1 = lerp(c[1][0][0], c[1][0][1], f[0]);
+    double y1z1 = lerp(c[1][1][0], c[1][1][1], f[0]);
+    double z0 = lerp(y0z0, y1z0, f[1]);
+    double z1 = lerp(y0z1, y1z1, f[1]);
+    return lerp(z0, z1, f[2]);
+}
+
+/* ------------------------------------------------------------------ */
+/* transfer function                                                    */
+/* ------------------------------------------------------------------ */
+
+/* Table with alpha corrected from unit voxel length to the step length. */
+static void correct_table(const vro_tf* tf, double step, double* lutc)
+{
+    for (int i = 0; i < tf->n_lut; ++i) {
+        for (int c = 0; c < 3; ++c) lutc[4 * i + c] = (double)tf->lut[4 * i + c];
+        double a = (double)tf->lut[4 * i + 3];
+        lutc[4 * i + 3] = 1.0 - pow(1.0 - a, step);
+    }
+}
+
+static void classify(const vro_tf* tf, const double* lutc, double s, double rgba[4])
+{
+    int n = tf->n_lut;
+    double x = (s - tf->v_lo) / (tf->v_hi - tf->v_lo);
+    if (x < 0.0) x = 0.0;
+    if (x > 1.0) x = 1.0;
+    x *= (double)(n - 1);
+    int i = (int)floor(x);
+    if (i > n - 2) i = n - 2;
+    double w = x - (double)i;
+    for (int c = 0; c < 4; ++c) rgba[c] = lerp(lutc[4 * i + c], lutc[4 * (i + 1) + c], w);
+}
+
+/* ------------------------------------------------------------------ */
+/* per-ray marches                                                      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double v[VRO_MAXALT][4];
+    int n;
+    int flags;
+} alts;
+
+static void push(alts* r, const double v[4])
+{
+    for (int i = 0; i < r->n; ++i)      /* identical results add nothing */
+        if (r->v[i][0] == v[0] && r->v[i][1] == v[1] && r->v[i][2] == v[2] &&
+            r->v[i][3] == v[3])
+            return;
+    if (r->n >= VRO_MAXALT) { r->flags |= 8; return; }
+    memcpy(r->v[r->n++], v, 4 * sizeof(double));
+}
+
+/* MIP or SUM over samples 0..K-1; returns the count of samples. */
+static int64_t march_scalar(const vro_volume* vol, int mode, const double o[3],
+                            const double d[3], double t_entry, int64_t K, double step,
+                            double* result)
+{
+    double m = -INFINITY, acc = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+        double s = sample(vol, o, d, t_entry + (double)k * step);
+        if (mode == VRO_MIP) { if (s > m) m = s; }
+        else acc += s * step;
+    }
+    *result = (mode == VRO_MIP) ? m : acc;
+    return K;
+}
+
+/* Emission-absorption march over samples 0..K-1.  flip_k >= 0 inverts the
+ * clip decision of that one sample.  The primary stopping state is pushed to
+ * *r first, then every other possible stopping state of the term band.  When
+ * more than VRO_MAXALT - 1 band states occur, the first VRO_MAXALT - 1 and the
+ * latest are kept (flag 8); all states in a band lie between those, because
+ * C and A never decrease.  Samples near the clip are reported through
+ * clip_k[] (up to VRO_MAXCLIP).  Returns the primary rule's sample count. */
+static int64_t march_composite(const vro_volume* vol, const vro_tf* tf,
+                               const double* lutc, const double o[3], const double d[3],
+                               double t_entry, int64_t K, double step, int64_t flip_k,
+                               const vro_bands* b, alts* r, int64_t* clip_k, int* n_clip)
+{
+    double C[3] = {0, 0, 0}, A = 0.0;
+    double ta = tf->term_alpha;
+    double clip_rgba[4];
+    classify(tf, lutc, tf->clip, clip_rgba);
+    double prim[4];
+    int have_prim = 0;
+    int64_t prim_count = K;
+    double cand[VRO_MAXALT][4];
+    int n_cand = 0;
+    if (n_clip) *n_clip = 0;
+    for (int64_t k = 0; k < K; ++k) {
+        double s = sample(vol, o, d, t_entry + (double)k * step);
+        int keep = !(s < tf->clip);
+        if (n_clip && clip_rgba[3] > 0.0 &&
+            fabs(s - tf->clip) <= b->band_clip * fmax(1.0, fabs(s)) &&
+            *n_clip < VRO_MAXCLIP)
+            clip_k[(*n_clip)++] = k;
+        if (k == flip_k) keep = !keep;
+        if (!keep) continue;
+        double rgba[4];
+        classify(tf, lutc, s, rgba);
+        double wgt = (1.0 - A) * rgba[3];
+        for (int c = 0; c < 3; ++c) C[c] += wgt * rgba[c];
+        A += wgt;
+        if (A >= ta - b->band_a) {
+            double st[4] = {C[0], C[1], C[2], A};
+            int slot;
+            if (n_cand < VRO_MAXALT) {
+                slot = n_cand++;
+            } else {
+                slot = VRO_MAXALT - 1;
+                r->flags |= 8;
+            }
+            memcpy(cand[slot], st, sizeof st);
+            if (!have_prim && A >= ta) {
+                memcpy(prim, st, sizeof st);
+                have_prim = 1;
+                prim_count = k + 1;
+            }
+            if (A >= ta + b->band_a) break;
+        }
+    }
+    if (!have_prim) {             /* never reached the threshold: end state */
+        prim[0] = C[0]; prim[1] = C[1]; prim[2] = C[2]; prim[3] = A;
+        prim_count = K;
+    }
+    int before = r->n;
+    push(r, prim);
+    for (int i = 0; i < n_cand; ++i) push(r, cand[i]);
+    if (r->n - before > 1) r->flags |= 4;
+    return prim_count;
+}
+
+/* ------------------------------------------------------------------ */
+/* one pixel                                                            */
+/* ------------------------------------------------------------------ */
+
+static void render_pixel(const vro_volume* vol, const vro_camera* cam, int w, int h,
+                         int px, int py, int mode, double step, const vro_tf* tf,
+                         const double* lutc, const vro_bands* b, alts* r,
+                         int64_t* nsamples)
+{
+    double o[3], d[3];
+    make_ray(cam, w, h, px, py, o, d);
+
+    double tn, tf_, miss_dist, face_dist;
+    slab(o, d, vol->n, &tn, &tf_, &miss_dist, &face_dist);
+    double t_entry = tn > 0.0 ? tn : 0.0;
+    double t_exit = tf_;
+    double q = (t_exit - t_entry) / step;
+    int hit = miss_dist == 0.0 && t_exit >= t_entry;
+
+    /* candidate sample counts, primary first */
+    int64_t Ks[4];
+    int nK = 0;
+    if (hit) {
+        double fl = floor(q);
+        int64_t K = (int64_t)fl + 1;
+        Ks[nK++] = K;
+        if (q - fl < b->band_k) Ks[nK++] = K - 1;
+        if (q - fl > 1.0 - b->band_k) Ks[nK++] = K + 1;
+        if (face_dist <= b->band_pos) Ks[nK++] = 0;
+    } else {
+        Ks[nK++] = 0;
+        /* a near miss: slightly different rounding could give a short hit */
+        if (miss_dist <= b->band_pos && q >= -b->band_k)
+            Ks[nK++] = q < 0.0 ? 1 : (int64_t)floor(q) + 1;
+    }
+    if (nK > 1) r->flags |= 1;
+
+    for (int ik = 0; ik < nK; ++ik) {
+        int64_t K = Ks[ik];
+        if (mode == VRO_COMPOSITE) {
+            if (K == 0) {
+                double z[4] = {0, 0, 0, 0};
+                push(r, z);
+                if (ik == 0) *nsamples = 0;
+                continue;
+            }
+            int64_t clip_k[VRO_MAXCLIP];
+            int n_clip = 0;
+            int64_t cnt = march_composite(vol, tf, lutc, o, d, t_entry, K, step, -1, b, r,
+                                          clip_k, &n_clip);
+            if (ik == 0) *nsamples = cnt;
+            for (int ic = 0; ic < n_clip; ++ic) {
+                r->flags |= 2;
+                march_composite(vol, tf, lutc, o, d, t_entry, K, step, clip_k[ic], b, r,
+                                NULL, NULL);
+            }
+        } else {
+            double v[4] = {0, 0, 0, 0};
+            int64_t cnt = march_scalar(vol, mode, o, d, t_entry, K, step, &v[0]);
+            push(r, v);
+            if (ik == 0) *nsamples = cnt;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* exported entry points                                                */
+/* ------------------------------------------------------------------ */
+
+int vro_maxalt(void) { return VRO_MAXALT; }
+
+int vro_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/*
+ * Render a list of pixels.  pix holds npix triples (view, px, py).  For pixel
+ * i, out[i*VRO_MAXALT*4 + a*4 + c] is channel c of acceptable result a
+ * (a < nalt[i]; a = 0 is the primary double-precision result; MIP and SUM use
+ * channel 0 only).  nsamples[i] is the primary result's count of evaluated
+ * samples.  nthreads <= 0 uses the OpenMP default.  Returns 0, or -1 on bad
+ * arguments.
+ */
+int vro_render(const vro_volume* vol, const vro_camera* cams, int n_views, int w, int h,
+               int mode, double step, const vro_tf* tf, const vro_bands* bands,
+               const int32_t* pix, int64_t npix, double* out, int32_t* nalt,
+               int32_t* flags, int64_t* nsamples, int nthreads)
+{
+    if (!vol || !cams || !tf || !bands || !pix || !out || !nalt || !flags || !nsamples)
+        return -1;
+    if (vol->n[0] < 2 || vol->n[1] < 2 || vol->n[2] < 2 || !(step > 0.0) ||
+        tf->n_lut < 2 || w <= 0 || h <= 0 || n_views <= 0)
+        return -1;
+    if (mode != VRO_MIP && mode != VRO_COMPOSITE && mode != VRO_SUM) return -1;
+    double* lutc = (double*)malloc(sizeof(double) * 4 * (size_t)tf->n_lut);
+    if (!lutc) return -1;
+    correct_table(tf, step, lutc);
+    int bad = 0;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt) reduction(| : bad)
+#endif
+    for (int64_t i = 0; i < npix; ++i) {
+        int view = pix[3 * i], px = pix[3 * i + 1], py = pix[3 * i + 2];
+        if (view < 0 || view >= n_views || px < 0 || px >= w || py < 0 || py >= h) {
+            bad = 1;
+            continue;
+        }
+        alts r;
+        r.n = 0;
+        r.flags = 0;
+        int64_t ns = 0;
+        render_pixel(vol, &cams[view], w, h, px, py, mode, step, tf, lutc, bands, &r, &ns);
+        memset(&out[i * VRO_MAXALT * 4], 0, sizeof(double) * VRO_MAXALT * 4);
+        for (int a = 0; a < r.n; ++a)
+            memcpy(&out[(i * VRO_MAXALT + a) * 4], r.v[a], 4 * sizeof(double));
+        nalt[i] = r.n;
+        flags[i] = r.flags;
+        nsamples[i] = ns;
+    }
+    (void)nthreads;
+    free(lutc);
+    return bad ? -1 : 0;
+}
+
+/* Exposed pieces for the oracle's own tests: one trilinear sample at a point
+ * and the corrected table entry for a value.                             */
+double vro_sample_at(const vro_volume* vol, double x, double y, double z)
+{
+    double o[3] = {x, y, z}, d[3] = {0, 0, 0};
+    return sample(vol, o, d, 0.0);
+}
+
+void vro_classify(const vro_tf* tf, double step, double s, double* rgba)
+{
+    double* lutc = (double*)malloc(sizeof(double) * 4 * (size_t)tf->n_lut);
+    if (!lutc) return;
+    correct_table(tf, step, lutc);
+    classify(tf, lutc, s, rgba);
+    free(lutc);
+}
+
+double vro_half_to_double(uint16_t h) { return half_to_double(h); }
