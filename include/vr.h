@@ -1,0 +1,186 @@
+/*
+ * vr.h -- C ABI of libvr, a ray caster for noisy RA x Dec x frequency
+ * spectral cubes on NVIDIA B300 (sm_103a).
+ *
+ * The operation (paper §3.1, process item 3): every output pixel is mapped
+ * to one ray through the cube, and the ray to a colour plus opacity (RGBA)
+ * through a pre-selected transfer function, or to a maximum-intensity value.
+ * The paper states the problem, not the arithmetic; the arithmetic this
+ * library implements is:
+ *
+ *   camera -> ray   u = px + 1/2 - w/2, v = py + 1/2 - h/2 (pixel centres);
+ *                   VR_ORTHO: origin eye + u du + v dv, direction fwd/|fwd|;
+ *                   VR_PERSP: origin eye, direction (fwd + u du + v dv)/|..|.
+ *   ray / box       box [0, n-1] on each axis (voxel centres at integers);
+ *                   slab test, an axis the ray is parallel to passes iff the
+ *                   origin lies within [0, n-1] on it.  t_entry = max(0,
+ *                   largest near distance), t_exit = smallest far distance.
+ *   samples         K = floor((t_exit - t_entry)/step) + 1 when the ray hits;
+ *                   sample k sits at t_entry + k*step (from the integer k,
+ *                   never an accumulated t), clamped to the box.
+ *   trilinear       i0 = min(floor(p), n-2), f = p - i0 per axis; the eight
+ *                   corners are interpolated along x, then y, then z.
+ *   transfer fn.    (paper abstract: special attention to low signal-to-
+ *                   noise data) samples below `clip` are fully transparent;
+ *                   others are looked up, with linear interpolation, in an
+ *                   RGBA table spanning [v_lo, v_hi] whose opacities are per
+ *                   unit voxel length and are corrected to the step as
+ *                   alpha' = 1 - (1 - alpha)^step.
+ *   VR_COMPOSITE    front to back: C += (1-A) alpha rgb, A += (1-A) alpha; a
+ *                   ray stops after the first composited sample with
+ *                   A >= term_alpha.  Output premultiplied RGBA, 0 on a miss.
+ *   VR_MIP          maximum sample value (raw data units), -inf on a miss.
+ *   VR_SUM          sum of sample * step (an additive mode for testing).
+ *
+ * Arithmetic is single precision with FP32 accumulation whatever the
+ * storage type.
+ *
+ * Memory.  The caller owns all device memory: the brick buffer of each
+ * volume (size from vr_volume_bytes), every source and every output buffer.
+ * The library owns only the small host-side handle.  Every call that takes a
+ * stream (a cudaStream_t passed as void*, NULL = legacy default stream) is
+ * asynchronous on it: argument errors are reported synchronously; a device
+ * fault surfaces at the caller's next synchronisation.  The library never
+ * synchronises the device on its own and never falls back to the CPU.
+ *
+ * Errors.  Every function returns VR_OK (0) or a negative VR_ERR_* code;
+ * vr_last_error() then gives a message (thread-local, valid until the next
+ * failing call on that thread).
+ *
+ * Thread safety.  Distinct volumes may be used from distinct threads.  A
+ * volume must not be modified (vr_set_transfer, vr_volume_upload,
+ * vr_volume_destroy) while another thread uses it.
+ */
+#ifndef VR_H
+#define VR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VR_OK 0
+#define VR_ERR_ARG (-1)          /* invalid argument (null, size, alignment) */
+#define VR_ERR_OOM (-2)          /* caller-provided buffer too small        */
+#define VR_ERR_CUDA (-3)         /* a CUDA call or kernel launch failed      */
+#define VR_ERR_TIMEOUT (-4)      /* a bounded device wait gave up            */
+#define VR_ERR_UNSUPPORTED (-5)  /* feature not available on this device    */
+
+#define VR_BRICK 32              /* bricks are 32 x 32 x 32 voxels           */
+#define VR_MAX_LUT 256           /* largest transfer-function table          */
+
+typedef enum { VR_F32 = 0, VR_F16 = 1, VR_I8 = 2 } vr_dtype;
+typedef enum { VR_MIP = 0, VR_COMPOSITE = 1, VR_SUM = 2 } vr_mode;
+typedef enum { VR_ORTHO = 0, VR_PERSP = 1 } vr_proj;
+
+/* One camera, 64 bytes, lengths in voxel units (paper §3.1 item 3: the
+ * camera is what maps each output pixel to a ray).  du and dv are the image
+ * plane's per-pixel steps (for VR_PERSP at unit distance from the eye);
+ * pixel rows run along dv.  `reserved` must be zero.                     */
+typedef struct {
+    int32_t proj;
+    float eye[3];
+    float fwd[3];
+    float du[3];
+    float dv[3];
+    float reserved[3];
+} vr_camera;
+
+typedef struct vr_volume_s* vr_volume;
+
+/* Device bytes a volume of the given dims (nx, ny, nz: x = RA fastest,
+ * y = Dec, z = frequency channel slowest) and storage dtype occupies: the
+ * voxels in 32^3 bricks (the paper's sub-cube partitioning, §3.1 process
+ * item 1, at on-chip granularity), plus for VR_I8 two float tables of nz
+ * entries.  Each dim must be in [2, 2^20] and the padded voxel count below
+ * 2^40.                                                                    */
+int vr_volume_bytes(const int64_t dims[3], int dtype, size_t* bytes_out);
+
+/* Bind a caller-owned device buffer as a volume and, when src is not NULL,
+ * pack the whole cube into it.
+ *   dims         nx, ny, nz as above.
+ *   dtype        storage type: VR_F32 (as given), VR_F16 (round to nearest
+ *                even), VR_I8 (per frequency plane z: lo = min, hi = max,
+ *                scale = (hi - lo)/254, offset = (hi + lo)/2, code =
+ *                clamp(rint((v - offset)/scale), -127, 127); a constant
+ *                plane gets scale 1 and code 0).  Decoding is
+ *                code * scale + offset, before interpolation.
+ *   src          float32 cube, linear, x fastest (nz*ny*nx values), or NULL
+ *                to bind without data (fill later with vr_volume_upload).
+ *   src_on_device 1: src is device memory.  0: src is page-locked host memory
+ *                (e.g. cudaHostAlloc'ed or registered), read by the packing
+ *                kernels directly; pageable host memory is rejected.
+ *   brick_buf    device memory of at least vr_volume_bytes(), 256-byte
+ *                aligned; owned by the caller, must outlive the volume.
+ *   stream       cudaStream_t as void*; src may be released once the stream
+ *                has passed this call.
+ *   out          receives the handle (library-owned host memory; release
+ *                with vr_volume_destroy).
+ * The volume starts with a default transfer function (clip -inf, a grey
+ * ramp over [0, 1], no early termination).                                 */
+int vr_volume_create(const int64_t dims[3], int dtype, const float* src,
+                     int src_on_device, void* brick_buf, size_t brick_bytes,
+                     void* stream, vr_volume* out);
+
+/* Pack planes [z0, z0 + nplanes) of the cube from a float32 source holding
+ * exactly those planes (nplanes*ny*nx values, x fastest).  Lets a cube be
+ * filled in slabs of frequency channels.  src_on_device and stream as in
+ * vr_volume_create.                                                        */
+int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* src,
+                     int src_on_device, void* stream);
+
+/* Set the transfer function (paper §3.1 item 3, "pre-selected transfer
+ * function"; abstract: low signal-to-noise emphasis -> the clip).
+ *   rgba_lut     host memory, n entries of (r, g, b, alpha), alpha per unit
+ *                voxel length in [0, 1]; copied, may be freed on return.
+ *   n            2 .. VR_MAX_LUT.
+ *   v_lo < v_hi  value domain the table spans (values outside clamp).
+ *   clip         samples below clip are skipped (transparent).
+ *   term_alpha   composite rays stop once A >= term_alpha (1 = only when
+ *                fully opaque; values > 1 disable termination).
+ * Applies to renders issued after the call returns.                        */
+int vr_set_transfer(vr_volume vol, const float* rgba_lut, int n, float v_lo,
+                     float v_hi, float clip, float term_alpha);
+
+/* Render n_views images of w x h pixels (spec call; paper §3.1 item 3
+ * and item 4: one image per view at the output resolution).
+ *   cams         host array of n_views cameras; copied, may be freed on
+ *                return.
+ *   mode         VR_MIP / VR_COMPOSITE / VR_SUM.
+ *   step         sample spacing in voxel lengths, > 0, and small enough
+ *                that no ray takes 2^24 samples or more.
+ *   out          device memory, 16-byte aligned: view-major, then row py,
+ *                then column px; 1 float per pixel (MIP, SUM) or 4 floats
+ *                (COMPOSITE: premultiplied r, g, b, A).
+ *   stream       cudaStream_t as void*.                                     */
+int vr_render(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
+              int mode, float step, float* out, void* stream);
+
+/* As vr_render, and also adds to *d_samples (device memory, 8-byte aligned)
+ * the number of samples evaluated: K per ray for MIP and SUM; for COMPOSITE
+ * the samples up to and including the one that ended the ray.              */
+int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w,
+                      int h, int mode, float step, float* out,
+                      unsigned long long* d_samples, void* stream);
+
+/* Release the handle (not the caller's brick buffer).  The caller must make
+ * sure no work using the volume is still pending on any stream.             */
+int vr_volume_destroy(vr_volume vol);
+
+/* Dimensions, dtype and device pointer of a volume (any pointer may be
+ * NULL).                                                                     */
+int vr_volume_info(vr_volume vol, int64_t dims[3], int* dtype, void** brick_buf);
+
+/* Message for the last failing call on this thread ("" if none).           */
+const char* vr_last_error(void);
+
+/* ABI version of this header: 1.                                            */
+int vr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VR_H */

@@ -1,0 +1,10 @@
+"""B300-native ray caster for noisy RA x Dec x frequency spectral cubes.
+
+The render path (paper §3.1, process item 3: every output pixel becomes a
+ray, mapped to RGBA through a pre-selected transfer function) runs in the
+CUDA kernels of ``libvr.so`` behind the C ABI of ``include/vr.h``; this
+package is the thin Python binding (``api``), the nvcc build (``build``) and
+the seeded synthetic inputs (``synth``).
+"""
+from .api import CAMERA_DTYPE, DTYPES, MODES, Volume, volume_bytes  # noqa: F401
+from ._lib import VRError, load  # noqa: F401

@@ -1,0 +1,133 @@
+"""Python front end of libvr: torch supplies device memory and streams, the
+library does all the work.  Every call here marshals arguments to one C-ABI
+entry point (include/vr.h) and returns torch tensors."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import VR_COMPOSITE, VR_F16, VR_F32, VR_I8, VR_MIP, VR_SUM, check, load
+
+DTYPES = {"f32": VR_F32, "f16": VR_F16, "i8": VR_I8}
+MODES = {"mip": VR_MIP, "composite": VR_COMPOSITE, "sum": VR_SUM}
+
+#: One camera record (64 bytes), identical to ``vr_camera``.
+CAMERA_DTYPE = np.dtype([
+    ("proj", "<i4"), ("eye", "<f4", 3), ("fwd", "<f4", 3),
+    ("du", "<f4", 3), ("dv", "<f4", 3), ("pad", "<f4", 3)])
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dims_arr(dims):
+    return (ctypes.c_int64 * 3)(*[int(d) for d in dims])
+
+
+def volume_bytes(dims, dtype="f32") -> int:
+    out = ctypes.c_size_t(0)
+    check(load().vr_volume_bytes(_dims_arr(dims), DTYPES[dtype], ctypes.byref(out)))
+    return out.value
+
+
+class Volume:
+    """A spectral cube resident on the GPU in the library's brick layout.
+
+    ``cube`` is a float32 tensor of shape (nz, ny, nx) (x = RA fastest, z =
+    frequency slowest) on the current CUDA device or in pinned host memory;
+    ``dtype`` is the storage type ("f32", "f16" or "i8").  The brick buffer
+    is a torch allocation owned by this object.
+    """
+
+    def __init__(self, cube: torch.Tensor | None = None, dtype: str = "f32", dims=None,
+                 stream=None, device=None):
+        lib = load()
+        if cube is not None:
+            if cube.dtype != torch.float32 or cube.dim() != 3:
+                raise ValueError("cube must be a 3-D float32 tensor (nz, ny, nx)")
+            cube = cube.contiguous()
+            nz, ny, nx = cube.shape
+            dims = (nx, ny, nz)
+        if dims is None:
+            raise ValueError("need a cube or dims")
+        self.dims = tuple(int(d) for d in dims)
+        self.dtype = dtype
+        self.nbytes = volume_bytes(self.dims, dtype)
+        dev = device if device is not None else (
+            cube.device if cube is not None and cube.is_cuda else torch.device("cuda"))
+        self.buffer = torch.empty(self.nbytes, dtype=torch.uint8, device=dev)
+        handle = ctypes.c_void_p(0)
+        src, on_dev = None, 1
+        if cube is not None:
+            src, on_dev = cube.data_ptr(), int(cube.is_cuda)
+        check(lib.vr_volume_create(_dims_arr(self.dims), DTYPES[dtype], src, on_dev,
+                                   self.buffer.data_ptr(), self.nbytes, _stream_ptr(stream),
+                                   ctypes.byref(handle)))
+        self._h = handle
+        self._keep = cube   # the source must live until the stream passes the pack
+
+    @property
+    def handle(self):
+        return self._h
+
+    def upload(self, z0: int, planes: torch.Tensor, stream=None):
+        """Pack planes [z0, z0 + planes.shape[0]) from a float32 (n, ny, nx)
+        tensor (device or pinned host)."""
+        planes = planes.contiguous()
+        check(load().vr_volume_upload(self._h, int(z0), int(planes.shape[0]), planes.data_ptr(),
+                                      int(planes.is_cuda), _stream_ptr(stream)))
+        self._keep = planes
+
+    def set_transfer(self, lut, v_lo: float, v_hi: float, clip: float, term_alpha: float = 1.0):
+        """RGBA table (n, 4) with alpha per unit voxel length over [v_lo, v_hi];
+        samples below ``clip`` are transparent; rays stop at ``term_alpha``."""
+        lut = np.ascontiguousarray(np.asarray(lut, dtype=np.float32))
+        if lut.ndim != 2 or lut.shape[1] != 4:
+            raise ValueError("lut must have shape (n, 4)")
+        check(load().vr_set_transfer(self._h, lut.ctypes.data, lut.shape[0], float(v_lo),
+                                     float(v_hi), float(clip), float(term_alpha)))
+
+    def render(self, cams: np.ndarray, w: int, h: int, mode: str = "composite",
+               step: float = 0.5, out: torch.Tensor | None = None, stream=None,
+               count: torch.Tensor | None = None) -> torch.Tensor:
+        """Render len(cams) views.  Returns (views, h, w) for "mip"/"sum" and
+        (views, h, w, 4) premultiplied RGBA for "composite".  ``count``, a
+        one-element int64 CUDA tensor, receives the evaluated-sample count
+        (added to its value)."""
+        cams = np.ascontiguousarray(cams)
+        if cams.dtype.itemsize != 64:
+            raise ValueError("cams must be an array of 64-byte camera records")
+        m = MODES[mode]
+        shape = (len(cams), h, w, 4) if m == VR_COMPOSITE else (len(cams), h, w)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=self.buffer.device)
+        elif tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 tensor of shape %s" % (shape,))
+        lib = load()
+        if count is None:
+            check(lib.vr_render(self._h, cams.ctypes.data, len(cams), w, h, m, float(step),
+                                out.data_ptr(), _stream_ptr(stream)))
+        else:
+            if count.dtype != torch.int64 or not count.is_cuda:
+                raise ValueError("count must be an int64 CUDA tensor")
+            check(lib.vr_render_counted(self._h, cams.ctypes.data, len(cams), w, h, m,
+                                        float(step), out.data_ptr(), count.data_ptr(),
+                                        _stream_ptr(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vr_volume_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

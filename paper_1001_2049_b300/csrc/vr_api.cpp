@@ -1,0 +1,344 @@
+// vr_api.cpp -- the C ABI of libvr (declared in include/vr.h): argument
+// validation, volume handles, transfer-function preparation and launch
+// planning.  No device memory is allocated here; all of it is the caller's.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "vr_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(VR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+size_t elem_size(int dtype) { return dtype == VR_F32 ? 4 : dtype == VR_F16 ? 2 : 1; }
+
+int check_dims(const int64_t dims[3], int dtype, vr::VolumeGeom* g)
+{
+    if (!dims) return fail(VR_ERR_ARG, "dims is NULL");
+    if (dtype != VR_F32 && dtype != VR_F16 && dtype != VR_I8)
+        return fail(VR_ERR_ARG, "unknown dtype %d", dtype);
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 2 || dims[a] > (int64_t(1) << 20))
+            return fail(VR_ERR_ARG, "dims[%d] = %lld outside [2, 2^20]", a, (long long)dims[a]);
+    int64_t nb[3];
+    for (int a = 0; a < 3; ++a) nb[a] = div_up(dims[a], vr::kBrick);
+    const double voxels = (double)nb[0] * nb[1] * nb[2] * vr::kBrickVoxels;
+    if (voxels >= std::ldexp(1.0, 40)) return fail(VR_ERR_ARG, "volume too large (>= 2^40 voxels)");
+    g->nx = (int)dims[0];
+    g->ny = (int)dims[1];
+    g->nz = (int)dims[2];
+    g->nbx = (int)nb[0];
+    g->nby = (int)nb[1];
+    g->nbz = (int)nb[2];
+    return VR_OK;
+}
+
+// Is p device memory of the current device?  (Managed memory counts.)
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int dev = -1;
+    cudaGetDevice(&dev);
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
+// Device-visible address of a page-locked host pointer, or nullptr.
+const void* host_to_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost) return nullptr;
+    return a.devicePointer;
+}
+
+bool finite3(const float v[3])
+{
+    return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+void default_transfer(vr::Volume* v)
+{
+    v->n_lut = 2;
+    const float lut[2][4] = {{0, 0, 0, 0}, {1, 1, 1, 1}};
+    std::memcpy(v->lut_raw, lut, sizeof lut);
+    v->v_lo = 0.0f;
+    v->v_hi = 1.0f;
+    v->clip = -INFINITY;
+    v->term_alpha = 2.0f;
+    v->lut_valid = false;
+}
+
+// Opacity-corrected table for the given step: alpha' = 1 - (1 - alpha)^step
+// (alpha is per unit voxel length), computed in double and rounded once.
+void prepare_lut(vr::Volume* v, float step)
+{
+    if (v->lut_valid && v->lut_step == step) return;
+    for (int i = 0; i < v->n_lut; ++i) {
+        for (int c = 0; c < 3; ++c) v->lut_corr[i][c] = v->lut_raw[i][c];
+        const double a = v->lut_raw[i][3];
+        v->lut_corr[i][3] = (float)(1.0 - std::pow(1.0 - a, (double)step));
+    }
+    v->lut_step = step;
+    v->lut_valid = true;
+}
+
+int render_impl(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
+                float step, float* out, unsigned long long* d_samples, void* stream)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (!cams) return fail(VR_ERR_ARG, "cams is NULL");
+    if (n_views < 1) return fail(VR_ERR_ARG, "n_views = %d < 1", n_views);
+    if (w < 1 || h < 1 || w > 65536 || h > 65536)
+        return fail(VR_ERR_ARG, "image size %d x %d outside [1, 65536]", w, h);
+    if (mode != VR_MIP && mode != VR_COMPOSITE && mode != VR_SUM)
+        return fail(VR_ERR_ARG, "unknown mode %d", mode);
+    if (!(step > 0.0f) || !std::isfinite(step)) return fail(VR_ERR_ARG, "step must be > 0");
+    const double hx = v->g.nx - 1.0, hy = v->g.ny - 1.0, hz = v->g.nz - 1.0;
+    const double diag = std::sqrt(hx * hx + hy * hy + hz * hz);
+    if (diag / step + 2.0 >= 16777216.0)
+        return fail(VR_ERR_ARG, "step %g too small: a ray could take 2^24 samples", (double)step);
+    if (!out) return fail(VR_ERR_ARG, "out is NULL");
+    if (reinterpret_cast<uintptr_t>(out) % 16 != 0)
+        return fail(VR_ERR_ARG, "out must be 16-byte aligned");
+    if (!is_device_ptr(out)) return fail(VR_ERR_ARG, "out is not device memory of this device");
+    if (d_samples) {
+        if (reinterpret_cast<uintptr_t>(d_samples) % 8 != 0)
+            return fail(VR_ERR_ARG, "d_samples must be 8-byte aligned");
+        if (!is_device_ptr(d_samples)) return fail(VR_ERR_ARG, "d_samples is not device memory");
+    }
+    for (int i = 0; i < n_views; ++i) {
+        const vr_camera& c = cams[i];
+        if (c.proj != VR_ORTHO && c.proj != VR_PERSP)
+            return fail(VR_ERR_ARG, "camera %d: unknown projection %d", i, c.proj);
+        if (!finite3(c.eye) || !finite3(c.fwd) || !finite3(c.du) || !finite3(c.dv))
+            return fail(VR_ERR_ARG, "camera %d: non-finite parameters", i);
+        if (c.fwd[0] == 0.0f && c.fwd[1] == 0.0f && c.fwd[2] == 0.0f)
+            return fail(VR_ERR_ARG, "camera %d: zero forward vector", i);
+    }
+
+    vr::MarchParams p;
+    std::memset(&p, 0, sizeof p);
+    p.bricks = v->bricks;
+    p.scale = v->scale;
+    p.offset = v->offset;
+    p.g = v->g;
+    p.hix = (float)hx;
+    p.hiy = (float)hy;
+    p.hiz = (float)hz;
+    p.w = w;
+    p.h = h;
+    p.step = step;
+    p.clip = v->clip;
+    p.term_alpha = v->term_alpha;
+    p.v_lo = v->v_lo;
+    p.lut_scale = (float)((v->n_lut - 1) / ((double)v->v_hi - (double)v->v_lo));
+    p.lut_max = (float)(v->n_lut - 1);
+    p.n_lut = v->n_lut;
+    p.samples = d_samples;
+    if (mode == VR_COMPOSITE) {
+        prepare_lut(v, step);
+        for (int i = 0; i < v->n_lut; ++i)
+            p.lut[i] = make_float4(v->lut_corr[i][0], v->lut_corr[i][1], v->lut_corr[i][2],
+                                   v->lut_corr[i][3]);
+    }
+    const size_t per_view = (size_t)w * h * (mode == VR_COMPOSITE ? 4 : 1);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int v0 = 0; v0 < n_views; v0 += vr::kMaxViewsPerLaunch) {
+        const int nv = std::min(vr::kMaxViewsPerLaunch, n_views - v0);
+        p.n_views = nv;
+        std::memcpy(p.cams, cams + v0, sizeof(vr_camera) * nv);
+        p.out = out + per_view * v0;
+        cudaError_t e = vr::launch_march(p, v->dtype, mode, s);
+        if (e != cudaSuccess) return cuda_fail(e, "march launch");
+    }
+    return VR_OK;
+}
+
+}  // namespace
+
+namespace vr {
+
+size_t brick_bytes(const VolumeGeom& g, int dtype)
+{
+    return (size_t)g.nbx * g.nby * g.nbz * kBrickVoxels * elem_size(dtype);
+}
+
+size_t table_offset(const VolumeGeom& g, int dtype)
+{
+    return align_up(brick_bytes(g, dtype), 256);
+}
+
+}  // namespace vr
+
+extern "C" {
+
+int vr_version(void) { return 1; }
+
+const char* vr_last_error(void) { return g_err.c_str(); }
+
+int vr_volume_bytes(const int64_t dims[3], int dtype, size_t* bytes_out)
+{
+    vr::VolumeGeom g;
+    int rc = check_dims(dims, dtype, &g);
+    if (rc) return rc;
+    if (!bytes_out) return fail(VR_ERR_ARG, "bytes_out is NULL");
+    size_t b = vr::brick_bytes(g, dtype);
+    if (dtype == VR_I8) b = vr::table_offset(g, dtype) + 2 * align_up((size_t)g.nz * 4, 256);
+    *bytes_out = b;
+    return VR_OK;
+}
+
+int vr_volume_create(const int64_t dims[3], int dtype, const float* src, int src_on_device,
+                     void* brick_buf, size_t brick_bytes, void* stream, vr_volume* out)
+{
+    if (!out) return fail(VR_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    vr::VolumeGeom g;
+    int rc = check_dims(dims, dtype, &g);
+    if (rc) return rc;
+    size_t need = 0;
+    vr_volume_bytes(dims, dtype, &need);
+    if (!brick_buf) return fail(VR_ERR_ARG, "brick_buf is NULL");
+    if (reinterpret_cast<uintptr_t>(brick_buf) % 256 != 0)
+        return fail(VR_ERR_ARG, "brick_buf must be 256-byte aligned");
+    if (brick_bytes < need)
+        return fail(VR_ERR_OOM, "brick_buf has %zu bytes, %zu needed", brick_bytes, need);
+    if (!is_device_ptr(brick_buf)) return fail(VR_ERR_ARG, "brick_buf is not device memory");
+    vr::Volume* v = new (std::nothrow) vr::Volume;
+    if (!v) return fail(VR_ERR_OOM, "out of host memory");
+    std::memset(v, 0, sizeof *v);
+    v->g = g;
+    v->dtype = dtype;
+    v->bricks = brick_buf;
+    v->bytes = brick_bytes;
+    if (dtype == VR_I8) {
+        char* base = static_cast<char*>(brick_buf) + vr::table_offset(g, dtype);
+        v->scale = reinterpret_cast<float*>(base);
+        v->offset = reinterpret_cast<float*>(base + align_up((size_t)g.nz * 4, 256));
+    }
+    default_transfer(v);
+    if (src) {
+        rc = vr_volume_upload(reinterpret_cast<vr_volume>(v), 0, g.nz, src, src_on_device, stream);
+        if (rc) {
+            delete v;
+            return rc;
+        }
+    }
+    *out = reinterpret_cast<vr_volume>(v);
+    return VR_OK;
+}
+
+int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* src,
+                     int src_on_device, void* stream)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (!src) return fail(VR_ERR_ARG, "src is NULL");
+    if (z0 < 0 || nplanes < 1 || z0 + nplanes > v->g.nz)
+        return fail(VR_ERR_ARG, "planes [%lld, %lld) outside [0, %d)", (long long)z0,
+                    (long long)(z0 + nplanes), v->g.nz);
+    const float* dsrc = src;
+    if (src_on_device) {
+        if (!is_device_ptr(src)) return fail(VR_ERR_ARG, "src is not device memory");
+    } else {
+        dsrc = static_cast<const float*>(host_to_device_ptr(src));
+        if (!dsrc) return fail(VR_ERR_ARG, "host src must be page-locked (pinned) memory");
+    }
+    cudaError_t e = vr::launch_pack(*v, z0, nplanes, dsrc, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+    return VR_OK;
+}
+
+int vr_set_transfer(vr_volume vol, const float* rgba_lut, int n, float v_lo, float v_hi,
+                    float clip, float term_alpha)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (!rgba_lut) return fail(VR_ERR_ARG, "rgba_lut is NULL");
+    if (n < 2 || n > VR_MAX_LUT) return fail(VR_ERR_ARG, "table size %d outside [2, %d]", n, VR_MAX_LUT);
+    if (!std::isfinite(v_lo) || !std::isfinite(v_hi) || !(v_lo < v_hi))
+        return fail(VR_ERR_ARG, "need finite v_lo < v_hi");
+    if (std::isnan(clip) || std::isnan(term_alpha)) return fail(VR_ERR_ARG, "clip/term_alpha NaN");
+    for (int i = 0; i < n; ++i) {
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(rgba_lut[4 * i + c]))
+                return fail(VR_ERR_ARG, "table entry %d is not finite", i);
+        if (rgba_lut[4 * i + 3] < 0.0f || rgba_lut[4 * i + 3] > 1.0f)
+            return fail(VR_ERR_ARG, "table alpha %d outside [0, 1]", i);
+    }
+    std::memcpy(v->lut_raw, rgba_lut, sizeof(float) * 4 * n);
+    v->n_lut = n;
+    v->v_lo = v_lo;
+    v->v_hi = v_hi;
+    v->clip = clip;
+    v->term_alpha = term_alpha;
+    v->lut_valid = false;
+    return VR_OK;
+}
+
+int vr_render(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
+              float step, float* out, void* stream)
+{
+    return render_impl(vol, cams, n_views, w, h, mode, step, out, nullptr, stream);
+}
+
+int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
+                      float step, float* out, unsigned long long* d_samples, void* stream)
+{
+    if (!d_samples) return fail(VR_ERR_ARG, "d_samples is NULL");
+    return render_impl(vol, cams, n_views, w, h, mode, step, out, d_samples, stream);
+}
+
+int vr_volume_destroy(vr_volume vol)
+{
+    delete reinterpret_cast<vr::Volume*>(vol);
+    return VR_OK;
+}
+
+int vr_volume_info(vr_volume vol, int64_t dims[3], int* dtype, void** brick_buf)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    const vr::Volume* v = reinterpret_cast<const vr::Volume*>(vol);
+    if (dims) {
+        dims[0] = v->g.nx;
+        dims[1] = v->g.ny;
+        dims[2] = v->g.nz;
+    }
+    if (dtype) *dtype = v->dtype;
+    if (brick_buf) *brick_buf = v->bricks;
+    return VR_OK;
+}
+
+}  // extern "C"

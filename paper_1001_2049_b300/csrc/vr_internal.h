@@ -1,0 +1,70 @@
+// vr_internal.h -- declarations shared by the host API and the CUDA kernels
+// of libvr.  Not part of the public ABI (include/vr.h is).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "vr.h"
+
+namespace vr {
+
+constexpr int kBrick = VR_BRICK;                  // 32
+constexpr int kBrickShift = 5;
+constexpr int64_t kBrickVoxels = 32 * 32 * 32;    // 32768
+constexpr int kMaxViewsPerLaunch = 64;            // cameras travel as kernel parameters
+
+// Geometry of a bricked volume, as the kernels see it.
+struct VolumeGeom {
+    int nx, ny, nz;         // voxel dims
+    int nbx, nby, nbz;      // brick counts per axis
+};
+
+// Host-side volume handle.
+struct Volume {
+    VolumeGeom g;
+    int dtype;
+    void* bricks;           // caller-owned device buffer
+    size_t bytes;
+    float* scale;           // VR_I8: per-plane tables inside the buffer
+    float* offset;
+    // transfer function as set by the user
+    float lut_raw[VR_MAX_LUT][4];
+    int n_lut;
+    float v_lo, v_hi, clip, term_alpha;
+    // opacity-corrected table cache (depends on the step)
+    float lut_step;
+    float lut_corr[VR_MAX_LUT][4];
+    bool lut_valid;
+};
+
+size_t brick_bytes(const VolumeGeom& g, int dtype);   // voxel part only
+size_t table_offset(const VolumeGeom& g, int dtype);  // where VR_I8 tables start
+
+// Kernel parameters of one march launch (passed by value; ~8.6 KB).
+struct MarchParams {
+    const void* bricks;
+    const float* scale;     // VR_I8 only
+    const float* offset;
+    VolumeGeom g;
+    float hix, hiy, hiz;    // n - 1 per axis
+    int w, h, n_views;
+    float step;
+    float clip, term_alpha;
+    float v_lo, lut_scale;  // x = (s - v_lo) * lut_scale, lut_scale = (N-1)/(v_hi-v_lo)
+    float lut_max;          // N - 1
+    int n_lut;
+    float* out;             // first view of this launch
+    unsigned long long* samples;   // may be null
+    vr_camera cams[kMaxViewsPerLaunch];
+    float4 lut[VR_MAX_LUT];
+};
+
+// Launchers (return a cudaError_t from the launch).
+cudaError_t launch_march(const MarchParams& p, int dtype, int mode, cudaStream_t s);
+cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
+                        cudaStream_t s);
+
+}  // namespace vr

@@ -1,0 +1,78 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry
+point include/vr.h declares; host-only calls behave (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1001_2049_b300 import _lib, build
+
+HEADER = os.path.join(build.ROOT, "include", "vr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(vr_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_north_star_calls():
+    names = declared_functions()
+    for n in ("vr_volume_create", "vr_set_transfer", "vr_render", "vr_volume_bytes",
+              "vr_volume_destroy", "vr_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    names = declared_functions()
+    assert names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(_lib.SIGNATURES), "binding lacks a signature"
+
+
+def test_library_is_built_for_sm_103a():
+    src = open(build.__file__).read()
+    assert "arch=compute_103a,code=sm_103a" in src
+    assert os.path.exists(build.build())
+
+
+def test_version_and_volume_bytes_host_only():
+    lib = _lib.load()
+    assert lib.vr_version() == 1
+    out = ctypes.c_size_t(0)
+    dims = (ctypes.c_int64 * 3)(64, 64, 128)
+    assert lib.vr_volume_bytes(dims, _lib.VR_F32, ctypes.byref(out)) == 0
+    assert out.value == 2 * 2 * 4 * 32768 * 4
+    assert lib.vr_volume_bytes(dims, _lib.VR_F16, ctypes.byref(out)) == 0
+    assert out.value == 2 * 2 * 4 * 32768 * 2
+    # int8: codes + two 256-byte aligned per-plane tables
+    assert lib.vr_volume_bytes(dims, _lib.VR_I8, ctypes.byref(out)) == 0
+    assert out.value == 2 * 2 * 4 * 32768 + 2 * 512
+    # ragged dims round up to whole bricks
+    dims = (ctypes.c_int64 * 3)(33, 2, 65)
+    assert lib.vr_volume_bytes(dims, _lib.VR_F32, ctypes.byref(out)) == 0
+    assert out.value == 2 * 1 * 3 * 32768 * 4
+
+
+@pytest.mark.parametrize("dims", [(1, 4, 4), (4, 0, 4), (4, 4, (1 << 20) + 1)])
+def test_volume_bytes_rejects_bad_dims(dims):
+    lib = _lib.load()
+    out = ctypes.c_size_t(0)
+    rc = lib.vr_volume_bytes((ctypes.c_int64 * 3)(*dims), _lib.VR_F32, ctypes.byref(out))
+    assert rc == _lib.VR_ERR_ARG
+    assert b"outside" in lib.vr_last_error()
+
+
+def test_null_arguments_are_rejected_synchronously():
+    lib = _lib.load()
+    assert lib.vr_volume_bytes(None, 0, None) == _lib.VR_ERR_ARG
+    assert lib.vr_set_transfer(None, None, 2, 0, 1, 0, 1) == _lib.VR_ERR_ARG
+    assert lib.vr_render(None, None, 1, 1, 1, 0, 0.5, None, None) == _lib.VR_ERR_ARG
+    assert lib.vr_volume_upload(None, 0, 1, None, 1, None) == _lib.VR_ERR_ARG
+    h = ctypes.c_void_p(0)
+    dims = (ctypes.c_int64 * 3)(8, 8, 8)
+    assert lib.vr_volume_create(dims, 7, None, 1, None, 0, None, ctypes.byref(h)) == _lib.VR_ERR_ARG
+    assert b"dtype" in lib.vr_last_error()

@@ -1,0 +1,347 @@
+"""Parity of the CUDA render path (through the C ABI) with the FP64 oracle.
+
+Every image is compared pixel by pixel with the oracle's acceptance set
+(primary double-precision result plus the alternatives at the three
+discontinuities), within the tolerances stated in tests/_util.py.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import quantize
+from paper_1001_2049_b300 import Volume, VRError, synth
+from paper_1001_2049_b300.api import volume_bytes
+
+from _util import TOL_FP32, TOL_PREC, bands_for, compare
+
+pytestmark = pytest.mark.gpu
+
+MODES = {"mip": oracle.MIP, "composite": oracle.COMPOSITE, "sum": oracle.SUM}
+
+
+def oracle_volume(cube: np.ndarray, dtype: str) -> oracle.Volume:
+    if dtype == "f32":
+        return oracle.Volume(cube)
+    if dtype == "f16":
+        return oracle.Volume(quantize.to_f16(cube))
+    q, s, o = quantize.quantize_i8(cube)
+    return oracle.Volume(q, s, o)
+
+
+def gpu_images(cube_t, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, count=None):
+    vol = Volume(cube_t.cuda(), dtype)
+    vol.set_transfer(lut, v_lo, v_hi, clip, ta)
+    out = vol.render(cams, w, h, mode, step, count=count)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def scale_for(mode, cube, got):
+    if mode == "mip":
+        return float(cube.max() - cube.min())
+    if mode == "sum":
+        fin = np.abs(got[np.isfinite(got)])
+        return max(1.0, float(fin.max()) if fin.size else 1.0)
+    return 1.0
+
+
+def run_parity(cube, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, tol=TOL_FP32,
+               reference="decoded", pixels=None, what=""):
+    """Render on the GPU and compare with the oracle (on the decoded storage
+    values, or on the float32 source with reference="source")."""
+    got = gpu_images(torch.from_numpy(cube), dtype, cams, w, h, mode, step, lut, v_lo, v_hi,
+                     clip, ta)
+    ovol = oracle_volume(cube, dtype if reference == "decoded" else "f32")
+    tf = oracle.TF(lut, v_lo, v_hi, clip, ta)
+    nz, ny, nx = cube.shape
+    res = oracle.render(ovol, cams, w, h, MODES[mode], step, tf, pixels=pixels,
+                        bands=bands_for((nx, ny, nz), cams, step))
+    ch = 4 if mode == "composite" else 1
+    flat = got.reshape(len(cams), h, w, ch) if ch == 4 else got.reshape(len(cams), h, w, 1)
+    if pixels is not None:
+        flat = flat[pixels[:, 0], pixels[:, 2], pixels[:, 1]]
+    rep = compare(res, flat, MODES[mode], tol, scale_for(mode, cube, got), what=what)
+    return got, res, rep
+
+
+# ---------------------------------------------------------------------------
+# the 64x64x128 workload: 256^2 orthographic view along the frequency axis
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small():
+    wl = synth.SMALL
+    cube = wl.cube("cpu").numpy()
+    lut = synth.default_lut()
+    return wl, cube, lut, synth.small_camera()
+
+
+@pytest.mark.parametrize("mode", ["mip", "composite", "sum"])
+def test_small_workload_fp32_full_frame(small, mode):
+    wl, cube, lut, cams = small
+    _, res, rep = run_parity(cube, "f32", cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi,
+                             wl.clip, wl.term_alpha, what="small fp32 " + mode)
+    # (t_exit - t_entry)/step = 127/0.5 is an integer for every ray of this
+    # view, so every pixel carries the K and K - 1 alternatives
+    assert (res.flags & 1).all()
+
+
+@pytest.mark.parametrize("dtype", ["f16", "i8"])
+@pytest.mark.parametrize("mode", ["mip", "composite"])
+def test_small_workload_reduced_precision(small, dtype, mode):
+    wl, cube, lut, cams = small
+    # kernel parity: against the oracle on the decoded storage values
+    run_parity(cube, dtype, cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+               wl.term_alpha, what="small %s %s decoded" % (dtype, mode))
+    # stated precision cost: against the oracle on the float32 source
+    run_parity(cube, dtype, cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+               wl.term_alpha, tol=TOL_PREC[dtype], reference="source",
+               what="small %s %s vs fp32 source" % (dtype, mode))
+
+
+def test_small_workload_sample_count(small):
+    wl, cube, lut, cams = small
+    for mode in ("mip", "composite"):
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        gpu_images(torch.from_numpy(cube), "f32", cams, 256, 256, mode, wl.step, lut, wl.clip,
+                   wl.v_hi, wl.clip, wl.term_alpha, count=cnt)
+        res = oracle.render(oracle.Volume(cube), cams, 256, 256, MODES[mode], wl.step,
+                            oracle.TF(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha),
+                            bands=bands_for(wl.dims, cams, wl.step))
+        want = int(res.nsamples.sum())
+        slack = 8 * int(np.count_nonzero(res.flags))
+        assert abs(int(cnt.item()) - want) <= slack
+    # every ray of this view takes K = 255 samples
+    assert int(res.nsamples.max()) == 255
+
+
+# ---------------------------------------------------------------------------
+# ragged cubes (several bricks plus partial ones), perspective cameras from
+# many directions (one inside the cube), ragged image tiles
+# ---------------------------------------------------------------------------
+RAGGED = [((37, 45, 70), 0.5), ((2, 2, 2), 0.25), ((33, 31, 65), 0.37), ((64, 5, 40), 0.5)]
+
+
+def ragged_case(dims, seed):
+    cube = synth.make_cube(dims, 3, ("uniform", 3.0, 8.0), seed).numpy()
+    cams = synth.random_sphere_cameras(dims, 3, 23, 17, seed, fov_deg=70.0)
+    c = np.array([(d - 1) / 2.0 for d in dims])
+    inside = synth.look_at_camera(c + 0.3, c + np.array([5.0, -3.0, 2.0]), 23, 17, 90.0)
+    cams = np.concatenate([cams, synth.cameras([inside]).astype(cams.dtype)])
+    lut = synth.default_lut(64)
+    return cube, cams, lut
+
+
+@pytest.mark.parametrize("dims,step", RAGGED)
+@pytest.mark.parametrize("mode", ["mip", "composite", "sum"])
+def test_ragged_cubes_perspective_fp32(dims, step, mode):
+    cube, cams, lut = ragged_case(dims, 17 + dims[0])
+    run_parity(cube, "f32", cams, 23, 17, mode, step, lut, 1.0, 8.0, 1.0, 0.95,
+               what="ragged %s %s" % (dims, mode))
+
+
+@pytest.mark.parametrize("dtype", ["f16", "i8"])
+def test_ragged_cube_reduced_precision(dtype):
+    cube, cams, lut = ragged_case((37, 45, 70), 3)
+    for mode in ("mip", "composite"):
+        run_parity(cube, dtype, cams, 23, 17, mode, 0.5, lut, 1.0, 8.0, 1.0, 0.95,
+                   what="ragged %s %s" % (dtype, mode))
+
+
+def test_orthographic_axis_views_and_misses():
+    # views along each axis, wider than the cube (many rays miss) and with
+    # rays lying exactly in the face planes
+    rng = np.random.default_rng(5)
+    dims = (9, 12, 7)
+    cube = rng.standard_normal((7, 12, 9)).astype(np.float32)
+    recs = [synth.axis_camera(dims, 16, 16, axis=a, sign=s) for a in range(3) for s in (1, -1)]
+    cams = synth.cameras(recs)
+    lut = synth.default_lut(16)
+    for mode in ("mip", "composite", "sum"):
+        run_parity(cube, "f32", cams, 16, 16, mode, 0.5, lut, -1.0, 2.0, -1.0, 1.0,
+                   what="axis views " + mode)
+
+
+def test_many_views_span_several_launches():
+    dims = (20, 18, 24)
+    cube = synth.make_cube(dims, 2, ("uniform", 4.0, 6.0), 9).numpy()
+    cams = synth.random_sphere_cameras(dims, 70, 8, 8, 21)
+    run_parity(cube, "f32", cams, 8, 8, "composite", 0.5, synth.default_lut(), 1.0, 6.0, 1.0,
+               0.99, what="70 views")
+
+
+def test_all_samples_below_clip_give_zero():
+    dims = (16, 16, 16)
+    cube = synth.make_cube(dims, 0, ("uniform", 1, 2), 1).numpy()
+    got = gpu_images(torch.from_numpy(cube), "f32", synth.random_sphere_cameras(dims, 2, 9, 9, 2),
+                     9, 9, "composite", 0.5, synth.default_lut(), 100.0, 200.0, 100.0, 1.0)
+    assert (got == 0).all()
+
+
+# ---------------------------------------------------------------------------
+# packing: bit-exact brick contents, host and slab uploads
+# ---------------------------------------------------------------------------
+def unbrick(buf: torch.Tensor, dims, dtype):
+    nx, ny, nz = dims
+    nb = [math.ceil(d / 32) for d in dims]
+    np_dt = {"f32": np.float32, "f16": np.float16, "i8": np.int8}[dtype]
+    n = nb[0] * nb[1] * nb[2] * 32768
+    raw = buf.cpu().numpy()
+    vox = raw[: n * np.dtype(np_dt).itemsize].view(np_dt)
+    a = vox.reshape(nb[2], nb[1], nb[0], 32, 32, 32).transpose(0, 3, 1, 4, 2, 5)
+    lin = a.reshape(nb[2] * 32, nb[1] * 32, nb[0] * 32)
+    tables = None
+    if dtype == "i8":
+        off = (n + 255) // 256 * 256
+        tsz = (nz * 4 + 255) // 256 * 256
+        scale = raw[off: off + nz * 4].view(np.float32)
+        offset = raw[off + tsz: off + tsz + nz * 4].view(np.float32)
+        tables = (scale, offset)
+    return lin, tables
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "i8"])
+def test_pack_is_bit_exact(dtype):
+    dims = (45, 33, 70)
+    cube = synth.make_cube(dims, 4, ("uniform", 3, 30), 11).numpy()
+    cube[5] = 2.5                                 # a constant plane
+    vol = Volume(torch.from_numpy(cube).cuda(), dtype)
+    torch.cuda.synchronize()
+    lin, tables = unbrick(vol.buffer, dims, dtype)
+    inner = lin[:70, :33, :45]
+    if dtype == "f32":
+        assert np.array_equal(inner, cube)
+    elif dtype == "f16":
+        assert np.array_equal(inner.view(np.uint16), quantize.to_f16(cube).view(np.uint16))
+    else:
+        q, s, o = quantize.quantize_i8(cube)
+        assert np.array_equal(inner, q)
+        assert np.array_equal(tables[0].view(np.uint32), s.view(np.uint32))
+        assert np.array_equal(tables[1].view(np.uint32), o.view(np.uint32))
+    # padding is zero
+    pad = lin.copy()
+    pad[:70, :33, :45] = 0
+    assert not pad.astype(np.float64).any()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_pinned_host_source_and_slab_uploads_match_device_source(dtype):
+    dims = (40, 36, 50)
+    cube_t = synth.make_cube(dims, 3, ("uniform", 3, 9), 12)
+    ref = Volume(cube_t.cuda(), dtype)
+    pinned = Volume(cube_t.pin_memory(), dtype)
+    slabs = Volume(dims=dims, dtype=dtype)
+    for z0, z1 in ((0, 7), (7, 33), (33, 50)):
+        slabs.upload(z0, cube_t[z0:z1].cuda())
+    torch.cuda.synchronize()
+    # compare the defined bytes: voxels, and for int8 the nz table entries
+    # (the tables' 256-byte alignment padding is never written)
+    a, ta = unbrick(ref.buffer, dims, dtype)
+    for other in (pinned, slabs):
+        b, tb = unbrick(other.buffer, dims, dtype)
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+        if ta is not None:
+            assert np.array_equal(ta[0].view(np.uint32), tb[0].view(np.uint32))
+            assert np.array_equal(ta[1].view(np.uint32), tb[1].view(np.uint32))
+
+
+# ---------------------------------------------------------------------------
+# determinism and argument errors
+# ---------------------------------------------------------------------------
+def test_repeated_views_are_bit_identical():
+    dims = (30, 30, 30)
+    cube = synth.make_cube(dims, 3, ("uniform", 3, 9), 13).cuda()
+    vol = Volume(cube, "f32")
+    vol.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 0.99)
+    cams = synth.random_sphere_cameras(dims, 1, 33, 31, 4)
+    out = vol.render(np.concatenate([cams, cams, cams]), 33, 31, "composite", 0.5)
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
+
+
+def test_argument_errors_raise():
+    dims = (16, 16, 16)
+    vol = Volume(synth.make_cube(dims, 0, ("uniform", 1, 2), 1).cuda(), "f32")
+    cams = synth.random_sphere_cameras(dims, 1, 8, 8, 1)
+    base = torch.empty(1 * 8 * 8 * 4 + 1, device="cuda")
+    with pytest.raises(VRError):
+        vol.render(cams, 8, 8, "composite", 0.5, out=base[1:].view(1, 8, 8, 4))  # misaligned
+    with pytest.raises(VRError):
+        vol.render(cams, 8, 8, "composite", 0.0)
+    with pytest.raises(VRError):
+        vol.render(cams, 8, 8, "composite", 1e-7)           # 2^24 samples per ray
+    bad = cams.copy()
+    bad[0]["eye"][0] = np.nan
+    with pytest.raises(VRError):
+        vol.render(bad, 8, 8, "mip", 0.5)
+    with pytest.raises(VRError):
+        vol.set_transfer(np.ones((1, 4), np.float32), 0, 1, 0)
+    with pytest.raises(VRError):
+        vol.set_transfer(np.full((4, 4), 2.0, np.float32), 0, 1, 0)
+    with pytest.raises(VRError):
+        vol.set_transfer(synth.default_lut(), 1.0, 1.0, 0)
+    with pytest.raises(ValueError):
+        vol.render(cams, 8, 8, "mip", 0.5, out=torch.empty(2, 8, 8, device="cuda"))
+
+
+def test_brick_buffer_too_small_is_rejected():
+    from paper_1001_2049_b300 import _lib
+    import ctypes
+    lib = _lib.load()
+    buf = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p(0)
+    dims = (ctypes.c_int64 * 3)(64, 64, 64)
+    rc = lib.vr_volume_create(dims, 0, None, 1, buf.data_ptr(), 1024, None, ctypes.byref(h))
+    assert rc == _lib.VR_ERR_OOM
+    assert volume_bytes((64, 64, 64), "f32") == 8 * 32768 * 4
+
+
+# ---------------------------------------------------------------------------
+# the 1024^3 workload at full size, in the benchmark's launch configuration
+# (32 orbiting 1920x1080 views in one call), checked on sampled pixels
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def large():
+    wl = synth.LARGE
+    cube = wl.cube("cuda")
+    host = cube.cpu().numpy()
+    return wl, cube, host
+
+
+def _sample_pixels(n_views, w, h, n, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.integers(0, n_views, n), rng.integers(0, w, n),
+                     rng.integers(0, h, n)], axis=1).astype(np.int32)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "i8"])
+def test_large_workload_sampled_pixels(large, dtype):
+    wl, cube, host = large
+    cams = synth.large_cameras()
+    w, h = 1920, 1080
+    lut = synth.default_lut()
+    vol = Volume(cube, dtype)
+    vol.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
+    pix = _sample_pixels(len(cams), w, h, 3000, 99)
+    ovol = oracle_volume(host, dtype)
+    src = oracle.Volume(host)
+    tf = oracle.TF(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
+    bands = bands_for(wl.dims, cams, wl.step)
+    reports = {}
+    for mode in ("composite", "mip"):
+        img = vol.render(cams, w, h, mode, wl.step)
+        torch.cuda.synchronize()
+        got = img.cpu().numpy()
+        ch = 4 if mode == "composite" else 1
+        flat = got.reshape(len(cams), h, w, ch)[pix[:, 0], pix[:, 2], pix[:, 1]]
+        sc = scale_for(mode, host, got)
+        res = oracle.render(ovol, cams, w, h, MODES[mode], wl.step, tf, pixels=pix, bands=bands)
+        reports[mode] = compare(res, flat, MODES[mode], TOL_FP32, sc,
+                                what="large %s %s" % (dtype, mode))
+        if dtype != "f32":
+            res = oracle.render(src, cams, w, h, MODES[mode], wl.step, tf, pixels=pix,
+                                bands=bands)
+            reports[mode + "_vs_source"] = compare(res, flat, MODES[mode], TOL_PREC[dtype], sc,
+                                                   what="large %s %s vs source" % (dtype, mode))
+    print("large", dtype, reports)
