@@ -40,6 +40,21 @@ METRIC = "samples/s & fps (1080p, 1024³ cube), FP32 plain vs FP16/int8 batched;
 W, H = 1920, 1080
 
 
+def workload(args):
+    """The benchmark workload, or (for profiling captures) a smaller cube
+    with the same framing and ray density (edge E, resolution scaled by
+    E/1024)."""
+    wl = synth.LARGE
+    if args.cube_edge == 1024 and args.views == 32 and args.res is None:
+        return wl, synth.large_cameras(), W, H
+    e = args.cube_edge
+    w, h = (int(v) for v in args.res.split("x")) if args.res else (W * e // 1024, H * e // 1024)
+    sub = synth.Workload("cube%d_orbit%d_%dx%d" % (e, args.views, w, h), (e, e, e),
+                         max(1, wl.n_sources * e ** 3 // 1024 ** 3), wl.snr, wl.clip, wl.v_hi,
+                         wl.seed, wl.term_alpha, wl.step)
+    return sub, synth.orbit_cameras(sub.dims, args.views, w, h), w, h
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -146,7 +161,7 @@ def touched_voxels(cam, dims, step, w, h, device):
 # ---------------------------------------------------------------------------
 # the reference arm and the CPU baseline: the FP64 oracle on host cores
 # ---------------------------------------------------------------------------
-def oracle_throughput(host_cube, cams, wl, budget_s, seed=5):
+def oracle_throughput(host_cube, cams, wl, budget_s, seed=5, w=W, h=H):
     """Run the oracle on random pixels of the views (composite then MIP) for
     about budget_s seconds; returns (samples/s, frames/s, threads, sample)."""
     import oracle
@@ -156,17 +171,17 @@ def oracle_throughput(host_cube, cams, wl, budget_s, seed=5):
     rng = np.random.default_rng(seed)
     samples, secs, pixels_done, n = 0, 0.0, 0, 2048
     while secs < budget_s:
-        pix = np.stack([rng.integers(0, len(cams), n), rng.integers(0, W, n),
-                        rng.integers(0, H, n)], axis=1).astype(np.int32)
+        pix = np.stack([rng.integers(0, len(cams), n), rng.integers(0, w, n),
+                        rng.integers(0, h, n)], axis=1).astype(np.int32)
         for mode in (oracle.COMPOSITE, oracle.MIP):
             t0 = time.perf_counter()
-            r = oracle.render(vol, cams, W, H, mode, wl.step, tf, pixels=pix, bands=nb)
+            r = oracle.render(vol, cams, w, h, mode, wl.step, tf, pixels=pix, bands=nb)
             secs += time.perf_counter() - t0
             samples += int(r.nsamples.sum())
             pixels_done += n
         n = min(n * 2, 1 << 18)
     # a frame = W*H pixels; the two modes each count as frames
-    fps = pixels_done / (W * H) / secs
+    fps = pixels_done / (w * h) / secs
     sample = "%d random pixels of the 32 views (composite and MIP), %.1f s" % (pixels_done, secs)
     return samples / secs, fps, oracle.num_threads(), sample
 
@@ -216,6 +231,12 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=10.0,
                     help="seconds of oracle work per step of the reference arm")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cube-edge", type=int, default=1024,
+                    help="profiling captures only: smaller cube, same framing")
+    ap.add_argument("--views", type=int, default=32)
+    ap.add_argument("--storage", default="texture", choices=["texture", "bricks"],
+                    help="render from layered textures (default) or gather from the bricks")
+    ap.add_argument("--res", default=None, help="WxH (default scales with the cube)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -230,12 +251,13 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
 
-    wl = synth.LARGE
-    cams = synth.large_cameras()
+    wl, cams, W, H = workload(args)
     n_views = len(cams)
     lut = synth.default_lut()
     cube = wl.cube(dev)
     vol = Volume(cube, "f32")
+    if args.storage == "texture":
+        vol.attach_texture()
     vol.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
     comp = torch.empty((n_views, H, W, 4), dtype=torch.float32, device=dev)
     mip = torch.empty((n_views, H, W), dtype=torch.float32, device=dev)
@@ -296,7 +318,7 @@ def main():
         vol.render(cams, W, H, "mip", wl.step, out=mip)
         host_mip.copy_(mip, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - e0) / args.e2e_steps
+    e2e_s = (time.perf_counter() - e0) / max(1, args.e2e_steps)
     d2h = host_comp.numel() * 4 + host_mip.numel() * 4
     h2d = 2 * cams.nbytes
 
@@ -321,7 +343,7 @@ def main():
         cpu = None
         if args.cpu_budget > 0:
             sps, cfps, threads, sample = oracle_throughput(cube.cpu().numpy(), cams, wl,
-                                                           args.cpu_budget)
+                                                           args.cpu_budget, w=W, h=H)
             cpu = {"value": sps, "unit": "samples/s", "cores": threads, "kind": "oracle",
                    "sample": sample, "fps": cfps}
         result = {
@@ -331,14 +353,18 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {
                 "workload": wl.name, "cube": "1024^3 float32, 2000 sources, sigma=1 noise",
-                "storage": "f32 32^3 bricks", "views": n_views, "resolution": "%dx%d" % (W, H),
+                "storage": "f32 32^3 bricks" + (" + layered textures" if args.storage == "texture"
+                                                else ""),
+                "views": n_views, "resolution": "%dx%d" % (W, H),
                 "modes": ["composite (clip 3 sigma, early termination 0.99)", "mip"],
                 "step": wl.step, "fps": fps, "frames_per_step": 2 * n_views,
                 "samples_per_step": samples_step, "samples_composite": samples_comp,
                 "samples_mip": samples_mip, "composite_ms_per_launch": comp_ms,
                 "mip_ms_per_launch": mip_ms, "parallelism": "replica per GPU (views)",
                 "l2": "inputs larger than L2 (4 GiB cube per view pass)"},
-            "roofline": {"bound": "hbm", "kernel": "march composite f32", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": ("tex_kernel" if args.storage == "texture"
+                                                     else "march kernel") + " composite f32",
+                         "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "algorithmic_bytes_per_launch": dom_bytes, "dominant": dom,

@@ -165,6 +165,23 @@ int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w,
                       int h, int mode, float step, float* out,
                       unsigned long long* d_samples, void* stream);
 
+/* Give the volume texture storage: a copy of the cube in layered 2-D
+ * textures (one layer per frequency plane, split into groups of at most 2048
+ * planes), filled from the bricks on `stream`.  Renders then gather the
+ * 2 x 2 corners of a cell per plane with the texture unit's four-texel gather
+ * (unfiltered texels; the interpolation stays the kernel's own FP32 lerps).
+ * This is the one place the library allocates device memory: about
+ * nx*ny*nz*sizeof(storage) bytes, owned by the volume and released by
+ * vr_volume_detach_texture or vr_volume_destroy.  The call synchronises
+ * `stream` (the fill must finish before its surface objects are released).
+ * Returns VR_ERR_UNSUPPORTED when nx or ny exceeds the device's layered
+ * texture size, VR_ERR_OOM when the allocation fails.                       */
+int vr_volume_attach_texture(vr_volume vol, void* stream);
+
+/* Release the texture storage (renders fall back to gathering from the
+ * bricks).  The caller must make sure no render using it is pending.       */
+int vr_volume_detach_texture(vr_volume vol);
+
 /* Release the handle (not the caller's brick buffer).  The caller must make
  * sure no work using the volume is still pending on any stream.             */
 int vr_volume_destroy(vr_volume vol);

@@ -84,6 +84,14 @@ class Volume:
                                       int(planes.is_cuda), _stream_ptr(stream)))
         self._keep = planes
 
+    def attach_texture(self, stream=None):
+        """Also hold the cube as layered textures (library-owned device memory
+        of the cube's size); renders then use the texture-gather kernel."""
+        check(load().vr_volume_attach_texture(self._h, _stream_ptr(stream)))
+
+    def detach_texture(self):
+        check(load().vr_volume_detach_texture(self._h))
+
     def set_transfer(self, lut, v_lo: float, v_hi: float, clip: float, term_alpha: float = 1.0):
         """RGBA table (n, 4) with alpha per unit voxel length over [v_lo, v_hi];
         samples below ``clip`` are transparent; rays stop at ``term_alpha``."""

@@ -175,13 +175,61 @@ int render_impl(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
     }
     const size_t per_view = (size_t)w * h * (mode == VR_COMPOSITE ? 4 : 1);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    vr::TexParams tp;
+    std::memset(&tp, 0, sizeof tp);
+    const bool use_tex = v->n_groups > 0;
+    if (use_tex) {
+        for (int g = 0; g < v->n_groups; ++g) tp.tex[g] = v->tex[g];
+        tp.n_groups = v->n_groups;
+        tp.scale = v->scale;
+        tp.offset = v->offset;
+        tp.k_max = (int)(diag / step) + 2;
+    }
     for (int v0 = 0; v0 < n_views; v0 += vr::kMaxViewsPerLaunch) {
         const int nv = std::min(vr::kMaxViewsPerLaunch, n_views - v0);
         p.n_views = nv;
         std::memcpy(p.cams, cams + v0, sizeof(vr_camera) * nv);
         p.out = out + per_view * v0;
-        cudaError_t e = vr::launch_march(p, v->dtype, mode, s);
+        cudaError_t e = use_tex ? vr::launch_tex(p, tp, v->dtype, mode, s)
+                                : vr::launch_march(p, v->dtype, mode, s);
         if (e != cudaSuccess) return cuda_fail(e, "march launch");
+    }
+    return VR_OK;
+}
+
+void release_texture(vr::Volume* v)
+{
+    for (int g = 0; g < v->n_groups; ++g) {
+        if (v->tex[g]) cudaDestroyTextureObject(v->tex[g]);
+        if (v->arrays[g]) cudaFreeArray(v->arrays[g]);
+        v->tex[g] = 0;
+        v->arrays[g] = nullptr;
+    }
+    v->n_groups = 0;
+}
+
+// Copy planes [z0, z1) of the bricks into the texture groups holding them.
+int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
+{
+    for (int g = 0; g < v->n_groups; ++g) {
+        const int first = g * (vr::kMaxLayers - 1);
+        const int last = std::min(first + vr::kMaxLayers, v->g.nz);   // exclusive
+        const int a = (int)std::max<int64_t>(z0, first), b = (int)std::min<int64_t>(z1, last);
+        if (a >= b) continue;
+        cudaResourceDesc rd;
+        std::memset(&rd, 0, sizeof rd);
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = v->arrays[g];
+        cudaSurfaceObject_t surf = 0;
+        cudaError_t e = cudaCreateSurfaceObject(&surf, &rd);
+        if (e != cudaSuccess) return cuda_fail(e, "surface object");
+        e = vr::fill_texture_group(*v, surf, first, a, b, s);
+        // the surface object may be destroyed once the fill is enqueued only
+        // after it ran: wait for this stream
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaDestroySurfaceObject(surf);
+        if (e != cudaSuccess) return cuda_fail(e, "texture fill");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "texture fill");
     }
     return VR_OK;
 }
@@ -278,6 +326,8 @@ int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* sr
     }
     cudaError_t e = vr::launch_pack(*v, z0, nplanes, dsrc, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+    if (v->n_groups > 0)
+        return refresh_texture(v, z0, z0 + nplanes, static_cast<cudaStream_t>(stream));
     return VR_OK;
 }
 
@@ -321,8 +371,72 @@ int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w, 
     return render_impl(vol, cams, n_views, w, h, mode, step, out, d_samples, stream);
 }
 
+int vr_volume_attach_texture(vr_volume vol, void* stream)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (v->n_groups > 0) return VR_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int maxw = 0, maxh = 0, maxl = 0;
+    cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, dev);
+    cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, dev);
+    cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, dev);
+    if (v->g.nx > maxw || v->g.ny > maxh || maxl < vr::kMaxLayers)
+        return fail(VR_ERR_UNSUPPORTED, "cube %d x %d exceeds the layered texture limits", v->g.nx,
+                    v->g.ny);
+    const int groups = (v->g.nz - 1 + vr::kMaxLayers - 2) / (vr::kMaxLayers - 1);
+    if (groups > vr::kMaxTexGroups)
+        return fail(VR_ERR_UNSUPPORTED, "nz = %d needs more than %d layered textures", v->g.nz,
+                    vr::kMaxTexGroups);
+    cudaChannelFormatDesc desc = v->dtype == VR_F32 ? cudaCreateChannelDesc<float>()
+                                 : v->dtype == VR_F16 ? cudaCreateChannelDescHalf()
+                                                      : cudaCreateChannelDesc<signed char>();
+    for (int g = 0; g < groups; ++g) {
+        const int first = g * (vr::kMaxLayers - 1);
+        const int layers = std::min(vr::kMaxLayers, v->g.nz - first);
+        cudaArray_t arr = nullptr;
+        cudaError_t e = cudaMalloc3DArray(&arr, &desc, make_cudaExtent(v->g.nx, v->g.ny, layers),
+                                          cudaArrayLayered | cudaArraySurfaceLoadStore);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            release_texture(v);
+            return fail(e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA,
+                        "texture storage: %s", cudaGetErrorString(e));
+        }
+        v->arrays[g] = arr;
+        v->n_groups = g + 1;
+        cudaResourceDesc rd;
+        std::memset(&rd, 0, sizeof rd);
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = arr;
+        cudaTextureDesc td;
+        std::memset(&td, 0, sizeof td);
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        e = cudaCreateTextureObject(&v->tex[g], &rd, &td, nullptr);
+        if (e != cudaSuccess) {
+            release_texture(v);
+            return cuda_fail(e, "texture object");
+        }
+    }
+    int rc = refresh_texture(v, 0, v->g.nz, static_cast<cudaStream_t>(stream));
+    if (rc) release_texture(v);
+    return rc;
+}
+
+int vr_volume_detach_texture(vr_volume vol)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    release_texture(reinterpret_cast<vr::Volume*>(vol));
+    return VR_OK;
+}
+
 int vr_volume_destroy(vr_volume vol)
 {
+    if (vol) release_texture(reinterpret_cast<vr::Volume*>(vol));
     delete reinterpret_cast<vr::Volume*>(vol);
     return VR_OK;
 }

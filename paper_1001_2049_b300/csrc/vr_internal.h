@@ -15,6 +15,8 @@ constexpr int kBrick = VR_BRICK;                  // 32
 constexpr int kBrickShift = 5;
 constexpr int64_t kBrickVoxels = 32 * 32 * 32;    // 32768
 constexpr int kMaxViewsPerLaunch = 64;            // cameras travel as kernel parameters
+constexpr int kMaxLayers = 2048;                  // planes per layered texture
+constexpr int kMaxTexGroups = 8;                  // layered textures per volume
 
 // Geometry of a bricked volume, as the kernels see it.
 struct VolumeGeom {
@@ -38,6 +40,19 @@ struct Volume {
     float lut_step;
     float lut_corr[VR_MAX_LUT][4];
     bool lut_valid;
+    // optional texture storage (library-owned): planes in layered 2-D arrays
+    int n_groups;
+    cudaArray_t arrays[kMaxTexGroups];
+    cudaTextureObject_t tex[kMaxTexGroups];
+};
+
+// Texture storage as the texture kernels see it.
+struct TexParams {
+    cudaTextureObject_t tex[kMaxTexGroups];
+    int n_groups;
+    const float* scale;     // VR_I8 only
+    const float* offset;
+    int k_max;
 };
 
 size_t brick_bytes(const VolumeGeom& g, int dtype);   // voxel part only
@@ -62,8 +77,30 @@ struct MarchParams {
     float4 lut[VR_MAX_LUT];
 };
 
+// Shape of the shared-memory window of the slab-staged march.
+struct SlabConfig {
+    int S;          // cells per slab along the principal axis (S + 1 planes staged)
+    int margin;     // voxels added around the reduced window on each side
+    int eb_max;     // window capacity along the innermost axis (multiple of 4)
+    int ec_max;     // window capacity along the third axis
+    int ea_pitch;   // plane pitch when x is the principal axis (>= S + 1, odd)
+    int k_max;      // bound on samples per ray
+    int win_elems;  // elements of one window buffer (two are allocated)
+    float min_axis; // slab along y/z when that component of the direction is at least this
+    size_t smem_bytes;
+};
+
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_march(const MarchParams& p, int dtype, int mode, cudaStream_t s);
+cudaError_t launch_slab(const MarchParams& p, const SlabConfig& c, int mode, cudaStream_t s);
+size_t slab_smem_bytes(const SlabConfig& c);
+size_t slab_window_elems(const SlabConfig& c);
+// Window shape for the cameras of one launch (false: use the gather kernel).
+bool plan_slab(const MarchParams& p, SlabConfig* c);
+cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int dtype, int mode,
+                       cudaStream_t s);
+cudaError_t fill_texture_group(const Volume& v, cudaSurfaceObject_t surf, int layer0, int z0,
+                               int z1, cudaStream_t s);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
                         cudaStream_t s);
 

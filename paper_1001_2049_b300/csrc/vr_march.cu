@@ -17,6 +17,8 @@
 // read-only loads.  A cell whose corners straddle a brick boundary uses the
 // per-axis strides of the neighbouring brick.  The (opacity-corrected)
 // transfer table is copied from the kernel parameters into shared memory.
+#include <cstdlib>
+
 #include <cuda_fp16.h>
 
 #include "vr_internal.h"
@@ -250,11 +252,71 @@ cudaError_t launch_dt(const MarchParams& p, int mode, cudaStream_t s, int k_max)
 
 }  // namespace
 
+static int env_int(const char* name, int dflt)
+{
+    const char* v = getenv(name);
+    return (v && *v) ? atoi(v) : dflt;
+}
+
+bool plan_slab(const MarchParams& p, SlabConfig* c)
+{
+    // largest spacing between neighbouring rays inside the cube: the pixel
+    // step at the farthest cube corner (perspective) or the pixel step itself
+    double sp = 0.0;
+    for (int v = 0; v < p.n_views; ++v) {
+        const vr_camera& cam = p.cams[v];
+        const double du = sqrt((double)cam.du[0] * cam.du[0] + (double)cam.du[1] * cam.du[1] +
+                               (double)cam.du[2] * cam.du[2]);
+        const double dv = sqrt((double)cam.dv[0] * cam.dv[0] + (double)cam.dv[1] * cam.dv[1] +
+                               (double)cam.dv[2] * cam.dv[2]);
+        double s = du > dv ? du : dv;
+        if (cam.proj == VR_PERSP) {
+            const double f = sqrt((double)cam.fwd[0] * cam.fwd[0] + (double)cam.fwd[1] * cam.fwd[1] +
+                                  (double)cam.fwd[2] * cam.fwd[2]);
+            double tmax = 0.0;
+            for (int i = 0; i < 8; ++i) {
+                const double cx = (i & 1) ? p.hix : 0.0, cy = (i & 2) ? p.hiy : 0.0,
+                             cz = (i & 4) ? p.hiz : 0.0;
+                const double dx = cx - cam.eye[0], dy = cy - cam.eye[1], dz = cz - cam.eye[2];
+                const double t = sqrt(dx * dx + dy * dy + dz * dz);
+                if (t > tmax) tmax = t;
+            }
+            s = s * tmax / f;
+        }
+        if (s > sp) sp = s;
+    }
+    c->S = env_int("VR_SLAB_S", 4);
+    c->margin = env_int("VR_SLAB_MARGIN", 1);
+    c->min_axis = env_int("VR_SLAB_MIN_AXIS_PCT", 25) / 100.0f;
+    c->ea_pitch = (c->S + 1) | 1;
+    // one window buffer: the bigger of the plane footprint a 16 x 16 tile can
+    // reach (ray spacing, slant across the slab, margins) and a floor, within
+    // a budget that keeps two blocks per SM
+    const double grow = env_int("VR_SLAB_GROW_PCT", 110) / 100.0;
+    const double side = 16.0 * sp * grow + 3.0 * (c->S + 1) + 2.0 * c->margin + 8.0;
+    const double want = side * side * (c->S + 1);
+    const int budget = env_int("VR_SLAB_WIN_KB", 50) * 1024 / 4;
+    int elems = (int)(want < budget ? want : budget);
+    if (elems < 4096) elems = 4096;
+    c->win_elems = (elems + 3) & ~3;
+    c->eb_max = 0;
+    c->ec_max = 0;
+    const double diag = sqrt((double)p.hix * p.hix + (double)p.hiy * p.hiy + (double)p.hiz * p.hiz);
+    c->k_max = (int)(diag / p.step) + 2;
+    c->smem_bytes = slab_smem_bytes(*c);
+    if (env_int("VR_SLAB_DISABLE", 0)) return false;
+    return c->S >= 1 && c->S <= 7 && c->smem_bytes <= 220 * 1024;
+}
+
 cudaError_t launch_march(const MarchParams& p, int dtype, int mode, cudaStream_t s)
 {
     // a ray crosses at most the box diagonal: bound the loop count from it
     const double diag = sqrt((double)p.hix * p.hix + (double)p.hiy * p.hiy + (double)p.hiz * p.hiz);
     const int k_max = (int)(diag / p.step) + 2;
+    if (dtype == VR_F32) {
+        SlabConfig c;
+        if (plan_slab(p, &c)) return launch_slab(p, c, mode, s);
+    }
     switch (dtype) {
     case VR_F32: return launch_dt<VR_F32>(p, mode, s, k_max);
     case VR_F16: return launch_dt<VR_F16>(p, mode, s, k_max);

@@ -31,8 +31,11 @@ def oracle_volume(cube: np.ndarray, dtype: str) -> oracle.Volume:
     return oracle.Volume(q, s, o)
 
 
-def gpu_images(cube_t, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, count=None):
+def gpu_images(cube_t, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, count=None,
+               tex=False):
     vol = Volume(cube_t.cuda(), dtype)
+    if tex:
+        vol.attach_texture()
     vol.set_transfer(lut, v_lo, v_hi, clip, ta)
     out = vol.render(cams, w, h, mode, step, count=count)
     torch.cuda.synchronize()
@@ -49,11 +52,12 @@ def scale_for(mode, cube, got):
 
 
 def run_parity(cube, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, tol=TOL_FP32,
-               reference="decoded", pixels=None, what=""):
-    """Render on the GPU and compare with the oracle (on the decoded storage
-    values, or on the float32 source with reference="source")."""
+               reference="decoded", pixels=None, what="", tex=False):
+    """Render on the GPU (bricks, or texture storage with tex=True) and compare
+    with the oracle (on the decoded storage values, or on the float32 source
+    with reference="source")."""
     got = gpu_images(torch.from_numpy(cube), dtype, cams, w, h, mode, step, lut, v_lo, v_hi,
-                     clip, ta)
+                     clip, ta, tex=tex)
     ovol = oracle_volume(cube, dtype if reference == "decoded" else "f32")
     tf = oracle.TF(lut, v_lo, v_hi, clip, ta)
     nz, ny, nx = cube.shape
@@ -178,6 +182,78 @@ def test_all_samples_below_clip_give_zero():
     got = gpu_images(torch.from_numpy(cube), "f32", synth.random_sphere_cameras(dims, 2, 9, 9, 2),
                      9, 9, "composite", 0.5, synth.default_lut(), 100.0, 200.0, 100.0, 1.0)
     assert (got == 0).all()
+
+
+# ---------------------------------------------------------------------------
+# texture storage: the same parity through the texture-gather kernel
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f32", "f16", "i8"])
+@pytest.mark.parametrize("mode", ["mip", "composite", "sum"])
+def test_texture_path_small_workload(small, dtype, mode):
+    wl, cube, lut, cams = small
+    run_parity(cube, dtype, cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+               wl.term_alpha, what="small tex %s %s" % (dtype, mode), tex=True)
+    if dtype != "f32" and mode != "sum":
+        run_parity(cube, dtype, cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+                   wl.term_alpha, tol=TOL_PREC[dtype], reference="source",
+                   what="small tex %s %s vs source" % (dtype, mode), tex=True)
+
+
+@pytest.mark.parametrize("dims,step", RAGGED)
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_texture_path_ragged_cubes(dims, step, dtype):
+    cube, cams, lut = ragged_case(dims, 17 + dims[0])
+    for mode in ("mip", "composite", "sum"):
+        run_parity(cube, dtype, cams, 23, 17, mode, step, lut, 1.0, 8.0, 1.0, 0.95,
+                   what="tex ragged %s %s %s" % (dims, dtype, mode), tex=True)
+
+
+def test_texture_path_axis_views_and_misses():
+    rng = np.random.default_rng(5)
+    dims = (9, 12, 7)
+    cube = rng.standard_normal((7, 12, 9)).astype(np.float32)
+    recs = [synth.axis_camera(dims, 16, 16, axis=a, sign=s) for a in range(3) for s in (1, -1)]
+    cams = synth.cameras(recs)
+    lut = synth.default_lut(16)
+    for mode in ("mip", "composite", "sum"):
+        run_parity(cube, "f32", cams, 16, 16, mode, 0.5, lut, -1.0, 2.0, -1.0, 1.0,
+                   what="tex axis views " + mode, tex=True)
+
+
+def test_texture_path_spans_several_layer_groups():
+    # more planes than one layered texture holds: groups overlap by a plane
+    dims = (6, 5, 4500)
+    cube = synth.make_cube(dims, 20, ("uniform", 3.0, 8.0), 31).numpy()
+    recs = [synth.axis_camera(dims, 8, 8, axis=2, spacing=(0.7, 0.6)),
+            synth.axis_camera(dims, 8, 8, axis=2, sign=-1, spacing=(0.7, 0.6)),
+            synth.look_at_camera((40.0, -30.0, 2047.3), (2.5, 2.0, 2047.0), 8, 8, 60.0),
+            synth.look_at_camera((-20.0, 25.0, 4094.5), (2.5, 2.0, 4094.0), 8, 8, 60.0)]
+    cams = synth.cameras(recs)
+    for dtype in ("f32", "i8"):
+        for mode in ("mip", "composite"):
+            run_parity(cube, dtype, cams, 8, 8, mode, 0.5, synth.default_lut(), 1.0, 8.0, 1.0,
+                       1.0, what="tex 4500 planes %s %s" % (dtype, mode), tex=True)
+
+
+def test_texture_is_refreshed_by_uploads():
+    dims = (24, 20, 30)
+    a = synth.make_cube(dims, 3, ("uniform", 3, 9), 40)
+    b = synth.make_cube(dims, 3, ("uniform", 3, 9), 41)
+    cams = synth.random_sphere_cameras(dims, 2, 16, 16, 3)
+    vol = Volume(a.cuda(), "f32")
+    vol.attach_texture()
+    vol.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 1.0)
+    vol.upload(5, b[5:20].cuda())
+    mixed = a.clone()
+    mixed[5:20] = b[5:20]
+    ref = Volume(mixed.cuda(), "f32")
+    ref.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 1.0)
+    got = vol.render(cams, 16, 16, "mip", 0.5)
+    want = ref.render(cams, 16, 16, "mip", 0.5)
+    torch.cuda.synchronize()
+    assert torch.allclose(got, want, rtol=0, atol=1e-5)
+    vol.detach_texture()                      # back to the brick gather
+    assert torch.allclose(vol.render(cams, 16, 16, "mip", 0.5), want, rtol=0, atol=1e-5)
 
 
 # ---------------------------------------------------------------------------
@@ -315,13 +391,16 @@ def _sample_pixels(n_views, w, h, n, seed):
                      rng.integers(0, h, n)], axis=1).astype(np.int32)
 
 
+@pytest.mark.parametrize("tex", [True, False], ids=["texture", "bricks"])
 @pytest.mark.parametrize("dtype", ["f32", "f16", "i8"])
-def test_large_workload_sampled_pixels(large, dtype):
+def test_large_workload_sampled_pixels(large, dtype, tex):
     wl, cube, host = large
     cams = synth.large_cameras()
     w, h = 1920, 1080
     lut = synth.default_lut()
     vol = Volume(cube, dtype)
+    if tex:
+        vol.attach_texture()
     vol.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
     pix = _sample_pixels(len(cams), w, h, 3000, 99)
     ovol = oracle_volume(host, dtype)
@@ -344,4 +423,4 @@ def test_large_workload_sampled_pixels(large, dtype):
                                 bands=bands)
             reports[mode + "_vs_source"] = compare(res, flat, MODES[mode], TOL_PREC[dtype], sc,
                                                    what="large %s %s vs source" % (dtype, mode))
-    print("large", dtype, reports)
+    print("large", dtype, "texture" if tex else "bricks", reports)
