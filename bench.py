@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1001_2049_b300 import Volume, synth  # noqa: E402
+from paper_1001_2049_b300.api import launch_shapes  # noqa: E402
 
 METRIC = "samples/s & fps (1080p, 1024³ cube), FP32 plain vs FP16/int8 batched; p99 ms"
 W, H = 1920, 1080
@@ -234,6 +235,7 @@ def main():
     ap.add_argument("--cube-edge", type=int, default=1024,
                     help="profiling captures only: smaller cube, same framing")
     ap.add_argument("--views", type=int, default=32)
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--storage", default="texture", choices=["texture", "bricks"],
                     help="render from layered textures (default) or gather from the bricks")
     ap.add_argument("--res", default=None, help="WxH (default scales with the cube)")
@@ -262,6 +264,13 @@ def main():
     comp = torch.empty((n_views, H, W, 4), dtype=torch.float32, device=dev)
     mip = torch.empty((n_views, H, W), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    # launch shapes chosen by the autotuner on these very views (untimed)
+    tuned = {}
+    if args.storage == "texture" and not args.no_tune:
+        for mode, out in (("composite", comp), ("mip", mip)):
+            cfg, ms = vol.autotune(cams, W, H, mode, wl.step, out=out)
+            tuned[mode] = {"config": cfg, "shape": list(launch_shapes()[cfg]), "ms": ms}
 
     # samples per step (untimed): counted by the kernels themselves
     cnt = torch.zeros(2, dtype=torch.int64, device=dev)
@@ -361,6 +370,7 @@ def main():
                 "samples_per_step": samples_step, "samples_composite": samples_comp,
                 "samples_mip": samples_mip, "composite_ms_per_launch": comp_ms,
                 "mip_ms_per_launch": mip_ms, "parallelism": "replica per GPU (views)",
+                "autotuned": tuned,
                 "l2": "inputs larger than L2 (4 GiB cube per view pass)"},
             "roofline": {"bound": "hbm", "kernel": ("tex_kernel" if args.storage == "texture"
                                                      else "march kernel") + " composite f32",

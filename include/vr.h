@@ -182,6 +182,26 @@ int vr_volume_attach_texture(vr_volume vol, void* stream);
  * bricks).  The caller must make sure no render using it is pending.       */
 int vr_volume_detach_texture(vr_volume vol);
 
+/* Launch shapes of the texture-gather kernel (the autotuner's search space):
+ * configuration cfg in [0, vr_tune_count()) renders blocks of block_x x
+ * block_y rays with warps holding packet_x x packet_y neighbouring rays, and
+ * asks the compiler for registers that let min_blocks blocks share an SM.   */
+int vr_tune_count(void);
+int vr_tune_describe(int cfg, int* block_x, int* block_y, int* packet_x, int* packet_y,
+                     int* min_blocks);
+
+/* Time every launch shape on this render (same arguments as vr_render; the
+ * images are written to `out`) and keep the fastest for `mode` on this
+ * volume.  A tuning call, not a render call: it records events on `stream`
+ * and waits for them, so it must not be captured into a CUDA graph.  Without
+ * texture storage there is nothing to choose and *best_ms is set to -1.    */
+int vr_autotune(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
+                float step, float* out, void* stream, int* best_cfg, float* best_ms);
+
+/* Use launch shape cfg for renders of `mode` on this volume (the default is
+ * 0, or whatever vr_autotune chose last).                                    */
+int vr_set_launch_config(vr_volume vol, int mode, int cfg);
+
 /* Release the handle (not the caller's brick buffer).  The caller must make
  * sure no work using the volume is still pending on any stream.             */
 int vr_volume_destroy(vr_volume vol);

@@ -35,6 +35,11 @@ SIGNATURES = {
     "vr_volume_detach_texture": (c_int, [c_void_p]),
     "vr_volume_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int),
                                ctypes.POINTER(c_void_p)]),
+    "vr_tune_count": (c_int, []),
+    "vr_tune_describe": (c_int, [c_int] + [ctypes.POINTER(c_int)] * 5),
+    "vr_autotune": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_void_p,
+                            c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_float)]),
+    "vr_set_launch_config": (c_int, [c_void_p, c_int, c_int]),
 }
 
 

@@ -30,6 +30,18 @@ def _dims_arr(dims):
     return (ctypes.c_int64 * 3)(*[int(d) for d in dims])
 
 
+def launch_shapes():
+    """The texture kernel's launch shapes: (block_x, block_y, packet_x,
+    packet_y, min_blocks) per configuration index."""
+    lib = load()
+    out = []
+    for c in range(lib.vr_tune_count()):
+        v = [ctypes.c_int(0) for _ in range(5)]
+        check(lib.vr_tune_describe(c, *[ctypes.byref(x) for x in v]))
+        out.append(tuple(x.value for x in v))
+    return out
+
+
 def volume_bytes(dims, dtype="f32") -> int:
     out = ctypes.c_size_t(0)
     check(load().vr_volume_bytes(_dims_arr(dims), DTYPES[dtype], ctypes.byref(out)))
@@ -128,6 +140,24 @@ class Volume:
                                         float(step), out.data_ptr(), count.data_ptr(),
                                         _stream_ptr(stream)))
         return out
+
+    def autotune(self, cams: np.ndarray, w: int, h: int, mode: str = "composite",
+                 step: float = 0.5, out: torch.Tensor | None = None, stream=None):
+        """Time the texture kernel's launch shapes on this render and keep the
+        fastest for ``mode``; returns (configuration, ms).  Synchronises."""
+        cams = np.ascontiguousarray(cams)
+        m = MODES[mode]
+        shape = (len(cams), h, w, 4) if m == VR_COMPOSITE else (len(cams), h, w)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=self.buffer.device)
+        best, ms = ctypes.c_int(0), ctypes.c_float(0)
+        check(load().vr_autotune(self._h, cams.ctypes.data, len(cams), w, h, m, float(step),
+                                 out.data_ptr(), _stream_ptr(stream), ctypes.byref(best),
+                                 ctypes.byref(ms)))
+        return best.value, ms.value
+
+    def set_launch_config(self, mode: str, cfg: int):
+        check(load().vr_set_launch_config(self._h, MODES[mode], int(cfg)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -113,8 +113,11 @@ void prepare_lut(vr::Volume* v, float step)
     v->lut_valid = true;
 }
 
-int render_impl(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
-                float step, float* out, unsigned long long* d_samples, void* stream)
+// Validate a render request and fill the launch parameters (all but the
+// cameras and the output pointer, which are set per launch of <= 64 views).
+int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
+            float step, float* out, unsigned long long* d_samples, vr::MarchParams* p,
+            vr::TexParams* tp)
 {
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
     vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
@@ -148,53 +151,67 @@ int render_impl(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
             return fail(VR_ERR_ARG, "camera %d: zero forward vector", i);
     }
 
-    vr::MarchParams p;
-    std::memset(&p, 0, sizeof p);
-    p.bricks = v->bricks;
-    p.scale = v->scale;
-    p.offset = v->offset;
-    p.g = v->g;
-    p.hix = (float)hx;
-    p.hiy = (float)hy;
-    p.hiz = (float)hz;
-    p.w = w;
-    p.h = h;
-    p.step = step;
-    p.clip = v->clip;
-    p.term_alpha = v->term_alpha;
-    p.v_lo = v->v_lo;
-    p.lut_scale = (float)((v->n_lut - 1) / ((double)v->v_hi - (double)v->v_lo));
-    p.lut_max = (float)(v->n_lut - 1);
-    p.n_lut = v->n_lut;
-    p.samples = d_samples;
+    std::memset(p, 0, sizeof *p);
+    p->bricks = v->bricks;
+    p->scale = v->scale;
+    p->offset = v->offset;
+    p->g = v->g;
+    p->hix = (float)hx;
+    p->hiy = (float)hy;
+    p->hiz = (float)hz;
+    p->w = w;
+    p->h = h;
+    p->step = step;
+    p->clip = v->clip;
+    p->term_alpha = v->term_alpha;
+    p->v_lo = v->v_lo;
+    p->lut_scale = (float)((v->n_lut - 1) / ((double)v->v_hi - (double)v->v_lo));
+    p->lut_max = (float)(v->n_lut - 1);
+    p->n_lut = v->n_lut;
+    p->samples = d_samples;
     if (mode == VR_COMPOSITE) {
         prepare_lut(v, step);
         for (int i = 0; i < v->n_lut; ++i)
-            p.lut[i] = make_float4(v->lut_corr[i][0], v->lut_corr[i][1], v->lut_corr[i][2],
-                                   v->lut_corr[i][3]);
+            p->lut[i] = make_float4(v->lut_corr[i][0], v->lut_corr[i][1], v->lut_corr[i][2],
+                                    v->lut_corr[i][3]);
     }
-    const size_t per_view = (size_t)w * h * (mode == VR_COMPOSITE ? 4 : 1);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    vr::TexParams tp;
-    std::memset(&tp, 0, sizeof tp);
-    const bool use_tex = v->n_groups > 0;
-    if (use_tex) {
-        for (int g = 0; g < v->n_groups; ++g) tp.tex[g] = v->tex[g];
-        tp.n_groups = v->n_groups;
-        tp.scale = v->scale;
-        tp.offset = v->offset;
-        tp.k_max = (int)(diag / step) + 2;
-    }
+    std::memset(tp, 0, sizeof *tp);
+    for (int g = 0; g < v->n_groups; ++g) tp->tex[g] = v->tex[g];
+    tp->n_groups = v->n_groups;
+    tp->scale = v->scale;
+    tp->offset = v->offset;
+    tp->k_max = (int)(diag / step) + 2;
+    return VR_OK;
+}
+
+// Launch the views in groups of at most kMaxViewsPerLaunch (cameras travel
+// in the kernel parameters).  cfg: texture-kernel shape.
+int launch_views(vr::Volume* v, vr::MarchParams& p, const vr::TexParams& tp, int mode, int cfg,
+                 const vr_camera* cams, int n_views, float* out, cudaStream_t s)
+{
+    const size_t per_view = (size_t)p.w * p.h * (mode == VR_COMPOSITE ? 4 : 1);
     for (int v0 = 0; v0 < n_views; v0 += vr::kMaxViewsPerLaunch) {
         const int nv = std::min(vr::kMaxViewsPerLaunch, n_views - v0);
         p.n_views = nv;
         std::memcpy(p.cams, cams + v0, sizeof(vr_camera) * nv);
         p.out = out + per_view * v0;
-        cudaError_t e = use_tex ? vr::launch_tex(p, tp, v->dtype, mode, s)
-                                : vr::launch_march(p, v->dtype, mode, s);
+        cudaError_t e = v->n_groups > 0 ? vr::launch_tex(p, tp, v->dtype, mode, cfg, s)
+                                        : vr::launch_march(p, v->dtype, mode, s);
         if (e != cudaSuccess) return cuda_fail(e, "march launch");
     }
     return VR_OK;
+}
+
+int render_impl(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
+                float step, float* out, unsigned long long* d_samples, void* stream)
+{
+    vr::MarchParams p;
+    vr::TexParams tp;
+    int rc = prepare(vol, cams, n_views, w, h, mode, step, out, d_samples, &p, &tp);
+    if (rc) return rc;
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    return launch_views(v, p, tp, mode, v->cfg[mode], cams, n_views, out,
+                        static_cast<cudaStream_t>(stream));
 }
 
 void release_texture(vr::Volume* v)
@@ -431,6 +448,85 @@ int vr_volume_detach_texture(vr_volume vol)
 {
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
     release_texture(reinterpret_cast<vr::Volume*>(vol));
+    return VR_OK;
+}
+
+int vr_tune_count(void) { return vr::tex_shape_count(); }
+
+int vr_tune_describe(int cfg, int* block_x, int* block_y, int* packet_x, int* packet_y,
+                     int* min_blocks)
+{
+    if (cfg < 0 || cfg >= vr::tex_shape_count())
+        return fail(VR_ERR_ARG, "launch configuration %d out of range", cfg);
+    int bx, by, px, py, mb;
+    vr::tex_shape(cfg, &bx, &by, &px, &py, &mb);
+    if (block_x) *block_x = bx;
+    if (block_y) *block_y = by;
+    if (packet_x) *packet_x = px;
+    if (packet_y) *packet_y = py;
+    if (min_blocks) *min_blocks = mb;
+    return VR_OK;
+}
+
+int vr_set_launch_config(vr_volume vol, int mode, int cfg)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    if (mode != VR_MIP && mode != VR_COMPOSITE && mode != VR_SUM)
+        return fail(VR_ERR_ARG, "unknown mode %d", mode);
+    if (cfg < 0 || cfg >= vr::tex_shape_count())
+        return fail(VR_ERR_ARG, "launch configuration %d out of range", cfg);
+    reinterpret_cast<vr::Volume*>(vol)->cfg[mode] = cfg;
+    return VR_OK;
+}
+
+int vr_autotune(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
+                float step, float* out, void* stream, int* best_cfg, float* best_ms)
+{
+    vr::MarchParams p;
+    vr::TexParams tp;
+    int rc = prepare(vol, cams, n_views, w, h, mode, step, out, nullptr, &p, &tp);
+    if (rc) return rc;
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (v->n_groups == 0) {   // only the texture kernel has shapes to choose from
+        if (best_cfg) *best_cfg = v->cfg[mode];
+        if (best_ms) *best_ms = -1.0f;
+        return VR_OK;
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "event");
+    }
+    int best = -1;
+    float best_t = 0.0f;
+    for (int c = 0; c < vr::tex_shape_count() && rc == VR_OK; ++c) {
+        float t = 1e30f;
+        for (int it = 0; it < 3 && rc == VR_OK; ++it) {    // first run warms up
+            cudaEventRecord(e0, s);
+            rc = launch_views(v, p, tp, mode, c, cams, n_views, out, s);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "autotune");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (it > 0 && ms < t) t = ms;
+        }
+        if (rc == VR_OK && (best < 0 || t < best_t)) {
+            best = c;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    v->cfg[mode] = best;
+    if (best_cfg) *best_cfg = best;
+    if (best_ms) *best_ms = best_t;
     return VR_OK;
 }
 

@@ -44,6 +44,7 @@ struct Volume {
     int n_groups;
     cudaArray_t arrays[kMaxTexGroups];
     cudaTextureObject_t tex[kMaxTexGroups];
+    int cfg[3];             // texture-kernel launch shape per mode (autotuned)
 };
 
 // Texture storage as the texture kernels see it.
@@ -97,8 +98,10 @@ size_t slab_smem_bytes(const SlabConfig& c);
 size_t slab_window_elems(const SlabConfig& c);
 // Window shape for the cameras of one launch (false: use the gather kernel).
 bool plan_slab(const MarchParams& p, SlabConfig* c);
-cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int dtype, int mode,
+cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int dtype, int mode, int cfg,
                        cudaStream_t s);
+int tex_shape_count();
+void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb);
 cudaError_t fill_texture_group(const Volume& v, cudaSurfaceObject_t surf, int layer0, int z0,
                                int z1, cudaStream_t s);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,

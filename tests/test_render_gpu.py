@@ -256,6 +256,30 @@ def test_texture_is_refreshed_by_uploads():
     assert torch.allclose(vol.render(cams, 16, 16, "mip", 0.5), want, rtol=0, atol=1e-5)
 
 
+def test_every_launch_shape_gives_identical_images():
+    # the per-ray arithmetic does not depend on the block or packet shape
+    from paper_1001_2049_b300.api import launch_shapes
+    dims = (40, 33, 57)
+    cube = synth.make_cube(dims, 4, ("uniform", 3, 9), 50).cuda()
+    vol = Volume(cube, "f32")
+    vol.attach_texture()
+    vol.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 0.97)
+    cams = synth.random_sphere_cameras(dims, 3, 45, 29, 7)
+    shapes = launch_shapes()
+    assert len(shapes) >= 4
+    for mode in ("composite", "mip"):
+        ref = None
+        for cfg in range(len(shapes)):
+            vol.set_launch_config(mode, cfg)
+            img = vol.render(cams, 45, 29, mode, 0.5)
+            if ref is None:
+                ref = img.clone()
+            assert torch.equal(img, ref), (mode, cfg, shapes[cfg])
+        best, ms = vol.autotune(cams, 45, 29, mode, 0.5)
+        assert 0 <= best < len(shapes) and ms > 0
+        assert torch.equal(vol.render(cams, 45, 29, mode, 0.5), ref)
+
+
 # ---------------------------------------------------------------------------
 # packing: bit-exact brick contents, host and slab uploads
 # ---------------------------------------------------------------------------
