@@ -182,6 +182,53 @@ int vr_volume_attach_texture(vr_volume vol, void* stream);
  * bricks).  The caller must make sure no render using it is pending.       */
 int vr_volume_detach_texture(vr_volume vol);
 
+/* ---- many requests in one persistent launch ------------------------------
+ * The paper's scheduler maps available tasks onto the computing resources
+ * (Fig. 1 caption; §3.1 module 1).  Here the tasks are the 16 x 16 ray tiles
+ * of every request and the resources are the SMs of one GPU.             */
+
+#define VR_BATCH_MAX 64          /* requests per kernel launch (more are split) */
+
+/* A transfer function given per request (same meaning as vr_set_transfer). */
+typedef struct {
+    const float* rgba_lut;       /* host, n x (r, g, b, alpha per unit length) */
+    int32_t n;
+    float v_lo, v_hi, clip, term_alpha;
+} vr_transfer;
+
+typedef struct {
+    vr_volume vol;               /* texture storage is used when attached      */
+    vr_camera cam;               /* one view                                   */
+    int32_t w, h, mode;          /* image size; VR_MIP / VR_COMPOSITE / VR_SUM  */
+    float step;
+    float* out;                  /* device, 16-byte aligned, one view          */
+    const vr_transfer* tf;       /* host; NULL: the volume's transfer function */
+    unsigned long long* samples; /* optional device counter (8-byte aligned):
+                                    the evaluated samples are added to it      */
+    unsigned int* done;          /* optional: device or mapped host word set to
+                                    done_value once this request's image is
+                                    complete (written after a system fence)    */
+    unsigned int done_value;
+} vr_request;
+
+/* Bytes of device workspace vr_render_batch needs (work and tile counters). */
+size_t vr_batch_workspace_bytes(void);
+
+/* Render n requests -- any mix of volumes, storage types, resolutions,
+ * modes and transfer functions -- with one persistent kernel launch per
+ * VR_BATCH_MAX requests (also split when a launch would need more than 8
+ * textured volumes or 2 distinct opacity-corrected tables).  Each block
+ * takes the next ray tile from a work counter in `workspace` (caller-owned
+ * device memory of vr_batch_workspace_bytes(), 16-byte aligned; zeroed on
+ * the stream by this call) and renders it with the same per-ray march as
+ * vr_render, so every image equals the one vr_render gives for the same
+ * request.  Requests, their tables and cameras are copied: the host arrays
+ * may be reused on return.  Asynchronous on `stream`; the launches contain
+ * no host synchronisation and can be captured into a CUDA graph (the
+ * captured graph replays the same requests).                               */
+int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,
+                    void* stream);
+
 /* Launch shapes of the texture-gather kernel (the autotuner's search space):
  * configuration cfg in [0, vr_tune_count()) renders blocks of block_x x
  * block_y rays with warps holding packet_x x packet_y neighbouring rays, and

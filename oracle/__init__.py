@@ -234,7 +234,8 @@ def match(result: Result, got: np.ndarray, tol: float, channels: int,
     """Compare a device result with the oracle's acceptance sets.
 
     ``got`` is (npix, channels).  A pixel passes when, for some acceptable
-    result a, max_c |got - value_a| / scale <= tol; for MIP a -infinity
+    result a, max_c |got - value_a| / scale <= tol (``scale`` a number, or an
+    (npix, 1, 1) array of per-pixel scales); for MIP a -infinity
     primary (a miss) must be matched exactly.  When the alternative list was
     truncated (flag 8) the pixel also passes if every channel lies within the
     per-channel range spanned by the listed alternatives (widened by tol),
@@ -254,8 +255,9 @@ def match(result: Result, got: np.ndarray, tol: float, channels: int,
     ok = err <= tol
     trunc = (result.flags & 8) != 0
     if trunc.any():
-        lo = np.where(valid[:, :, None], vals, np.inf).min(axis=1) - tol * scale
-        hi = np.where(valid[:, :, None], vals, -np.inf).max(axis=1) + tol * scale
+        sc = np.asarray(scale, dtype=np.float64).reshape(-1, 1) if np.ndim(scale) else scale
+        lo = np.where(valid[:, :, None], vals, np.inf).min(axis=1) - tol * sc
+        hi = np.where(valid[:, :, None], vals, -np.inf).max(axis=1) + tol * sc
         inside = ((got >= lo) & (got <= hi)).all(axis=1)
         ok = ok | (trunc & inside)
     return ok, err

@@ -6,5 +6,6 @@ CUDA kernels of ``libvr.so`` behind the C ABI of ``include/vr.h``; this
 package is the thin Python binding (``api``), the nvcc build (``build``) and
 the seeded synthetic inputs (``synth``).
 """
-from .api import CAMERA_DTYPE, DTYPES, MODES, Volume, volume_bytes  # noqa: F401
+from .api import (CAMERA_DTYPE, DTYPES, MODES, Request, Volume, batch_workspace,  # noqa: F401
+                  render_batch, volume_bytes)
 from ._lib import VRError, load  # noqa: F401

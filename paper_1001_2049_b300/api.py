@@ -4,6 +4,7 @@ entry point (include/vr.h) and returns torch tensors."""
 from __future__ import annotations
 
 import ctypes
+from dataclasses import dataclass
 
 import numpy as np
 import torch
@@ -28,6 +29,94 @@ def _stream_ptr(stream) -> int:
 
 def _dims_arr(dims):
     return (ctypes.c_int64 * 3)(*[int(d) for d in dims])
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("proj", ctypes.c_int32), ("eye", ctypes.c_float * 3), ("fwd", ctypes.c_float * 3),
+                ("du", ctypes.c_float * 3), ("dv", ctypes.c_float * 3),
+                ("reserved", ctypes.c_float * 3)]
+
+
+class _Transfer(ctypes.Structure):
+    _fields_ = [("rgba_lut", ctypes.c_void_p), ("n", ctypes.c_int32), ("v_lo", ctypes.c_float),
+                ("v_hi", ctypes.c_float), ("clip", ctypes.c_float),
+                ("term_alpha", ctypes.c_float)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("vol", ctypes.c_void_p), ("cam", _Camera), ("w", ctypes.c_int32),
+                ("h", ctypes.c_int32), ("mode", ctypes.c_int32), ("step", ctypes.c_float),
+                ("out", ctypes.c_void_p), ("tf", ctypes.c_void_p),
+                ("samples", ctypes.c_void_p), ("done", ctypes.c_void_p),
+                ("done_value", ctypes.c_uint32)]
+
+
+assert ctypes.sizeof(_Camera) == 64 and ctypes.sizeof(_Request) == 128
+
+
+@dataclass
+class Request:
+    """One view of one volume for ``render_batch``.  ``tf`` = (lut, v_lo,
+    v_hi, clip, term_alpha) overrides the volume's transfer function;
+    ``done`` = (int32 tensor, index) gets ``done_value`` when the image is
+    complete (a pinned host tensor lets the host watch it)."""
+    volume: "Volume"
+    cam: np.void
+    w: int
+    h: int
+    mode: str = "composite"
+    step: float = 0.5
+    out: torch.Tensor | None = None
+    tf: tuple | None = None
+    samples: torch.Tensor | None = None
+    done: tuple | None = None
+    done_value: int = 1
+
+
+def batch_workspace(device=None) -> torch.Tensor:
+    n = load().vr_batch_workspace_bytes()
+    return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
+
+
+def render_batch(requests, workspace: torch.Tensor | None = None, stream=None):
+    """Render every request with the batched persistent kernel; returns the
+    output tensors (allocated here when a request has none)."""
+    n = len(requests)
+    arr = (_Request * max(n, 1))()
+    keep, outs = [], []
+    for i, rq in enumerate(requests):
+        m = MODES[rq.mode]
+        shape = (rq.h, rq.w, 4) if m == VR_COMPOSITE else (rq.h, rq.w)
+        out = rq.out
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=rq.volume.buffer.device)
+        elif tuple(out.shape[-len(shape):]) != shape or out.numel() != int(np.prod(shape)):
+            raise ValueError("request %d: out must hold %s floats" % (i, shape))
+        outs.append(out)
+        r = arr[i]
+        r.vol = rq.volume.handle.value
+        cam = np.ascontiguousarray(np.asarray(rq.cam).reshape(1))
+        ctypes.memmove(ctypes.addressof(r.cam), cam.ctypes.data, 64)
+        r.w, r.h, r.mode, r.step = rq.w, rq.h, m, float(rq.step)
+        r.out = out.data_ptr()
+        if rq.tf is not None:
+            lut, v_lo, v_hi, clip, ta = rq.tf
+            lut = np.ascontiguousarray(np.asarray(lut, dtype=np.float32))
+            t = _Transfer(lut.ctypes.data, lut.shape[0], v_lo, v_hi, clip, ta)
+            keep += [lut, t]
+            r.tf = ctypes.addressof(t)
+        if rq.samples is not None:
+            r.samples = rq.samples.data_ptr()
+        if rq.done is not None:
+            flags, idx = rq.done
+            r.done = flags.data_ptr() + 4 * int(idx)
+            r.done_value = int(rq.done_value)
+    if workspace is None:
+        workspace = batch_workspace(outs[0].device if outs else None)
+    check(load().vr_render_batch(arr, n, workspace.data_ptr(), workspace.numel(),
+                                 _stream_ptr(stream)))
+    del keep
+    return outs
 
 
 def launch_shapes():

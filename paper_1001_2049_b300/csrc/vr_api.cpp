@@ -214,6 +214,155 @@ int render_impl(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
                         static_cast<cudaStream_t>(stream));
 }
 
+// Fill the kernel record of one request; tables and textured volumes are
+// looked up in (or added to) the launch's slots.  Returns VR_OK, a negative
+// error, or 1 when the launch has no free slot left (start a new launch).
+int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_tex,
+                  vr::Volume** tex_vols, int* n_lut, float* lut_steps, int* lut_ns)
+{
+    if (!rq.vol) return fail(VR_ERR_ARG, "request %d: volume is NULL", index);
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(rq.vol);
+    vr::MarchParams mp;
+    vr::TexParams tp;
+    // validation of the view as vr_render does it (one camera)
+    int rc = prepare(rq.vol, &rq.cam, 1, rq.w, rq.h, rq.mode, rq.step, rq.out, rq.samples, &mp,
+                     &tp);
+    if (rc) return rc;
+    if (rq.done && reinterpret_cast<uintptr_t>(rq.done) % 4 != 0)
+        return fail(VR_ERR_ARG, "request %d: done must be 4-byte aligned", index);
+    vr::BatchReq& q = B->req[B->n];
+    std::memset(&q, 0, sizeof q);
+    // transfer function: the request's own or the volume's
+    const float* raw = &v->lut_raw[0][0];
+    int nl = v->n_lut;
+    float v_lo = v->v_lo, v_hi = v->v_hi, clip = v->clip, ta = v->term_alpha;
+    if (rq.tf) {
+        const vr_transfer& t = *rq.tf;
+        if (!t.rgba_lut || t.n < 2 || t.n > VR_MAX_LUT)
+            return fail(VR_ERR_ARG, "request %d: bad transfer table", index);
+        if (!std::isfinite(t.v_lo) || !std::isfinite(t.v_hi) || !(t.v_lo < t.v_hi) ||
+            std::isnan(t.clip) || std::isnan(t.term_alpha))
+            return fail(VR_ERR_ARG, "request %d: bad transfer domain", index);
+        for (int i = 0; i < 4 * t.n; ++i)
+            if (!std::isfinite(t.rgba_lut[i]) || ((i & 3) == 3 && (t.rgba_lut[i] < 0.0f ||
+                                                                   t.rgba_lut[i] > 1.0f)))
+                return fail(VR_ERR_ARG, "request %d: bad transfer table entry", index);
+        raw = t.rgba_lut;
+        nl = t.n;
+        v_lo = t.v_lo;
+        v_hi = t.v_hi;
+        clip = t.clip;
+        ta = t.term_alpha;
+    }
+    int lut_slot = 0;
+    if (rq.mode == VR_COMPOSITE) {
+        // opacity-corrected table for this step, shared with an identical one
+        float4 corr[VR_MAX_LUT];
+        for (int i = 0; i < nl; ++i) {
+            const double a = raw[4 * i + 3];
+            corr[i] = make_float4(raw[4 * i], raw[4 * i + 1], raw[4 * i + 2],
+                                  (float)(1.0 - std::pow(1.0 - a, (double)rq.step)));
+        }
+        lut_slot = -1;
+        for (int i = 0; i < *n_lut; ++i)
+            if (lut_ns[i] == nl && std::memcmp(B->lut[i], corr, sizeof(float4) * nl) == 0)
+                lut_slot = i;
+        if (lut_slot < 0) {
+            if (*n_lut == vr::kMaxBatchLut) return 1;
+            lut_slot = (*n_lut)++;
+            std::memcpy(B->lut[lut_slot], corr, sizeof(float4) * nl);
+            lut_ns[lut_slot] = nl;
+            lut_steps[lut_slot] = rq.step;
+        }
+    }
+    int tex_slot = -1;
+    if (v->n_groups > 0) {
+        for (int i = 0; i < *n_tex; ++i)
+            if (tex_vols[i] == v) tex_slot = i;
+        if (tex_slot < 0) {
+            if (*n_tex == vr::kMaxBatchTex) return 1;
+            tex_slot = (*n_tex)++;
+            tex_vols[tex_slot] = v;
+            vr::BatchTex& T = B->tex[tex_slot];
+            std::memset(&T, 0, sizeof T);
+            for (int g = 0; g < v->n_groups; ++g) T.tex[g] = v->tex[g];
+            T.n_groups = v->n_groups;
+            T.scale = v->scale;
+            T.offset = v->offset;
+        }
+    }
+    q.cam = rq.cam;
+    q.out = rq.out;
+    q.bricks = v->bricks;
+    q.scale = v->scale;
+    q.offset = v->offset;
+    q.samples = rq.samples;
+    q.done = rq.done;
+    q.done_value = rq.done_value;
+    q.g = v->g;
+    q.hix = mp.hix;
+    q.hiy = mp.hiy;
+    q.hiz = mp.hiz;
+    q.step = rq.step;
+    q.clip = clip;
+    q.term_alpha = ta;
+    q.v_lo = v_lo;
+    q.lut_scale = (float)((nl - 1) / ((double)v_hi - (double)v_lo));
+    q.lut_max = (float)(nl - 1);
+    q.n_lut = nl;
+    q.k_max = tp.k_max;
+    q.w = rq.w;
+    q.h = rq.h;
+    q.mode = rq.mode;
+    q.dtype = v->dtype;
+    q.tex_slot = tex_slot;
+    q.lut_slot = lut_slot;
+    q.tiles_x = (rq.w + 15) / 16;
+    q.n_tiles = q.tiles_x * ((rq.h + 15) / 16);
+    q.first_item = B->total_items;
+    B->total_items += q.n_tiles;
+    B->n++;
+    return VR_OK;
+}
+
+int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
+{
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = (sms > 0 ? sms : 1) * vr::batch_blocks_per_sm();
+    }
+    vr::BatchParams* B = new (std::nothrow) vr::BatchParams;
+    if (!B) return fail(VR_ERR_OOM, "out of host memory");
+    int i = 0, rc = VR_OK;
+    while (i < n && rc == VR_OK) {
+        B->n = 0;
+        B->total_items = 0;
+        int n_tex = 0, n_lut = 0;
+        vr::Volume* tex_vols[vr::kMaxBatchTex];
+        float lut_steps[vr::kMaxBatchLut];
+        int lut_ns[vr::kMaxBatchLut];
+        while (i < n && B->n < vr::kMaxBatch) {
+            const int r = batch_request(reqs[i], i, B, &n_tex, tex_vols, &n_lut, lut_steps,
+                                        lut_ns);
+            if (r < 0) {
+                rc = r;
+                break;
+            }
+            if (r == 1) break;           // slots full: launch what we have
+            ++i;
+        }
+        if (rc == VR_OK && B->n > 0) {
+            cudaError_t e = vr::launch_batch(*B, ws, grid, s);
+            if (e != cudaSuccess) rc = cuda_fail(e, "batch launch");
+        }
+    }
+    delete B;
+    return rc;
+}
+
 void release_texture(vr::Volume* v)
 {
     for (int g = 0; g < v->n_groups; ++g) {
@@ -449,6 +598,28 @@ int vr_volume_detach_texture(vr_volume vol)
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
     release_texture(reinterpret_cast<vr::Volume*>(vol));
     return VR_OK;
+}
+
+size_t vr_batch_workspace_bytes(void)
+{
+    return align_up(sizeof(unsigned) * (1 + vr::kMaxBatch), 256);
+}
+
+int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,
+                    void* stream)
+{
+    if (n < 0) return fail(VR_ERR_ARG, "n = %d < 0", n);
+    if (n == 0) return VR_OK;
+    if (!reqs) return fail(VR_ERR_ARG, "reqs is NULL");
+    if (!workspace) return fail(VR_ERR_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
+        return fail(VR_ERR_ARG, "workspace must be 16-byte aligned");
+    if (ws_bytes < vr_batch_workspace_bytes())
+        return fail(VR_ERR_OOM, "workspace has %zu bytes, %zu needed", ws_bytes,
+                    vr_batch_workspace_bytes());
+    if (!is_device_ptr(workspace)) return fail(VR_ERR_ARG, "workspace is not device memory");
+    return batch_impl(reqs, n, static_cast<unsigned*>(workspace),
+                      static_cast<cudaStream_t>(stream));
 }
 
 int vr_tune_count(void) { return vr::tex_shape_count(); }

@@ -1,0 +1,243 @@
+// vr_batch.cu -- many render requests (mixed cubes, storage types,
+// resolutions, modes and transfer functions) in one persistent launch.
+//
+// The paper's scheduling module maps the available tasks onto the computing
+// resources (Fig. 1 caption, §3.1 module 1); on one GPU the tasks are the
+// 16 x 16 ray tiles of every requested view and the resources are the SMs.
+// The launch puts about as many blocks as fit on the device at once; each
+// block repeatedly takes the next tile from a work counter in the caller's
+// workspace (an atomic add, no waiting on anything), renders it with the
+// same per-ray march as the single-view kernels (vr_ray.cuh), and counts the
+// tile as done in its request's counter.  The block that completes a
+// request's last tile optionally writes the request's `done` word (device or
+// mapped host memory) after a system-scope fence, so a caller can see
+// requests finish while the rest of the batch is still running.
+#include "vr_internal.h"
+#include "vr_ray.cuh"
+
+namespace vr {
+namespace {
+
+constexpr int kTile = 16;
+constexpr int kThreads = kTile * kTile;
+
+// Find the request whose items contain `item` (first_item ascending).
+__device__ __forceinline__ int find_request(const BatchParams& B, int item)
+{
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.req[mid].first_item <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// The batched kernel serves any mix of storage types and modes in one
+// launch, so its march takes the mode, the storage type and the number of
+// texture groups as run-time values (uniform over a block: the branches on
+// them do not diverge) instead of template parameters; only the two fetch
+// paths, textures and bricks, are separate code.
+
+struct AccRT {
+    float r = 0.0f, g = 0.0f, b = 0.0f, A = 0.0f, m;
+    int mode;
+    __device__ explicit AccRT(int md) : m(md == VR_MIP ? -INFINITY : 0.0f), mode(md) {}
+
+    __device__ __forceinline__ bool add(const BatchReq& P, const float4* __restrict__ lut, float s)
+    {
+        if (mode == VR_MIP) {
+            m = fmaxf(m, s);
+            return false;
+        }
+        if (mode == VR_SUM) {
+            m = fmaf(s, P.step, m);
+            return false;
+        }
+        if (!(s >= P.clip)) return false;
+        const float x = fminf(fmaxf((s - P.v_lo) * P.lut_scale, 0.0f), P.lut_max);
+        const int i = min((int)x, P.n_lut - 2);
+        const float f = x - (float)i;
+        const float4 a = lut[i], c = lut[i + 1];
+        const float alpha = ray::lerpf(a.w, c.w, f);
+        const float wgt = (1.0f - A) * alpha;
+        r = fmaf(wgt, ray::lerpf(a.x, c.x, f), r);
+        g = fmaf(wgt, ray::lerpf(a.y, c.y, f), g);
+        b = fmaf(wgt, ray::lerpf(a.z, c.z, f), b);
+        A += wgt;
+        return A >= P.term_alpha;
+    }
+};
+
+// One plane's 2 x 2 corners: float texels (f32, f16) or int8 codes decoded
+// with the plane's scale and offset.
+__device__ __forceinline__ float4 plane_rt(const BatchTex& T, int z, float x, float y, bool i8)
+{
+    const int g = T.n_groups > 1 ? min(z / (kMaxLayers - 1), T.n_groups - 1) : 0;
+    const cudaTextureObject_t t = T.tex[g];
+    const int l = z - g * (kMaxLayers - 1);
+    if (!i8) return ray::gather<VR_F32>(t, l, x, y);
+    const float4 q = ray::gather<VR_I8>(t, l, x, y);
+    const float sc = __ldg(T.scale + z), of = __ldg(T.offset + z);
+    return make_float4(fmaf(q.x, sc, of), fmaf(q.y, sc, of), fmaf(q.z, sc, of),
+                       fmaf(q.w, sc, of));
+}
+
+__device__ __forceinline__ void next_rt(const BatchTex& T, const ray::Geo& c, const float4& c0,
+                                        const float4& c1, const ray::Geo& n, float4& n0,
+                                        float4& n1, bool i8)
+{
+    if (n.gx == c.gx && n.gy == c.gy) {
+        if (n.iz == c.iz) {
+            n0 = c0;
+            n1 = c1;
+            return;
+        }
+        if (n.iz == c.iz + 1) {
+            n0 = c1;
+            n1 = plane_rt(T, n.iz + 1, n.gx, n.gy, i8);
+            return;
+        }
+    }
+    n0 = plane_rt(T, n.iz, n.gx, n.gy, i8);
+    n1 = plane_rt(T, n.iz + 1, n.gx, n.gy, i8);
+}
+
+// Texture path: as ray::march_tex (pipelined one sample ahead, corners reused).
+__device__ __forceinline__ int march_tex_rt(const BatchReq& P, const BatchTex& T,
+                                            const float4* __restrict__ lut, const ray::Ray& r,
+                                            AccRT& acc)
+{
+    if (r.K <= 0) return 0;
+    const bool i8 = P.dtype == VR_I8;
+    int k = 0;
+    ray::Geo ga = ray::geo(P, r, 0.0f), gb;
+    float4 a0 = plane_rt(T, ga.iz, ga.gx, ga.gy, i8);
+    float4 a1 = plane_rt(T, ga.iz + 1, ga.gx, ga.gy, i8);
+    float4 b0, b1;
+    float kf = 1.0f;
+    for (;;) {
+        gb = ray::geo(P, r, kf);
+        next_rt(T, ga, a0, a1, gb, b0, b1, i8);
+        ++k;
+        if (acc.add(P, lut, ray::interp(a0, a1, ga)) || k >= r.K) break;
+        kf += 1.0f;
+        ga = ray::geo(P, r, kf);
+        next_rt(T, gb, b0, b1, ga, a0, a1, i8);
+        ++k;
+        if (acc.add(P, lut, ray::interp(b0, b1, gb)) || k >= r.K) break;
+        kf += 1.0f;
+    }
+    return k;
+}
+
+// Brick path: eight loads per sample (storage type at run time).
+__device__ __forceinline__ int march_bricks_rt(const BatchReq& P, const float4* __restrict__ lut,
+                                               const ray::Ray& r, AccRT& acc)
+{
+    int k = 0;
+    float kf = 0.0f;
+    for (; k < r.K; ++k, kf += 1.0f) {
+        const float t = fmaf(kf, P.step, r.te);
+        const float qx = fminf(fmaxf(fmaf(t, r.dx, r.ox), 0.0f), P.hix);
+        const float qy = fminf(fmaxf(fmaf(t, r.dy, r.oy), 0.0f), P.hiy);
+        const float qz = fminf(fmaxf(fmaf(t, r.dz, r.oz), 0.0f), P.hiz);
+        float s;
+        if (P.dtype == VR_F32)
+            s = ray::sample_bricks<VR_F32>(P, qx, qy, qz);
+        else if (P.dtype == VR_F16)
+            s = ray::sample_bricks<VR_F16>(P, qx, qy, qz);
+        else
+            s = ray::sample_bricks<VR_I8>(P, qx, qy, qz);
+        if (acc.add(P, lut, s)) {
+            ++k;
+            break;
+        }
+    }
+    return k;
+}
+
+__global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__ BatchParams B,
+                                                         unsigned* __restrict__ ws)
+{
+    __shared__ float4 s_lut[VR_MAX_LUT];
+    __shared__ int s_item;
+    __shared__ int s_lut_slot;
+    unsigned* next_item = ws;           // work counter
+    unsigned* tiles_done = ws + 1;      // one per request
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_lut_slot = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
+        __syncthreads();
+        const int item = s_item;
+        const int lut_slot_loaded = s_lut_slot;
+        __syncthreads();                 // s_item / s_lut_slot are rewritten below
+        if (item >= B.total_items) break;
+        const int ri = find_request(B, item);
+        const BatchReq& q = B.req[ri];
+        if (q.mode == VR_COMPOSITE && q.lut_slot != lut_slot_loaded) {
+            for (int i = threadIdx.x; i < q.n_lut; i += kThreads)
+                s_lut[i] = B.lut[q.lut_slot][i];
+            if (threadIdx.x == 0) s_lut_slot = q.lut_slot;
+            __syncthreads();
+        }
+        const int t = item - q.first_item;
+        const int tx = t % q.tiles_x, ty = t / q.tiles_x;
+        const int px = tx * kTile + (warp & 1) * 8 + (lane & 7);
+        const int py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+        unsigned count = 0;
+        if (px < q.w && py < q.h) {
+            const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
+            AccRT acc(q.mode);
+            const int k = q.tex_slot >= 0 ? march_tex_rt(q, B.tex[q.tex_slot], s_lut, r, acc)
+                                          : march_bricks_rt(q, s_lut, r, acc);
+            count = (unsigned)k;
+            const size_t pix = (size_t)py * q.w + px;
+            if (q.mode == VR_COMPOSITE)
+                reinterpret_cast<float4*>(q.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);
+            else
+                q.out[pix] = acc.m;
+        }
+        if (q.samples) {
+            const unsigned tot = __reduce_add_sync(0xffffffffu, count);
+            if (lane == 0 && tot) atomicAdd(q.samples, (unsigned long long)tot);
+        }
+        // every thread's pixel of this tile is written: count the tile
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned done = atomicAdd(&tiles_done[ri], 1u) + 1u;
+            if (done == (unsigned)q.n_tiles && q.done) {
+                __threadfence_system();
+                *reinterpret_cast<volatile unsigned*>(q.done) = q.done_value;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, cudaStream_t s)
+{
+    // the counters start at zero for every launch (stream-ordered, capturable)
+    cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned) * (1 + b.n), s);
+    if (e != cudaSuccess) return e;
+    batch_kernel<<<grid, kThreads, 0, s>>>(b, ws);
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel, kThreads, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+}  // namespace vr

@@ -78,6 +78,48 @@ struct MarchParams {
     float4 lut[VR_MAX_LUT];
 };
 
+// ---- batched persistent launch ----
+constexpr int kMaxBatch = VR_BATCH_MAX;        // requests per launch
+constexpr int kMaxBatchTex = 8;                // textured volumes per launch
+constexpr int kMaxBatchLut = 2;                // distinct corrected tables per launch
+
+struct BatchTex {
+    cudaTextureObject_t tex[kMaxTexGroups];
+    int n_groups;
+    const float* scale;
+    const float* offset;
+};
+
+// One request as the batched kernel sees it (field names shared with
+// MarchParams so the per-ray march templates accept either).
+struct BatchReq {
+    vr_camera cam;
+    float* out;
+    const void* bricks;
+    const float* scale;
+    const float* offset;
+    unsigned long long* samples;
+    unsigned* done;
+    VolumeGeom g;
+    float hix, hiy, hiz, step;
+    float clip, term_alpha, v_lo, lut_scale, lut_max;
+    int w, h, n_lut, k_max, mode, dtype;
+    int tex_slot;          // -1: gather from the bricks
+    int lut_slot;
+    int tiles_x, n_tiles, first_item;
+    unsigned done_value;
+};
+
+struct BatchParams {
+    int n, total_items;
+    BatchReq req[kMaxBatch];
+    BatchTex tex[kMaxBatchTex];
+    float4 lut[kMaxBatchLut][VR_MAX_LUT];
+};
+
+cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, cudaStream_t s);
+int batch_blocks_per_sm();
+
 // Shape of the shared-memory window of the slab-staged march.
 struct SlabConfig {
     int S;          // cells per slab along the principal axis (S + 1 planes staged)

@@ -1,0 +1,349 @@
+// vr_ray.cuh -- the per-ray march shared by the render kernels (device code).
+//
+// One ray per thread (paper §3.1 process item 3; definition in include/vr.h):
+// camera -> ray -> box -> K samples at t_entry + k*step -> trilinear value ->
+// MIP / SUM / clipped table + front-to-back compositing with termination.
+// Two ways to fetch a cell's eight corners:
+//   * texture storage: one unfiltered four-texel gather (tld4) per plane of
+//     a layered 2-D texture (one layer per frequency plane), pipelined one
+//     sample ahead, with the last cell's corners reused;
+//   * brick storage: eight read-only loads from 32^3 bricks.
+// The functions are templated on the parameter record (PP: image, volume and
+// transfer scalars) so the per-view kernel and the batched kernel share them.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "vr_internal.h"
+
+namespace vr {
+namespace ray {
+
+__device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(f, b - a, a); }
+
+// Four texels around (x, y) of a layer: with x = i + 1, y = j + 1 (texel
+// centres at +0.5) the footprint is texels i..i+1, j..j+1, returned as
+// (i, j+1), (i+1, j+1), (i+1, j), (i, j).
+template <int DT>
+__device__ __forceinline__ float4 gather(cudaTextureObject_t t, int layer, float x, float y);
+
+template <>
+__device__ __forceinline__ float4 gather<VR_F32>(cudaTextureObject_t t, int layer, float x,
+                                                 float y)
+{
+    float4 r;
+    asm volatile("tld4.r.a2d.v4.f32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(t), "r"(layer), "f"(x), "f"(y));
+    return r;
+}
+
+template <>
+__device__ __forceinline__ float4 gather<VR_F16>(cudaTextureObject_t t, int layer, float x,
+                                                 float y)
+{
+    return gather<VR_F32>(t, layer, x, y);   // half texels are returned as floats
+}
+
+template <>
+__device__ __forceinline__ float4 gather<VR_I8>(cudaTextureObject_t t, int layer, float x,
+                                                float y)
+{
+    int q0, q1, q2, q3;
+    asm volatile("tld4.r.a2d.v4.s32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+                 : "=r"(q0), "=r"(q1), "=r"(q2), "=r"(q3)
+                 : "l"(t), "r"(layer), "f"(x), "f"(y));
+    return make_float4((float)q0, (float)q1, (float)q2, (float)q3);
+}
+
+struct Ray {
+    float ox, oy, oz, dx, dy, dz, te;
+    int K;
+};
+
+// Camera -> ray -> box -> sample count K (0 for a miss or a degenerate
+// direction).  PP supplies w, h, hix, hiy, hiz and step.
+template <typename PP>
+__device__ __forceinline__ Ray setup_ray(const PP& P, const vr_camera& c, int px, int py,
+                                         int k_max)
+{
+    Ray r;
+    const float u = ((float)px + 0.5f) - 0.5f * (float)P.w;
+    const float v = ((float)py + 0.5f) - 0.5f * (float)P.h;
+    float d0, d1, d2;
+    if (c.proj == VR_ORTHO) {
+        r.ox = fmaf(v, c.dv[0], fmaf(u, c.du[0], c.eye[0]));
+        r.oy = fmaf(v, c.dv[1], fmaf(u, c.du[1], c.eye[1]));
+        r.oz = fmaf(v, c.dv[2], fmaf(u, c.du[2], c.eye[2]));
+        d0 = c.fwd[0];
+        d1 = c.fwd[1];
+        d2 = c.fwd[2];
+    } else {
+        r.ox = c.eye[0];
+        r.oy = c.eye[1];
+        r.oz = c.eye[2];
+        d0 = fmaf(v, c.dv[0], fmaf(u, c.du[0], c.fwd[0]));
+        d1 = fmaf(v, c.dv[1], fmaf(u, c.du[1], c.fwd[1]));
+        d2 = fmaf(v, c.dv[2], fmaf(u, c.du[2], c.fwd[2]));
+    }
+    const float nrm = sqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+    r.dx = d0 / nrm;
+    r.dy = d1 / nrm;
+    r.dz = d2 / nrm;
+    r.K = 0;
+    r.te = 0.0f;
+    if (!(nrm > 0.0f) || !isfinite(nrm)) return r;
+    float tn = -INFINITY, tf = INFINITY;
+    bool inside = true;
+    const float o[3] = {r.ox, r.oy, r.oz};
+    const float d[3] = {r.dx, r.dy, r.dz};
+    const float hi[3] = {P.hix, P.hiy, P.hiz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0f) {
+            const float ta = (0.0f - o[a]) / d[a];
+            const float tb = (hi[a] - o[a]) / d[a];
+            tn = fmaxf(tn, fminf(ta, tb));
+            tf = fminf(tf, fmaxf(ta, tb));
+        } else if (o[a] < 0.0f || o[a] > hi[a]) {
+            inside = false;
+        }
+    }
+    const float te = fmaxf(tn, 0.0f);
+    if (inside && tf >= te) {
+        const float q = floorf((tf - te) / P.step);
+        r.K = (q < (float)k_max) ? (int)q + 1 : k_max;
+        r.te = te;
+    }
+    return r;
+}
+
+// Decode int8 codes of plane z (scale/offset); identity for float storage.
+// TT supplies tex[], n_groups, scale and offset.
+template <int DT, typename TT>
+__device__ __forceinline__ float4 decode(const TT& T, float4 q, int z)
+{
+    if (DT != VR_I8) return q;
+    const float s = __ldg(T.scale + z), o = __ldg(T.offset + z);
+    return make_float4(fmaf(q.x, s, o), fmaf(q.y, s, o), fmaf(q.z, s, o), fmaf(q.w, s, o));
+}
+
+// The two planes z and z + 1 of the cell whose x/y corner is texel (x-1, y-1).
+template <int DT, bool MULTI, typename TT>
+__device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z, float x,
+                                     float y, float4& q0, float4& q1)
+{
+    if (!MULTI) {
+        q0 = gather<DT>(t0, z, x, y);
+        q1 = gather<DT>(t0, z + 1, x, y);
+    } else {
+        // plane pair (z, z + 1) lies in group min(z / (L-1), last)
+        const int g = min(z / (kMaxLayers - 1), T.n_groups - 1);
+        const cudaTextureObject_t t = T.tex[g];
+        const int l = z - g * (kMaxLayers - 1);
+        q0 = gather<DT>(t, l, x, y);
+        q1 = gather<DT>(t, l + 1, x, y);
+    }
+    q0 = decode<DT>(T, q0, z);
+    q1 = decode<DT>(T, q1, z + 1);
+}
+
+// Corners of the cell of sample geometry `n` given the cell `c` whose corners
+// (c0, c1) are held: nothing is fetched when the cell is the same, one plane
+// when only z moved by one, both planes otherwise.  The texture return path
+// is what bounds this kernel, so every gather saved counts.
+template <int DT, bool MULTI, typename TT, typename G>
+__device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, const G& c,
+                                          const float4& c0, const float4& c1, const G& n,
+                                          float4& n0, float4& n1)
+{
+    if (n.gx == c.gx && n.gy == c.gy) {
+        if (n.iz == c.iz) {
+            n0 = c0;
+            n1 = c1;
+            return;
+        }
+        if (n.iz == c.iz + 1) {
+            float4 u0, u1;
+            n0 = c1;
+            if (!MULTI) {
+                n1 = decode<DT>(T, gather<DT>(t0, n.iz + 1, n.gx, n.gy), n.iz + 1);
+            } else {
+                cell<DT, MULTI>(T, t0, n.iz, n.gx, n.gy, u0, u1);
+                n1 = u1;
+            }
+            return;
+        }
+    }
+    cell<DT, MULTI>(T, t0, n.iz, n.gx, n.gy, n0, n1);
+}
+
+// Per-sample geometry: the gather coordinates of the cell and the weights.
+// x and y are not clamped to the box: a position just outside a face (by
+// rounding) has both its corners clamped to the edge texel by the texture
+// unit, which gives the edge value exactly as clamping the position would.
+// z is the layer index and is clamped explicitly (cell in [0, nz - 2],
+// weight in [0, 1]).
+struct Geo {
+    float gx, gy;     // gather coordinates (cell corner + 1)
+    float fx, fy, fz;
+    int iz;
+};
+
+template <typename PP>
+__device__ __forceinline__ Geo geo(const PP& P, const Ray& r, float kf)
+{
+    Geo g;
+    const float t = fmaf(kf, P.step, r.te);
+    const float px = fmaf(t, r.dx, r.ox), py = fmaf(t, r.dy, r.oy), pz = fmaf(t, r.dz, r.oz);
+    const float flx = floorf(px), fly = floorf(py);
+    const float flz = fminf(fmaxf(floorf(pz), 0.0f), P.hiz - 1.0f);
+    g.gx = flx + 1.0f;
+    g.gy = fly + 1.0f;
+    g.fx = px - flx;
+    g.fy = py - fly;
+    g.fz = fminf(fmaxf(pz - flz, 0.0f), 1.0f);
+    g.iz = (int)flz;
+    return g;
+}
+
+__device__ __forceinline__ float interp(const float4& q0, const float4& q1, const Geo& g)
+{
+    // q = ((x0,y1), (x1,y1), (x1,y0), (x0,y0)) of planes z0 (q0) and z0 + 1 (q1)
+    const float y0z0 = lerpf(q0.w, q0.z, g.fx);
+    const float y1z0 = lerpf(q0.x, q0.y, g.fx);
+    const float y0z1 = lerpf(q1.w, q1.z, g.fx);
+    const float y1z1 = lerpf(q1.x, q1.y, g.fx);
+    return lerpf(lerpf(y0z0, y1z0, g.fy), lerpf(y0z1, y1z1, g.fy), g.fz);
+}
+
+// Accumulate one sample; returns true when the ray terminates.
+template <int MODE>
+struct Acc {
+    float r = 0.0f, g = 0.0f, b = 0.0f, A = 0.0f;
+    float m = (MODE == VR_MIP) ? -INFINITY : 0.0f;
+
+    template <typename PP>
+    __device__ __forceinline__ bool add(const PP& P, const float4* __restrict__ lut, float s)
+    {
+        if (MODE == VR_MIP) {
+            m = fmaxf(m, s);
+            return false;
+        }
+        if (MODE == VR_SUM) {
+            m = fmaf(s, P.step, m);
+            return false;
+        }
+        if (!(s >= P.clip)) return false;
+        const float x = fminf(fmaxf((s - P.v_lo) * P.lut_scale, 0.0f), P.lut_max);
+        const int i = min((int)x, P.n_lut - 2);
+        const float f = x - (float)i;
+        const float4 a = lut[i], c = lut[i + 1];
+        const float alpha = lerpf(a.w, c.w, f);
+        const float wgt = (1.0f - A) * alpha;
+        r = fmaf(wgt, lerpf(a.x, c.x, f), r);
+        g = fmaf(wgt, lerpf(a.y, c.y, f), g);
+        b = fmaf(wgt, lerpf(a.z, c.z, f), b);
+        A += wgt;
+        return A >= P.term_alpha;
+    }
+};
+
+// The gathers of sample k + 1 are issued before sample k is interpolated, so
+// the texture latency overlaps the arithmetic of the current sample.  The
+// loop is unrolled twice with two register sets that swap roles, so a
+// pending gather result is only copied when the next sample reuses it.
+// Returns the number of samples evaluated.
+template <int DT, int MODE, bool MULTI, typename PP, typename TT>
+__device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4* __restrict__ lut,
+                                         const Ray& r, Acc<MODE>& acc)
+{
+    int k = 0;
+    if (r.K <= 0) return 0;
+    const cudaTextureObject_t t0 = T.tex[0];
+    Geo ga = geo(P, r, 0.0f), gb;
+    float4 a0, a1, b0, b1;
+    cell<DT, MULTI>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
+    float kf = 1.0f;
+    for (;;) {
+        gb = geo(P, r, kf);
+        next_cell<DT, MULTI>(T, t0, ga, a0, a1, gb, b0, b1);
+        ++k;
+        if (acc.add(P, lut, interp(a0, a1, ga)) || k >= r.K) break;
+        kf += 1.0f;
+        ga = geo(P, r, kf);
+        next_cell<DT, MULTI>(T, t0, gb, b0, b1, ga, a0, a1);
+        ++k;
+        if (acc.add(P, lut, interp(b0, b1, gb)) || k >= r.K) break;
+        kf += 1.0f;
+    }
+    return k;
+}
+
+template <int DT>
+__device__ __forceinline__ float load_voxel(const void* b, size_t i)
+{
+    if (DT == VR_F32) return __ldg(static_cast<const float*>(b) + i);
+    if (DT == VR_F16) return __half2float(__ldg(static_cast<const __half*>(b) + i));
+    return (float)__ldg(static_cast<const signed char*>(b) + i);
+}
+
+// Trilinear sample from the bricks at a point already clamped to the box.
+// PP supplies bricks, g, scale and offset.
+template <int DT, typename PP>
+__device__ __forceinline__ float sample_bricks(const PP& P, float px, float py, float pz)
+{
+    const VolumeGeom& g = P.g;
+    const int ix = min((int)px, g.nx - 2);
+    const int iy = min((int)py, g.ny - 2);
+    const int iz = min((int)pz, g.nz - 2);
+    const float fx = px - (float)ix, fy = py - (float)iy, fz = pz - (float)iz;
+    const size_t brick = ((size_t)(iz >> kBrickShift) * g.nby + (iy >> kBrickShift)) * g.nbx +
+                         (ix >> kBrickShift);
+    const size_t base = brick * kBrickVoxels + ((iz & 31) << 10) + ((iy & 31) << 5) + (ix & 31);
+    const size_t sx = ((ix & 31) == 31) ? (size_t)(kBrickVoxels - 31) : 1;
+    const size_t sy = ((iy & 31) == 31) ? (size_t)g.nbx * kBrickVoxels - 31 * 32 : 32;
+    const size_t sz = ((iz & 31) == 31) ? (size_t)g.nbx * g.nby * kBrickVoxels - 31 * 1024 : 1024;
+    float c000 = load_voxel<DT>(P.bricks, base);
+    float c100 = load_voxel<DT>(P.bricks, base + sx);
+    float c010 = load_voxel<DT>(P.bricks, base + sy);
+    float c110 = load_voxel<DT>(P.bricks, base + sx + sy);
+    float c001 = load_voxel<DT>(P.bricks, base + sz);
+    float c101 = load_voxel<DT>(P.bricks, base + sz + sx);
+    float c011 = load_voxel<DT>(P.bricks, base + sz + sy);
+    float c111 = load_voxel<DT>(P.bricks, base + sz + sx + sy);
+    if (DT == VR_I8) {
+        const float s0 = __ldg(P.scale + iz), o0 = __ldg(P.offset + iz);
+        const float s1 = __ldg(P.scale + iz + 1), o1 = __ldg(P.offset + iz + 1);
+        c000 = fmaf(c000, s0, o0); c100 = fmaf(c100, s0, o0);
+        c010 = fmaf(c010, s0, o0); c110 = fmaf(c110, s0, o0);
+        c001 = fmaf(c001, s1, o1); c101 = fmaf(c101, s1, o1);
+        c011 = fmaf(c011, s1, o1); c111 = fmaf(c111, s1, o1);
+    }
+    const float y0z0 = lerpf(c000, c100, fx), y1z0 = lerpf(c010, c110, fx);
+    const float y0z1 = lerpf(c001, c101, fx), y1z1 = lerpf(c011, c111, fx);
+    return lerpf(lerpf(y0z0, y1z0, fy), lerpf(y0z1, y1z1, fy), fz);
+}
+
+// The march with brick gathers; returns the number of samples evaluated.
+template <int DT, int MODE, typename PP>
+__device__ __forceinline__ int march_bricks(const PP& P, const float4* __restrict__ lut,
+                                            const Ray& r, Acc<MODE>& acc)
+{
+    int k = 0;
+    float kf = 0.0f;
+    for (; k < r.K; ++k, kf += 1.0f) {
+        const float t = fmaf(kf, P.step, r.te);
+        const float qx = fminf(fmaxf(fmaf(t, r.dx, r.ox), 0.0f), P.hix);
+        const float qy = fminf(fmaxf(fmaf(t, r.dy, r.oy), 0.0f), P.hiy);
+        const float qz = fminf(fmaxf(fmaf(t, r.dz, r.oz), 0.0f), P.hiz);
+        if (acc.add(P, lut, sample_bricks<DT>(P, qx, qy, qz))) {
+            ++k;
+            break;
+        }
+    }
+    return k;
+}
+
+}  // namespace ray
+}  // namespace vr

@@ -1,0 +1,153 @@
+"""The batched persistent launch (many requests, mixed cubes, storage
+types, resolutions, modes and transfer functions) against per-view renders
+and the oracle, its completion flags, splitting and CUDA-graph replay."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import quantize
+from paper_1001_2049_b300 import Request, Volume, batch_workspace, render_batch, synth
+
+from _util import TOL_FP32, bands_for, compare, sum_scale
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scene():
+    specs = [((40, 36, 50), "f32", True), ((33, 45, 70), "f16", False),
+             ((30, 30, 2100), "i8", True), ((24, 20, 28), "f32", False)]
+    vols = []
+    for i, (dims, dt, tex) in enumerate(specs):
+        cube = synth.make_cube(dims, 4, ("uniform", 3.0, 9.0), 60 + i)
+        v = Volume(cube.cuda(), dt)
+        if tex:
+            v.attach_texture()
+        v.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 0.97)
+        vols.append((v, cube.numpy(), dims, dt))
+    torch.cuda.synchronize()
+    return vols
+
+
+def requests_for(scene, n, seed):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        v, cube, dims, dt = scene[i % len(scene)]
+        w, h = (int(x) for x in rng.integers(5, 40, 2))
+        cam = synth.random_sphere_cameras(dims, 1, w, h, seed * 100 + i)[0]
+        mode = ["composite", "mip", "sum"][int(rng.integers(0, 3))]
+        tf = None
+        if mode == "composite" and rng.random() < 0.5:
+            clip = float(rng.uniform(1.0, 4.0))
+            tf = (synth.default_lut(), clip, 9.0, clip, 0.95)
+        reqs.append(Request(v, cam, w, h, mode, 0.5, tf=tf))
+    return reqs
+
+
+def single(rq):
+    """The same request through vr_render."""
+    v = rq.volume
+    if rq.tf is not None:
+        v.set_transfer(*rq.tf)
+    img = v.render(np.asarray([rq.cam]), rq.w, rq.h, rq.mode, rq.step)[0]
+    if rq.tf is not None:
+        v.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 0.97)
+    return img
+
+
+def test_batch_equals_per_view_renders(scene):
+    reqs = requests_for(scene, 40, 1)
+    outs = render_batch(reqs)
+    torch.cuda.synchronize()
+    for rq, out in zip(reqs, outs):
+        ref = single(rq)
+        torch.cuda.synchronize()
+        assert torch.allclose(out, ref, rtol=0, atol=1e-6, equal_nan=True), rq.mode
+
+
+def test_batch_matches_oracle(scene):
+    reqs = requests_for(scene, 12, 2)
+    outs = render_batch(reqs)
+    torch.cuda.synchronize()
+    modes = {"mip": oracle.MIP, "composite": oracle.COMPOSITE, "sum": oracle.SUM}
+    for rq, out in zip(reqs, outs):
+        v, cube, dims, dt = next(s for s in scene if s[0] is rq.volume)
+        ovol = (oracle.Volume(cube) if dt == "f32" else
+                oracle.Volume(quantize.to_f16(cube)) if dt == "f16" else
+                oracle.Volume(*quantize.quantize_i8(cube)))
+        lut, lo, hi, clip, ta = rq.tf or (synth.default_lut(), 1.0, 9.0, 1.0, 0.97)
+        cams = np.asarray([rq.cam])
+        res = oracle.render(ovol, cams, rq.w, rq.h, modes[rq.mode], rq.step,
+                            oracle.TF(lut, lo, hi, clip, ta), bands=bands_for(dims, cams, rq.step))
+        got = out.cpu().numpy()
+        scale = 1.0
+        if rq.mode == "mip":
+            scale = float(cube.max() - cube.min())
+        elif rq.mode == "sum":
+            scale = sum_scale(oracle.Volume(cube), cams, rq.w, rq.h, rq.step, got)
+        compare(res, got, modes[rq.mode], TOL_FP32, scale, what="batch %s %s" % (dt, rq.mode))
+
+
+def test_batch_splits_large_and_varied_batches(scene):
+    # more than 64 requests and more than two distinct tables
+    reqs = requests_for(scene, 150, 3)
+    for i, rq in enumerate(reqs):
+        if rq.mode == "composite":
+            clip = 1.0 + 0.01 * i
+            rq.tf = (synth.default_lut(), clip, 9.0, clip, 0.99)
+    outs = render_batch(reqs)
+    torch.cuda.synchronize()
+    for rq, out in list(zip(reqs, outs))[::7]:
+        assert torch.allclose(out, single(rq), rtol=0, atol=1e-6, equal_nan=True)
+
+
+def test_done_flags_in_pinned_host_memory(scene):
+    reqs = requests_for(scene, 20, 4)
+    flags = torch.zeros(len(reqs), dtype=torch.int32).pin_memory()
+    for i, rq in enumerate(reqs):
+        rq.done = (flags, i)
+        rq.done_value = 1000 + i
+    counts = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for rq in reqs:
+        rq.samples = counts
+    render_batch(reqs)
+    torch.cuda.synchronize()
+    assert flags.tolist() == [1000 + i for i in range(len(reqs))]
+    assert int(counts.item()) > 0
+
+
+def test_batch_replays_from_a_cuda_graph(scene):
+    reqs = requests_for(scene, 16, 5)
+    ws = batch_workspace()
+    outs = [torch.empty((rq.h, rq.w, 4) if rq.mode == "composite" else (rq.h, rq.w),
+                        device="cuda") for rq in reqs]
+    for rq, o in zip(reqs, outs):
+        rq.out = o
+    render_batch(reqs, ws)             # warm-up outside the capture
+    torch.cuda.synchronize()
+    refs = [o.clone() for o in outs]
+    for o in outs:
+        o.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            render_batch(reqs, ws, stream=s)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
+
+
+def test_batch_argument_errors(scene):
+    from paper_1001_2049_b300 import VRError
+    v = scene[0][0]
+    cam = synth.random_sphere_cameras(scene[0][2], 1, 8, 8, 1)[0]
+    with pytest.raises(VRError):
+        render_batch([Request(v, cam, 8, 8, "mip", 0.0)])
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(VRError):
+        render_batch([Request(v, cam, 8, 8, "mip", 0.5)], workspace=small)

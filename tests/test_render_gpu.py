@@ -15,7 +15,7 @@ from oracle import quantize
 from paper_1001_2049_b300 import Volume, VRError, synth
 from paper_1001_2049_b300.api import volume_bytes
 
-from _util import TOL_FP32, TOL_PREC, bands_for, compare
+from _util import TOL_FP32, TOL_PREC, bands_for, compare, sum_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +67,10 @@ def run_parity(cube, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, t
     flat = got.reshape(len(cams), h, w, ch) if ch == 4 else got.reshape(len(cams), h, w, 1)
     if pixels is not None:
         flat = flat[pixels[:, 0], pixels[:, 2], pixels[:, 1]]
-    rep = compare(res, flat, MODES[mode], tol, scale_for(mode, cube, got), what=what)
+    scale = scale_for(mode, cube, got)
+    if mode == "sum":
+        scale = sum_scale(oracle.Volume(cube), cams, w, h, step, got, pixels)
+    rep = compare(res, flat, MODES[mode], tol, scale, what=what)
     return got, res, rep
 
 
