@@ -229,6 +229,24 @@ size_t vr_batch_workspace_bytes(void);
 int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,
                     void* stream);
 
+/* vr_render_batch for callers that cannot allocate device memory (no
+ * counterpart in the paper: this is a deployment convenience).  Code that
+ * must not allocate -- a fixed-budget real-time loop, a plugin handed no
+ * allocator, a process that may not grow after start-up -- cannot supply
+ * the workspace vr_render_batch asks for.  This call renders the same
+ * requests the same way but keeps its work and tile counters in a fixed
+ * array inside the library's device image (260 bytes on every GPU that
+ * loads the library, held until the process exits), so it allocates
+ * nothing itself and calls nothing that does.
+ *   n <= VR_BATCH_MAX; larger batches are rejected with VR_ERR_ARG (use
+ *   vr_render_batch).  The first call on a device looks up the array's
+ *   device address (cudaGetSymbolAddress); make that first call before any
+ *   stream capture.  All calls share the one array and each launch zeroes it
+ *   on `stream` before use, so two of these calls whose work overlaps on the
+ *   GPU (different streams, or devices sharing nothing but this array) race
+ *   and must be ordered by the caller.                                       */
+int vr_render_batch_noalloc(const vr_request* reqs, int n, void* stream);
+
 /* Launch shapes of the texture-gather kernel (the autotuner's search space):
  * configuration cfg in [0, vr_tune_count()) renders blocks of block_x x
  * block_y rays with warps holding packet_x x packet_y neighbouring rays, and

@@ -37,6 +37,7 @@ SIGNATURES = {
                                ctypes.POINTER(c_void_p)]),
     "vr_batch_workspace_bytes": (c_size_t, []),
     "vr_render_batch": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_void_p]),
+    "vr_render_batch_noalloc": (c_int, [c_void_p, c_int, c_void_p]),
     "vr_tune_count": (c_int, []),
     "vr_tune_describe": (c_int, [c_int] + [ctypes.POINTER(c_int)] * 5),
     "vr_autotune": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_void_p,

@@ -404,6 +404,15 @@ int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
 
 namespace vr {
 
+// Entry points for the allocation-free batch call (vr_noalloc.cu): plan and
+// launch a batch on counters the caller supplies, and record an error.
+int batch_with_counters(const vr_request* reqs, int n, unsigned* counters, cudaStream_t s)
+{
+    return batch_impl(reqs, n, counters, s);
+}
+
+int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 size_t brick_bytes(const VolumeGeom& g, int dtype)
 {
     return (size_t)g.nbx * g.nby * g.nbz * kBrickVoxels * elem_size(dtype);

@@ -119,6 +119,8 @@ struct BatchParams {
 
 cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, cudaStream_t s);
 int batch_blocks_per_sm();
+int batch_with_counters(const vr_request* reqs, int n, unsigned* counters, cudaStream_t s);
+int record_error(int code, const char* msg);
 
 // Shape of the shared-memory window of the slab-staged march.
 struct SlabConfig {
