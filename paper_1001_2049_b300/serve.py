@@ -1,0 +1,216 @@
+"""Continuous-batching render server over resident cubes.
+
+The paper's thin client turns user interaction into render commands for the
+scheduler (Fig. 1 caption) and its framework aims at interactive control of
+the rendering (abstract; §3.1 module 4).  This module is that loop on one
+GPU: render requests (a camera, a resolution, a mode and a transfer
+function for one of the resident cubes) arrive at any time; the server
+
+  * admits a request when a launch slot is free and its output image fits in
+    the memory budget still unused by requests in flight (admission by
+    memory, first come first served);
+  * batches everything admitted since the last launch into one persistent
+    launch (``vr_render_batch``) on the next free stream, so requests that
+    arrive while others are on the GPU run in the next launch, overlapping
+    the running one on the device (continuous batching);
+  * sees each request finish individually through its completion word in
+    page-locked host memory, written by the kernel once the request's image
+    is complete, and records its latency (completion - arrival, host
+    monotonic clock) for p50 / p99.
+
+All rendering is done by the library's kernels; this is host-side control.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from .api import MODES, Request, Volume, batch_workspace, render_batch
+from ._lib import VR_COMPOSITE
+
+
+@dataclass
+class RenderJob:
+    """One render request as submitted to the server."""
+    cube: str
+    cam: np.void
+    w: int
+    h: int
+    mode: str = "composite"
+    step: float = 0.5
+    tf: tuple | None = None
+    arrival: float = 0.0                 # host monotonic time, set on submit
+    admitted: float = 0.0
+    finished: float = 0.0
+    out: torch.Tensor | None = None
+    slot: int = -1
+    ticket: int = -1
+
+    @property
+    def out_bytes(self):
+        return self.w * self.h * (16 if MODES[self.mode] == VR_COMPOSITE else 4)
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+@dataclass
+class _Launch:
+    jobs: list
+    stream: torch.cuda.Stream
+    event: torch.cuda.Event
+    flags: torch.Tensor                 # pinned int32, one per job
+    issued: float = 0.0
+
+
+class Server:
+    """Render server over ``volumes`` (name -> Volume, resident on the GPU).
+
+    ``mem_budget`` bounds the bytes of output images of requests in flight;
+    ``max_batch`` the requests per launch; ``streams`` the launches that can
+    be on the device at once.
+    """
+
+    def __init__(self, volumes: dict, mem_budget: int = 1 << 30, max_batch: int = 64,
+                 streams: int = 2, keep_outputs: bool = False):
+        self.volumes = volumes
+        self.mem_budget = int(mem_budget)
+        self.max_batch = int(max_batch)
+        self.keep_outputs = keep_outputs
+        self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        self.workspaces = [batch_workspace() for _ in range(streams)]
+        self.free_streams = collections.deque(range(streams))
+        self.pending = collections.deque()       # submitted, not admitted
+        self.admitted = []                       # admitted, not launched
+        self.in_flight = []                      # launches on the device
+        self.done = []                           # finished jobs
+        self.mem_in_use = 0
+        self.lock = threading.Lock()
+        self.next_ticket = 0
+        self.launches = 0
+        self.rejected = 0
+
+    # -- client side ---------------------------------------------------------
+    def submit(self, job: RenderJob) -> int:
+        if job.cube not in self.volumes:
+            raise KeyError("unknown cube %r" % job.cube)
+        if job.out_bytes > self.mem_budget:
+            self.rejected += 1
+            raise ValueError("request needs %d bytes, more than the whole budget" % job.out_bytes)
+        with self.lock:
+            job.arrival = time.monotonic()
+            job.ticket = self.next_ticket
+            self.next_ticket += 1
+            self.pending.append(job)
+        return job.ticket
+
+    # -- server side ---------------------------------------------------------
+    def _admit(self):
+        with self.lock:
+            while self.pending and len(self.admitted) < self.max_batch:
+                job = self.pending[0]
+                if self.mem_in_use + job.out_bytes > self.mem_budget:
+                    break                          # first come, first served
+                self.pending.popleft()
+                self.mem_in_use += job.out_bytes
+                job.admitted = time.monotonic()
+                self.admitted.append(job)
+
+    def _launch(self):
+        if not self.admitted or not self.free_streams:
+            return False
+        si = self.free_streams.popleft()
+        stream = self.streams[si]
+        jobs, self.admitted = self.admitted, []
+        flags = torch.zeros(len(jobs), dtype=torch.int32).pin_memory()
+        reqs = []
+        with torch.cuda.stream(stream):
+            for i, job in enumerate(jobs):
+                shape = (job.h, job.w, 4) if MODES[job.mode] == VR_COMPOSITE else (job.h, job.w)
+                job.out = torch.empty(shape, dtype=torch.float32, device="cuda")
+                job.slot = i
+                reqs.append(Request(self.volumes[job.cube], job.cam, job.w, job.h, job.mode,
+                                    job.step, out=job.out, tf=job.tf, done=(flags, i),
+                                    done_value=1))
+            render_batch(reqs, self.workspaces[si], stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.in_flight.append(_Launch(jobs, stream, ev, flags, time.monotonic()))
+        self.launches += 1
+        return True
+
+    def _reap(self):
+        """Record jobs whose completion word is set; free finished launches."""
+        now = time.monotonic()
+        still = []
+        for ln in self.in_flight:
+            f = ln.flags.numpy()
+            for job in ln.jobs:
+                if job.finished == 0.0 and f[job.slot] != 0:
+                    job.finished = now
+            if ln.event.query():
+                for job in ln.jobs:
+                    if job.finished == 0.0:
+                        job.finished = now
+                    self.mem_in_use -= job.out_bytes
+                    if not self.keep_outputs:
+                        job.out = None
+                    self.done.append(job)
+                self.free_streams.append(self.streams.index(ln.stream))
+            else:
+                still.append(ln)
+        self.in_flight = still
+
+    def step(self):
+        """One turn of the serving loop: reap, admit, launch."""
+        self._reap()
+        self._admit()
+        self._launch()
+
+    def idle(self):
+        with self.lock:
+            return not self.pending and not self.admitted and not self.in_flight
+
+    def drain(self, timeout: float = 120.0):
+        t0 = time.monotonic()
+        while not self.idle():
+            self.step()
+            if time.monotonic() - t0 > timeout:
+                raise TimeoutError("server did not drain")
+
+
+def latency_stats(jobs):
+    lat = np.array([j.latency for j in jobs]) * 1000.0
+    if lat.size == 0:
+        return {"n": 0}
+    return {"n": int(lat.size), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "max_ms": float(lat.max())}
+
+
+def run_poisson(server: Server, make_job, rate: float, duration: float, seed: int = 0):
+    """Submit jobs at Poisson arrival times (``rate`` per second) for
+    ``duration`` seconds of wall clock while serving them; returns the
+    finished jobs and the wall time until the last one finished."""
+    rng = np.random.default_rng(seed)
+    t0 = time.monotonic()
+    next_t = t0 + rng.exponential(1.0 / rate)
+    n = 0
+    while True:
+        now = time.monotonic()
+        while next_t <= now and next_t < t0 + duration:
+            server.submit(make_job(n))
+            n += 1
+            next_t += rng.exponential(1.0 / rate)
+        server.step()
+        if now >= t0 + duration and server.idle():
+            break
+        if now - t0 > duration + 120.0:
+            raise TimeoutError("serving did not finish")
+    return server.done, time.monotonic() - t0, n
