@@ -219,6 +219,126 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# batched and served legs (reported beside the headline number)
+# ---------------------------------------------------------------------------
+def event_ms(fn, reps, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def batched_leg(dev, reps=3):
+    """64 mixed views of four resident cubes (f32, f16, f16, int8; texture
+    storage, pair texels for f16 and int8): one persistent launch (replayed
+    from a CUDA graph) against the plain FP32 path (the same views as 64
+    per-request renders of FP32 copies with texture storage)."""
+    from paper_1001_2049_b300 import Request, batch_workspace, render_batch
+    lut = synth.default_lut()
+    vols, f32 = [], []
+    for i, (name, dims, dt) in enumerate(synth.BATCH_CUBES):
+        cube = synth.batch_cube(i, dev)
+        v = Volume(cube, dt)
+        v.attach_pair_texture() if dt != "f32" else v.attach_texture()
+        v.set_transfer(lut, 3.0, 50.0, 3.0, 0.99)
+        p = Volume(cube, "f32")
+        p.attach_texture()
+        p.set_transfer(lut, 3.0, 50.0, 3.0, 0.99)
+        del cube
+        vols.append(v)
+        f32.append(p)
+    views = synth.batch_views()
+    stream = torch.cuda.current_stream(dev)
+    outs = [torch.empty((h, w, 4) if m == "composite" else (h, w), device=dev)
+            for (_, _, w, h, m) in views]
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    reqs = [Request(vols[c], cam, w, h, m, 0.5, out=o, samples=cnt)
+            for (c, cam, w, h, m), o in zip(views, outs)]
+    ws = batch_workspace(dev)
+    render_batch(reqs, ws)
+    torch.cuda.synchronize()
+    samples = int(cnt.item())
+    for r in reqs:
+        r.samples = None
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        render_batch(reqs, ws, stream=side)
+        with torch.cuda.graph(g, stream=side):
+            render_batch(reqs, ws, stream=side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    batch_ms = event_ms(g.replay, reps, stream)
+    launch_ms = event_ms(lambda: render_batch(reqs, ws), reps, stream)
+
+    def per_request():
+        for (c, cam, w, h, m), o in zip(views, outs):
+            f32[c].render(np.asarray([cam]), w, h, m, 0.5, out=o.view((1,) + tuple(o.shape)))
+    per_request()
+    plain_ms = event_ms(per_request, reps, stream)
+    n = len(views)
+    res = {"views": n, "cubes": [c[0] for c in synth.BATCH_CUBES],
+           "samples_per_batch": samples,
+           "batched_graph_ms": batch_ms, "batched_fps": n / (batch_ms / 1000.0),
+           "batched_samples_per_s": samples / (batch_ms / 1000.0),
+           "batched_launch_ms": launch_ms,
+           "plain_f32_per_request_ms": plain_ms, "plain_f32_fps": n / (plain_ms / 1000.0),
+           "speedup_vs_plain_f32": plain_ms / batch_ms}
+    for v in vols + f32:
+        v.close()
+    return res
+
+
+def serving_leg(dev, rates=(50.0, 200.0), duration=2.0):
+    """Poisson arrivals of random requests (random direction, resolution
+    512^2..1920x1080, 80 % composite, clip U[2,5] sigma) over the resident
+    cubes of the batched leg, served with continuous batching (reduced
+    precision storage, textures) and, for comparison, one request at a time
+    on the plain FP32 path."""
+    from paper_1001_2049_b300.serve import RenderJob, Server, latency_stats, run_poisson
+    lut = synth.default_lut()
+    served, plain, dims = {}, {}, {}
+    for i, (name, d, dt) in enumerate(synth.BATCH_CUBES):
+        cube = synth.batch_cube(i, dev)
+        v = Volume(cube, dt)
+        v.attach_pair_texture() if dt != "f32" else v.attach_texture()
+        v.set_transfer(lut, 3.0, 50.0, 3.0, 0.99)
+        p = Volume(cube, "f32")
+        p.attach_texture()
+        p.set_transfer(lut, 3.0, 50.0, 3.0, 0.99)
+        del cube
+        served[name], plain[name], dims[name] = v, p, d
+    names = sorted(served)
+    out = {"cubes": names, "duration_s": duration, "rates": {}}
+    for rate in rates:
+        row = {}
+        for label, vols, mb, ns in (("continuous_batching", served, 64, 2),
+                                    ("plain_f32_one_at_a_time", plain, 1, 1)):
+            rng = np.random.default_rng(synth.SERVE_SEED + int(rate))
+
+            def make(i):
+                name = names[int(rng.integers(0, len(names)))]
+                cam, w, h, mode, tf = synth.serve_request(dims[name], rng)
+                return RenderJob(name, cam, w, h, mode, 0.5, tf)
+            server = Server(vols, mem_budget=8 << 30, max_batch=mb, streams=ns)
+            done, wall, n = run_poisson(server, make, rate, duration, seed=int(rate))
+            st = latency_stats(done)
+            st["throughput_req_s"] = n / wall
+            st["launches"] = server.launches
+            row[label] = st
+        out["rates"][str(int(rate))] = row
+    for v in list(served.values()) + list(plain.values()):
+        v.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -236,6 +356,8 @@ def main():
                     help="profiling captures only: smaller cube, same framing")
     ap.add_argument("--views", type=int, default=32)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched and served legs")
     ap.add_argument("--storage", default="texture", choices=["texture", "bricks"],
                     help="render from layered textures (default) or gather from the bricks")
     ap.add_argument("--res", default=None, help="WxH (default scales with the cube)")
@@ -355,6 +477,15 @@ def main():
                                                            args.cpu_budget, w=W, h=H)
             cpu = {"value": sps, "unit": "samples/s", "cores": threads, "kind": "oracle",
                    "sample": sample, "fps": cfps}
+        extra = {}
+        if not args.no_extra and W == 1920:
+            del comp, mip, host_comp, host_mip
+            vol.close()
+            del vol, cube
+            torch.cuda.empty_cache()
+            extra["batched"] = batched_leg(dev)
+            torch.cuda.empty_cache()
+            extra["serving"] = serving_leg(dev)
         result = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -386,6 +517,7 @@ def main():
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
         }
+        result.update(extra)
         print(json.dumps(result))
     if dist:
         dist.barrier()

@@ -178,6 +178,16 @@ int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w,
  * texture size, VR_ERR_OOM when the allocation fails.                       */
 int vr_volume_attach_texture(vr_volume vol, void* stream);
 
+/* Texture storage in pair format, for VR_F16 and VR_I8 volumes: each texel
+ * packs a voxel with its neighbour in the next frequency plane (two binary16
+ * values in 32 bits, or two int8 codes in 16 bits), one layer per cell plane
+ * (nz - 1 layers, groups of at most 2048), so one four-texel gather returns
+ * all eight corners of a cell.  Twice the bytes of vr_volume_attach_texture
+ * (2 x nx*ny*(nz-1)*sizeof(storage)); replaces a plain texture storage if
+ * one is attached.  Otherwise as vr_volume_attach_texture; VR_F32 volumes
+ * give VR_ERR_UNSUPPORTED.                                                   */
+int vr_volume_attach_pair_texture(vr_volume vol, void* stream);
+
 /* Release the texture storage (renders fall back to gathering from the
  * bricks).  The caller must make sure no render using it is pending.       */
 int vr_volume_detach_texture(vr_volume vol);
@@ -217,12 +227,13 @@ size_t vr_batch_workspace_bytes(void);
 /* Render n requests -- any mix of volumes, storage types, resolutions,
  * modes and transfer functions -- with one persistent kernel launch per
  * VR_BATCH_MAX requests (also split when a launch would need more than 8
- * textured volumes or 2 distinct opacity-corrected tables).  Each block
- * takes the next ray tile from a work counter in `workspace` (caller-owned
- * device memory of vr_batch_workspace_bytes(), 16-byte aligned; zeroed on
- * the stream by this call) and renders it with the same per-ray march as
- * vr_render, so every image equals the one vr_render gives for the same
- * request.  Requests, their tables and cameras are copied: the host arrays
+ * textured volumes or 2 distinct opacity-corrected tables; requests with
+ * texture storage and requests without go to separate launches).  Each
+ * block takes the next ray tile from a work counter in `workspace`
+ * (caller-owned device memory of vr_batch_workspace_bytes(), 16-byte
+ * aligned; zeroed on the stream by this call) and renders it with the same
+ * per-ray arithmetic as vr_render, so every image equals the one vr_render
+ * gives for the same request.  Requests, their tables and cameras are copied: the host arrays
  * may be reused on return.  Asynchronous on `stream`; the launches contain
  * no host synchronisation and can be captured into a CUDA graph (the
  * captured graph replays the same requests).                               */

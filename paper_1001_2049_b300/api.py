@@ -190,6 +190,12 @@ class Volume:
         of the cube's size); renders then use the texture-gather kernel."""
         check(load().vr_volume_attach_texture(self._h, _stream_ptr(stream)))
 
+    def attach_pair_texture(self, stream=None):
+        """FP16 / int8 volumes: texture storage whose texels pack a voxel with
+        its neighbour in the next plane, so one gather yields a whole cell
+        (twice the bytes of attach_texture)."""
+        check(load().vr_volume_attach_pair_texture(self._h, _stream_ptr(stream)))
+
     def detach_texture(self):
         check(load().vr_volume_detach_texture(self._h))
 

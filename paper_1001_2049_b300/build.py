@@ -50,6 +50,9 @@ def build(force: bool = False, ptxas_info: bool = False, verbose: bool = False) 
            "-o", tmp, *sources()]
     if ptxas_info:
         cmd.insert(1, "-Xptxas=-v")
+    extra = os.environ.get("VR_NVCC_EXTRA", "").split()
+    if extra:                      # e.g. -DVR_BATCH_MIN_BLOCKS=3 for tuning builds
+        cmd[1:1] = extra
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     res = subprocess.run(cmd, capture_output=True, text=True)

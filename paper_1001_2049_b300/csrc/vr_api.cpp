@@ -195,7 +195,7 @@ int launch_views(vr::Volume* v, vr::MarchParams& p, const vr::TexParams& tp, int
         p.n_views = nv;
         std::memcpy(p.cams, cams + v0, sizeof(vr_camera) * nv);
         p.out = out + per_view * v0;
-        cudaError_t e = v->n_groups > 0 ? vr::launch_tex(p, tp, v->dtype, mode, cfg, s)
+        cudaError_t e = v->n_groups > 0 ? vr::launch_tex(p, tp, v->tex_format, mode, cfg, s)
                                         : vr::launch_march(p, v->dtype, mode, s);
         if (e != cudaSuccess) return cuda_fail(e, "march launch");
     }
@@ -287,6 +287,7 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
             std::memset(&T, 0, sizeof T);
             for (int g = 0; g < v->n_groups; ++g) T.tex[g] = v->tex[g];
             T.n_groups = v->n_groups;
+            T.format = v->tex_format;
             T.scale = v->scale;
             T.offset = v->offset;
         }
@@ -325,38 +326,56 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
     return VR_OK;
 }
 
+// A launch holds requests of one storage kind (texture or bricks), so that
+// each kernel instance compiles one fetch path: textured requests go first,
+// then the others, each group split into launches as its slots fill.
 int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
 {
-    static int grid = 0;
-    if (grid == 0) {
+    static int grid[2] = {0, 0};
+    if (grid[0] == 0) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid = (sms > 0 ? sms : 1) * vr::batch_blocks_per_sm();
+        if (sms < 1) sms = 1;
+        grid[0] = sms * vr::batch_blocks_per_sm(false);
+        grid[1] = sms * vr::batch_blocks_per_sm(true);
     }
     vr::BatchParams* B = new (std::nothrow) vr::BatchParams;
     if (!B) return fail(VR_ERR_OOM, "out of host memory");
-    int i = 0, rc = VR_OK;
-    while (i < n && rc == VR_OK) {
-        B->n = 0;
-        B->total_items = 0;
-        int n_tex = 0, n_lut = 0;
-        vr::Volume* tex_vols[vr::kMaxBatchTex];
-        float lut_steps[vr::kMaxBatchLut];
-        int lut_ns[vr::kMaxBatchLut];
-        while (i < n && B->n < vr::kMaxBatch) {
-            const int r = batch_request(reqs[i], i, B, &n_tex, tex_vols, &n_lut, lut_steps,
-                                        lut_ns);
-            if (r < 0) {
-                rc = r;
-                break;
+    int rc = VR_OK;
+    for (int kind = 1; kind >= 0 && rc == VR_OK; --kind) {
+        int i = 0;
+        while (rc == VR_OK) {
+            // skip requests of the other kind
+            while (i < n && (reqs[i].vol &&
+                             (reinterpret_cast<vr::Volume*>(reqs[i].vol)->n_groups > 0) != kind))
+                ++i;
+            if (i >= n) break;
+            B->n = 0;
+            B->total_items = 0;
+            int n_tex = 0, n_lut = 0;
+            vr::Volume* tex_vols[vr::kMaxBatchTex];
+            float lut_steps[vr::kMaxBatchLut];
+            int lut_ns[vr::kMaxBatchLut];
+            while (i < n && B->n < vr::kMaxBatch) {
+                if (reqs[i].vol &&
+                    (reinterpret_cast<vr::Volume*>(reqs[i].vol)->n_groups > 0) != kind) {
+                    ++i;
+                    continue;
+                }
+                const int r = batch_request(reqs[i], i, B, &n_tex, tex_vols, &n_lut, lut_steps,
+                                            lut_ns);
+                if (r < 0) {
+                    rc = r;
+                    break;
+                }
+                if (r == 1) break;       // slots full: launch what we have
+                ++i;
             }
-            if (r == 1) break;           // slots full: launch what we have
-            ++i;
-        }
-        if (rc == VR_OK && B->n > 0) {
-            cudaError_t e = vr::launch_batch(*B, ws, grid, s);
-            if (e != cudaSuccess) rc = cuda_fail(e, "batch launch");
+            if (rc == VR_OK && B->n > 0) {
+                cudaError_t e = vr::launch_batch(*B, ws, grid[kind], s);
+                if (e != cudaSuccess) rc = cuda_fail(e, "batch launch");
+            }
         }
     }
     delete B;
@@ -375,12 +394,17 @@ void release_texture(vr::Volume* v)
 }
 
 // Copy planes [z0, z1) of the bricks into the texture groups holding them.
+// Copy planes [z0, z1) of the bricks into the texture groups holding them
+// (for pair formats: the cells whose texels include one of those planes).
 int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
 {
+    const bool pair = v->tex_format == vr::kF16Pair || v->tex_format == vr::kI8Pair;
+    if (pair) z0 = std::max<int64_t>(z0 - 1, 0);     // cell z0 - 1 holds plane z0
     for (int g = 0; g < v->n_groups; ++g) {
-        const int first = g * (vr::kMaxLayers - 1);
-        const int last = std::min(first + vr::kMaxLayers, v->g.nz);   // exclusive
-        const int a = (int)std::max<int64_t>(z0, first), b = (int)std::min<int64_t>(z1, last);
+        int first = 0, layers = 0;
+        vr::texture_group(*v, g, &first, &layers);
+        const int a = (int)std::max<int64_t>(z0, first);
+        const int b = (int)std::min<int64_t>(z1, first + layers);
         if (a >= b) continue;
         cudaResourceDesc rd;
         std::memset(&rd, 0, sizeof rd);
@@ -400,6 +424,71 @@ int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
     return VR_OK;
 }
 
+int attach_texture(vr_volume vol, bool pair, void* stream)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (pair && v->dtype == VR_F32)
+        return fail(VR_ERR_UNSUPPORTED, "pair textures hold FP16 or int8 storage only");
+    const int format = pair ? (v->dtype == VR_F16 ? vr::kF16Pair : vr::kI8Pair) : v->dtype;
+    if (v->n_groups > 0) {
+        if (v->tex_format == format) return VR_OK;
+        release_texture(v);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int maxw = 0, maxh = 0, maxl = 0;
+    cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, dev);
+    cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, dev);
+    cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, dev);
+    if (v->g.nx > maxw || v->g.ny > maxh || maxl < vr::kMaxLayers)
+        return fail(VR_ERR_UNSUPPORTED, "cube %d x %d exceeds the layered texture limits", v->g.nx,
+                    v->g.ny);
+    v->tex_format = format;
+    const int groups = vr::texture_groups(*v);
+    if (groups > vr::kMaxTexGroups)
+        return fail(VR_ERR_UNSUPPORTED, "nz = %d needs more than %d layered textures", v->g.nz,
+                    vr::kMaxTexGroups);
+    cudaChannelFormatDesc desc = format == VR_F32    ? cudaCreateChannelDesc<float>()
+                                 : format == VR_F16   ? cudaCreateChannelDescHalf()
+                                 : format == VR_I8    ? cudaCreateChannelDesc<signed char>()
+                                 : format == vr::kF16Pair ? cudaCreateChannelDesc<unsigned int>()
+                                                          : cudaCreateChannelDesc<unsigned short>();
+    for (int g = 0; g < groups; ++g) {
+        int first = 0, layers = 0;
+        vr::texture_group(*v, g, &first, &layers);
+        cudaArray_t arr = nullptr;
+        cudaError_t e = cudaMalloc3DArray(&arr, &desc, make_cudaExtent(v->g.nx, v->g.ny, layers),
+                                          cudaArrayLayered | cudaArraySurfaceLoadStore);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            release_texture(v);
+            return fail(e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA,
+                        "texture storage: %s", cudaGetErrorString(e));
+        }
+        v->arrays[g] = arr;
+        v->n_groups = g + 1;
+        cudaResourceDesc rd;
+        std::memset(&rd, 0, sizeof rd);
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = arr;
+        cudaTextureDesc td;
+        std::memset(&td, 0, sizeof td);
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        e = cudaCreateTextureObject(&v->tex[g], &rd, &td, nullptr);
+        if (e != cudaSuccess) {
+            release_texture(v);
+            return cuda_fail(e, "texture object");
+        }
+    }
+    int rc = refresh_texture(v, 0, v->g.nz, static_cast<cudaStream_t>(stream));
+    if (rc) release_texture(v);
+    return rc;
+}
+
 }  // namespace
 
 namespace vr {
@@ -412,6 +501,28 @@ int batch_with_counters(const vr_request* reqs, int n, unsigned* counters, cudaS
 }
 
 int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+// Plain formats: group g holds planes [g (L-1), g (L-1) + L), overlapping its
+// neighbour by one plane so a cell's two planes share a group.  Pair formats:
+// group g holds cells [g L, g L + L) (each texel already holds both planes).
+int texture_groups(const Volume& v)
+{
+    const int cells = v.g.nz - 1;
+    if (v.tex_format == kF16Pair || v.tex_format == kI8Pair)
+        return (cells + kMaxLayers - 1) / kMaxLayers;
+    return (cells + kMaxLayers - 2) / (kMaxLayers - 1);
+}
+
+void texture_group(const Volume& v, int g, int* first, int* layers)
+{
+    if (v.tex_format == kF16Pair || v.tex_format == kI8Pair) {
+        *first = g * kMaxLayers;
+        *layers = std::min(kMaxLayers, (v.g.nz - 1) - *first);
+    } else {
+        *first = g * (kMaxLayers - 1);
+        *layers = std::min(kMaxLayers, v.g.nz - *first);
+    }
+}
 
 size_t brick_bytes(const VolumeGeom& g, int dtype)
 {
@@ -548,58 +659,12 @@ int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w, 
 
 int vr_volume_attach_texture(vr_volume vol, void* stream)
 {
-    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
-    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
-    if (v->n_groups > 0) return VR_OK;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int maxw = 0, maxh = 0, maxl = 0;
-    cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, dev);
-    cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, dev);
-    cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, dev);
-    if (v->g.nx > maxw || v->g.ny > maxh || maxl < vr::kMaxLayers)
-        return fail(VR_ERR_UNSUPPORTED, "cube %d x %d exceeds the layered texture limits", v->g.nx,
-                    v->g.ny);
-    const int groups = (v->g.nz - 1 + vr::kMaxLayers - 2) / (vr::kMaxLayers - 1);
-    if (groups > vr::kMaxTexGroups)
-        return fail(VR_ERR_UNSUPPORTED, "nz = %d needs more than %d layered textures", v->g.nz,
-                    vr::kMaxTexGroups);
-    cudaChannelFormatDesc desc = v->dtype == VR_F32 ? cudaCreateChannelDesc<float>()
-                                 : v->dtype == VR_F16 ? cudaCreateChannelDescHalf()
-                                                      : cudaCreateChannelDesc<signed char>();
-    for (int g = 0; g < groups; ++g) {
-        const int first = g * (vr::kMaxLayers - 1);
-        const int layers = std::min(vr::kMaxLayers, v->g.nz - first);
-        cudaArray_t arr = nullptr;
-        cudaError_t e = cudaMalloc3DArray(&arr, &desc, make_cudaExtent(v->g.nx, v->g.ny, layers),
-                                          cudaArrayLayered | cudaArraySurfaceLoadStore);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            release_texture(v);
-            return fail(e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA,
-                        "texture storage: %s", cudaGetErrorString(e));
-        }
-        v->arrays[g] = arr;
-        v->n_groups = g + 1;
-        cudaResourceDesc rd;
-        std::memset(&rd, 0, sizeof rd);
-        rd.resType = cudaResourceTypeArray;
-        rd.res.array.array = arr;
-        cudaTextureDesc td;
-        std::memset(&td, 0, sizeof td);
-        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
-        td.filterMode = cudaFilterModePoint;
-        td.readMode = cudaReadModeElementType;
-        td.normalizedCoords = 0;
-        e = cudaCreateTextureObject(&v->tex[g], &rd, &td, nullptr);
-        if (e != cudaSuccess) {
-            release_texture(v);
-            return cuda_fail(e, "texture object");
-        }
-    }
-    int rc = refresh_texture(v, 0, v->g.nz, static_cast<cudaStream_t>(stream));
-    if (rc) release_texture(v);
-    return rc;
+    return attach_texture(vol, false, stream);
+}
+
+int vr_volume_attach_pair_texture(vr_volume vol, void* stream)
+{
+    return attach_texture(vol, true, stream);
 }
 
 int vr_volume_detach_texture(vr_volume vol)
@@ -611,7 +676,7 @@ int vr_volume_detach_texture(vr_volume vol)
 
 size_t vr_batch_workspace_bytes(void)
 {
-    return align_up(sizeof(unsigned) * (1 + vr::kMaxBatch), 256);
+    return align_up(sizeof(unsigned) * vr::kBatchWords, 256);
 }
 
 int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,

@@ -20,6 +20,9 @@ namespace {
 
 constexpr int kTile = 16;
 constexpr int kThreads = kTile * kTile;
+#ifndef VR_BATCH_MIN_BLOCKS
+#define VR_BATCH_MIN_BLOCKS 4     // resident blocks per SM the registers must allow
+#endif
 
 // Find the request whose items contain `item` (first_item ascending).
 __device__ __forceinline__ int find_request(const BatchParams& B, int item)
@@ -85,9 +88,36 @@ __device__ __forceinline__ float4 plane_rt(const BatchTex& T, int z, float x, fl
                        fmaf(q.w, sc, of));
 }
 
+// Both planes of a cell: one gather for the pair formats, two otherwise.
+__device__ __forceinline__ void cell_rt(const BatchTex& T, int z, float x, float y, float4& c0,
+                                        float4& c1)
+{
+    if (T.format >= kF16Pair) {
+        const int g = T.n_groups > 1 ? min(z / kMaxLayers, T.n_groups - 1) : 0;
+        const uint4 p = ray::gather_u32(T.tex[g], z - g * kMaxLayers, x, y);
+        if (T.format == kF16Pair) {
+            c0 = make_float4(ray::half_bits(p.x), ray::half_bits(p.y), ray::half_bits(p.z),
+                             ray::half_bits(p.w));
+            c1 = make_float4(ray::half_bits(p.x >> 16), ray::half_bits(p.y >> 16),
+                             ray::half_bits(p.z >> 16), ray::half_bits(p.w >> 16));
+        } else {
+            const float s0 = __ldg(T.scale + z), o0 = __ldg(T.offset + z);
+            const float s1 = __ldg(T.scale + z + 1), o1 = __ldg(T.offset + z + 1);
+            c0 = make_float4(fmaf(ray::code_lo(p.x), s0, o0), fmaf(ray::code_lo(p.y), s0, o0),
+                             fmaf(ray::code_lo(p.z), s0, o0), fmaf(ray::code_lo(p.w), s0, o0));
+            c1 = make_float4(fmaf(ray::code_hi(p.x), s1, o1), fmaf(ray::code_hi(p.y), s1, o1),
+                             fmaf(ray::code_hi(p.z), s1, o1), fmaf(ray::code_hi(p.w), s1, o1));
+        }
+    } else {
+        const bool i8 = T.format == VR_I8;
+        c0 = plane_rt(T, z, x, y, i8);
+        c1 = plane_rt(T, z + 1, x, y, i8);
+    }
+}
+
 __device__ __forceinline__ void next_rt(const BatchTex& T, const ray::Geo& c, const float4& c0,
                                         const float4& c1, const ray::Geo& n, float4& n0,
-                                        float4& n1, bool i8)
+                                        float4& n1)
 {
     if (n.gx == c.gx && n.gy == c.gy) {
         if (n.iz == c.iz) {
@@ -95,14 +125,13 @@ __device__ __forceinline__ void next_rt(const BatchTex& T, const ray::Geo& c, co
             n1 = c1;
             return;
         }
-        if (n.iz == c.iz + 1) {
+        if (T.format < kF16Pair && n.iz == c.iz + 1) {
             n0 = c1;
-            n1 = plane_rt(T, n.iz + 1, n.gx, n.gy, i8);
+            n1 = plane_rt(T, n.iz + 1, n.gx, n.gy, T.format == VR_I8);
             return;
         }
     }
-    n0 = plane_rt(T, n.iz, n.gx, n.gy, i8);
-    n1 = plane_rt(T, n.iz + 1, n.gx, n.gy, i8);
+    cell_rt(T, n.iz, n.gx, n.gy, n0, n1);
 }
 
 // Texture path: as ray::march_tex (pipelined one sample ahead, corners reused).
@@ -111,21 +140,19 @@ __device__ __forceinline__ int march_tex_rt(const BatchReq& P, const BatchTex& T
                                             AccRT& acc)
 {
     if (r.K <= 0) return 0;
-    const bool i8 = P.dtype == VR_I8;
     int k = 0;
     ray::Geo ga = ray::geo(P, r, 0.0f), gb;
-    float4 a0 = plane_rt(T, ga.iz, ga.gx, ga.gy, i8);
-    float4 a1 = plane_rt(T, ga.iz + 1, ga.gx, ga.gy, i8);
-    float4 b0, b1;
+    float4 a0, a1, b0, b1;
+    cell_rt(T, ga.iz, ga.gx, ga.gy, a0, a1);
     float kf = 1.0f;
     for (;;) {
         gb = ray::geo(P, r, kf);
-        next_rt(T, ga, a0, a1, gb, b0, b1, i8);
+        next_rt(T, ga, a0, a1, gb, b0, b1);
         ++k;
         if (acc.add(P, lut, ray::interp(a0, a1, ga)) || k >= r.K) break;
         kf += 1.0f;
         ga = ray::geo(P, r, kf);
-        next_rt(T, gb, b0, b1, ga, a0, a1, i8);
+        next_rt(T, gb, b0, b1, ga, a0, a1);
         ++k;
         if (acc.add(P, lut, ray::interp(b0, b1, gb)) || k >= r.K) break;
         kf += 1.0f;
@@ -159,7 +186,11 @@ __device__ __forceinline__ int march_bricks_rt(const BatchReq& P, const float4* 
     return k;
 }
 
-__global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__ BatchParams B,
+// TEX: every request of the launch has texture storage (true) or none has
+// (false); the host groups requests by storage so that each launch compiles
+// only one fetch path.
+template <bool TEX>
+__global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(const __grid_constant__ BatchParams B,
                                                          unsigned* __restrict__ ws)
 {
     __shared__ float4 s_lut[VR_MAX_LUT];
@@ -192,8 +223,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
         if (px < q.w && py < q.h) {
             const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
             AccRT acc(q.mode);
-            const int k = q.tex_slot >= 0 ? march_tex_rt(q, B.tex[q.tex_slot], s_lut, r, acc)
-                                          : march_bricks_rt(q, s_lut, r, acc);
+            const int k = TEX ? march_tex_rt(q, B.tex[q.tex_slot], s_lut, r, acc)
+                              : march_bricks_rt(q, s_lut, r, acc);
             count = (unsigned)k;
             const size_t pix = (size_t)py * q.w + px;
             if (q.mode == VR_COMPOSITE)
@@ -225,15 +256,21 @@ cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, cudaStrea
     // the counters start at zero for every launch (stream-ordered, capturable)
     cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned) * (1 + b.n), s);
     if (e != cudaSuccess) return e;
-    batch_kernel<<<grid, kThreads, 0, s>>>(b, ws);
+    if (b.n > 0 && b.req[0].tex_slot >= 0)
+        batch_kernel<true><<<grid, kThreads, 0, s>>>(b, ws);
+    else
+        batch_kernel<false><<<grid, kThreads, 0, s>>>(b, ws);
     return cudaGetLastError();
 }
 
-int batch_blocks_per_sm()
+int batch_blocks_per_sm(bool tex)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel, kThreads, 0) !=
-        cudaSuccess) {
+    cudaError_t e = tex ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<true>,
+                                                                        kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<false>,
+                                                                        kThreads, 0);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }

@@ -17,6 +17,13 @@ constexpr int64_t kBrickVoxels = 32 * 32 * 32;    // 32768
 constexpr int kMaxViewsPerLaunch = 64;            // cameras travel as kernel parameters
 constexpr int kMaxLayers = 2048;                  // planes per layered texture
 constexpr int kMaxTexGroups = 8;                  // layered textures per volume
+// Texel formats of texture storage, also the storage codes the texture
+// kernels are specialised on: the plain storage types (VR_F32, VR_F16, VR_I8:
+// one voxel per texel) and the pair formats, where a texel packs a voxel with
+// its neighbour in the next frequency plane (two binary16 in 32 bits, or two
+// int8 codes in 16 bits), so one gather returns all eight corners of a cell.
+constexpr int kF16Pair = 3;
+constexpr int kI8Pair = 4;
 
 // Geometry of a bricked volume, as the kernels see it.
 struct VolumeGeom {
@@ -42,6 +49,7 @@ struct Volume {
     bool lut_valid;
     // optional texture storage (library-owned): planes in layered 2-D arrays
     int n_groups;
+    int tex_format;         // VR_F32 / VR_F16 / VR_I8, or kF16Pair / kI8Pair
     cudaArray_t arrays[kMaxTexGroups];
     cudaTextureObject_t tex[kMaxTexGroups];
     int cfg[3];             // texture-kernel launch shape per mode (autotuned)
@@ -82,10 +90,14 @@ struct MarchParams {
 constexpr int kMaxBatch = VR_BATCH_MAX;        // requests per launch
 constexpr int kMaxBatchTex = 8;                // textured volumes per launch
 constexpr int kMaxBatchLut = 2;                // distinct corrected tables per launch
+// Workspace words of one launch: the work counter and one tile counter per
+// request.
+constexpr int kBatchWords = 1 + kMaxBatch;
 
 struct BatchTex {
     cudaTextureObject_t tex[kMaxTexGroups];
     int n_groups;
+    int format;            // texel format (see kF16Pair)
     const float* scale;
     const float* offset;
 };
@@ -118,7 +130,7 @@ struct BatchParams {
 };
 
 cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, cudaStream_t s);
-int batch_blocks_per_sm();
+int batch_blocks_per_sm(bool tex);
 int batch_with_counters(const vr_request* reqs, int n, unsigned* counters, cudaStream_t s);
 int record_error(int code, const char* msg);
 
@@ -142,12 +154,16 @@ size_t slab_smem_bytes(const SlabConfig& c);
 size_t slab_window_elems(const SlabConfig& c);
 // Window shape for the cameras of one launch (false: use the gather kernel).
 bool plan_slab(const MarchParams& p, SlabConfig* c);
-cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int dtype, int mode, int cfg,
+cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int format, int mode, int cfg,
                        cudaStream_t s);
 int tex_shape_count();
 void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb);
 cudaError_t fill_texture_group(const Volume& v, cudaSurfaceObject_t surf, int layer0, int z0,
                                int z1, cudaStream_t s);
+// First plane (plain formats) or cell (pair formats) of texture group g,
+// and the number of layers it holds.
+void texture_group(const Volume& v, int g, int* first, int* layers);
+int texture_groups(const Volume& v);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
                         cudaStream_t s);
 

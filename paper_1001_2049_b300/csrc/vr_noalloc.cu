@@ -21,10 +21,11 @@
 namespace vr {
 namespace {
 
-// One work counter plus one tile counter per request of a launch.  Every
-// GPU that loads the library holds these bytes until the process exits.
+// The counters of one launch: the work counter and a tile counter per request
+// (kBatchWords words, 260 bytes).  Every GPU that loads the library holds
+// these bytes until the process exits.
 constexpr int kStaticRequests = VR_BATCH_MAX;
-static __device__ __align__(256) unsigned g_batch_counters[1 + kStaticRequests];
+static __device__ __align__(256) unsigned g_batch_counters[kBatchWords];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_lock;

@@ -128,30 +128,69 @@ __device__ __forceinline__ float4 decode(const TT& T, float4 q, int z)
     return make_float4(fmaf(q.x, s, o), fmaf(q.y, s, o), fmaf(q.z, s, o), fmaf(q.w, s, o));
 }
 
+__device__ __forceinline__ uint4 gather_u32(cudaTextureObject_t t, int layer, float x, float y)
+{
+    uint4 r;
+    asm volatile("tld4.r.a2d.v4.u32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(t), "r"(layer), "f"(x), "f"(y));
+    return r;
+}
+
+__device__ __forceinline__ float half_bits(unsigned b)
+{
+    return __half2float(__ushort_as_half((unsigned short)(b & 0xffffu)));
+}
+
+__device__ __forceinline__ float code_lo(unsigned b) { return (float)(signed char)(b & 0xffu); }
+__device__ __forceinline__ float code_hi(unsigned b)
+{
+    return (float)(signed char)((b >> 8) & 0xffu);
+}
+
 // The two planes z and z + 1 of the cell whose x/y corner is texel (x-1, y-1).
+// Pair formats: one gather of layer z (cell plane) holds both planes.
 template <int DT, bool MULTI, typename TT>
 __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z, float x,
                                      float y, float4& q0, float4& q1)
 {
-    if (!MULTI) {
-        q0 = gather<DT>(t0, z, x, y);
-        q1 = gather<DT>(t0, z + 1, x, y);
+    if constexpr (DT == kF16Pair || DT == kI8Pair) {
+        const int g = MULTI ? min(z / kMaxLayers, T.n_groups - 1) : 0;
+        const uint4 p = gather_u32(MULTI ? T.tex[g] : t0, z - g * kMaxLayers, x, y);
+        if constexpr (DT == kF16Pair) {
+            q0 = make_float4(half_bits(p.x), half_bits(p.y), half_bits(p.z), half_bits(p.w));
+            q1 = make_float4(half_bits(p.x >> 16), half_bits(p.y >> 16), half_bits(p.z >> 16),
+                             half_bits(p.w >> 16));
+        } else {
+            const float s0 = __ldg(T.scale + z), o0 = __ldg(T.offset + z);
+            const float s1 = __ldg(T.scale + z + 1), o1 = __ldg(T.offset + z + 1);
+            q0 = make_float4(fmaf(code_lo(p.x), s0, o0), fmaf(code_lo(p.y), s0, o0),
+                             fmaf(code_lo(p.z), s0, o0), fmaf(code_lo(p.w), s0, o0));
+            q1 = make_float4(fmaf(code_hi(p.x), s1, o1), fmaf(code_hi(p.y), s1, o1),
+                             fmaf(code_hi(p.z), s1, o1), fmaf(code_hi(p.w), s1, o1));
+        }
     } else {
-        // plane pair (z, z + 1) lies in group min(z / (L-1), last)
-        const int g = min(z / (kMaxLayers - 1), T.n_groups - 1);
-        const cudaTextureObject_t t = T.tex[g];
-        const int l = z - g * (kMaxLayers - 1);
-        q0 = gather<DT>(t, l, x, y);
-        q1 = gather<DT>(t, l + 1, x, y);
+        if (!MULTI) {
+            q0 = gather<DT>(t0, z, x, y);
+            q1 = gather<DT>(t0, z + 1, x, y);
+        } else {
+            // plane pair (z, z + 1) lies in group min(z / (L-1), last)
+            const int g = min(z / (kMaxLayers - 1), T.n_groups - 1);
+            const cudaTextureObject_t t = T.tex[g];
+            const int l = z - g * (kMaxLayers - 1);
+            q0 = gather<DT>(t, l, x, y);
+            q1 = gather<DT>(t, l + 1, x, y);
+        }
+        q0 = decode<DT>(T, q0, z);
+        q1 = decode<DT>(T, q1, z + 1);
     }
-    q0 = decode<DT>(T, q0, z);
-    q1 = decode<DT>(T, q1, z + 1);
 }
 
 // Corners of the cell of sample geometry `n` given the cell `c` whose corners
-// (c0, c1) are held: nothing is fetched when the cell is the same, one plane
-// when only z moved by one, both planes otherwise.  The texture return path
-// is what bounds this kernel, so every gather saved counts.
+// (c0, c1) are held: nothing is fetched when the cell is the same; with plain
+// texels, one plane when only z moved by one, both planes otherwise.  The
+// texture return path is what bounds this kernel, so every gather saved
+// counts.
 template <int DT, bool MULTI, typename TT, typename G>
 __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, const G& c,
                                           const float4& c0, const float4& c1, const G& n,
@@ -163,16 +202,18 @@ __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, c
             n1 = c1;
             return;
         }
-        if (n.iz == c.iz + 1) {
-            float4 u0, u1;
-            n0 = c1;
-            if (!MULTI) {
-                n1 = decode<DT>(T, gather<DT>(t0, n.iz + 1, n.gx, n.gy), n.iz + 1);
-            } else {
-                cell<DT, MULTI>(T, t0, n.iz, n.gx, n.gy, u0, u1);
-                n1 = u1;
+        if constexpr (DT != kF16Pair && DT != kI8Pair) {
+            if (n.iz == c.iz + 1) {
+                float4 u0, u1;
+                n0 = c1;
+                if (!MULTI) {
+                    n1 = decode<DT>(T, gather<DT>(t0, n.iz + 1, n.gx, n.gy), n.iz + 1);
+                } else {
+                    cell<DT, MULTI>(T, t0, n.iz, n.gx, n.gy, u0, u1);
+                    n1 = u1;
+                }
+                return;
             }
-            return;
         }
     }
     cell<DT, MULTI>(T, t0, n.iz, n.gx, n.gy, n0, n1);

@@ -18,6 +18,8 @@
 // Layers: a layered texture holds at most kMaxLayers planes, so the cube is
 // split into groups of planes [g*(L-1), g*(L-1) + L) that overlap by one
 // plane; the plane pair (z0, z0 + 1) always lies in one group.
+#include <type_traits>
+
 #include <cuda_fp16.h>
 
 #include "vr_internal.h"
@@ -130,15 +132,41 @@ __global__ void __launch_bounds__(256) fill_kernel(const T* __restrict__ bricks,
     }
 }
 
+// Pair formats: layer l of the group holds cell plane c = first + l, i.e. the
+// voxels of planes c and c + 1 packed into one texel (low bits: plane c).
+template <typename T, typename W>
+__global__ void __launch_bounds__(256) fill_pair_kernel(const T* __restrict__ bricks, VolumeGeom g,
+                                                        cudaSurfaceObject_t surf, int first,
+                                                        int c0, int c1)
+{
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= g.nx || y >= g.ny) return;
+    const size_t row = ((size_t)(y >> kBrickShift) * g.nbx + (x >> kBrickShift)) * kBrickVoxels +
+                       ((y & 31) << 5) + (x & 31);
+    const size_t slab = (size_t)g.nbx * g.nby * kBrickVoxels;
+    for (int c = c0 + blockIdx.z; c < c1; c += gridDim.z) {
+        const T lo = bricks[(size_t)(c >> kBrickShift) * slab + row + ((c & 31) << 10)];
+        const int c_ = c + 1;
+        const T hi = bricks[(size_t)(c_ >> kBrickShift) * slab + row + ((c_ & 31) << 10)];
+        const W packed = (W)((W)(unsigned)(typename std::make_unsigned<T>::type)lo |
+                             ((W)(unsigned)(typename std::make_unsigned<T>::type)hi
+                              << (8 * sizeof(T))));
+        surf2DLayeredwrite(packed, surf, x * (int)sizeof(W), y, c - first);
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int dtype, int mode, int cfg,
+cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int format, int mode, int cfg,
                        cudaStream_t s)
 {
     if (cfg < 0 || cfg >= kNumShapes) cfg = 0;
-    switch (dtype) {
+    switch (format) {
     case VR_F32: return launch_dt<VR_F32>(p, t, mode, cfg, s);
     case VR_F16: return launch_dt<VR_F16>(p, t, mode, cfg, s);
+    case kF16Pair: return launch_dt<kF16Pair>(p, t, mode, cfg, s);
+    case kI8Pair: return launch_dt<kI8Pair>(p, t, mode, cfg, s);
     default: return launch_dt<VR_I8>(p, t, mode, cfg, s);
     }
 }
@@ -160,6 +188,16 @@ cudaError_t fill_texture_group(const Volume& v, cudaSurfaceObject_t surf, int la
 {
     dim3 grid((unsigned)((v.g.nx + 31) / 32), (unsigned)((v.g.ny + 7) / 8),
               (unsigned)((z1 - z0) < 1024 ? (z1 - z0) : 1024));
+    if (v.tex_format == kF16Pair) {
+        fill_pair_kernel<unsigned short, unsigned int><<<grid, 256, 0, s>>>(
+            (const unsigned short*)v.bricks, v.g, surf, layer0, z0, z1);
+        return cudaGetLastError();
+    }
+    if (v.tex_format == kI8Pair) {
+        fill_pair_kernel<signed char, unsigned short><<<grid, 256, 0, s>>>(
+            (const signed char*)v.bricks, v.g, surf, layer0, z0, z1);
+        return cudaGetLastError();
+    }
     switch (v.dtype) {
     case VR_F32:
         fill_kernel<float><<<grid, 256, 0, s>>>((const float*)v.bricks, v.g, surf, layer0, z0, z1);

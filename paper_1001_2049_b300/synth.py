@@ -268,3 +268,51 @@ def small_camera(w=256, h=256):
 def large_cameras(n_views=32, w=1920, h=1080):
     """The orbiting perspective views of the 1024^3 cube."""
     return orbit_cameras(LARGE.dims, n_views, w, h)
+
+
+# ---------------------------------------------------------------------------
+# batched and served workloads (several resident cubes, mixed requests)
+# ---------------------------------------------------------------------------
+#: The four resident cubes of the batched workload: (name, dims, storage).
+BATCH_CUBES = [("cube256_f32", (256, 256, 256), "f32"),
+               ("cube512x512x2048_f16", (512, 512, 2048), "f16"),
+               ("cube1024_f16", (1024, 1024, 1024), "f16"),
+               ("cube768x768x3072_i8", (768, 768, 3072), "i8")]
+BATCH_SEED = 1004
+SERVE_SEED = 1005
+
+
+def batch_cube(i, device="cpu"):
+    """Cube i of the batched workload as float32 (noise + sources scaled to
+    the cube's volume, SNR log-uniform 2-50)."""
+    name, dims, _ = BATCH_CUBES[i]
+    n_src = max(5, int(2000 * dims[0] * dims[1] * dims[2] / 1024 ** 3))
+    return make_cube(dims, n_src, ("loguniform", 2.0, 50.0), BATCH_SEED + 10 * i,
+                     device=device)
+
+
+def batch_views(n_views=64, seed=BATCH_SEED):
+    """(cube index, camera record, w, h, mode) for the batched workload: view
+    i renders cube i mod 4 from an orbit position, at a resolution drawn from
+    {256^2, 512^2, 1024^2, 2048^2} and a mode drawn from {mip, composite}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_views):
+        c = i % len(BATCH_CUBES)
+        res = int(rng.choice([256, 512, 1024, 2048]))
+        mode = ["mip", "composite"][int(rng.integers(0, 2))]
+        dims = BATCH_CUBES[c][1]
+        cam = orbit_cameras(dims, 16, res, res)[(i // len(BATCH_CUBES)) % 16]
+        out.append((c, cam, res, res, mode))
+    return out
+
+
+def serve_request(dims, rng):
+    """One served request: a random direction around the cube, a resolution
+    from {512^2, 1024^2, 1280x720, 1920x1080}, composite (80 %) or MIP, and a
+    clip level U[2, 5] sigma (the table spans [clip, 50 sigma])."""
+    w, h = [(512, 512), (1024, 1024), (1280, 720), (1920, 1080)][int(rng.integers(0, 4))]
+    cam = random_sphere_cameras(dims, 1, w, h, int(rng.integers(0, 2 ** 31)))[0]
+    mode = "composite" if rng.random() < 0.8 else "mip"
+    clip = float(rng.uniform(2.0, 5.0))
+    return cam, w, h, mode, (default_lut(), clip, 50.0, clip, 0.99)

@@ -17,12 +17,15 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def scene():
     specs = [((40, 36, 50), "f32", True), ((33, 45, 70), "f16", False),
-             ((30, 30, 2100), "i8", True), ((24, 20, 28), "f32", False)]
+             ((30, 30, 2100), "i8", True), ((24, 20, 28), "f32", False),
+             ((35, 30, 2200), "f16", "pair"), ((28, 33, 40), "i8", "pair")]
     vols = []
     for i, (dims, dt, tex) in enumerate(specs):
         cube = synth.make_cube(dims, 4, ("uniform", 3.0, 9.0), 60 + i)
         v = Volume(cube.cuda(), dt)
-        if tex:
+        if tex == "pair":
+            v.attach_pair_texture()
+        elif tex:
             v.attach_texture()
         v.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 0.97)
         vols.append((v, cube.numpy(), dims, dt))

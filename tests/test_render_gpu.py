@@ -34,7 +34,9 @@ def oracle_volume(cube: np.ndarray, dtype: str) -> oracle.Volume:
 def gpu_images(cube_t, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, count=None,
                tex=False):
     vol = Volume(cube_t.cuda(), dtype)
-    if tex:
+    if tex == "pair":
+        vol.attach_pair_texture()
+    elif tex:
         vol.attach_texture()
     vol.set_transfer(lut, v_lo, v_hi, clip, ta)
     out = vol.render(cams, w, h, mode, step, count=count)
@@ -236,6 +238,58 @@ def test_texture_path_spans_several_layer_groups():
         for mode in ("mip", "composite"):
             run_parity(cube, dtype, cams, 8, 8, mode, 0.5, synth.default_lut(), 1.0, 8.0, 1.0,
                        1.0, what="tex 4500 planes %s %s" % (dtype, mode), tex=True)
+
+
+@pytest.mark.parametrize("dtype", ["f16", "i8"])
+@pytest.mark.parametrize("mode", ["mip", "composite", "sum"])
+def test_pair_texture_small_workload(small, dtype, mode):
+    wl, cube, lut, cams = small
+    run_parity(cube, dtype, cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+               wl.term_alpha, what="small pair %s %s" % (dtype, mode), tex="pair")
+
+
+@pytest.mark.parametrize("dims,step", RAGGED)
+@pytest.mark.parametrize("dtype", ["f16", "i8"])
+def test_pair_texture_ragged_cubes(dims, step, dtype):
+    cube, cams, lut = ragged_case(dims, 17 + dims[0])
+    for mode in ("mip", "composite"):
+        run_parity(cube, dtype, cams, 23, 17, mode, step, lut, 1.0, 8.0, 1.0, 0.95,
+                   what="pair ragged %s %s %s" % (dims, dtype, mode), tex="pair")
+
+
+def test_pair_texture_spans_several_layer_groups():
+    dims = (6, 5, 4500)
+    cube = synth.make_cube(dims, 20, ("uniform", 3.0, 8.0), 31).numpy()
+    recs = [synth.axis_camera(dims, 8, 8, axis=2, spacing=(0.7, 0.6)),
+            synth.axis_camera(dims, 8, 8, axis=2, sign=-1, spacing=(0.7, 0.6)),
+            synth.look_at_camera((40.0, -30.0, 2048.3), (2.5, 2.0, 2048.0), 8, 8, 60.0),
+            synth.look_at_camera((-20.0, 25.0, 4096.5), (2.5, 2.0, 4096.0), 8, 8, 60.0)]
+    cams = synth.cameras(recs)
+    for dtype in ("f16", "i8"):
+        for mode in ("mip", "composite"):
+            run_parity(cube, dtype, cams, 8, 8, mode, 0.5, synth.default_lut(), 1.0, 8.0, 1.0,
+                       1.0, what="pair 4500 planes %s %s" % (dtype, mode), tex="pair")
+
+
+def test_pair_texture_is_refreshed_by_uploads_and_refused_for_f32():
+    dims = (24, 20, 30)
+    a = synth.make_cube(dims, 3, ("uniform", 3, 9), 40)
+    b = synth.make_cube(dims, 3, ("uniform", 3, 9), 41)
+    cams = synth.random_sphere_cameras(dims, 2, 16, 16, 3)
+    vol = Volume(a.cuda(), "i8")
+    vol.attach_pair_texture()
+    vol.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 1.0)
+    vol.upload(5, b[5:20].cuda())
+    mixed = a.clone()
+    mixed[5:20] = b[5:20]
+    ref = Volume(mixed.cuda(), "i8")
+    ref.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 1.0)
+    got = vol.render(cams, 16, 16, "mip", 0.5)
+    want = ref.render(cams, 16, 16, "mip", 0.5)
+    torch.cuda.synchronize()
+    assert torch.allclose(got, want, rtol=0, atol=1e-5)
+    with pytest.raises(VRError):
+        Volume(a.cuda(), "f32").attach_pair_texture()
 
 
 def test_texture_is_refreshed_by_uploads():
