@@ -356,6 +356,8 @@ def main():
                     help="profiling captures only: smaller cube, same framing")
     ap.add_argument("--views", type=int, default=32)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--bounds", action="store_true",
+                    help="render with the empty-space bounds grid")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and served legs")
     ap.add_argument("--storage", default="texture", choices=["texture", "bricks"],
@@ -382,6 +384,8 @@ def main():
     vol = Volume(cube, "f32")
     if args.storage == "texture":
         vol.attach_texture()
+        if args.bounds:
+            vol.attach_bounds()
     vol.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
     comp = torch.empty((n_views, H, W, 4), dtype=torch.float32, device=dev)
     mip = torch.empty((n_views, H, W), dtype=torch.float32, device=dev)
@@ -437,6 +441,23 @@ def main():
         dist.barrier()
     comp_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     mip_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+
+    # context only (outside the timed region): the same launches without the
+    # empty-space bounds
+    no_bounds = None
+    if args.storage == "texture" and args.bounds:
+        vol.detach_bounds()
+        nb = []
+        for mode, out in (("composite", comp), ("mip", mip)):
+            vol.render(cams, W, H, mode, wl.step, out=out)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            vol.render(cams, W, H, mode, wl.step, out=out)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            nb.append(e[0].elapsed_time(e[1]))
+        no_bounds = {"composite_ms_per_launch": nb[0], "mip_ms_per_launch": nb[1]}
+        vol.attach_bounds()
 
     # end to end through the public API: cameras in, images back to pinned host
     host_comp = torch.empty(comp.shape, dtype=torch.float32, pin_memory=True)
@@ -501,6 +522,8 @@ def main():
                 "samples_per_step": samples_step, "samples_composite": samples_comp,
                 "samples_mip": samples_mip, "composite_ms_per_launch": comp_ms,
                 "mip_ms_per_launch": mip_ms, "parallelism": "replica per GPU (views)",
+                "empty_space_bounds": args.storage == "texture" and args.bounds,
+                "without_bounds": no_bounds,
                 "autotuned": tuned,
                 "l2": "inputs larger than L2 (4 GiB cube per view pass)"},
             "roofline": {"bound": "hbm", "kernel": ("tex_kernel" if args.storage == "texture"

@@ -165,6 +165,25 @@ int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w,
                       int h, int mode, float step, float* out,
                       unsigned long long* d_samples, void* stream);
 
+/* Bytes of the volume's empty-space bounds grid: one float per macrocell of
+ * 4 x 4 x 4 cells, ((nx-2)/4 + 1) * ((ny-2)/4 + 1) * ((nz-2)/4 + 1) floats.
+ * Host-only; no device work.                                                */
+int vr_volume_bounds_bytes(vr_volume vol, size_t* bytes_out);
+
+/* Give the volume an empty-space bounds grid in the caller-owned device
+ * buffer `buf` (16-byte aligned, at least vr_volume_bounds_bytes bytes;
+ * owned by the caller, who keeps it alive while the volume renders), built
+ * from the bricks on `stream`.  Each entry is an upper bound on every value
+ * a render can interpolate in its macrocell (voxels [4m, 4m + 4] per axis).
+ * Renders then pass over runs of samples that cannot change the image:
+ * macrocells whose bound is below the clip (COMPOSITE: such samples are
+ * transparent, §3.1 item 3 with the noise clip) or not above the ray's
+ * running maximum (MIP).  Images and sample counts are identical to those
+ * without the grid; only the work differs.  vr_volume_upload keeps the grid
+ * current.  buf = NULL detaches it (no device work).  Used by the
+ * texture-gather renders; the paper describes no such structure.           */
+int vr_volume_attach_bounds(vr_volume vol, void* buf, size_t bytes, void* stream);
+
 /* Give the volume texture storage: a copy of the cube in layered 2-D
  * textures (one layer per frequency plane, split into groups of at most 2048
  * planes), filled from the bricks on `stream`.  Renders then gather the
@@ -180,12 +199,15 @@ int vr_volume_attach_texture(vr_volume vol, void* stream);
 
 /* Texture storage in pair format, for VR_F16 and VR_I8 volumes: each texel
  * packs a voxel with its neighbour in the next frequency plane (two binary16
- * values in 32 bits, or two int8 codes in 16 bits), one layer per cell plane
- * (nz - 1 layers, groups of at most 2048), so one four-texel gather returns
- * all eight corners of a cell.  Twice the bytes of vr_volume_attach_texture
- * (2 x nx*ny*(nz-1)*sizeof(storage)); replaces a plain texture storage if
- * one is attached.  Otherwise as vr_volume_attach_texture; VR_F32 volumes
- * give VR_ERR_UNSUPPORTED.                                                   */
+ * values in 32 bits, or two int8 codes in 16 bits), one 2-D plane per cell
+ * plane (nz - 1 of them), so one four-texel gather returns all eight corners
+ * of a cell.  The cell planes live in one layered texture, 2^s per layer
+ * (the smallest s that needs at most 2048 layers), each with a copy of its
+ * first and last row around it.  About twice the bytes of
+ * vr_volume_attach_texture (2 x nx*(ny+2)*(nz-1)*sizeof(storage)); replaces
+ * a plain texture storage if one is attached.  Otherwise as
+ * vr_volume_attach_texture; VR_F32 volumes, and cubes whose stacked planes
+ * exceed the layered texture height, give VR_ERR_UNSUPPORTED.               */
 int vr_volume_attach_pair_texture(vr_volume vol, void* stream);
 
 /* Release the texture storage (renders fall back to gathering from the
@@ -227,8 +249,10 @@ size_t vr_batch_workspace_bytes(void);
 /* Render n requests -- any mix of volumes, storage types, resolutions,
  * modes and transfer functions -- with one persistent kernel launch per
  * VR_BATCH_MAX requests (also split when a launch would need more than 8
- * textured volumes or 2 distinct opacity-corrected tables; requests with
- * texture storage and requests without go to separate launches).  Each
+ * textured volumes or 2 distinct opacity-corrected tables; requests on
+ * volumes without texture storage, with texture storage in one layered
+ * texture, and with plain texture storage spanning several layer groups
+ * (more than 2049 planes) go to separate launches).  Each
  * block takes the next ray tile from a work counter in `workspace`
  * (caller-owned device memory of vr_batch_workspace_bytes(), 16-byte
  * aligned; zeroed on the stream by this call) and renders it with the same

@@ -34,6 +34,9 @@ int cuda_fail(cudaError_t e, const char* what)
 int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
+// Macrocells along an axis of n voxels (cells 0 .. n - 2, four per macrocell).
+int macro_count(int n) { return ((n - 2) >> vr::kMacroShift) + 1; }
+
 size_t elem_size(int dtype) { return dtype == VR_F32 ? 4 : dtype == VR_F16 ? 2 : 1; }
 
 int check_dims(const int64_t dims[3], int dtype, vr::VolumeGeom* g)
@@ -178,9 +181,14 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
     std::memset(tp, 0, sizeof *tp);
     for (int g = 0; g < v->n_groups; ++g) tp->tex[g] = v->tex[g];
     tp->n_groups = v->n_groups;
+    tp->stack_shift = v->stack_shift;
+    tp->stack_pitch = v->stack_pitch;
     tp->scale = v->scale;
     tp->offset = v->offset;
     tp->k_max = (int)(diag / step) + 2;
+    p->bound = v->bound;
+    p->bnx = v->bnx;
+    p->bny = v->bny;
     return VR_OK;
 }
 
@@ -287,6 +295,8 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
             std::memset(&T, 0, sizeof T);
             for (int g = 0; g < v->n_groups; ++g) T.tex[g] = v->tex[g];
             T.n_groups = v->n_groups;
+            T.stack_shift = v->stack_shift;
+            T.stack_pitch = v->stack_pitch;
             T.format = v->tex_format;
             T.scale = v->scale;
             T.offset = v->offset;
@@ -300,6 +310,9 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
     q.samples = rq.samples;
     q.done = rq.done;
     q.done_value = rq.done_value;
+    q.bound = v->bound;
+    q.bnx = v->bnx;
+    q.bny = v->bny;
     q.g = v->g;
     q.hix = mp.hix;
     q.hiy = mp.hiy;
@@ -329,27 +342,32 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
 // A launch holds requests of one storage kind (texture or bricks), so that
 // each kernel instance compiles one fetch path: textured requests go first,
 // then the others, each group split into launches as its slots fill.
+int batch_class(const vr_request& r)
+{
+    const vr::Volume* v = reinterpret_cast<const vr::Volume*>(r.vol);
+    if (!v || v->n_groups == 0) return vr::kBatchBricks;
+    return v->n_groups > 1 ? vr::kBatchTexGroups : vr::kBatchTex;
+}
+
 int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
 {
-    static int grid[2] = {0, 0};
+    static int grid[3] = {0, 0, 0};
     if (grid[0] == 0) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms < 1) sms = 1;
-        grid[0] = sms * vr::batch_blocks_per_sm(false);
-        grid[1] = sms * vr::batch_blocks_per_sm(true);
+        for (int c = 0; c < 3; ++c) grid[c] = sms * vr::batch_blocks_per_sm(c);
     }
     vr::BatchParams* B = new (std::nothrow) vr::BatchParams;
     if (!B) return fail(VR_ERR_OOM, "out of host memory");
     int rc = VR_OK;
-    for (int kind = 1; kind >= 0 && rc == VR_OK; --kind) {
+    const int order[3] = {vr::kBatchTex, vr::kBatchTexGroups, vr::kBatchBricks};
+    for (int oi = 0; oi < 3 && rc == VR_OK; ++oi) {
+        const int cls = order[oi];
         int i = 0;
         while (rc == VR_OK) {
-            // skip requests of the other kind
-            while (i < n && (reqs[i].vol &&
-                             (reinterpret_cast<vr::Volume*>(reqs[i].vol)->n_groups > 0) != kind))
-                ++i;
+            while (i < n && batch_class(reqs[i]) != cls) ++i;    // other classes
             if (i >= n) break;
             B->n = 0;
             B->total_items = 0;
@@ -358,8 +376,7 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
             float lut_steps[vr::kMaxBatchLut];
             int lut_ns[vr::kMaxBatchLut];
             while (i < n && B->n < vr::kMaxBatch) {
-                if (reqs[i].vol &&
-                    (reinterpret_cast<vr::Volume*>(reqs[i].vol)->n_groups > 0) != kind) {
+                if (batch_class(reqs[i]) != cls) {
                     ++i;
                     continue;
                 }
@@ -373,7 +390,7 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
                 ++i;
             }
             if (rc == VR_OK && B->n > 0) {
-                cudaError_t e = vr::launch_batch(*B, ws, grid[kind], s);
+                cudaError_t e = vr::launch_batch(*B, ws, grid[cls], cls, s);
                 if (e != cudaSuccess) rc = cuda_fail(e, "batch launch");
             }
         }
@@ -445,6 +462,18 @@ int attach_texture(vr_volume vol, bool pair, void* stream)
         return fail(VR_ERR_UNSUPPORTED, "cube %d x %d exceeds the layered texture limits", v->g.nx,
                     v->g.ny);
     v->tex_format = format;
+    v->stack_shift = 0;
+    v->stack_pitch = v->g.ny + 2;
+    if (pair) {
+        // cell planes stacked 2^shift per layer so that one layered texture
+        // holds every cell plane
+        const int cells = v->g.nz - 1;
+        while (((cells + (1 << v->stack_shift) - 1) >> v->stack_shift) > vr::kMaxLayers)
+            ++v->stack_shift;
+        if ((int64_t)v->stack_pitch << v->stack_shift > maxh)
+            return fail(VR_ERR_UNSUPPORTED, "cube %d x %d x %d exceeds the layered texture limits",
+                        v->g.nx, v->g.ny, v->g.nz);
+    }
     const int groups = vr::texture_groups(*v);
     if (groups > vr::kMaxTexGroups)
         return fail(VR_ERR_UNSUPPORTED, "nz = %d needs more than %d layered textures", v->g.nz,
@@ -458,7 +487,11 @@ int attach_texture(vr_volume vol, bool pair, void* stream)
         int first = 0, layers = 0;
         vr::texture_group(*v, g, &first, &layers);
         cudaArray_t arr = nullptr;
-        cudaError_t e = cudaMalloc3DArray(&arr, &desc, make_cudaExtent(v->g.nx, v->g.ny, layers),
+        const cudaExtent ext =
+            pair ? make_cudaExtent(v->g.nx, (size_t)v->stack_pitch << v->stack_shift,
+                                   (layers + (1 << v->stack_shift) - 1) >> v->stack_shift)
+                 : make_cudaExtent(v->g.nx, v->g.ny, layers);
+        cudaError_t e = cudaMalloc3DArray(&arr, &desc, ext,
                                           cudaArrayLayered | cudaArraySurfaceLoadStore);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -504,20 +537,20 @@ int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 // Plain formats: group g holds planes [g (L-1), g (L-1) + L), overlapping its
 // neighbour by one plane so a cell's two planes share a group.  Pair formats:
-// group g holds cells [g L, g L + L) (each texel already holds both planes).
+// one texture holds every cell plane (stacked, see attach_texture); its
+// "layers" here count cell planes.
 int texture_groups(const Volume& v)
 {
     const int cells = v.g.nz - 1;
-    if (v.tex_format == kF16Pair || v.tex_format == kI8Pair)
-        return (cells + kMaxLayers - 1) / kMaxLayers;
+    if (v.tex_format == kF16Pair || v.tex_format == kI8Pair) return 1;
     return (cells + kMaxLayers - 2) / (kMaxLayers - 1);
 }
 
 void texture_group(const Volume& v, int g, int* first, int* layers)
 {
     if (v.tex_format == kF16Pair || v.tex_format == kI8Pair) {
-        *first = g * kMaxLayers;
-        *layers = std::min(kMaxLayers, (v.g.nz - 1) - *first);
+        *first = 0;
+        *layers = v.g.nz - 1;
     } else {
         *first = g * (kMaxLayers - 1);
         *layers = std::min(kMaxLayers, v.g.nz - *first);
@@ -612,6 +645,13 @@ int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* sr
     }
     cudaError_t e = vr::launch_pack(*v, z0, nplanes, dsrc, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+    if (v->bound) {
+        // macrocells whose voxel planes [4m, 4m + 4] meet [z0, z0 + nplanes)
+        const int mz0 = z0 > 0 ? (int)((z0 - 1) >> vr::kMacroShift) : 0;
+        const int mz1 = std::min(v->bnz, (int)((z0 + nplanes - 1) >> vr::kMacroShift) + 1);
+        e = vr::launch_bounds(*v, mz0, mz1, static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "bounds launch");
+    }
     if (v->n_groups > 0)
         return refresh_texture(v, z0, z0 + nplanes, static_cast<cudaStream_t>(stream));
     return VR_OK;
@@ -671,6 +711,42 @@ int vr_volume_detach_texture(vr_volume vol)
 {
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
     release_texture(reinterpret_cast<vr::Volume*>(vol));
+    return VR_OK;
+}
+
+int vr_volume_bounds_bytes(vr_volume vol, size_t* bytes_out)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    if (!bytes_out) return fail(VR_ERR_ARG, "bytes_out is NULL");
+    const vr::Volume* v = reinterpret_cast<const vr::Volume*>(vol);
+    *bytes_out = sizeof(float) * (size_t)macro_count(v->g.nx) * macro_count(v->g.ny) *
+                 macro_count(v->g.nz);
+    return VR_OK;
+}
+
+int vr_volume_attach_bounds(vr_volume vol, void* buf, size_t bytes, void* stream)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (!buf) {
+        v->bound = nullptr;
+        return VR_OK;
+    }
+    size_t need = 0;
+    vr_volume_bounds_bytes(vol, &need);
+    if (reinterpret_cast<uintptr_t>(buf) % 16 != 0)
+        return fail(VR_ERR_ARG, "bounds buffer must be 16-byte aligned");
+    if (bytes < need) return fail(VR_ERR_OOM, "bounds buffer has %zu bytes, %zu needed", bytes, need);
+    if (!is_device_ptr(buf)) return fail(VR_ERR_ARG, "bounds buffer is not device memory");
+    v->bound = static_cast<float*>(buf);
+    v->bnx = macro_count(v->g.nx);
+    v->bny = macro_count(v->g.ny);
+    v->bnz = macro_count(v->g.nz);
+    cudaError_t e = vr::launch_bounds(*v, 0, v->bnz, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        v->bound = nullptr;
+        return cuda_fail(e, "bounds launch");
+    }
     return VR_OK;
 }
 

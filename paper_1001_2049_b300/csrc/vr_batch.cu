@@ -93,8 +93,9 @@ __device__ __forceinline__ void cell_rt(const BatchTex& T, int z, float x, float
                                         float4& c1)
 {
     if (T.format >= kF16Pair) {
-        const int g = T.n_groups > 1 ? min(z / kMaxLayers, T.n_groups - 1) : 0;
-        const uint4 p = ray::gather_u32(T.tex[g], z - g * kMaxLayers, x, y);
+        const int sub = z & ((1 << T.stack_shift) - 1);
+        const uint4 p = ray::gather_u32(T.tex[0], z >> T.stack_shift, x,
+                                        y + (float)(sub * T.stack_pitch + 1));
         if (T.format == kF16Pair) {
             c0 = make_float4(ray::half_bits(p.x), ray::half_bits(p.y), ray::half_bits(p.z),
                              ray::half_bits(p.w));
@@ -186,10 +187,59 @@ __device__ __forceinline__ int march_bricks_rt(const BatchReq& P, const float4* 
     return k;
 }
 
-// TEX: every request of the launch has texture storage (true) or none has
-// (false); the host groups requests by storage so that each launch compiles
-// only one fetch path.
-template <bool TEX>
+// Texture path, specialised: the march of the single-view texture kernel for
+// one texel format, mode and group count (template parameters), so a block
+// renders its tile with exactly the code the per-view kernel runs.
+template <int DT, int MODE, bool MULTI>
+__device__ __forceinline__ unsigned tex_pixel(const BatchReq& q, const BatchTex& T,
+                                              const float4* __restrict__ lut, int px, int py)
+{
+    const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
+    ray::Acc<MODE> acc;
+    const int k = ray::march_tex<DT, MODE, MULTI>(q, T, lut, r, acc);
+    const size_t pix = (size_t)py * q.w + px;
+    if (MODE == VR_COMPOSITE)
+        reinterpret_cast<float4*>(q.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);
+    else
+        q.out[pix] = acc.m;
+    return (unsigned)k;
+}
+
+// Kind of a textured request: (texel format, mode, more than one group).
+__host__ __device__ constexpr int tex_kind(int format, int mode, bool multi)
+{
+    return (format * 3 + mode) * 2 + (multi ? 1 : 0);
+}
+
+// One switch over the kinds (uniform over the block: a tile belongs to one
+// request); each case is the specialised march of one texel format and mode
+// for a volume held in one layered texture.  (Volumes whose plain-format
+// texture spans several layer groups go to their own launch with the
+// run-time dispatched march: specialising them here as well makes the
+// compiler merge the cases' code and spill.)
+__device__ __forceinline__ unsigned tex_pixel_any(const BatchReq& q, const BatchTex& T,
+                                                  const float4* __restrict__ lut, int px, int py)
+{
+    switch (tex_kind(T.format, q.mode, T.n_groups > 1)) {
+#define VR_KIND(F, M) \
+    case tex_kind(F, M, false): return tex_pixel<F, M, false>(q, T, lut, px, py);
+#define VR_FORMAT(F) VR_KIND(F, VR_MIP) VR_KIND(F, VR_COMPOSITE) VR_KIND(F, VR_SUM)
+        VR_FORMAT(VR_F32)
+        VR_FORMAT(VR_F16)
+        VR_FORMAT(VR_I8)
+        VR_FORMAT(kF16Pair)
+        VR_FORMAT(kI8Pair)
+#undef VR_FORMAT
+#undef VR_KIND
+    default: return 0;
+    }
+}
+
+// CLS (BatchClass): every request of the launch is of one class, so each
+// kernel instance compiles one fetch path: bricks (run-time storage type),
+// one layered texture (specialised per kind), several layer groups
+// (run-time dispatched texture march).
+template <int CLS>
 __global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(const __grid_constant__ BatchParams B,
                                                          unsigned* __restrict__ ws)
 {
@@ -221,16 +271,21 @@ __global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(co
         const int py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
         unsigned count = 0;
         if (px < q.w && py < q.h) {
-            const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
-            AccRT acc(q.mode);
-            const int k = TEX ? march_tex_rt(q, B.tex[q.tex_slot], s_lut, r, acc)
-                              : march_bricks_rt(q, s_lut, r, acc);
-            count = (unsigned)k;
-            const size_t pix = (size_t)py * q.w + px;
-            if (q.mode == VR_COMPOSITE)
-                reinterpret_cast<float4*>(q.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);
-            else
-                q.out[pix] = acc.m;
+            if constexpr (CLS == kBatchTex) {
+                count = tex_pixel_any(q, B.tex[q.tex_slot], s_lut, px, py);
+            } else {
+                const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
+                AccRT acc(q.mode);
+                count = CLS == kBatchTexGroups
+                            ? (unsigned)march_tex_rt(q, B.tex[q.tex_slot], s_lut, r, acc)
+                            : (unsigned)march_bricks_rt(q, s_lut, r, acc);
+                const size_t pix = (size_t)py * q.w + px;
+                if (q.mode == VR_COMPOSITE)
+                    reinterpret_cast<float4*>(q.out)[pix] =
+                        make_float4(acc.r, acc.g, acc.b, acc.A);
+                else
+                    q.out[pix] = acc.m;
+            }
         }
         if (q.samples) {
             const unsigned tot = __reduce_add_sync(0xffffffffu, count);
@@ -251,25 +306,30 @@ __global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(co
 
 }  // namespace
 
-cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, cudaStream_t s)
+cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, int cls, cudaStream_t s)
 {
     // the counters start at zero for every launch (stream-ordered, capturable)
     cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned) * (1 + b.n), s);
     if (e != cudaSuccess) return e;
-    if (b.n > 0 && b.req[0].tex_slot >= 0)
-        batch_kernel<true><<<grid, kThreads, 0, s>>>(b, ws);
-    else
-        batch_kernel<false><<<grid, kThreads, 0, s>>>(b, ws);
+    switch (cls) {
+    case kBatchTex: batch_kernel<kBatchTex><<<grid, kThreads, 0, s>>>(b, ws); break;
+    case kBatchTexGroups: batch_kernel<kBatchTexGroups><<<grid, kThreads, 0, s>>>(b, ws); break;
+    default: batch_kernel<kBatchBricks><<<grid, kThreads, 0, s>>>(b, ws); break;
+    }
     return cudaGetLastError();
 }
 
-int batch_blocks_per_sm(bool tex)
+int batch_blocks_per_sm(int cls)
 {
     int n = 0;
-    cudaError_t e = tex ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<true>,
-                                                                        kThreads, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<false>,
-                                                                        kThreads, 0);
+    cudaError_t e =
+        cls == kBatchTex
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<kBatchTex>, kThreads, 0)
+        : cls == kBatchTexGroups
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<kBatchTexGroups>,
+                                                            kThreads, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<kBatchBricks>,
+                                                            kThreads, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;

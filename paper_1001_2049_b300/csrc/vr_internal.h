@@ -24,6 +24,11 @@ constexpr int kMaxTexGroups = 8;                  // layered textures per volume
 // int8 codes in 16 bits), so one gather returns all eight corners of a cell.
 constexpr int kF16Pair = 3;
 constexpr int kI8Pair = 4;
+// Empty-space bounds: one float per macrocell of kMacro^3 cells (cells
+// [4m, 4m + 3] per axis, i.e. voxels [4m, 4m + 4]), an upper bound on every
+// trilinear value the kernels can compute inside it.
+constexpr int kMacroShift = 2;
+constexpr int kMacro = 1 << kMacroShift;
 
 // Geometry of a bricked volume, as the kernels see it.
 struct VolumeGeom {
@@ -52,13 +57,19 @@ struct Volume {
     int tex_format;         // VR_F32 / VR_F16 / VR_I8, or kF16Pair / kI8Pair
     cudaArray_t arrays[kMaxTexGroups];
     cudaTextureObject_t tex[kMaxTexGroups];
+    int stack_shift;        // pair formats: 2^shift cell planes stacked per layer
+    int stack_pitch;        // rows per stacked cell plane (ny + 2)
     int cfg[3];             // texture-kernel launch shape per mode (autotuned)
+    // optional empty-space bounds (caller-owned device buffer)
+    float* bound;
+    int bnx, bny, bnz;      // macrocells per axis
 };
 
 // Texture storage as the texture kernels see it.
 struct TexParams {
     cudaTextureObject_t tex[kMaxTexGroups];
     int n_groups;
+    int stack_shift, stack_pitch;   // pair formats (see Volume)
     const float* scale;     // VR_I8 only
     const float* offset;
     int k_max;
@@ -82,6 +93,8 @@ struct MarchParams {
     int n_lut;
     float* out;             // first view of this launch
     unsigned long long* samples;   // may be null
+    const float* bound;     // empty-space bounds, or null (no skipping)
+    int bnx, bny;
     vr_camera cams[kMaxViewsPerLaunch];
     float4 lut[VR_MAX_LUT];
 };
@@ -97,6 +110,7 @@ constexpr int kBatchWords = 1 + kMaxBatch;
 struct BatchTex {
     cudaTextureObject_t tex[kMaxTexGroups];
     int n_groups;
+    int stack_shift, stack_pitch;   // pair formats (see Volume)
     int format;            // texel format (see kF16Pair)
     const float* scale;
     const float* offset;
@@ -112,6 +126,8 @@ struct BatchReq {
     const float* offset;
     unsigned long long* samples;
     unsigned* done;
+    const float* bound;    // empty-space bounds, or null
+    int bnx, bny;
     VolumeGeom g;
     float hix, hiy, hiz, step;
     float clip, term_alpha, v_lo, lut_scale, lut_max;
@@ -129,8 +145,13 @@ struct BatchParams {
     float4 lut[kMaxBatchLut][VR_MAX_LUT];
 };
 
-cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, cudaStream_t s);
-int batch_blocks_per_sm(bool tex);
+// Launch classes of the batched kernel: requests on volumes without texture
+// storage, on volumes held in one layered texture, and on volumes whose
+// texture spans several layer groups (plain formats with more than 2049
+// planes), each compiled as its own kernel.
+enum BatchClass { kBatchBricks = 0, kBatchTex = 1, kBatchTexGroups = 2 };
+cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, int cls, cudaStream_t s);
+int batch_blocks_per_sm(int cls);
 int batch_with_counters(const vr_request* reqs, int n, unsigned* counters, cudaStream_t s);
 int record_error(int code, const char* msg);
 
@@ -156,6 +177,19 @@ size_t slab_window_elems(const SlabConfig& c);
 bool plan_slab(const MarchParams& p, SlabConfig* c);
 cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int format, int mode, int cfg,
                        cudaStream_t s);
+// One texel format each (vr_tex_<format>.cu).
+cudaError_t launch_tex_f32(const MarchParams& p, const TexParams& t, int mode, int cfg,
+                           cudaStream_t s);
+cudaError_t launch_tex_f16(const MarchParams& p, const TexParams& t, int mode, int cfg,
+                           cudaStream_t s);
+cudaError_t launch_tex_i8(const MarchParams& p, const TexParams& t, int mode, int cfg,
+                          cudaStream_t s);
+cudaError_t launch_tex_f16pair(const MarchParams& p, const TexParams& t, int mode, int cfg,
+                               cudaStream_t s);
+cudaError_t launch_tex_i8pair(const MarchParams& p, const TexParams& t, int mode, int cfg,
+                              cudaStream_t s);
+// Empty-space bounds of macrocell planes [mz0, mz1) from the bricks.
+cudaError_t launch_bounds(const Volume& v, int mz0, int mz1, cudaStream_t s);
 int tex_shape_count();
 void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb);
 cudaError_t fill_texture_group(const Volume& v, cudaSurfaceObject_t surf, int layer0, int z0,

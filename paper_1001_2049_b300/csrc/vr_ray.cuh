@@ -148,6 +148,31 @@ __device__ __forceinline__ float code_hi(unsigned b)
     return (float)(signed char)((b >> 8) & 0xffu);
 }
 
+// Texture handles of a volume's layer groups, per block in shared memory:
+// a kernel that marches a volume with several groups fills this table
+// (fill_group_table) before the march.  Reading a handle by the run-time
+// group index from shared memory keeps the handles out of registers and
+// out of local memory.
+__device__ __forceinline__ cudaTextureObject_t* group_table()
+{
+    __shared__ cudaTextureObject_t s_group_tex[kMaxTexGroups];
+    return s_group_tex;
+}
+
+// Called by every thread of the block; ends with a barrier.
+template <typename TT>
+__device__ __forceinline__ void fill_group_table(const TT& T)
+{
+    if (threadIdx.x < kMaxTexGroups) group_table()[threadIdx.x] = T.tex[threadIdx.x];
+    __syncthreads();
+}
+
+template <typename TT>
+__device__ __forceinline__ cudaTextureObject_t group_tex(const TT&, int g)
+{
+    return group_table()[g];
+}
+
 // The two planes z and z + 1 of the cell whose x/y corner is texel (x-1, y-1).
 // Pair formats: one gather of layer z (cell plane) holds both planes.
 template <int DT, bool MULTI, typename TT>
@@ -155,8 +180,11 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
                                      float y, float4& q0, float4& q1)
 {
     if constexpr (DT == kF16Pair || DT == kI8Pair) {
-        const int g = MULTI ? min(z / kMaxLayers, T.n_groups - 1) : 0;
-        const uint4 p = gather_u32(MULTI ? T.tex[g] : t0, z - g * kMaxLayers, x, y);
+        // one texture; cell plane z is sub-plane z & (2^shift - 1) of layer
+        // z >> shift, whose data rows start at row sub * pitch + 1
+        const int sub = z & ((1 << T.stack_shift) - 1);
+        const uint4 p = gather_u32(t0, z >> T.stack_shift, x,
+                                   y + (float)(sub * T.stack_pitch + 1));
         if constexpr (DT == kF16Pair) {
             q0 = make_float4(half_bits(p.x), half_bits(p.y), half_bits(p.z), half_bits(p.w));
             q1 = make_float4(half_bits(p.x >> 16), half_bits(p.y >> 16), half_bits(p.z >> 16),
@@ -176,7 +204,7 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
         } else {
             // plane pair (z, z + 1) lies in group min(z / (L-1), last)
             const int g = min(z / (kMaxLayers - 1), T.n_groups - 1);
-            const cudaTextureObject_t t = T.tex[g];
+            const cudaTextureObject_t t = group_tex(T, g);
             const int l = z - g * (kMaxLayers - 1);
             q0 = gather<DT>(t, l, x, y);
             q1 = gather<DT>(t, l + 1, x, y);
@@ -288,7 +316,138 @@ struct Acc {
         A += wgt;
         return A >= P.term_alpha;
     }
+
+    // True when no sample whose value is at most `bound` can change the
+    // result: below the clip it is transparent (composite); not above the
+    // running maximum it leaves the maximum as it is (MIP).  SUM never skips.
+    template <typename PP>
+    __device__ __forceinline__ bool skippable(const PP& P, float bound) const
+    {
+        if (MODE == VR_MIP) return bound <= m;
+        if (MODE == VR_COMPOSITE) return bound < P.clip;
+        return false;
+    }
 };
+
+// ---- empty-space skipping ----
+// A sample's macrocell is that of its cell clamped to the box (positions a
+// rounding error outside a face read the edge voxels, which the edge
+// macrocell covers).  Every coordinate of the computed sample position
+// fma(fma(k, step, t_entry), d, o) is a monotone function of k (each
+// rounding is monotone), so the samples of one macrocell form one contiguous
+// range of k: if the first and the last sample of a range lie in it, all do.
+struct Macro {
+    int x, y, z;
+    size_t i;
+};
+
+template <typename PP>
+__device__ __forceinline__ Macro macro_of(const PP& P, const Geo& g)
+{
+    Macro m;
+    m.x = min(max((int)g.gx - 1, 0), P.g.nx - 2) >> kMacroShift;
+    m.y = min(max((int)g.gy - 1, 0), P.g.ny - 2) >> kMacroShift;
+    m.z = g.iz >> kMacroShift;
+    m.i = ((size_t)m.z * P.bny + m.y) * P.bnx + m.x;
+    return m;
+}
+
+// First sample index after the samples of macrocell `m`, starting from
+// sample k (which lies in m).  The exit is estimated from the ray's
+// crossing of the macrocell's faces (the first and last macrocell of an
+// axis extend to infinity) and accepted only when the sample before it is
+// checked to lie in m; after two rejected estimates only sample k is
+// passed over.  Never returns more than K or less than k + 1.
+template <typename PP>
+__device__ __forceinline__ int macro_exit(const PP& P, const Ray& r, const Macro& m, int k)
+{
+    float tout = INFINITY;
+    if (r.dx > 0.0f && m.x < P.bnx - 1)
+        tout = fminf(tout, __fdividef((float)((m.x + 1) << kMacroShift) - r.ox, r.dx));
+    else if (r.dx < 0.0f && m.x > 0)
+        tout = fminf(tout, __fdividef((float)(m.x << kMacroShift) - r.ox, r.dx));
+    if (r.dy > 0.0f && m.y < P.bny - 1)
+        tout = fminf(tout, __fdividef((float)((m.y + 1) << kMacroShift) - r.oy, r.dy));
+    else if (r.dy < 0.0f && m.y > 0)
+        tout = fminf(tout, __fdividef((float)(m.y << kMacroShift) - r.oy, r.dy));
+    const int bnz = ((P.g.nz - 2) >> kMacroShift) + 1;
+    if (r.dz > 0.0f && m.z < bnz - 1)
+        tout = fminf(tout, __fdividef((float)((m.z + 1) << kMacroShift) - r.oz, r.dz));
+    else if (r.dz < 0.0f && m.z > 0)
+        tout = fminf(tout, __fdividef((float)(m.z << kMacroShift) - r.oz, r.dz));
+    const float q = ceilf(__fdividef(tout - r.te, P.step));
+    int kc = (q < (float)r.K) ? (int)fmaxf(q, 0.0f) : r.K;
+    kc = max(kc, k + 1);
+#pragma unroll 1
+    for (int tries = 0; kc - 1 > k; ++tries) {
+        if (tries == 2) return k + 1;
+        if (macro_of(P, geo(P, r, (float)(kc - 1))).i == m.i) return kc;
+        --kc;
+    }
+    return kc;
+}
+
+// march_tex with empty-space skipping: runs of samples in macrocells whose
+// bound makes them skippable are passed over in one step each; the other
+// samples are marched as in march_tex (gathers one sample ahead, two
+// register sets).  The result is identical to march_tex's: every skipped
+// sample is one march_tex would have left without effect.  Returns the
+// number of samples up to termination, skipped ones included.
+template <int DT, int MODE, bool MULTI, typename PP, typename TT>
+__device__ __forceinline__ int march_tex_skip(const PP& P, const TT& T,
+                                              const float4* __restrict__ lut, const Ray& r,
+                                              Acc<MODE>& acc)
+{
+    if (r.K <= 0) return 0;
+    const cudaTextureObject_t t0 = T.tex[0];
+    int k = 0;
+    Geo ga = geo(P, r, 0.0f), gb;
+    Macro ma = macro_of(P, ga);
+    float bnd = __ldg(P.bound + ma.i);
+    float4 a0, a1, b0, b1;
+    for (;;) {
+        while (acc.skippable(P, bnd)) {
+            k = macro_exit(P, r, ma, k);
+            if (k >= r.K) return k;
+            ga = geo(P, r, (float)k);
+            ma = macro_of(P, ga);
+            bnd = __ldg(P.bound + ma.i);
+        }
+        cell<DT, MULTI>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
+        float kf = (float)(k + 1);
+        for (;;) {
+            gb = geo(P, r, kf);
+            next_cell<DT, MULTI>(T, t0, ga, a0, a1, gb, b0, b1);
+            Macro mn = macro_of(P, gb);
+            const bool moved = mn.i != ma.i;
+            const float nb = moved ? __ldg(P.bound + mn.i) : bnd;
+            ++k;
+            if (acc.add(P, lut, interp(a0, a1, ga)) || k >= r.K) return k;
+            kf += 1.0f;
+            if (moved) {
+                ma = mn;
+                bnd = nb;
+                if (acc.skippable(P, bnd)) {
+                    ga = gb;
+                    break;
+                }
+            }
+            ga = geo(P, r, kf);
+            next_cell<DT, MULTI>(T, t0, gb, b0, b1, ga, a0, a1);
+            mn = macro_of(P, ga);
+            const bool moved2 = mn.i != ma.i;
+            const float nb2 = moved2 ? __ldg(P.bound + mn.i) : bnd;
+            ++k;
+            if (acc.add(P, lut, interp(b0, b1, gb)) || k >= r.K) return k;
+            kf += 1.0f;
+            if (moved2) {
+                ma = mn;
+                bnd = nb2;
+                if (acc.skippable(P, bnd)) break;
+            }
+        }
+    }
+}
 
 // The gathers of sample k + 1 are issued before sample k is interpolated, so
 // the texture latency overlaps the arithmetic of the current sample.  The

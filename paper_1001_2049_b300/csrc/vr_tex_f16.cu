@@ -1,0 +1,13 @@
+// vr_tex_f16.cu -- the texture-gather march instantiated for one texel
+// format (see vr_tex_kernel.cuh).
+#include "vr_tex_kernel.cuh"
+
+namespace vr {
+
+cudaError_t launch_tex_f16(const MarchParams& p, const TexParams& t, int mode, int cfg,
+                           cudaStream_t s)
+{
+    return tex::launch_dt<VR_F16>(p, t, mode, cfg, s);
+}
+
+}  // namespace vr

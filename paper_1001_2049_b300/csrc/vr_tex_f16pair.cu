@@ -1,0 +1,13 @@
+// vr_tex_f16pair.cu -- the texture-gather march instantiated for one texel
+// format (see vr_tex_kernel.cuh).
+#include "vr_tex_kernel.cuh"
+
+namespace vr {
+
+cudaError_t launch_tex_f16pair(const MarchParams& p, const TexParams& t, int mode, int cfg,
+                               cudaStream_t s)
+{
+    return tex::launch_dt<kF16Pair>(p, t, mode, cfg, s);
+}
+
+}  // namespace vr

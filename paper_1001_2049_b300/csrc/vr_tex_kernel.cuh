@@ -1,0 +1,126 @@
+// vr_tex_kernel.cuh -- the texture-gather ray-march kernel template and its
+// launchers.  Instantiated once per texel format (vr_tex_<format>.cu) so the
+// formats compile in parallel; vr_tex.cu dispatches between them.
+//
+// Same rendering as vr_march.cu (paper §3.1 process item 3; definition in
+// include/vr.h).  The difference is where the eight corners of a cell come
+// from: the cube is also held as layered 2-D textures (one layer per
+// frequency plane z, block-linear in x and y), and one `tld4` (four-texel
+// gather) returns the 2 x 2 corners of a cell in one plane.  A sample needs
+// at most two gathers (planes z0 and z0 + 1) and no address arithmetic; the
+// texture unit's 2-D tiling keeps the neighbouring rays of a warp on few
+// cache lines whichever way the rays run.  The gathers return the stored
+// texels unfiltered, so the interpolation (x, then y, then z, FP32) is the
+// kernel's own and the results are those of the definition.
+//
+// The gathers of the next sample are issued before the current sample is
+// interpolated, which hides the texture latency behind the arithmetic.
+// With empty-space bounds attached (SKIP), runs of samples in macrocells
+// that cannot change the result are passed over (vr_ray.cuh).
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "vr_internal.h"
+#include "vr_ray.cuh"
+
+namespace vr {
+namespace tex {
+
+// Launch shapes the autotuner chooses from: a block of BX x BY rays (one
+// thread each), warps holding PX x PY packets of neighbouring rays, and the
+// minimum number of resident blocks per SM the register budget must allow.
+struct Shape {
+    int bx, by, px, py, minb;
+};
+constexpr Shape kShapes[] = {
+    {16, 16, 8, 4, 1}, {16, 16, 8, 4, 6}, {32, 8, 8, 4, 5}, {16, 16, 16, 2, 5},
+    {16, 16, 4, 8, 5}, {8, 8, 8, 4, 16},
+};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <int DT, int MODE, bool MULTI, int CFG, bool SKIP>
+__global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG].minb)
+    tex_kernel(const __grid_constant__ MarchParams P, const __grid_constant__ TexParams T)
+{
+    constexpr Shape S = kShapes[CFG];
+    __shared__ float4 s_lut[VR_MAX_LUT];
+    if (MODE == VR_COMPOSITE) {
+        for (int i = threadIdx.x; i < P.n_lut; i += blockDim.x) s_lut[i] = P.lut[i];
+        __syncthreads();
+    }
+    if (MULTI) ray::fill_group_table(T);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int wpr = S.bx / S.px;                 // warps per block row
+    const int px = blockIdx.x * S.bx + (warp % wpr) * S.px + (lane % S.px);
+    const int py = blockIdx.y * S.by + (warp / wpr) * S.py + (lane / S.px);
+    const int view = blockIdx.z;
+    const bool valid = px < P.w && py < P.h;
+    unsigned count = 0;
+    if (valid) {
+        const ray::Ray r = ray::setup_ray(P, P.cams[view], px, py, T.k_max);
+        ray::Acc<MODE> acc;
+        if constexpr (SKIP)
+            count = (unsigned)ray::march_tex_skip<DT, MODE, MULTI>(P, T, s_lut, r, acc);
+        else
+            count = (unsigned)ray::march_tex<DT, MODE, MULTI>(P, T, s_lut, r, acc);
+        const size_t pix = ((size_t)view * P.h + py) * P.w + px;
+        if (MODE == VR_COMPOSITE)
+            reinterpret_cast<float4*>(P.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);
+        else
+            P.out[pix] = acc.m;
+    }
+    if (P.samples) {
+        const unsigned tot = __reduce_add_sync(0xffffffffu, count);
+        if (lane == 0 && tot) atomicAdd(P.samples, (unsigned long long)tot);
+    }
+}
+
+template <int DT, int MODE, bool MULTI, int CFG>
+cudaError_t launch_c(const MarchParams& p, const TexParams& t, cudaStream_t s)
+{
+    constexpr bool kCanSkip = MODE != VR_SUM;
+    constexpr Shape S = kShapes[CFG];
+    dim3 grid((unsigned)((p.w + S.bx - 1) / S.bx), (unsigned)((p.h + S.by - 1) / S.by),
+              (unsigned)p.n_views);
+    if (kCanSkip && p.bound)
+        tex_kernel<DT, MODE, MULTI, CFG, kCanSkip><<<grid, S.bx * S.by, 0, s>>>(p, t);
+    else
+        tex_kernel<DT, MODE, MULTI, CFG, false><<<grid, S.bx * S.by, 0, s>>>(p, t);
+    return cudaGetLastError();
+}
+
+template <int DT, int MODE, bool MULTI>
+cudaError_t launch_m(const MarchParams& p, const TexParams& t, int cfg, cudaStream_t s)
+{
+    switch (cfg) {
+    case 1: return launch_c<DT, MODE, MULTI, 1>(p, t, s);
+    case 2: return launch_c<DT, MODE, MULTI, 2>(p, t, s);
+    case 3: return launch_c<DT, MODE, MULTI, 3>(p, t, s);
+    case 4: return launch_c<DT, MODE, MULTI, 4>(p, t, s);
+    case 5: return launch_c<DT, MODE, MULTI, 5>(p, t, s);
+    default: return launch_c<DT, MODE, MULTI, 0>(p, t, s);
+    }
+}
+static_assert(kNumShapes == 6, "launch_m lists every shape");
+
+template <int DT, int MODE>
+cudaError_t launch_t(const MarchParams& p, const TexParams& t, int cfg, cudaStream_t s)
+{
+    return t.n_groups > 1 ? launch_m<DT, MODE, true>(p, t, cfg, s)
+                          : launch_m<DT, MODE, false>(p, t, cfg, s);
+}
+
+template <int DT>
+cudaError_t launch_dt(const MarchParams& p, const TexParams& t, int mode, int cfg,
+                      cudaStream_t s)
+{
+    switch (mode) {
+    case VR_MIP: return launch_t<DT, VR_MIP>(p, t, cfg, s);
+    case VR_COMPOSITE: return launch_t<DT, VR_COMPOSITE>(p, t, cfg, s);
+    default: return launch_t<DT, VR_SUM>(p, t, cfg, s);
+    }
+}
+
+}  // namespace tex
+}  // namespace vr

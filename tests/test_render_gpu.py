@@ -32,12 +32,14 @@ def oracle_volume(cube: np.ndarray, dtype: str) -> oracle.Volume:
 
 
 def gpu_images(cube_t, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, count=None,
-               tex=False):
+               tex=False, bounds=False):
     vol = Volume(cube_t.cuda(), dtype)
     if tex == "pair":
         vol.attach_pair_texture()
     elif tex:
         vol.attach_texture()
+    if bounds:
+        vol.attach_bounds()
     vol.set_transfer(lut, v_lo, v_hi, clip, ta)
     out = vol.render(cams, w, h, mode, step, count=count)
     torch.cuda.synchronize()
@@ -54,12 +56,13 @@ def scale_for(mode, cube, got):
 
 
 def run_parity(cube, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, tol=TOL_FP32,
-               reference="decoded", pixels=None, what="", tex=False):
-    """Render on the GPU (bricks, or texture storage with tex=True) and compare
-    with the oracle (on the decoded storage values, or on the float32 source
-    with reference="source")."""
+               reference="decoded", pixels=None, what="", tex=False, bounds=False):
+    """Render on the GPU (bricks, or texture storage with tex=True, with the
+    empty-space bounds grid with bounds=True) and compare with the oracle (on
+    the decoded storage values, or on the float32 source with
+    reference="source")."""
     got = gpu_images(torch.from_numpy(cube), dtype, cams, w, h, mode, step, lut, v_lo, v_hi,
-                     clip, ta, tex=tex)
+                     clip, ta, tex=tex, bounds=bounds)
     ovol = oracle_volume(cube, dtype if reference == "decoded" else "f32")
     tf = oracle.TF(lut, v_lo, v_hi, clip, ta)
     nz, ny, nx = cube.shape
@@ -455,6 +458,124 @@ def test_brick_buffer_too_small_is_rejected():
 
 
 # ---------------------------------------------------------------------------
+# empty-space bounds: every entry bounds its macrocell's values, and renders
+# with the grid are identical to renders without it
+# ---------------------------------------------------------------------------
+def _decoded(cube, dtype):
+    """Storage values as the kernels decode them (float32)."""
+    if dtype == "f32":
+        return cube.astype(np.float32)
+    if dtype == "f16":
+        return quantize.to_f16(cube).astype(np.float32)
+    q, sc, of = quantize.quantize_i8(cube)
+    return (q.astype(np.float64) * sc.astype(np.float64)[:, None, None]
+            + of.astype(np.float64)[:, None, None]).astype(np.float32)
+
+
+def _macro_reduce(a, fn, fill):
+    """fn over voxels [4m, 4m + 4] of every macrocell (a is (nz, ny, nx))."""
+    for axis in range(3):
+        n = a.shape[axis]
+        bn = ((n - 2) >> 2) + 1
+        pad = [(0, 0)] * 3
+        pad[axis] = (0, 4 * bn + 1 - n)
+        a = np.pad(a, pad, constant_values=fill)
+        a = fn.reduce([np.take(a, np.arange(j, j + 4 * bn, 4), axis=axis) for j in range(5)])
+    return a
+
+
+BOUND_DIMS = [(37, 45, 70), (2, 2, 2), (6, 5, 9), (64, 3, 33)]
+
+
+@pytest.mark.parametrize("dims", BOUND_DIMS)
+@pytest.mark.parametrize("dtype", ["f32", "f16", "i8"])
+def test_bounds_grid_bounds_every_macrocell(dims, dtype):
+    cube = synth.make_cube(dims, 3, ("uniform", 3.0, 8.0), 40 + dims[0]).numpy()
+    vol = Volume(torch.from_numpy(cube).cuda(), dtype)
+    vol.attach_bounds()
+    torch.cuda.synchronize()
+    dec = _decoded(cube, dtype).astype(np.float64)
+    hi = _macro_reduce(dec, np.maximum, -np.inf)
+    mag = _macro_reduce(np.abs(dec), np.maximum, 0.0)
+    got = vol._bounds.cpu().numpy().astype(np.float64)[:hi.size].reshape(hi.shape)
+    assert vol.bounds_bytes() == 4 * hi.size
+    # above every value by more than any interpolation rounding (< 10 u |v|),
+    # and not by more than the stated margin
+    assert (got >= hi + 2.0 ** -21 * mag).all()
+    assert (got <= hi + 2.0 ** -18 * mag).all()
+
+
+def _skip_cases(dims, seed):
+    cube = synth.make_cube(dims, 3, ("uniform", 3.0, 8.0), seed).numpy()
+    cams = synth.random_sphere_cameras(dims, 4, 29, 19, seed, fov_deg=70.0)
+    c = np.array([(d - 1) / 2.0 for d in dims])
+    recs = [synth.look_at_camera(c + 0.3, c + np.array([5.0, -3.0, 2.0]), 29, 19, 90.0)]
+    recs += [synth.axis_camera(dims, 29, 19, axis=a, sign=sg) for a in range(3) for sg in (1, -1)]
+    cams = np.concatenate([cams, synth.cameras(recs).astype(cams.dtype)])
+    return cube, cams
+
+
+@pytest.mark.parametrize("dims", BOUND_DIMS)
+@pytest.mark.parametrize("store", ["f32", "f16", "i8", "f16-pair", "i8-pair"])
+def test_bounds_leave_images_and_counts_unchanged(dims, store):
+    dtype, _, pair = store.partition("-")
+    cube, cams = _skip_cases(dims, 50 + dims[1])
+    vol = Volume(torch.from_numpy(cube).cuda(), dtype)
+    if pair:
+        vol.attach_pair_texture()
+    else:
+        vol.attach_texture()
+    lut = synth.default_lut(64)
+    for clip in (-10.0, 1.0, 3.0, 100.0):       # nothing, some, most, everything skippable
+        vol.set_transfer(lut, min(clip, 7.0), 8.0, clip, 0.95)
+        for mode in ("composite", "mip"):
+            outs = []
+            for b in (False, True):
+                if b:
+                    vol.attach_bounds()
+                n = torch.zeros(1, dtype=torch.int64, device="cuda")
+                img = vol.render(cams, 29, 19, mode, 0.37, count=n)
+                torch.cuda.synchronize()
+                outs.append((img.cpu(), int(n.item())))
+                vol.detach_bounds()
+            assert torch.equal(outs[0][0], outs[1][0]), (store, dims, clip, mode)
+            assert outs[0][1] == outs[1][1], (store, dims, clip, mode)
+
+
+def test_bounds_skip_almost_everything_on_a_sparse_cube():
+    # one bright voxel in an empty cube: composite skips every macrocell but
+    # the few around it; MIP skips once the running maximum reaches 0
+    dims = (40, 36, 50)
+    cube = np.zeros((50, 36, 40), dtype=np.float32)
+    cube[21, 17, 13] = 9.0
+    cams = synth.random_sphere_cameras(dims, 6, 31, 31, 7, fov_deg=40.0)
+    recs = [synth.axis_camera(dims, 40, 36, axis=2, sign=1)]
+    cams = np.concatenate([cams, synth.cameras(recs).astype(cams.dtype)])
+    lut = synth.default_lut(32)
+    for mode in ("composite", "mip"):
+        run_parity(cube, "f32", cams, 31, 31, mode, 0.5, lut, 0.5, 9.0, 0.5, 1.0,
+                   what="sparse bounds " + mode, tex=True, bounds=True)
+
+
+@pytest.mark.parametrize("tex", [True, "pair"], ids=["texture", "pair"])
+@pytest.mark.parametrize("mode", ["mip", "composite"])
+def test_bounds_small_workload(small, tex, mode):
+    wl, cube, lut, cams = small
+    dtype = "f32" if tex is True else "f16"
+    run_parity(cube, dtype, cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+               wl.term_alpha, what="small bounds %s %s" % (dtype, mode), tex=tex, bounds=True)
+
+
+@pytest.mark.parametrize("dims,step", RAGGED)
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_bounds_ragged_cubes(dims, step, dtype):
+    cube, cams, lut = ragged_case(dims, 17 + dims[0])
+    for mode in ("mip", "composite"):
+        run_parity(cube, dtype, cams, 23, 17, mode, step, lut, 1.0, 8.0, 3.0, 0.95,
+                   what="bounds ragged %s %s %s" % (dims, dtype, mode), tex=True, bounds=True)
+
+
+# ---------------------------------------------------------------------------
 # the 1024^3 workload at full size, in the benchmark's launch configuration
 # (32 orbiting 1920x1080 views in one call), checked on sampled pixels
 # ---------------------------------------------------------------------------
@@ -490,7 +611,19 @@ def test_large_workload_sampled_pixels(large, dtype, tex):
     bands = bands_for(wl.dims, cams, wl.step)
     reports = {}
     for mode in ("composite", "mip"):
-        img = vol.render(cams, w, h, mode, wl.step)
+        n0 = torch.zeros(1, dtype=torch.int64, device="cuda")
+        img = vol.render(cams, w, h, mode, wl.step, count=n0)
+        if tex:
+            # with the empty-space bounds (the benchmark's configuration) the
+            # images and the sample counts are the same, bit for bit
+            vol.attach_bounds()
+            n1 = torch.zeros(1, dtype=torch.int64, device="cuda")
+            img1 = vol.render(cams, w, h, mode, wl.step, count=n1)
+            vol.detach_bounds()
+            torch.cuda.synchronize()
+            assert torch.equal(img, img1), "large %s %s: bounds change the image" % (dtype, mode)
+            assert int(n0.item()) == int(n1.item())
+            img = img1
         torch.cuda.synchronize()
         got = img.cpu().numpy()
         ch = 4 if mode == "composite" else 1
