@@ -356,8 +356,8 @@ def main():
                     help="profiling captures only: smaller cube, same framing")
     ap.add_argument("--views", type=int, default=32)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
-    ap.add_argument("--bounds", action="store_true",
-                    help="render with the empty-space bounds grid")
+    ap.add_argument("--no-masks", action="store_true",
+                    help="composite without the empty-space masks")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and served legs")
     ap.add_argument("--storage", default="texture", choices=["texture", "bricks"],
@@ -384,8 +384,8 @@ def main():
     vol = Volume(cube, "f32")
     if args.storage == "texture":
         vol.attach_texture()
-        if args.bounds:
-            vol.attach_bounds()
+        if not args.no_masks:
+            vol.attach_masks()
     vol.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
     comp = torch.empty((n_views, H, W, 4), dtype=torch.float32, device=dev)
     mip = torch.empty((n_views, H, W), dtype=torch.float32, device=dev)
@@ -442,13 +442,13 @@ def main():
     comp_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     mip_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
 
-    # context only (outside the timed region): the same launches without the
-    # empty-space bounds
-    no_bounds = None
-    if args.storage == "texture" and args.bounds:
-        vol.detach_bounds()
+    # context only (outside the timed region): the composite launch without
+    # the empty-space masks
+    no_masks = None
+    if args.storage == "texture" and not args.no_masks:
+        vol.detach_masks()
         nb = []
-        for mode, out in (("composite", comp), ("mip", mip)):
+        for mode, out in (("composite", comp),):
             vol.render(cams, W, H, mode, wl.step, out=out)
             e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             e[0].record(stream)
@@ -456,8 +456,8 @@ def main():
             e[1].record(stream)
             torch.cuda.synchronize()
             nb.append(e[0].elapsed_time(e[1]))
-        no_bounds = {"composite_ms_per_launch": nb[0], "mip_ms_per_launch": nb[1]}
-        vol.attach_bounds()
+        no_masks = {"composite_ms_per_launch": nb[0]}
+        vol.attach_masks()
 
     # end to end through the public API: cameras in, images back to pinned host
     host_comp = torch.empty(comp.shape, dtype=torch.float32, pin_memory=True)
@@ -522,8 +522,8 @@ def main():
                 "samples_per_step": samples_step, "samples_composite": samples_comp,
                 "samples_mip": samples_mip, "composite_ms_per_launch": comp_ms,
                 "mip_ms_per_launch": mip_ms, "parallelism": "replica per GPU (views)",
-                "empty_space_bounds": args.storage == "texture" and args.bounds,
-                "without_bounds": no_bounds,
+                "empty_space_masks": args.storage == "texture" and not args.no_masks,
+                "without_masks": no_masks,
                 "autotuned": tuned,
                 "l2": "inputs larger than L2 (4 GiB cube per view pass)"},
             "roofline": {"bound": "hbm", "kernel": ("tex_kernel" if args.storage == "texture"
@@ -534,9 +534,9 @@ def main():
                          "algorithmic_bytes_per_launch": dom_bytes, "dominant": dom,
                          "touched_voxels_per_view": touched},
             "cpu_baseline": cpu,
-            "e2e": {"value": samples_step / e2e_s * world, "unit": "samples/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": 1000.0 * e2e_s},
+            "e2e": ({"value": samples_step / e2e_s * world, "unit": "samples/s",
+                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                     "ms_per_step": 1000.0 * e2e_s} if args.e2e_steps > 0 else None),
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
         }

@@ -165,24 +165,24 @@ int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w,
                       int h, int mode, float step, float* out,
                       unsigned long long* d_samples, void* stream);
 
-/* Bytes of the volume's empty-space bounds grid: one float per macrocell of
- * 4 x 4 x 4 cells, ((nx-2)/4 + 1) * ((ny-2)/4 + 1) * ((nz-2)/4 + 1) floats.
+/* Bytes of the volume's empty-space masks: 8 bytes per macrocell of
+ * 4 x 4 x 4 cells, (nx/4 + 1) * (ny/4 + 1) * ((nz-2)/4 + 1) macrocells.
  * Host-only; no device work.                                                */
-int vr_volume_bounds_bytes(vr_volume vol, size_t* bytes_out);
+int vr_volume_mask_bytes(vr_volume vol, size_t* bytes_out);
 
-/* Give the volume an empty-space bounds grid in the caller-owned device
- * buffer `buf` (16-byte aligned, at least vr_volume_bounds_bytes bytes;
- * owned by the caller, who keeps it alive while the volume renders), built
- * from the bricks on `stream`.  Each entry is an upper bound on every value
- * a render can interpolate in its macrocell (voxels [4m, 4m + 4] per axis).
- * Renders then pass over runs of samples that cannot change the image:
- * macrocells whose bound is below the clip (COMPOSITE: such samples are
- * transparent, §3.1 item 3 with the noise clip) or not above the ray's
- * running maximum (MIP).  Images and sample counts are identical to those
- * without the grid; only the work differs.  vr_volume_upload keeps the grid
- * current.  buf = NULL detaches it (no device work).  Used by the
- * texture-gather renders; the paper describes no such structure.           */
-int vr_volume_attach_bounds(vr_volume vol, void* buf, size_t bytes, void* stream);
+/* Give the volume empty-space masks in the caller-owned device buffer `buf`
+ * (16-byte aligned, at least vr_volume_mask_bytes bytes; the caller keeps it
+ * alive while the volume renders).  COMPOSITE renders of a texture-stored
+ * volume then skip the fetch and evaluation of samples whose cell cannot
+ * reach the clip level (such samples are transparent: §3.1 item 3 with the
+ * noise clip), with the warp's rays kept in step.  The masks depend on the
+ * clip: they are (re)built on the render's stream by the first COMPOSITE
+ * render (or autotune) after this call, a vr_set_transfer that changes the
+ * clip, or a vr_volume_upload.  Images and sample counts are identical to
+ * those without masks; only the work differs.  MIP, SUM, brick-gather and
+ * batched renders do not use them.  buf = NULL detaches.  No device work
+ * here.  The paper describes no such structure.                            */
+int vr_volume_attach_masks(vr_volume vol, void* buf, size_t bytes);
 
 /* Give the volume texture storage: a copy of the cube in layered 2-D
  * textures (one layer per frequency plane, split into groups of at most 2048

@@ -32,8 +32,8 @@ SIGNATURES = {
                                   c_void_p, c_void_p, c_void_p]),
     "vr_volume_destroy": (c_int, [c_void_p]),
     "vr_volume_attach_texture": (c_int, [c_void_p, c_void_p]),
-    "vr_volume_bounds_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
-    "vr_volume_attach_bounds": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p]),
+    "vr_volume_mask_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "vr_volume_attach_masks": (c_int, [c_void_p, c_void_p, c_size_t]),
     "vr_volume_attach_pair_texture": (c_int, [c_void_p, c_void_p]),
     "vr_volume_detach_texture": (c_int, [c_void_p]),
     "vr_volume_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int),

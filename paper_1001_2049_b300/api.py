@@ -199,25 +199,24 @@ class Volume:
     def detach_texture(self):
         check(load().vr_volume_detach_texture(self._h))
 
-    def bounds_bytes(self) -> int:
+    def mask_bytes(self) -> int:
         n = ctypes.c_size_t(0)
-        check(load().vr_volume_bounds_bytes(self._h, ctypes.byref(n)))
+        check(load().vr_volume_mask_bytes(self._h, ctypes.byref(n)))
         return int(n.value)
 
-    def attach_bounds(self, stream=None):
-        """Build the empty-space bounds grid (one float per 4^3-cell
-        macrocell, in a torch-owned device buffer kept by this object);
-        renders then pass over samples that cannot change the image."""
-        buf = torch.empty(max(1, self.bounds_bytes() // 4), dtype=torch.float32,
+    def attach_masks(self):
+        """Empty-space masks (8 bytes per 4^3-cell macrocell, in a torch-owned
+        device buffer kept by this object): composite renders then skip the
+        samples the clip makes transparent, with identical results."""
+        buf = torch.empty(max(1, self.mask_bytes() // 8), dtype=torch.int64,
                           device=self.buffer.device)
-        check(load().vr_volume_attach_bounds(self._h, buf.data_ptr(), buf.numel() * 4,
-                                             _stream_ptr(stream)))
-        self._bounds = buf
+        check(load().vr_volume_attach_masks(self._h, buf.data_ptr(), buf.numel() * 8))
+        self._masks = buf
         return buf
 
-    def detach_bounds(self):
-        check(load().vr_volume_attach_bounds(self._h, None, 0, None))
-        self._bounds = None
+    def detach_masks(self):
+        check(load().vr_volume_attach_masks(self._h, None, 0))
+        self._masks = None
 
     def set_transfer(self, lut, v_lo: float, v_hi: float, clip: float, term_alpha: float = 1.0):
         """RGBA table (n, 4) with alpha per unit voxel length over [v_lo, v_hi];

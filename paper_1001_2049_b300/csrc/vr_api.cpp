@@ -34,8 +34,13 @@ int cuda_fail(cudaError_t e, const char* what)
 int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
-// Macrocells along an axis of n voxels (cells 0 .. n - 2, four per macrocell).
-int macro_count(int n) { return ((n - 2) >> vr::kMacroShift) + 1; }
+// Macrocells of the empty-space masks: x and y cover gather coordinates
+// 0 .. n (cells -1 .. n - 1), z cells 0 .. nz - 2, four per macrocell.
+size_t mask_macrocells(const vr::VolumeGeom& g)
+{
+    return (size_t)((g.nx >> vr::kMacroShift) + 1) * ((g.ny >> vr::kMacroShift) + 1) *
+           (((g.nz - 2) >> vr::kMacroShift) + 1);
+}
 
 size_t elem_size(int dtype) { return dtype == VR_F32 ? 4 : dtype == VR_F16 ? 2 : 1; }
 
@@ -186,9 +191,20 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
     tp->scale = v->scale;
     tp->offset = v->offset;
     tp->k_max = (int)(diag / step) + 2;
-    p->bound = v->bound;
-    p->bnx = v->bnx;
-    p->bny = v->bny;
+    p->mask = v->mask;
+    p->mnx = v->mnx;
+    p->mny = v->mny;
+    return VR_OK;
+}
+
+// Composite renders with empty-space masks use the masks of the volume's clip
+// level: rebuild them (on the render's stream) when the clip has changed.
+int ensure_masks(vr::Volume* v, int mode, cudaStream_t s)
+{
+    if (!v->mask || mode != VR_COMPOSITE || v->mask_clip == v->clip) return VR_OK;
+    cudaError_t e = vr::launch_masks(*v, v->clip, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mask launch");
+    v->mask_clip = v->clip;
     return VR_OK;
 }
 
@@ -218,6 +234,8 @@ int render_impl(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
     int rc = prepare(vol, cams, n_views, w, h, mode, step, out, d_samples, &p, &tp);
     if (rc) return rc;
     vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    rc = ensure_masks(v, mode, static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
     return launch_views(v, p, tp, mode, v->cfg[mode], cams, n_views, out,
                         static_cast<cudaStream_t>(stream));
 }
@@ -310,9 +328,7 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
     q.samples = rq.samples;
     q.done = rq.done;
     q.done_value = rq.done_value;
-    q.bound = v->bound;
-    q.bnx = v->bnx;
-    q.bny = v->bny;
+    q.mask = nullptr;      // the batched kernel marches every sample
     q.g = v->g;
     q.hix = mp.hix;
     q.hiy = mp.hiy;
@@ -645,13 +661,7 @@ int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* sr
     }
     cudaError_t e = vr::launch_pack(*v, z0, nplanes, dsrc, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "pack launch");
-    if (v->bound) {
-        // macrocells whose voxel planes [4m, 4m + 4] meet [z0, z0 + nplanes)
-        const int mz0 = z0 > 0 ? (int)((z0 - 1) >> vr::kMacroShift) : 0;
-        const int mz1 = std::min(v->bnz, (int)((z0 + nplanes - 1) >> vr::kMacroShift) + 1);
-        e = vr::launch_bounds(*v, mz0, mz1, static_cast<cudaStream_t>(stream));
-        if (e != cudaSuccess) return cuda_fail(e, "bounds launch");
-    }
+    v->mask_clip = NAN;               // masks are rebuilt by the next composite render
     if (v->n_groups > 0)
         return refresh_texture(v, z0, z0 + nplanes, static_cast<cudaStream_t>(stream));
     return VR_OK;
@@ -714,39 +724,36 @@ int vr_volume_detach_texture(vr_volume vol)
     return VR_OK;
 }
 
-int vr_volume_bounds_bytes(vr_volume vol, size_t* bytes_out)
+int vr_volume_mask_bytes(vr_volume vol, size_t* bytes_out)
 {
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
     if (!bytes_out) return fail(VR_ERR_ARG, "bytes_out is NULL");
     const vr::Volume* v = reinterpret_cast<const vr::Volume*>(vol);
-    *bytes_out = sizeof(float) * (size_t)macro_count(v->g.nx) * macro_count(v->g.ny) *
-                 macro_count(v->g.nz);
+    *bytes_out = sizeof(unsigned long long) * mask_macrocells(v->g);
     return VR_OK;
 }
 
-int vr_volume_attach_bounds(vr_volume vol, void* buf, size_t bytes, void* stream)
+int vr_volume_attach_masks(vr_volume vol, void* buf, size_t bytes)
 {
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
     vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
     if (!buf) {
-        v->bound = nullptr;
+        v->mask = nullptr;
         return VR_OK;
     }
-    size_t need = 0;
-    vr_volume_bounds_bytes(vol, &need);
+    const size_t nm = mask_macrocells(v->g);
+    if (nm > 0x7fffffffu) return fail(VR_ERR_UNSUPPORTED, "more than 2^31 macrocells");
     if (reinterpret_cast<uintptr_t>(buf) % 16 != 0)
-        return fail(VR_ERR_ARG, "bounds buffer must be 16-byte aligned");
-    if (bytes < need) return fail(VR_ERR_OOM, "bounds buffer has %zu bytes, %zu needed", bytes, need);
-    if (!is_device_ptr(buf)) return fail(VR_ERR_ARG, "bounds buffer is not device memory");
-    v->bound = static_cast<float*>(buf);
-    v->bnx = macro_count(v->g.nx);
-    v->bny = macro_count(v->g.ny);
-    v->bnz = macro_count(v->g.nz);
-    cudaError_t e = vr::launch_bounds(*v, 0, v->bnz, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) {
-        v->bound = nullptr;
-        return cuda_fail(e, "bounds launch");
-    }
+        return fail(VR_ERR_ARG, "mask buffer must be 16-byte aligned");
+    if (bytes < nm * sizeof(unsigned long long))
+        return fail(VR_ERR_OOM, "mask buffer has %zu bytes, %zu needed", bytes,
+                    nm * sizeof(unsigned long long));
+    if (!is_device_ptr(buf)) return fail(VR_ERR_ARG, "mask buffer is not device memory");
+    v->mask = static_cast<unsigned long long*>(buf);
+    v->mask_clip = NAN;                       // built by the next composite render
+    v->mnx = (v->g.nx >> vr::kMacroShift) + 1;
+    v->mny = (v->g.ny >> vr::kMacroShift) + 1;
+    v->mnz = ((v->g.nz - 2) >> vr::kMacroShift) + 1;
     return VR_OK;
 }
 
@@ -814,6 +821,8 @@ int vr_autotune(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
         if (best_ms) *best_ms = -1.0f;
         return VR_OK;
     }
+    rc = ensure_masks(v, mode, s);
+    if (rc) return rc;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
     if (cudaEventCreate(&e1) != cudaSuccess) {

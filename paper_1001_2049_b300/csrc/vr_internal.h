@@ -24,9 +24,12 @@ constexpr int kMaxTexGroups = 8;                  // layered textures per volume
 // int8 codes in 16 bits), so one gather returns all eight corners of a cell.
 constexpr int kF16Pair = 3;
 constexpr int kI8Pair = 4;
-// Empty-space bounds: one float per macrocell of kMacro^3 cells (cells
-// [4m, 4m + 3] per axis, i.e. voxels [4m, 4m + 4]), an upper bound on every
-// trilinear value the kernels can compute inside it.
+// Empty-space masks: per macrocell of 4 x 4 x 4 cells, a 64-bit mask of the
+// cells that a clip level leaves visible (bit (x & 3) | (y & 3) << 2 |
+// (z & 3) << 4).  Cells are indexed by their gather coordinates: x and y run
+// over cells -1 .. n - 1 stored at x + 1 (the outermost ones are positions a
+// rounding error outside the box, which read the edge voxels), z over cells
+// 0 .. nz - 2.
 constexpr int kMacroShift = 2;
 constexpr int kMacro = 1 << kMacroShift;
 
@@ -60,9 +63,10 @@ struct Volume {
     int stack_shift;        // pair formats: 2^shift cell planes stacked per layer
     int stack_pitch;        // rows per stacked cell plane (ny + 2)
     int cfg[3];             // texture-kernel launch shape per mode (autotuned)
-    // optional empty-space bounds (caller-owned device buffer)
-    float* bound;
-    int bnx, bny, bnz;      // macrocells per axis
+    // optional empty-space masks (caller-owned device buffer)
+    unsigned long long* mask;   // valid for clip level mask_clip
+    float mask_clip;            // NaN: not built
+    int mnx, mny, mnz;          // macrocells per axis
 };
 
 // Texture storage as the texture kernels see it.
@@ -93,8 +97,8 @@ struct MarchParams {
     int n_lut;
     float* out;             // first view of this launch
     unsigned long long* samples;   // may be null
-    const float* bound;     // empty-space bounds, or null (no skipping)
-    int bnx, bny;
+    const unsigned long long* mask;   // empty-space masks for `clip` (COMPOSITE), or null
+    int mnx, mny;
     vr_camera cams[kMaxViewsPerLaunch];
     float4 lut[VR_MAX_LUT];
 };
@@ -126,8 +130,8 @@ struct BatchReq {
     const float* offset;
     unsigned long long* samples;
     unsigned* done;
-    const float* bound;    // empty-space bounds, or null
-    int bnx, bny;
+    const unsigned long long* mask;   // empty-space masks, or null
+    int mnx, mny;
     VolumeGeom g;
     float hix, hiy, hiz, step;
     float clip, term_alpha, v_lo, lut_scale, lut_max;
@@ -188,8 +192,8 @@ cudaError_t launch_tex_f16pair(const MarchParams& p, const TexParams& t, int mod
                                cudaStream_t s);
 cudaError_t launch_tex_i8pair(const MarchParams& p, const TexParams& t, int mode, int cfg,
                               cudaStream_t s);
-// Empty-space bounds of macrocell planes [mz0, mz1) from the bricks.
-cudaError_t launch_bounds(const Volume& v, int mz0, int mz1, cudaStream_t s);
+// Empty-space masks of every macrocell for clip level `clip`.
+cudaError_t launch_masks(const Volume& v, float clip, cudaStream_t s);
 int tex_shape_count();
 void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb);
 cudaError_t fill_texture_group(const Volume& v, cudaSurfaceObject_t surf, int layer0, int z0,

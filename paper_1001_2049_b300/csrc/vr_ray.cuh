@@ -317,136 +317,94 @@ struct Acc {
         return A >= P.term_alpha;
     }
 
-    // True when no sample whose value is at most `bound` can change the
-    // result: below the clip it is transparent (composite); not above the
-    // running maximum it leaves the maximum as it is (MIP).  SUM never skips.
-    template <typename PP>
-    __device__ __forceinline__ bool skippable(const PP& P, float bound) const
+    // Lockstep skipping (march_tex_lock, COMPOSITE): may the sample whose
+    // macrocell mask is `rec` and whose cell is bit `bit` of it be visible?
+    __device__ __forceinline__ bool need(unsigned long long rec, int bit) const
     {
-        if (MODE == VR_MIP) return bound <= m;
-        if (MODE == VR_COMPOSITE) return bound < P.clip;
-        return false;
+        return (rec >> bit) & 1ull;
     }
 };
 
 // ---- empty-space skipping ----
-// A sample's macrocell is that of its cell clamped to the box (positions a
-// rounding error outside a face read the edge voxels, which the edge
-// macrocell covers).  Every coordinate of the computed sample position
-// fma(fma(k, step, t_entry), d, o) is a monotone function of k (each
-// rounding is monotone), so the samples of one macrocell form one contiguous
-// range of k: if the first and the last sample of a range lie in it, all do.
-struct Macro {
-    int x, y, z;
-    size_t i;
-};
-
+// A sample's macrocell and its cell's bit there, from the gather coordinates
+// (x, y: cell + 1, in [0, n] for positions inside the box up to rounding;
+// z: the clamped cell).
 template <typename PP>
-__device__ __forceinline__ Macro macro_of(const PP& P, const Geo& g)
+__device__ __forceinline__ int macro_of(const PP& P, const Geo& g, int& bit)
 {
-    Macro m;
-    m.x = min(max((int)g.gx - 1, 0), P.g.nx - 2) >> kMacroShift;
-    m.y = min(max((int)g.gy - 1, 0), P.g.ny - 2) >> kMacroShift;
-    m.z = g.iz >> kMacroShift;
-    m.i = ((size_t)m.z * P.bny + m.y) * P.bnx + m.x;
-    return m;
+    const int x = (int)g.gx, y = (int)g.gy, z = g.iz;
+    bit = (x & 3) | ((y & 3) << 2) | ((z & 3) << 4);
+    return ((z >> kMacroShift) * P.mny + (y >> kMacroShift)) * P.mnx + (x >> kMacroShift);
 }
 
-// First sample index after the samples of macrocell `m`, starting from
-// sample k (which lies in m).  The exit is estimated from the ray's
-// crossing of the macrocell's faces (the first and last macrocell of an
-// axis extend to infinity) and accepted only when the sample before it is
-// checked to lie in m; after two rejected estimates only sample k is
-// passed over.  Never returns more than K or less than k + 1.
-template <typename PP>
-__device__ __forceinline__ int macro_exit(const PP& P, const Ray& r, const Macro& m, int k)
-{
-    float tout = INFINITY;
-    if (r.dx > 0.0f && m.x < P.bnx - 1)
-        tout = fminf(tout, __fdividef((float)((m.x + 1) << kMacroShift) - r.ox, r.dx));
-    else if (r.dx < 0.0f && m.x > 0)
-        tout = fminf(tout, __fdividef((float)(m.x << kMacroShift) - r.ox, r.dx));
-    if (r.dy > 0.0f && m.y < P.bny - 1)
-        tout = fminf(tout, __fdividef((float)((m.y + 1) << kMacroShift) - r.oy, r.dy));
-    else if (r.dy < 0.0f && m.y > 0)
-        tout = fminf(tout, __fdividef((float)(m.y << kMacroShift) - r.oy, r.dy));
-    const int bnz = ((P.g.nz - 2) >> kMacroShift) + 1;
-    if (r.dz > 0.0f && m.z < bnz - 1)
-        tout = fminf(tout, __fdividef((float)((m.z + 1) << kMacroShift) - r.oz, r.dz));
-    else if (r.dz < 0.0f && m.z > 0)
-        tout = fminf(tout, __fdividef((float)(m.z << kMacroShift) - r.oz, r.dz));
-    const float q = ceilf(__fdividef(tout - r.te, P.step));
-    int kc = (q < (float)r.K) ? (int)fmaxf(q, 0.0f) : r.K;
-    kc = max(kc, k + 1);
-#pragma unroll 1
-    for (int tries = 0; kc - 1 > k; ++tries) {
-        if (tries == 2) return k + 1;
-        if (macro_of(P, geo(P, r, (float)(kc - 1))).i == m.i) return kc;
-        --kc;
-    }
-    return kc;
-}
-
-// march_tex with empty-space skipping: runs of samples in macrocells whose
-// bound makes them skippable are passed over in one step each; the other
-// samples are marched as in march_tex (gathers one sample ahead, two
-// register sets).  The result is identical to march_tex's: every skipped
-// sample is one march_tex would have left without effect.  Returns the
-// number of samples up to termination, skipped ones included.
+// march_tex with empty-space skipping in lockstep (COMPOSITE): every lane
+// steps through its samples at the same pace as without skipping (the
+// warp's rays stay side by side, so their gathers share cache lines), but a
+// lane fetches and evaluates a sample only when its cell's mask bit says the
+// clip can leave it visible; when no lane of the warp needs its sample, the
+// step costs the geometry alone.  Masks are loaded one sample ahead of the
+// gathers, gathers one sample ahead of the interpolation.  The result and
+// the sample count are those of march_tex.
 template <int DT, int MODE, bool MULTI, typename PP, typename TT>
-__device__ __forceinline__ int march_tex_skip(const PP& P, const TT& T,
+__device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
                                               const float4* __restrict__ lut, const Ray& r,
                                               Acc<MODE>& acc)
 {
+    static_assert(MODE == VR_COMPOSITE, "skipping is for compositing");
+    using Rec = unsigned long long;
     if (r.K <= 0) return 0;
     const cudaTextureObject_t t0 = T.tex[0];
     int k = 0;
-    Geo ga = geo(P, r, 0.0f), gb;
-    Macro ma = macro_of(P, ga);
-    float bnd = __ldg(P.bound + ma.i);
-    float4 a0, a1, b0, b1;
+    // g0: sample k (corners a, present iff n0); g1: sample k + 1 (record rX,
+    // macrocell mX, cell bit b1)
+    Geo g0 = geo(P, r, 0.0f), g1 = geo(P, r, 1.0f);
+    int b0, b1;
+    const int m0 = macro_of(P, g0, b0);
+    int mX = macro_of(P, g1, b1);
+    const Rec r0 = __ldg(P.mask + m0);
+    Rec rX = (mX == m0) ? r0 : __ldg(P.mask + mX), rY;
+    bool n0 = acc.need(r0, b0);
+    float4 a0, a1, c0, c1;
+    if (n0) cell<DT, MULTI>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
+    float kf = 2.0f;
     for (;;) {
-        while (acc.skippable(P, bnd)) {
-            k = macro_exit(P, r, ma, k);
-            if (k >= r.K) return k;
-            ga = geo(P, r, (float)k);
-            ma = macro_of(P, ga);
-            bnd = __ldg(P.bound + ma.i);
+        // sample k + 2: geometry and record; sample k + 1: gathers; sample k
+        Geo g2 = geo(P, r, kf);
+        int b2;
+        const int m2 = macro_of(P, g2, b2);
+        rY = (m2 == mX) ? rX : __ldg(P.mask + m2);
+        const bool n1 = acc.need(rX, b1);
+        if (n1) {
+            if (n0)
+                next_cell<DT, MULTI>(T, t0, g0, a0, a1, g1, c0, c1);
+            else
+                cell<DT, MULTI>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
         }
-        cell<DT, MULTI>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
-        float kf = (float)(k + 1);
-        for (;;) {
-            gb = geo(P, r, kf);
-            next_cell<DT, MULTI>(T, t0, ga, a0, a1, gb, b0, b1);
-            Macro mn = macro_of(P, gb);
-            const bool moved = mn.i != ma.i;
-            const float nb = moved ? __ldg(P.bound + mn.i) : bnd;
-            ++k;
-            if (acc.add(P, lut, interp(a0, a1, ga)) || k >= r.K) return k;
-            kf += 1.0f;
-            if (moved) {
-                ma = mn;
-                bnd = nb;
-                if (acc.skippable(P, bnd)) {
-                    ga = gb;
-                    break;
-                }
-            }
-            ga = geo(P, r, kf);
-            next_cell<DT, MULTI>(T, t0, gb, b0, b1, ga, a0, a1);
-            mn = macro_of(P, ga);
-            const bool moved2 = mn.i != ma.i;
-            const float nb2 = moved2 ? __ldg(P.bound + mn.i) : bnd;
-            ++k;
-            if (acc.add(P, lut, interp(b0, b1, gb)) || k >= r.K) return k;
-            kf += 1.0f;
-            if (moved2) {
-                ma = mn;
-                bnd = nb2;
-                if (acc.skippable(P, bnd)) break;
-            }
+        ++k;
+        if ((n0 && acc.add(P, lut, interp(a0, a1, g0))) || k >= r.K) break;
+        kf += 1.0f;
+        // the same one sample further on, the two register sets swapped
+        const Geo g3 = geo(P, r, kf);
+        int b3;
+        const int m3 = macro_of(P, g3, b3);
+        rX = (m3 == m2) ? rY : __ldg(P.mask + m3);
+        mX = m3;
+        const bool n2 = acc.need(rY, b2);
+        if (n2) {
+            if (n1)
+                next_cell<DT, MULTI>(T, t0, g1, c0, c1, g2, a0, a1);
+            else
+                cell<DT, MULTI>(T, t0, g2.iz, g2.gx, g2.gy, a0, a1);
         }
+        ++k;
+        if ((n1 && acc.add(P, lut, interp(c0, c1, g1))) || k >= r.K) break;
+        kf += 1.0f;
+        g0 = g2;
+        g1 = g3;
+        b1 = b3;
+        n0 = n2;
     }
+    return k;
 }
 
 // The gathers of sample k + 1 are issued before sample k is interpolated, so

@@ -15,8 +15,8 @@
 //
 // The gathers of the next sample are issued before the current sample is
 // interpolated, which hides the texture latency behind the arithmetic.
-// With empty-space bounds attached (SKIP), runs of samples in macrocells
-// that cannot change the result are passed over (vr_ray.cuh).
+// With empty-space masks attached (SKIP, COMPOSITE), samples whose cell the
+// clip makes transparent are not fetched (vr_ray.cuh, march_tex_lock).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG
         const ray::Ray r = ray::setup_ray(P, P.cams[view], px, py, T.k_max);
         ray::Acc<MODE> acc;
         if constexpr (SKIP)
-            count = (unsigned)ray::march_tex_skip<DT, MODE, MULTI>(P, T, s_lut, r, acc);
+            count = (unsigned)ray::march_tex_lock<DT, MODE, MULTI>(P, T, s_lut, r, acc);
         else
             count = (unsigned)ray::march_tex<DT, MODE, MULTI>(P, T, s_lut, r, acc);
         const size_t pix = ((size_t)view * P.h + py) * P.w + px;
@@ -79,11 +79,16 @@ __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG
 template <int DT, int MODE, bool MULTI, int CFG>
 cudaError_t launch_c(const MarchParams& p, const TexParams& t, cudaStream_t s)
 {
-    constexpr bool kCanSkip = MODE != VR_SUM;
+    // skipping is for COMPOSITE (the clip makes most cells transparent); a
+    // MIP sample could only be passed over when no corner of its cell
+    // exceeds the ray's running maximum of interpolated values, and on noise
+    // about a quarter of the cells have such a corner: nearly every warp
+    // step would have a lane needing its sample, so MIP marches every sample
+    constexpr bool kCanSkip = MODE == VR_COMPOSITE;
     constexpr Shape S = kShapes[CFG];
     dim3 grid((unsigned)((p.w + S.bx - 1) / S.bx), (unsigned)((p.h + S.by - 1) / S.by),
               (unsigned)p.n_views);
-    if (kCanSkip && p.bound)
+    if (kCanSkip && p.mask != nullptr)
         tex_kernel<DT, MODE, MULTI, CFG, kCanSkip><<<grid, S.bx * S.by, 0, s>>>(p, t);
     else
         tex_kernel<DT, MODE, MULTI, CFG, false><<<grid, S.bx * S.by, 0, s>>>(p, t);

@@ -32,14 +32,14 @@ def oracle_volume(cube: np.ndarray, dtype: str) -> oracle.Volume:
 
 
 def gpu_images(cube_t, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, count=None,
-               tex=False, bounds=False):
+               tex=False, masks=False):
     vol = Volume(cube_t.cuda(), dtype)
     if tex == "pair":
         vol.attach_pair_texture()
     elif tex:
         vol.attach_texture()
-    if bounds:
-        vol.attach_bounds()
+    if masks:
+        vol.attach_masks()
     vol.set_transfer(lut, v_lo, v_hi, clip, ta)
     out = vol.render(cams, w, h, mode, step, count=count)
     torch.cuda.synchronize()
@@ -56,13 +56,13 @@ def scale_for(mode, cube, got):
 
 
 def run_parity(cube, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, tol=TOL_FP32,
-               reference="decoded", pixels=None, what="", tex=False, bounds=False):
+               reference="decoded", pixels=None, what="", tex=False, masks=False):
     """Render on the GPU (bricks, or texture storage with tex=True, with the
-    empty-space bounds grid with bounds=True) and compare with the oracle (on
-    the decoded storage values, or on the float32 source with
+    empty-space masks with masks=True) and compare with the oracle (on the
+    decoded storage values, or on the float32 source with
     reference="source")."""
     got = gpu_images(torch.from_numpy(cube), dtype, cams, w, h, mode, step, lut, v_lo, v_hi,
-                     clip, ta, tex=tex, bounds=bounds)
+                     clip, ta, tex=tex, masks=masks)
     ovol = oracle_volume(cube, dtype if reference == "decoded" else "f32")
     tf = oracle.TF(lut, v_lo, v_hi, clip, ta)
     nz, ny, nx = cube.shape
@@ -458,8 +458,8 @@ def test_brick_buffer_too_small_is_rejected():
 
 
 # ---------------------------------------------------------------------------
-# empty-space bounds: every entry bounds its macrocell's values, and renders
-# with the grid are identical to renders without it
+# empty-space masks: every cell whose bit is clear is below the clip, and
+# composite renders with the masks are identical to renders without them
 # ---------------------------------------------------------------------------
 def _decoded(cube, dtype):
     """Storage values as the kernels decode them (float32)."""
@@ -472,37 +472,50 @@ def _decoded(cube, dtype):
             + of.astype(np.float64)[:, None, None]).astype(np.float32)
 
 
-def _macro_reduce(a, fn, fill):
-    """fn over voxels [4m, 4m + 4] of every macrocell (a is (nz, ny, nx))."""
-    for axis in range(3):
-        n = a.shape[axis]
-        bn = ((n - 2) >> 2) + 1
-        pad = [(0, 0)] * 3
-        pad[axis] = (0, 4 * bn + 1 - n)
-        a = np.pad(a, pad, constant_values=fill)
-        a = fn.reduce([np.take(a, np.arange(j, j + 4 * bn, 4), axis=axis) for j in range(5)])
-    return a
+MASK_DIMS = [(37, 45, 70), (2, 2, 2), (6, 5, 9), (64, 3, 33)]
 
 
-BOUND_DIMS = [(37, 45, 70), (2, 2, 2), (6, 5, 9), (64, 3, 33)]
-
-
-@pytest.mark.parametrize("dims", BOUND_DIMS)
+@pytest.mark.parametrize("dims", MASK_DIMS)
 @pytest.mark.parametrize("dtype", ["f32", "f16", "i8"])
-def test_bounds_grid_bounds_every_macrocell(dims, dtype):
+def test_masks_mark_every_cell_that_can_reach_the_clip(dims, dtype):
     cube = synth.make_cube(dims, 3, ("uniform", 3.0, 8.0), 40 + dims[0]).numpy()
     vol = Volume(torch.from_numpy(cube).cuda(), dtype)
-    vol.attach_bounds()
-    torch.cuda.synchronize()
+    vol.attach_texture()
+    vol.attach_masks()
+    nx, ny, nz = dims
+    mnx, mny, mnz = (nx >> 2) + 1, (ny >> 2) + 1, ((nz - 2) >> 2) + 1
+    assert vol.mask_bytes() == 8 * mnx * mny * mnz
     dec = _decoded(cube, dtype).astype(np.float64)
-    hi = _macro_reduce(dec, np.maximum, -np.inf)
-    mag = _macro_reduce(np.abs(dec), np.maximum, 0.0)
-    got = vol._bounds.cpu().numpy().astype(np.float64)[:hi.size].reshape(hi.shape)
-    assert vol.bounds_bytes() == 4 * hi.size
-    # above every value by more than any interpolation rounding (< 10 u |v|),
-    # and not by more than the stated margin
-    assert (got >= hi + 2.0 ** -21 * mag).all()
-    assert (got <= hi + 2.0 ** -18 * mag).all()
+    # bound of each cell's eight corners, for gather coordinates x, y in
+    # [0, n] (cells -1 .. n - 1, the outermost reading the edge cell) and z
+    # in [0, nz - 2]
+    hi = np.full((nz - 1, ny - 1, nx - 1), -np.inf)
+    mag = np.zeros_like(hi)
+    for c in range(8):
+        sl = dec[(c >> 2):nz - 1 + (c >> 2), ((c >> 1) & 1):ny - 1 + ((c >> 1) & 1),
+                 (c & 1):nx - 1 + (c & 1)]
+        hi = np.maximum(hi, sl)
+        mag = np.maximum(mag, np.abs(sl))
+    bound = hi + 2.0 ** -19 * mag
+    gx = np.clip(np.arange(nx + 1) - 1, 0, nx - 2)
+    gy = np.clip(np.arange(ny + 1) - 1, 0, ny - 2)
+    bound = bound[:, gy][:, :, gx]                       # (nz - 1, ny + 1, nx + 1)
+    cams = synth.random_sphere_cameras(dims, 1, 4, 4, 3)
+    z, y, x = np.meshgrid(np.arange(nz - 1), np.arange(ny + 1), np.arange(nx + 1),
+                          indexing="ij")
+    bit = ((x & 3) | ((y & 3) << 2) | ((z & 3) << 4)).astype(np.uint64)
+    for clip in (2.0, 4.5):
+        vol.set_transfer(synth.default_lut(16), clip, 9.0, clip, 1.0)
+        vol.render(cams, 4, 4, "composite", 0.5)     # builds the masks for this clip
+        torch.cuda.synchronize()
+        words = vol._masks.cpu().numpy().view(np.uint64)[:mnx * mny * mnz]
+        words = words.reshape(mnz, mny, mnx)
+        got = ((words[z >> 2, y >> 2, x >> 2] >> bit) & np.uint64(1)).astype(bool)
+        want = bound >= clip
+        clear = np.abs(bound - clip) > 1e-5 * max(1.0, abs(clip))   # not a rounding tie
+        assert (got == want)[clear].all(), (dtype, dims, clip)
+        # a clear bit never hides a corner at or above the clip
+        assert not (~got & (hi[:, gy][:, :, gx] >= clip)).any()
 
 
 def _skip_cases(dims, seed):
@@ -515,9 +528,9 @@ def _skip_cases(dims, seed):
     return cube, cams
 
 
-@pytest.mark.parametrize("dims", BOUND_DIMS)
+@pytest.mark.parametrize("dims", MASK_DIMS)
 @pytest.mark.parametrize("store", ["f32", "f16", "i8", "f16-pair", "i8-pair"])
-def test_bounds_leave_images_and_counts_unchanged(dims, store):
+def test_masks_leave_images_and_counts_unchanged(dims, store):
     dtype, _, pair = store.partition("-")
     cube, cams = _skip_cases(dims, 50 + dims[1])
     vol = Volume(torch.from_numpy(cube).cuda(), dtype)
@@ -528,51 +541,70 @@ def test_bounds_leave_images_and_counts_unchanged(dims, store):
     lut = synth.default_lut(64)
     for clip in (-10.0, 1.0, 3.0, 100.0):       # nothing, some, most, everything skippable
         vol.set_transfer(lut, min(clip, 7.0), 8.0, clip, 0.95)
-        for mode in ("composite", "mip"):
-            outs = []
-            for b in (False, True):
-                if b:
-                    vol.attach_bounds()
-                n = torch.zeros(1, dtype=torch.int64, device="cuda")
-                img = vol.render(cams, 29, 19, mode, 0.37, count=n)
-                torch.cuda.synchronize()
-                outs.append((img.cpu(), int(n.item())))
-                vol.detach_bounds()
-            assert torch.equal(outs[0][0], outs[1][0]), (store, dims, clip, mode)
-            assert outs[0][1] == outs[1][1], (store, dims, clip, mode)
+        outs = []
+        for masks in (False, True):
+            if masks:
+                vol.attach_masks()
+            n = torch.zeros(1, dtype=torch.int64, device="cuda")
+            img = vol.render(cams, 29, 19, "composite", 0.37, count=n)
+            torch.cuda.synchronize()
+            outs.append((img.cpu(), int(n.item())))
+            vol.detach_masks()
+        assert torch.equal(outs[0][0], outs[1][0]), (store, dims, clip)
+        assert outs[0][1] == outs[1][1], (store, dims, clip)
 
 
-def test_bounds_skip_almost_everything_on_a_sparse_cube():
-    # one bright voxel in an empty cube: composite skips every macrocell but
-    # the few around it; MIP skips once the running maximum reaches 0
+def test_masks_follow_clip_changes_and_uploads():
+    dims = (40, 36, 50)
+    cube = synth.make_cube(dims, 4, ("uniform", 3.0, 8.0), 61).numpy()
+    cams = synth.random_sphere_cameras(dims, 3, 21, 21, 5)
+    vol = Volume(torch.from_numpy(cube).cuda(), "f32")
+    vol.attach_texture()
+    ref = Volume(torch.from_numpy(cube).cuda(), "f32")
+    ref.attach_texture()
+    vol.attach_masks()
+    lut = synth.default_lut(32)
+    for clip in (3.0, 1.0, 3.0):
+        for v in (vol, ref):
+            v.set_transfer(lut, clip, 8.0, clip, 1.0)
+        assert torch.equal(vol.render(cams, 21, 21, "composite", 0.5),
+                           ref.render(cams, 21, 21, "composite", 0.5))
+    # new planes: the masks are rebuilt for them
+    cube2 = cube.copy()
+    cube2[20:30] += 5.0
+    for v in (vol, ref):
+        v.upload(20, torch.from_numpy(cube2[20:30]).cuda())
+    assert torch.equal(vol.render(cams, 21, 21, "composite", 0.5),
+                       ref.render(cams, 21, 21, "composite", 0.5))
+
+
+def test_masks_on_a_sparse_cube():
+    # one bright voxel in an empty cube: every cell but the eight around it
+    # is skipped
     dims = (40, 36, 50)
     cube = np.zeros((50, 36, 40), dtype=np.float32)
     cube[21, 17, 13] = 9.0
     cams = synth.random_sphere_cameras(dims, 6, 31, 31, 7, fov_deg=40.0)
     recs = [synth.axis_camera(dims, 40, 36, axis=2, sign=1)]
     cams = np.concatenate([cams, synth.cameras(recs).astype(cams.dtype)])
-    lut = synth.default_lut(32)
-    for mode in ("composite", "mip"):
-        run_parity(cube, "f32", cams, 31, 31, mode, 0.5, lut, 0.5, 9.0, 0.5, 1.0,
-                   what="sparse bounds " + mode, tex=True, bounds=True)
+    run_parity(cube, "f32", cams, 31, 31, "composite", 0.5, synth.default_lut(32), 0.5, 9.0,
+               0.5, 1.0, what="sparse masks", tex=True, masks=True)
 
 
 @pytest.mark.parametrize("tex", [True, "pair"], ids=["texture", "pair"])
-@pytest.mark.parametrize("mode", ["mip", "composite"])
-def test_bounds_small_workload(small, tex, mode):
+def test_masks_small_workload(small, tex):
     wl, cube, lut, cams = small
     dtype = "f32" if tex is True else "f16"
-    run_parity(cube, dtype, cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi, wl.clip,
-               wl.term_alpha, what="small bounds %s %s" % (dtype, mode), tex=tex, bounds=True)
+    run_parity(cube, dtype, cams, 256, 256, "composite", wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+               wl.term_alpha, what="small masks " + dtype, tex=tex, masks=True)
 
 
 @pytest.mark.parametrize("dims,step", RAGGED)
 @pytest.mark.parametrize("dtype", ["f32", "i8"])
-def test_bounds_ragged_cubes(dims, step, dtype):
+def test_masks_ragged_cubes(dims, step, dtype):
     cube, cams, lut = ragged_case(dims, 17 + dims[0])
-    for mode in ("mip", "composite"):
-        run_parity(cube, dtype, cams, 23, 17, mode, step, lut, 1.0, 8.0, 3.0, 0.95,
-                   what="bounds ragged %s %s %s" % (dims, dtype, mode), tex=True, bounds=True)
+    run_parity(cube, dtype, cams, 23, 17, "composite", step, lut, 1.0, 8.0, 3.0, 0.95,
+               what="masks ragged %s %s" % (dims, dtype), tex=True, masks=True)
 
 
 # ---------------------------------------------------------------------------
@@ -613,15 +645,15 @@ def test_large_workload_sampled_pixels(large, dtype, tex):
     for mode in ("composite", "mip"):
         n0 = torch.zeros(1, dtype=torch.int64, device="cuda")
         img = vol.render(cams, w, h, mode, wl.step, count=n0)
-        if tex:
-            # with the empty-space bounds (the benchmark's configuration) the
+        if tex and mode == "composite":
+            # with the empty-space masks (the benchmark's configuration) the
             # images and the sample counts are the same, bit for bit
-            vol.attach_bounds()
+            vol.attach_masks()
             n1 = torch.zeros(1, dtype=torch.int64, device="cuda")
             img1 = vol.render(cams, w, h, mode, wl.step, count=n1)
-            vol.detach_bounds()
+            vol.detach_masks()
             torch.cuda.synchronize()
-            assert torch.equal(img, img1), "large %s %s: bounds change the image" % (dtype, mode)
+            assert torch.equal(img, img1), "large %s %s: masks change the image" % (dtype, mode)
             assert int(n0.item()) == int(n1.item())
             img = img1
         torch.cuda.synchronize()
