@@ -184,30 +184,29 @@ int vr_volume_mask_bytes(vr_volume vol, size_t* bytes_out);
  * here.  The paper describes no such structure.                            */
 int vr_volume_attach_masks(vr_volume vol, void* buf, size_t bytes);
 
-/* Give the volume texture storage: a copy of the cube in layered 2-D
- * textures (one layer per frequency plane, split into groups of at most 2048
- * planes), filled from the bricks on `stream`.  Renders then gather the
- * 2 x 2 corners of a cell per plane with the texture unit's four-texel gather
- * (unfiltered texels; the interpolation stays the kernel's own FP32 lerps).
- * This is the one place the library allocates device memory: about
+/* Give the volume texture storage: a copy of the cube in one layered 2-D
+ * texture, one 2-D slice per frequency plane, filled from the bricks on
+ * `stream`.  A layered texture has at most 2048 layers: deeper cubes stack
+ * 2^s slices per layer (the smallest s that fits), each with a copy of its
+ * first and last row around it.  Renders then gather the 2 x 2 corners of a
+ * cell per plane with the texture unit's four-texel gather (unfiltered
+ * texels; the interpolation stays the kernel's own FP32 lerps).  This is the
+ * one place the library allocates device memory: about
  * nx*ny*nz*sizeof(storage) bytes, owned by the volume and released by
  * vr_volume_detach_texture or vr_volume_destroy.  The call synchronises
- * `stream` (the fill must finish before its surface objects are released).
- * Returns VR_ERR_UNSUPPORTED when nx or ny exceeds the device's layered
- * texture size, VR_ERR_OOM when the allocation fails.                       */
+ * `stream` (the fill must finish before its surface object is released).
+ * Returns VR_ERR_UNSUPPORTED when nx or the stacked height exceeds the
+ * device's layered texture size, VR_ERR_OOM when the allocation fails.      */
 int vr_volume_attach_texture(vr_volume vol, void* stream);
 
 /* Texture storage in pair format, for VR_F16 and VR_I8 volumes: each texel
  * packs a voxel with its neighbour in the next frequency plane (two binary16
- * values in 32 bits, or two int8 codes in 16 bits), one 2-D plane per cell
- * plane (nz - 1 of them), so one four-texel gather returns all eight corners
- * of a cell.  The cell planes live in one layered texture, 2^s per layer
- * (the smallest s that needs at most 2048 layers), each with a copy of its
- * first and last row around it.  About twice the bytes of
- * vr_volume_attach_texture (2 x nx*(ny+2)*(nz-1)*sizeof(storage)); replaces
- * a plain texture storage if one is attached.  Otherwise as
- * vr_volume_attach_texture; VR_F32 volumes, and cubes whose stacked planes
- * exceed the layered texture height, give VR_ERR_UNSUPPORTED.               */
+ * values in 32 bits, or two int8 codes in 16 bits), one 2-D slice per cell
+ * plane (nz - 1 of them, stacked as in vr_volume_attach_texture), so one
+ * four-texel gather returns all eight corners of a cell.  About twice the
+ * bytes of vr_volume_attach_texture; replaces a plain texture storage if one
+ * is attached.  Otherwise as vr_volume_attach_texture; VR_F32 volumes give
+ * VR_ERR_UNSUPPORTED.                                                       */
 int vr_volume_attach_pair_texture(vr_volume vol, void* stream);
 
 /* Release the texture storage (renders fall back to gathering from the

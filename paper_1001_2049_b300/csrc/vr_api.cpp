@@ -184,8 +184,7 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
                                     v->lut_corr[i][3]);
     }
     std::memset(tp, 0, sizeof *tp);
-    for (int g = 0; g < v->n_groups; ++g) tp->tex[g] = v->tex[g];
-    tp->n_groups = v->n_groups;
+    tp->tex = v->tex;
     tp->stack_shift = v->stack_shift;
     tp->stack_pitch = v->stack_pitch;
     tp->scale = v->scale;
@@ -219,7 +218,7 @@ int launch_views(vr::Volume* v, vr::MarchParams& p, const vr::TexParams& tp, int
         p.n_views = nv;
         std::memcpy(p.cams, cams + v0, sizeof(vr_camera) * nv);
         p.out = out + per_view * v0;
-        cudaError_t e = v->n_groups > 0 ? vr::launch_tex(p, tp, v->tex_format, mode, cfg, s)
+        cudaError_t e = v->has_tex ? vr::launch_tex(p, tp, v->tex_format, mode, cfg, s)
                                         : vr::launch_march(p, v->dtype, mode, s);
         if (e != cudaSuccess) return cuda_fail(e, "march launch");
     }
@@ -302,7 +301,7 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
         }
     }
     int tex_slot = -1;
-    if (v->n_groups > 0) {
+    if (v->has_tex) {
         for (int i = 0; i < *n_tex; ++i)
             if (tex_vols[i] == v) tex_slot = i;
         if (tex_slot < 0) {
@@ -311,8 +310,7 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
             tex_vols[tex_slot] = v;
             vr::BatchTex& T = B->tex[tex_slot];
             std::memset(&T, 0, sizeof T);
-            for (int g = 0; g < v->n_groups; ++g) T.tex[g] = v->tex[g];
-            T.n_groups = v->n_groups;
+            T.tex = v->tex;
             T.stack_shift = v->stack_shift;
             T.stack_pitch = v->stack_pitch;
             T.format = v->tex_format;
@@ -361,25 +359,24 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
 int batch_class(const vr_request& r)
 {
     const vr::Volume* v = reinterpret_cast<const vr::Volume*>(r.vol);
-    if (!v || v->n_groups == 0) return vr::kBatchBricks;
-    return v->n_groups > 1 ? vr::kBatchTexGroups : vr::kBatchTex;
+    return v && v->has_tex ? vr::kBatchTex : vr::kBatchBricks;
 }
 
 int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
 {
-    static int grid[3] = {0, 0, 0};
+    static int grid[2] = {0, 0};
     if (grid[0] == 0) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms < 1) sms = 1;
-        for (int c = 0; c < 3; ++c) grid[c] = sms * vr::batch_blocks_per_sm(c);
+        for (int c = 0; c < 2; ++c) grid[c] = sms * vr::batch_blocks_per_sm(c);
     }
     vr::BatchParams* B = new (std::nothrow) vr::BatchParams;
     if (!B) return fail(VR_ERR_OOM, "out of host memory");
     int rc = VR_OK;
-    const int order[3] = {vr::kBatchTex, vr::kBatchTexGroups, vr::kBatchBricks};
-    for (int oi = 0; oi < 3 && rc == VR_OK; ++oi) {
+    const int order[2] = {vr::kBatchTex, vr::kBatchBricks};
+    for (int oi = 0; oi < 2 && rc == VR_OK; ++oi) {
         const int cls = order[oi];
         int i = 0;
         while (rc == VR_OK) {
@@ -417,43 +414,36 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
 
 void release_texture(vr::Volume* v)
 {
-    for (int g = 0; g < v->n_groups; ++g) {
-        if (v->tex[g]) cudaDestroyTextureObject(v->tex[g]);
-        if (v->arrays[g]) cudaFreeArray(v->arrays[g]);
-        v->tex[g] = 0;
-        v->arrays[g] = nullptr;
-    }
-    v->n_groups = 0;
+    if (v->tex) cudaDestroyTextureObject(v->tex);
+    if (v->array) cudaFreeArray(v->array);
+    v->tex = 0;
+    v->array = nullptr;
+    v->has_tex = false;
 }
 
-// Copy planes [z0, z1) of the bricks into the texture groups holding them.
-// Copy planes [z0, z1) of the bricks into the texture groups holding them
-// (for pair formats: the cells whose texels include one of those planes).
+// Copy planes [z0, z1) of the bricks into the texture (for pair formats: the
+// cell planes whose texels include one of those planes).
 int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
 {
     const bool pair = v->tex_format == vr::kF16Pair || v->tex_format == vr::kI8Pair;
-    if (pair) z0 = std::max<int64_t>(z0 - 1, 0);     // cell z0 - 1 holds plane z0
-    for (int g = 0; g < v->n_groups; ++g) {
-        int first = 0, layers = 0;
-        vr::texture_group(*v, g, &first, &layers);
-        const int a = (int)std::max<int64_t>(z0, first);
-        const int b = (int)std::min<int64_t>(z1, first + layers);
-        if (a >= b) continue;
-        cudaResourceDesc rd;
-        std::memset(&rd, 0, sizeof rd);
-        rd.resType = cudaResourceTypeArray;
-        rd.res.array.array = v->arrays[g];
-        cudaSurfaceObject_t surf = 0;
-        cudaError_t e = cudaCreateSurfaceObject(&surf, &rd);
-        if (e != cudaSuccess) return cuda_fail(e, "surface object");
-        e = vr::fill_texture_group(*v, surf, first, a, b, s);
-        // the surface object may be destroyed once the fill is enqueued only
-        // after it ran: wait for this stream
-        cudaError_t e2 = cudaStreamSynchronize(s);
-        cudaDestroySurfaceObject(surf);
-        if (e != cudaSuccess) return cuda_fail(e, "texture fill");
-        if (e2 != cudaSuccess) return cuda_fail(e2, "texture fill");
+    if (pair) {
+        z0 = std::max<int64_t>(z0 - 1, 0);     // cell z0 - 1 holds plane z0
+        z1 = std::min<int64_t>(z1, v->g.nz - 1);
     }
+    if (z0 >= z1) return VR_OK;
+    cudaResourceDesc rd;
+    std::memset(&rd, 0, sizeof rd);
+    rd.resType = cudaResourceTypeArray;
+    rd.res.array.array = v->array;
+    cudaSurfaceObject_t surf = 0;
+    cudaError_t e = cudaCreateSurfaceObject(&surf, &rd);
+    if (e != cudaSuccess) return cuda_fail(e, "surface object");
+    e = vr::fill_texture(*v, surf, (int)z0, (int)z1, s);
+    // the surface object may only be destroyed after the fill ran: wait
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaDestroySurfaceObject(surf);
+    if (e != cudaSuccess) return cuda_fail(e, "texture fill");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "texture fill");
     return VR_OK;
 }
 
@@ -464,7 +454,7 @@ int attach_texture(vr_volume vol, bool pair, void* stream)
     if (pair && v->dtype == VR_F32)
         return fail(VR_ERR_UNSUPPORTED, "pair textures hold FP16 or int8 storage only");
     const int format = pair ? (v->dtype == VR_F16 ? vr::kF16Pair : vr::kI8Pair) : v->dtype;
-    if (v->n_groups > 0) {
+    if (v->has_tex) {
         if (v->tex_format == format) return VR_OK;
         release_texture(v);
     }
@@ -474,64 +464,50 @@ int attach_texture(vr_volume vol, bool pair, void* stream)
     cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, dev);
     cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, dev);
     cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, dev);
-    if (v->g.nx > maxw || v->g.ny > maxh || maxl < vr::kMaxLayers)
-        return fail(VR_ERR_UNSUPPORTED, "cube %d x %d exceeds the layered texture limits", v->g.nx,
-                    v->g.ny);
-    v->tex_format = format;
-    v->stack_shift = 0;
-    v->stack_pitch = v->g.ny + 2;
-    if (pair) {
-        // cell planes stacked 2^shift per layer so that one layered texture
-        // holds every cell plane
-        const int cells = v->g.nz - 1;
-        while (((cells + (1 << v->stack_shift) - 1) >> v->stack_shift) > vr::kMaxLayers)
-            ++v->stack_shift;
-        if ((int64_t)v->stack_pitch << v->stack_shift > maxh)
-            return fail(VR_ERR_UNSUPPORTED, "cube %d x %d x %d exceeds the layered texture limits",
-                        v->g.nx, v->g.ny, v->g.nz);
-    }
-    const int groups = vr::texture_groups(*v);
-    if (groups > vr::kMaxTexGroups)
-        return fail(VR_ERR_UNSUPPORTED, "nz = %d needs more than %d layered textures", v->g.nz,
-                    vr::kMaxTexGroups);
+    maxl = std::min(maxl, vr::kMaxLayers);
+    // slices: planes (plain) or cell planes (pair), stacked 2^shift per layer
+    // (each with a copy of its edge rows) when they outnumber the layers
+    const int slices = pair ? v->g.nz - 1 : v->g.nz;
+    int shift = 0;
+    while (((slices + (1 << shift) - 1) >> shift) > maxl) ++shift;
+    const int pitch = shift > 0 ? v->g.ny + 2 : v->g.ny;
+    if (v->g.nx > maxw || (int64_t)pitch << shift > maxh)
+        return fail(VR_ERR_UNSUPPORTED, "cube %d x %d x %d exceeds the layered texture limits",
+                    v->g.nx, v->g.ny, v->g.nz);
     cudaChannelFormatDesc desc = format == VR_F32    ? cudaCreateChannelDesc<float>()
                                  : format == VR_F16   ? cudaCreateChannelDescHalf()
                                  : format == VR_I8    ? cudaCreateChannelDesc<signed char>()
                                  : format == vr::kF16Pair ? cudaCreateChannelDesc<unsigned int>()
                                                           : cudaCreateChannelDesc<unsigned short>();
-    for (int g = 0; g < groups; ++g) {
-        int first = 0, layers = 0;
-        vr::texture_group(*v, g, &first, &layers);
-        cudaArray_t arr = nullptr;
-        const cudaExtent ext =
-            pair ? make_cudaExtent(v->g.nx, (size_t)v->stack_pitch << v->stack_shift,
-                                   (layers + (1 << v->stack_shift) - 1) >> v->stack_shift)
-                 : make_cudaExtent(v->g.nx, v->g.ny, layers);
-        cudaError_t e = cudaMalloc3DArray(&arr, &desc, ext,
-                                          cudaArrayLayered | cudaArraySurfaceLoadStore);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            release_texture(v);
-            return fail(e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA,
-                        "texture storage: %s", cudaGetErrorString(e));
-        }
-        v->arrays[g] = arr;
-        v->n_groups = g + 1;
-        cudaResourceDesc rd;
-        std::memset(&rd, 0, sizeof rd);
-        rd.resType = cudaResourceTypeArray;
-        rd.res.array.array = arr;
-        cudaTextureDesc td;
-        std::memset(&td, 0, sizeof td);
-        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
-        td.filterMode = cudaFilterModePoint;
-        td.readMode = cudaReadModeElementType;
-        td.normalizedCoords = 0;
-        e = cudaCreateTextureObject(&v->tex[g], &rd, &td, nullptr);
-        if (e != cudaSuccess) {
-            release_texture(v);
-            return cuda_fail(e, "texture object");
-        }
+    cudaArray_t arr = nullptr;
+    cudaError_t e = cudaMalloc3DArray(
+        &arr, &desc,
+        make_cudaExtent(v->g.nx, (size_t)pitch << shift, (slices + (1 << shift) - 1) >> shift),
+        cudaArrayLayered | cudaArraySurfaceLoadStore);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA,
+                    "texture storage: %s", cudaGetErrorString(e));
+    }
+    v->array = arr;
+    v->has_tex = true;
+    v->tex_format = format;
+    v->stack_shift = shift;
+    v->stack_pitch = pitch;
+    cudaResourceDesc rd;
+    std::memset(&rd, 0, sizeof rd);
+    rd.resType = cudaResourceTypeArray;
+    rd.res.array.array = arr;
+    cudaTextureDesc td;
+    std::memset(&td, 0, sizeof td);
+    td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+    td.filterMode = cudaFilterModePoint;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    e = cudaCreateTextureObject(&v->tex, &rd, &td, nullptr);
+    if (e != cudaSuccess) {
+        release_texture(v);
+        return cuda_fail(e, "texture object");
     }
     int rc = refresh_texture(v, 0, v->g.nz, static_cast<cudaStream_t>(stream));
     if (rc) release_texture(v);
@@ -550,28 +526,6 @@ int batch_with_counters(const vr_request* reqs, int n, unsigned* counters, cudaS
 }
 
 int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
-
-// Plain formats: group g holds planes [g (L-1), g (L-1) + L), overlapping its
-// neighbour by one plane so a cell's two planes share a group.  Pair formats:
-// one texture holds every cell plane (stacked, see attach_texture); its
-// "layers" here count cell planes.
-int texture_groups(const Volume& v)
-{
-    const int cells = v.g.nz - 1;
-    if (v.tex_format == kF16Pair || v.tex_format == kI8Pair) return 1;
-    return (cells + kMaxLayers - 2) / (kMaxLayers - 1);
-}
-
-void texture_group(const Volume& v, int g, int* first, int* layers)
-{
-    if (v.tex_format == kF16Pair || v.tex_format == kI8Pair) {
-        *first = 0;
-        *layers = v.g.nz - 1;
-    } else {
-        *first = g * (kMaxLayers - 1);
-        *layers = std::min(kMaxLayers, v.g.nz - *first);
-    }
-}
 
 size_t brick_bytes(const VolumeGeom& g, int dtype)
 {
@@ -662,7 +616,7 @@ int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* sr
     cudaError_t e = vr::launch_pack(*v, z0, nplanes, dsrc, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "pack launch");
     v->mask_clip = NAN;               // masks are rebuilt by the next composite render
-    if (v->n_groups > 0)
+    if (v->has_tex)
         return refresh_texture(v, z0, z0 + nplanes, static_cast<cudaStream_t>(stream));
     return VR_OK;
 }
@@ -816,7 +770,7 @@ int vr_autotune(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
     if (rc) return rc;
     vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (v->n_groups == 0) {   // only the texture kernel has shapes to choose from
+    if (!v->has_tex) {   // only the texture kernel has shapes to choose from
         if (best_cfg) *best_cfg = v->cfg[mode];
         if (best_ms) *best_ms = -1.0f;
         return VR_OK;

@@ -38,11 +38,10 @@ __device__ __forceinline__ int find_request(const BatchParams& B, int item)
     return lo;
 }
 
-// The batched kernel serves any mix of storage types and modes in one
-// launch, so its march takes the mode, the storage type and the number of
-// texture groups as run-time values (uniform over a block: the branches on
-// them do not diverge) instead of template parameters; only the two fetch
-// paths, textures and bricks, are separate code.
+// Requests on volumes with texture storage run the single-view kernels'
+// march specialised per texel format, mode and plane stacking (one switch,
+// uniform over a block).  Requests on volumes without texture storage gather
+// from the bricks with the mode and storage type as run-time values.
 
 struct AccRT {
     float r = 0.0f, g = 0.0f, b = 0.0f, A = 0.0f, m;
@@ -74,93 +73,6 @@ struct AccRT {
     }
 };
 
-// One plane's 2 x 2 corners: float texels (f32, f16) or int8 codes decoded
-// with the plane's scale and offset.
-__device__ __forceinline__ float4 plane_rt(const BatchTex& T, int z, float x, float y, bool i8)
-{
-    const int g = T.n_groups > 1 ? min(z / (kMaxLayers - 1), T.n_groups - 1) : 0;
-    const cudaTextureObject_t t = T.tex[g];
-    const int l = z - g * (kMaxLayers - 1);
-    if (!i8) return ray::gather<VR_F32>(t, l, x, y);
-    const float4 q = ray::gather<VR_I8>(t, l, x, y);
-    const float sc = __ldg(T.scale + z), of = __ldg(T.offset + z);
-    return make_float4(fmaf(q.x, sc, of), fmaf(q.y, sc, of), fmaf(q.z, sc, of),
-                       fmaf(q.w, sc, of));
-}
-
-// Both planes of a cell: one gather for the pair formats, two otherwise.
-__device__ __forceinline__ void cell_rt(const BatchTex& T, int z, float x, float y, float4& c0,
-                                        float4& c1)
-{
-    if (T.format >= kF16Pair) {
-        const int sub = z & ((1 << T.stack_shift) - 1);
-        const uint4 p = ray::gather_u32(T.tex[0], z >> T.stack_shift, x,
-                                        y + (float)(sub * T.stack_pitch + 1));
-        if (T.format == kF16Pair) {
-            c0 = make_float4(ray::half_bits(p.x), ray::half_bits(p.y), ray::half_bits(p.z),
-                             ray::half_bits(p.w));
-            c1 = make_float4(ray::half_bits(p.x >> 16), ray::half_bits(p.y >> 16),
-                             ray::half_bits(p.z >> 16), ray::half_bits(p.w >> 16));
-        } else {
-            const float s0 = __ldg(T.scale + z), o0 = __ldg(T.offset + z);
-            const float s1 = __ldg(T.scale + z + 1), o1 = __ldg(T.offset + z + 1);
-            c0 = make_float4(fmaf(ray::code_lo(p.x), s0, o0), fmaf(ray::code_lo(p.y), s0, o0),
-                             fmaf(ray::code_lo(p.z), s0, o0), fmaf(ray::code_lo(p.w), s0, o0));
-            c1 = make_float4(fmaf(ray::code_hi(p.x), s1, o1), fmaf(ray::code_hi(p.y), s1, o1),
-                             fmaf(ray::code_hi(p.z), s1, o1), fmaf(ray::code_hi(p.w), s1, o1));
-        }
-    } else {
-        const bool i8 = T.format == VR_I8;
-        c0 = plane_rt(T, z, x, y, i8);
-        c1 = plane_rt(T, z + 1, x, y, i8);
-    }
-}
-
-__device__ __forceinline__ void next_rt(const BatchTex& T, const ray::Geo& c, const float4& c0,
-                                        const float4& c1, const ray::Geo& n, float4& n0,
-                                        float4& n1)
-{
-    if (n.gx == c.gx && n.gy == c.gy) {
-        if (n.iz == c.iz) {
-            n0 = c0;
-            n1 = c1;
-            return;
-        }
-        if (T.format < kF16Pair && n.iz == c.iz + 1) {
-            n0 = c1;
-            n1 = plane_rt(T, n.iz + 1, n.gx, n.gy, T.format == VR_I8);
-            return;
-        }
-    }
-    cell_rt(T, n.iz, n.gx, n.gy, n0, n1);
-}
-
-// Texture path: as ray::march_tex (pipelined one sample ahead, corners reused).
-__device__ __forceinline__ int march_tex_rt(const BatchReq& P, const BatchTex& T,
-                                            const float4* __restrict__ lut, const ray::Ray& r,
-                                            AccRT& acc)
-{
-    if (r.K <= 0) return 0;
-    int k = 0;
-    ray::Geo ga = ray::geo(P, r, 0.0f), gb;
-    float4 a0, a1, b0, b1;
-    cell_rt(T, ga.iz, ga.gx, ga.gy, a0, a1);
-    float kf = 1.0f;
-    for (;;) {
-        gb = ray::geo(P, r, kf);
-        next_rt(T, ga, a0, a1, gb, b0, b1);
-        ++k;
-        if (acc.add(P, lut, ray::interp(a0, a1, ga)) || k >= r.K) break;
-        kf += 1.0f;
-        ga = ray::geo(P, r, kf);
-        next_rt(T, gb, b0, b1, ga, a0, a1);
-        ++k;
-        if (acc.add(P, lut, ray::interp(b0, b1, gb)) || k >= r.K) break;
-        kf += 1.0f;
-    }
-    return k;
-}
-
 // Brick path: eight loads per sample (storage type at run time).
 __device__ __forceinline__ int march_bricks_rt(const BatchReq& P, const float4* __restrict__ lut,
                                                const ray::Ray& r, AccRT& acc)
@@ -188,15 +100,15 @@ __device__ __forceinline__ int march_bricks_rt(const BatchReq& P, const float4* 
 }
 
 // Texture path, specialised: the march of the single-view texture kernel for
-// one texel format, mode and group count (template parameters), so a block
-// renders its tile with exactly the code the per-view kernel runs.
-template <int DT, int MODE, bool MULTI>
+// one texel format, mode and plane stacking (template parameters), so a
+// block renders its tile with exactly the code the per-view kernel runs.
+template <int DT, int MODE, bool STACK>
 __device__ __forceinline__ unsigned tex_pixel(const BatchReq& q, const BatchTex& T,
                                               const float4* __restrict__ lut, int px, int py)
 {
     const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
     ray::Acc<MODE> acc;
-    const int k = ray::march_tex<DT, MODE, MULTI>(q, T, lut, r, acc);
+    const int k = ray::march_tex<DT, MODE, STACK>(q, T, lut, r, acc);
     const size_t pix = (size_t)py * q.w + px;
     if (MODE == VR_COMPOSITE)
         reinterpret_cast<float4*>(q.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);
@@ -205,24 +117,21 @@ __device__ __forceinline__ unsigned tex_pixel(const BatchReq& q, const BatchTex&
     return (unsigned)k;
 }
 
-// Kind of a textured request: (texel format, mode, more than one group).
-__host__ __device__ constexpr int tex_kind(int format, int mode, bool multi)
+// Kind of a textured request: (texel format, mode, stacked planes).
+__host__ __device__ constexpr int tex_kind(int format, int mode, bool stack)
 {
-    return (format * 3 + mode) * 2 + (multi ? 1 : 0);
+    return (format * 3 + mode) * 2 + (stack ? 1 : 0);
 }
 
 // One switch over the kinds (uniform over the block: a tile belongs to one
-// request); each case is the specialised march of one texel format and mode
-// for a volume held in one layered texture.  (Volumes whose plain-format
-// texture spans several layer groups go to their own launch with the
-// run-time dispatched march: specialising them here as well makes the
-// compiler merge the cases' code and spill.)
+// request); each case is the specialised march of one kind.
 __device__ __forceinline__ unsigned tex_pixel_any(const BatchReq& q, const BatchTex& T,
                                                   const float4* __restrict__ lut, int px, int py)
 {
-    switch (tex_kind(T.format, q.mode, T.n_groups > 1)) {
-#define VR_KIND(F, M) \
-    case tex_kind(F, M, false): return tex_pixel<F, M, false>(q, T, lut, px, py);
+    switch (tex_kind(T.format, q.mode, T.stack_shift > 0)) {
+#define VR_KIND(F, M)                                                              \
+    case tex_kind(F, M, false): return tex_pixel<F, M, false>(q, T, lut, px, py);  \
+    case tex_kind(F, M, true): return tex_pixel<F, M, true>(q, T, lut, px, py);
 #define VR_FORMAT(F) VR_KIND(F, VR_MIP) VR_KIND(F, VR_COMPOSITE) VR_KIND(F, VR_SUM)
         VR_FORMAT(VR_F32)
         VR_FORMAT(VR_F16)
@@ -236,9 +145,8 @@ __device__ __forceinline__ unsigned tex_pixel_any(const BatchReq& q, const Batch
 }
 
 // CLS (BatchClass): every request of the launch is of one class, so each
-// kernel instance compiles one fetch path: bricks (run-time storage type),
-// one layered texture (specialised per kind), several layer groups
-// (run-time dispatched texture march).
+// kernel instance compiles one fetch path: bricks (run-time storage type) or
+// texture (specialised per kind).
 template <int CLS>
 __global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(const __grid_constant__ BatchParams B,
                                                          unsigned* __restrict__ ws)
@@ -276,9 +184,7 @@ __global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(co
             } else {
                 const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
                 AccRT acc(q.mode);
-                count = CLS == kBatchTexGroups
-                            ? (unsigned)march_tex_rt(q, B.tex[q.tex_slot], s_lut, r, acc)
-                            : (unsigned)march_bricks_rt(q, s_lut, r, acc);
+                count = (unsigned)march_bricks_rt(q, s_lut, r, acc);
                 const size_t pix = (size_t)py * q.w + px;
                 if (q.mode == VR_COMPOSITE)
                     reinterpret_cast<float4*>(q.out)[pix] =
@@ -313,7 +219,6 @@ cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, int cls, 
     if (e != cudaSuccess) return e;
     switch (cls) {
     case kBatchTex: batch_kernel<kBatchTex><<<grid, kThreads, 0, s>>>(b, ws); break;
-    case kBatchTexGroups: batch_kernel<kBatchTexGroups><<<grid, kThreads, 0, s>>>(b, ws); break;
     default: batch_kernel<kBatchBricks><<<grid, kThreads, 0, s>>>(b, ws); break;
     }
     return cudaGetLastError();
@@ -325,9 +230,6 @@ int batch_blocks_per_sm(int cls)
     cudaError_t e =
         cls == kBatchTex
             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<kBatchTex>, kThreads, 0)
-        : cls == kBatchTexGroups
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<kBatchTexGroups>,
-                                                            kThreads, 0)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<kBatchBricks>,
                                                             kThreads, 0);
     if (e != cudaSuccess) {

@@ -15,8 +15,7 @@ constexpr int kBrick = VR_BRICK;                  // 32
 constexpr int kBrickShift = 5;
 constexpr int64_t kBrickVoxels = 32 * 32 * 32;    // 32768
 constexpr int kMaxViewsPerLaunch = 64;            // cameras travel as kernel parameters
-constexpr int kMaxLayers = 2048;                  // planes per layered texture
-constexpr int kMaxTexGroups = 8;                  // layered textures per volume
+constexpr int kMaxLayers = 2048;                  // layers of a layered texture
 // Texel formats of texture storage, also the storage codes the texture
 // kernels are specialised on: the plain storage types (VR_F32, VR_F16, VR_I8:
 // one voxel per texel) and the pair formats, where a texel packs a voxel with
@@ -55,13 +54,15 @@ struct Volume {
     float lut_step;
     float lut_corr[VR_MAX_LUT][4];
     bool lut_valid;
-    // optional texture storage (library-owned): planes in layered 2-D arrays
-    int n_groups;
+    // optional texture storage (library-owned): one layered 2-D texture,
+    // one plane (plain formats) or cell plane (pair formats) per 2-D slice,
+    // 2^stack_shift slices stacked per layer
+    bool has_tex;
     int tex_format;         // VR_F32 / VR_F16 / VR_I8, or kF16Pair / kI8Pair
-    cudaArray_t arrays[kMaxTexGroups];
-    cudaTextureObject_t tex[kMaxTexGroups];
-    int stack_shift;        // pair formats: 2^shift cell planes stacked per layer
-    int stack_pitch;        // rows per stacked cell plane (ny + 2)
+    cudaArray_t array;
+    cudaTextureObject_t tex;
+    int stack_shift;        // 0: a layer per slice
+    int stack_pitch;        // rows per stacked slice (ny + 2) when stacked
     int cfg[3];             // texture-kernel launch shape per mode (autotuned)
     // optional empty-space masks (caller-owned device buffer)
     unsigned long long* mask;   // valid for clip level mask_clip
@@ -71,9 +72,8 @@ struct Volume {
 
 // Texture storage as the texture kernels see it.
 struct TexParams {
-    cudaTextureObject_t tex[kMaxTexGroups];
-    int n_groups;
-    int stack_shift, stack_pitch;   // pair formats (see Volume)
+    cudaTextureObject_t tex;
+    int stack_shift, stack_pitch;   // see Volume
     const float* scale;     // VR_I8 only
     const float* offset;
     int k_max;
@@ -112,9 +112,8 @@ constexpr int kMaxBatchLut = 2;                // distinct corrected tables per 
 constexpr int kBatchWords = 1 + kMaxBatch;
 
 struct BatchTex {
-    cudaTextureObject_t tex[kMaxTexGroups];
-    int n_groups;
-    int stack_shift, stack_pitch;   // pair formats (see Volume)
+    cudaTextureObject_t tex;
+    int stack_shift, stack_pitch;   // see Volume
     int format;            // texel format (see kF16Pair)
     const float* scale;
     const float* offset;
@@ -150,10 +149,8 @@ struct BatchParams {
 };
 
 // Launch classes of the batched kernel: requests on volumes without texture
-// storage, on volumes held in one layered texture, and on volumes whose
-// texture spans several layer groups (plain formats with more than 2049
-// planes), each compiled as its own kernel.
-enum BatchClass { kBatchBricks = 0, kBatchTex = 1, kBatchTexGroups = 2 };
+// storage and on volumes with it, each compiled as its own kernel.
+enum BatchClass { kBatchBricks = 0, kBatchTex = 1 };
 cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, int cls, cudaStream_t s);
 int batch_blocks_per_sm(int cls);
 int batch_with_counters(const vr_request* reqs, int n, unsigned* counters, cudaStream_t s);
@@ -196,12 +193,10 @@ cudaError_t launch_tex_i8pair(const MarchParams& p, const TexParams& t, int mode
 cudaError_t launch_masks(const Volume& v, float clip, cudaStream_t s);
 int tex_shape_count();
 void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb);
-cudaError_t fill_texture_group(const Volume& v, cudaSurfaceObject_t surf, int layer0, int z0,
-                               int z1, cudaStream_t s);
-// First plane (plain formats) or cell (pair formats) of texture group g,
-// and the number of layers it holds.
-void texture_group(const Volume& v, int g, int* first, int* layers);
-int texture_groups(const Volume& v);
+// Copy planes (plain formats) or cell planes (pair formats) [z0, z1) from
+// the bricks into the volume's texture through surface `surf`.
+cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int z0, int z1,
+                         cudaStream_t s);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
                         cudaStream_t s);
 

@@ -119,7 +119,7 @@ __device__ __forceinline__ Ray setup_ray(const PP& P, const vr_camera& c, int px
 }
 
 // Decode int8 codes of plane z (scale/offset); identity for float storage.
-// TT supplies tex[], n_groups, scale and offset.
+// TT supplies tex, stack_shift, stack_pitch, scale and offset.
 template <int DT, typename TT>
 __device__ __forceinline__ float4 decode(const TT& T, float4 q, int z)
 {
@@ -148,43 +148,35 @@ __device__ __forceinline__ float code_hi(unsigned b)
     return (float)(signed char)((b >> 8) & 0xffu);
 }
 
-// Texture handles of a volume's layer groups, per block in shared memory:
-// a kernel that marches a volume with several groups fills this table
-// (fill_group_table) before the march.  Reading a handle by the run-time
-// group index from shared memory keeps the handles out of registers and
-// out of local memory.
-__device__ __forceinline__ cudaTextureObject_t* group_table()
+// Layer and row offset of plane z (plain formats) or cell plane z (pair
+// formats) of a volume's texture.  Unstacked (a layer per plane): layer z,
+// rows as stored.  Stacked: 2^shift planes per layer, plane z at sub-plane
+// z & (2^shift - 1) of layer z >> shift, whose ny data rows start at row
+// sub * pitch + 1 (rows sub * pitch and sub * pitch + ny + 1 copy its first
+// and last rows, so a gather one row outside the data reads the edge row as
+// the texture's clamp addressing does for an unstacked layer).
+// Returns the layer; `yt` is the gather's y coordinate y in that layer.
+template <bool STACK, typename TT>
+__device__ __forceinline__ int plane_layer(const TT& T, int z, float y, float& yt)
 {
-    __shared__ cudaTextureObject_t s_group_tex[kMaxTexGroups];
-    return s_group_tex;
-}
-
-// Called by every thread of the block; ends with a barrier.
-template <typename TT>
-__device__ __forceinline__ void fill_group_table(const TT& T)
-{
-    if (threadIdx.x < kMaxTexGroups) group_table()[threadIdx.x] = T.tex[threadIdx.x];
-    __syncthreads();
-}
-
-template <typename TT>
-__device__ __forceinline__ cudaTextureObject_t group_tex(const TT&, int g)
-{
-    return group_table()[g];
+    if (!STACK) {
+        yt = y;
+        return z;
+    }
+    yt = y + (float)((z & ((1 << T.stack_shift) - 1)) * T.stack_pitch + 1);
+    return z >> T.stack_shift;
 }
 
 // The two planes z and z + 1 of the cell whose x/y corner is texel (x-1, y-1).
-// Pair formats: one gather of layer z (cell plane) holds both planes.
-template <int DT, bool MULTI, typename TT>
+// Pair formats: one gather of cell plane z holds both planes.
+template <int DT, bool STACK, typename TT>
 __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z, float x,
                                      float y, float4& q0, float4& q1)
 {
+    float yt;
+    const int l = plane_layer<STACK>(T, z, y, yt);
     if constexpr (DT == kF16Pair || DT == kI8Pair) {
-        // one texture; cell plane z is sub-plane z & (2^shift - 1) of layer
-        // z >> shift, whose data rows start at row sub * pitch + 1
-        const int sub = z & ((1 << T.stack_shift) - 1);
-        const uint4 p = gather_u32(t0, z >> T.stack_shift, x,
-                                   y + (float)(sub * T.stack_pitch + 1));
+        const uint4 p = gather_u32(t0, l, x, yt);
         if constexpr (DT == kF16Pair) {
             q0 = make_float4(half_bits(p.x), half_bits(p.y), half_bits(p.z), half_bits(p.w));
             q1 = make_float4(half_bits(p.x >> 16), half_bits(p.y >> 16), half_bits(p.z >> 16),
@@ -198,19 +190,10 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
                              fmaf(code_hi(p.z), s1, o1), fmaf(code_hi(p.w), s1, o1));
         }
     } else {
-        if (!MULTI) {
-            q0 = gather<DT>(t0, z, x, y);
-            q1 = gather<DT>(t0, z + 1, x, y);
-        } else {
-            // plane pair (z, z + 1) lies in group min(z / (L-1), last)
-            const int g = min(z / (kMaxLayers - 1), T.n_groups - 1);
-            const cudaTextureObject_t t = group_tex(T, g);
-            const int l = z - g * (kMaxLayers - 1);
-            q0 = gather<DT>(t, l, x, y);
-            q1 = gather<DT>(t, l + 1, x, y);
-        }
-        q0 = decode<DT>(T, q0, z);
-        q1 = decode<DT>(T, q1, z + 1);
+        float yt1;
+        const int l1 = plane_layer<STACK>(T, z + 1, y, yt1);
+        q0 = decode<DT>(T, gather<DT>(t0, l, x, yt), z);
+        q1 = decode<DT>(T, gather<DT>(t0, l1, x, yt1), z + 1);
     }
 }
 
@@ -219,7 +202,7 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
 // texels, one plane when only z moved by one, both planes otherwise.  The
 // texture return path is what bounds this kernel, so every gather saved
 // counts.
-template <int DT, bool MULTI, typename TT, typename G>
+template <int DT, bool STACK, typename TT, typename G>
 __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, const G& c,
                                           const float4& c0, const float4& c1, const G& n,
                                           float4& n0, float4& n1)
@@ -232,19 +215,15 @@ __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, c
         }
         if constexpr (DT != kF16Pair && DT != kI8Pair) {
             if (n.iz == c.iz + 1) {
-                float4 u0, u1;
+                float yt;
+                const int l = plane_layer<STACK>(T, n.iz + 1, n.gy, yt);
                 n0 = c1;
-                if (!MULTI) {
-                    n1 = decode<DT>(T, gather<DT>(t0, n.iz + 1, n.gx, n.gy), n.iz + 1);
-                } else {
-                    cell<DT, MULTI>(T, t0, n.iz, n.gx, n.gy, u0, u1);
-                    n1 = u1;
-                }
+                n1 = decode<DT>(T, gather<DT>(t0, l, n.gx, yt), n.iz + 1);
                 return;
             }
         }
     }
-    cell<DT, MULTI>(T, t0, n.iz, n.gx, n.gy, n0, n1);
+    cell<DT, STACK>(T, t0, n.iz, n.gx, n.gy, n0, n1);
 }
 
 // Per-sample geometry: the gather coordinates of the cell and the weights.
@@ -345,7 +324,7 @@ __device__ __forceinline__ int macro_of(const PP& P, const Geo& g, int& bit)
 // step costs the geometry alone.  Masks are loaded one sample ahead of the
 // gathers, gathers one sample ahead of the interpolation.  The result and
 // the sample count are those of march_tex.
-template <int DT, int MODE, bool MULTI, typename PP, typename TT>
+template <int DT, int MODE, bool STACK, typename PP, typename TT>
 __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
                                               const float4* __restrict__ lut, const Ray& r,
                                               Acc<MODE>& acc)
@@ -353,7 +332,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
     static_assert(MODE == VR_COMPOSITE, "skipping is for compositing");
     using Rec = unsigned long long;
     if (r.K <= 0) return 0;
-    const cudaTextureObject_t t0 = T.tex[0];
+    const cudaTextureObject_t t0 = T.tex;
     int k = 0;
     // g0: sample k (corners a, present iff n0); g1: sample k + 1 (record rX,
     // macrocell mX, cell bit b1)
@@ -365,7 +344,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
     Rec rX = (mX == m0) ? r0 : __ldg(P.mask + mX), rY;
     bool n0 = acc.need(r0, b0);
     float4 a0, a1, c0, c1;
-    if (n0) cell<DT, MULTI>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
+    if (n0) cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
     float kf = 2.0f;
     for (;;) {
         // sample k + 2: geometry and record; sample k + 1: gathers; sample k
@@ -376,9 +355,9 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
         const bool n1 = acc.need(rX, b1);
         if (n1) {
             if (n0)
-                next_cell<DT, MULTI>(T, t0, g0, a0, a1, g1, c0, c1);
+                next_cell<DT, STACK>(T, t0, g0, a0, a1, g1, c0, c1);
             else
-                cell<DT, MULTI>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
+                cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
         }
         ++k;
         if ((n0 && acc.add(P, lut, interp(a0, a1, g0))) || k >= r.K) break;
@@ -392,9 +371,9 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
         const bool n2 = acc.need(rY, b2);
         if (n2) {
             if (n1)
-                next_cell<DT, MULTI>(T, t0, g1, c0, c1, g2, a0, a1);
+                next_cell<DT, STACK>(T, t0, g1, c0, c1, g2, a0, a1);
             else
-                cell<DT, MULTI>(T, t0, g2.iz, g2.gx, g2.gy, a0, a1);
+                cell<DT, STACK>(T, t0, g2.iz, g2.gx, g2.gy, a0, a1);
         }
         ++k;
         if ((n1 && acc.add(P, lut, interp(c0, c1, g1))) || k >= r.K) break;
@@ -412,25 +391,25 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
 // loop is unrolled twice with two register sets that swap roles, so a
 // pending gather result is only copied when the next sample reuses it.
 // Returns the number of samples evaluated.
-template <int DT, int MODE, bool MULTI, typename PP, typename TT>
+template <int DT, int MODE, bool STACK, typename PP, typename TT>
 __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4* __restrict__ lut,
                                          const Ray& r, Acc<MODE>& acc)
 {
     int k = 0;
     if (r.K <= 0) return 0;
-    const cudaTextureObject_t t0 = T.tex[0];
+    const cudaTextureObject_t t0 = T.tex;
     Geo ga = geo(P, r, 0.0f), gb;
     float4 a0, a1, b0, b1;
-    cell<DT, MULTI>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
+    cell<DT, STACK>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
     float kf = 1.0f;
     for (;;) {
         gb = geo(P, r, kf);
-        next_cell<DT, MULTI>(T, t0, ga, a0, a1, gb, b0, b1);
+        next_cell<DT, STACK>(T, t0, ga, a0, a1, gb, b0, b1);
         ++k;
         if (acc.add(P, lut, interp(a0, a1, ga)) || k >= r.K) break;
         kf += 1.0f;
         ga = geo(P, r, kf);
-        next_cell<DT, MULTI>(T, t0, gb, b0, b1, ga, a0, a1);
+        next_cell<DT, STACK>(T, t0, gb, b0, b1, ga, a0, a1);
         ++k;
         if (acc.add(P, lut, interp(b0, b1, gb)) || k >= r.K) break;
         kf += 1.0f;

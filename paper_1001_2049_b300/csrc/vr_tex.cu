@@ -2,9 +2,8 @@
 // layered textures, the texel-format dispatch of the texture-gather march
 // (the kernel itself: vr_tex_kernel.cuh) and the launch-shape table.
 //
-// Layers: a layered texture holds at most kMaxLayers planes, so the cube is
-// split into groups of planes [g*(L-1), g*(L-1) + L) that overlap by one
-// plane; the plane pair (z0, z0 + 1) always lies in one group.
+// Layers: a layered texture holds at most kMaxLayers layers, so deeper cubes
+// stack 2^shift planes per layer (see write_slice_row).
 #include <type_traits>
 
 #include <cuda_fp16.h>
@@ -15,11 +14,32 @@
 namespace vr {
 namespace {
 
-// Copy planes [z0, z1) from the bricks into texture group g (surface writes).
+// Plane (plain formats) or cell plane (pair formats) z of the texture is 2-D
+// slice z & (2^shift - 1) of layer z >> shift.  Unstacked (shift 0) a slice
+// is the ny rows of data; stacked, a slice spans `pitch` = ny + 2 rows: a
+// copy of data row 0, the ny data rows, a copy of data row ny - 1, so a
+// gather one row outside the data reads the edge row exactly as the
+// texture's clamp addressing does for an unstacked layer.
+template <typename W>
+__device__ __forceinline__ void write_slice_row(cudaSurfaceObject_t surf, W v, int x, int y,
+                                                int z, int ny, int shift, int pitch)
+{
+    const int layer = z >> shift;
+    if (shift == 0) {
+        surf2DLayeredwrite(v, surf, x * (int)sizeof(W), y, layer);
+        return;
+    }
+    const int base = (z & ((1 << shift) - 1)) * pitch + 1;
+    surf2DLayeredwrite(v, surf, x * (int)sizeof(W), base + y, layer);
+    if (y == 0) surf2DLayeredwrite(v, surf, x * (int)sizeof(W), base - 1, layer);
+    if (y == ny - 1) surf2DLayeredwrite(v, surf, x * (int)sizeof(W), base + ny, layer);
+}
+
+// Plain formats: planes [z0, z1) of the bricks into the texture.
 template <typename T>
 __global__ void __launch_bounds__(256) fill_kernel(const T* __restrict__ bricks, VolumeGeom g,
-                                                   cudaSurfaceObject_t surf, int layer0, int z0,
-                                                   int z1)
+                                                   cudaSurfaceObject_t surf, int z0, int z1,
+                                                   int shift, int pitch)
 {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -28,16 +48,12 @@ __global__ void __launch_bounds__(256) fill_kernel(const T* __restrict__ bricks,
         const size_t brick = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) * g.nbx +
                              (x >> kBrickShift);
         const T v = bricks[brick * kBrickVoxels + ((z & 31) << 10) + ((y & 31) << 5) + (x & 31)];
-        surf2DLayeredwrite(v, surf, x * (int)sizeof(T), y, z - layer0);
+        write_slice_row(surf, v, x, y, z, g.ny, shift, pitch);
     }
 }
 
-// Pair formats: cell plane c (the voxels of planes c and c + 1 packed into one
-// texel, low bits plane c) is sub-plane c & (2^shift - 1) of layer c >> shift.
-// A sub-plane spans `pitch` = ny + 2 rows: a copy of data row 0, the ny data
-// rows, a copy of data row ny - 1, so a gather one row outside the data
-// (positions a rounding error outside a y face) reads the edge row exactly as
-// the texture's clamp addressing does for plain formats.
+// Pair formats: cell planes [c0, c1), each texel the voxels of planes c and
+// c + 1 packed (low bits plane c).
 template <typename T, typename W>
 __global__ void __launch_bounds__(256) fill_pair_kernel(const T* __restrict__ bricks, VolumeGeom g,
                                                         cudaSurfaceObject_t surf, int c0, int c1,
@@ -56,11 +72,7 @@ __global__ void __launch_bounds__(256) fill_pair_kernel(const T* __restrict__ br
         const W packed = (W)((W)(unsigned)(typename std::make_unsigned<T>::type)lo |
                              ((W)(unsigned)(typename std::make_unsigned<T>::type)hi
                               << (8 * sizeof(T))));
-        const int layer = c >> shift;
-        const int base = (c & ((1 << shift) - 1)) * pitch + 1;
-        surf2DLayeredwrite(packed, surf, x * (int)sizeof(W), base + y, layer);
-        if (y == 0) surf2DLayeredwrite(packed, surf, x * (int)sizeof(W), base - 1, layer);
-        if (y == g.ny - 1) surf2DLayeredwrite(packed, surf, x * (int)sizeof(W), base + g.ny, layer);
+        write_slice_row(surf, packed, x, y, c, g.ny, shift, pitch);
     }
 }
 
@@ -91,32 +103,33 @@ void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb)
     *minb = sh.minb;
 }
 
-cudaError_t fill_texture_group(const Volume& v, cudaSurfaceObject_t surf, int layer0, int z0,
-                               int z1, cudaStream_t s)
+cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int z0, int z1, cudaStream_t s)
 {
+    if (z1 <= z0) return cudaSuccess;
     dim3 grid((unsigned)((v.g.nx + 31) / 32), (unsigned)((v.g.ny + 7) / 8),
               (unsigned)((z1 - z0) < 1024 ? (z1 - z0) : 1024));
+    const int sh = v.stack_shift, pt = v.stack_pitch;
     if (v.tex_format == kF16Pair) {
         fill_pair_kernel<unsigned short, unsigned int><<<grid, 256, 0, s>>>(
-            (const unsigned short*)v.bricks, v.g, surf, z0, z1, v.stack_shift, v.stack_pitch);
+            (const unsigned short*)v.bricks, v.g, surf, z0, z1, sh, pt);
         return cudaGetLastError();
     }
     if (v.tex_format == kI8Pair) {
         fill_pair_kernel<signed char, unsigned short><<<grid, 256, 0, s>>>(
-            (const signed char*)v.bricks, v.g, surf, z0, z1, v.stack_shift, v.stack_pitch);
+            (const signed char*)v.bricks, v.g, surf, z0, z1, sh, pt);
         return cudaGetLastError();
     }
     switch (v.dtype) {
     case VR_F32:
-        fill_kernel<float><<<grid, 256, 0, s>>>((const float*)v.bricks, v.g, surf, layer0, z0, z1);
+        fill_kernel<float><<<grid, 256, 0, s>>>((const float*)v.bricks, v.g, surf, z0, z1, sh, pt);
         break;
     case VR_F16:   // binary16 bit patterns moved as 16-bit words
         fill_kernel<unsigned short><<<grid, 256, 0, s>>>((const unsigned short*)v.bricks, v.g,
-                                                         surf, layer0, z0, z1);
+                                                         surf, z0, z1, sh, pt);
         break;
     default:
-        fill_kernel<signed char><<<grid, 256, 0, s>>>((const signed char*)v.bricks, v.g, surf,
-                                                      layer0, z0, z1);
+        fill_kernel<signed char><<<grid, 256, 0, s>>>((const signed char*)v.bricks, v.g, surf, z0,
+                                                      z1, sh, pt);
         break;
     }
     return cudaGetLastError();

@@ -39,7 +39,7 @@ constexpr Shape kShapes[] = {
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-template <int DT, int MODE, bool MULTI, int CFG, bool SKIP>
+template <int DT, int MODE, bool STACK, int CFG, bool SKIP>
 __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG].minb)
     tex_kernel(const __grid_constant__ MarchParams P, const __grid_constant__ TexParams T)
 {
@@ -49,7 +49,6 @@ __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG
         for (int i = threadIdx.x; i < P.n_lut; i += blockDim.x) s_lut[i] = P.lut[i];
         __syncthreads();
     }
-    if (MULTI) ray::fill_group_table(T);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int wpr = S.bx / S.px;                 // warps per block row
     const int px = blockIdx.x * S.bx + (warp % wpr) * S.px + (lane % S.px);
@@ -61,9 +60,9 @@ __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG
         const ray::Ray r = ray::setup_ray(P, P.cams[view], px, py, T.k_max);
         ray::Acc<MODE> acc;
         if constexpr (SKIP)
-            count = (unsigned)ray::march_tex_lock<DT, MODE, MULTI>(P, T, s_lut, r, acc);
+            count = (unsigned)ray::march_tex_lock<DT, MODE, STACK>(P, T, s_lut, r, acc);
         else
-            count = (unsigned)ray::march_tex<DT, MODE, MULTI>(P, T, s_lut, r, acc);
+            count = (unsigned)ray::march_tex<DT, MODE, STACK>(P, T, s_lut, r, acc);
         const size_t pix = ((size_t)view * P.h + py) * P.w + px;
         if (MODE == VR_COMPOSITE)
             reinterpret_cast<float4*>(P.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);
@@ -76,7 +75,7 @@ __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG
     }
 }
 
-template <int DT, int MODE, bool MULTI, int CFG>
+template <int DT, int MODE, bool STACK, int CFG>
 cudaError_t launch_c(const MarchParams& p, const TexParams& t, cudaStream_t s)
 {
     // skipping is for COMPOSITE (the clip makes most cells transparent); a
@@ -89,22 +88,22 @@ cudaError_t launch_c(const MarchParams& p, const TexParams& t, cudaStream_t s)
     dim3 grid((unsigned)((p.w + S.bx - 1) / S.bx), (unsigned)((p.h + S.by - 1) / S.by),
               (unsigned)p.n_views);
     if (kCanSkip && p.mask != nullptr)
-        tex_kernel<DT, MODE, MULTI, CFG, kCanSkip><<<grid, S.bx * S.by, 0, s>>>(p, t);
+        tex_kernel<DT, MODE, STACK, CFG, kCanSkip><<<grid, S.bx * S.by, 0, s>>>(p, t);
     else
-        tex_kernel<DT, MODE, MULTI, CFG, false><<<grid, S.bx * S.by, 0, s>>>(p, t);
+        tex_kernel<DT, MODE, STACK, CFG, false><<<grid, S.bx * S.by, 0, s>>>(p, t);
     return cudaGetLastError();
 }
 
-template <int DT, int MODE, bool MULTI>
+template <int DT, int MODE, bool STACK>
 cudaError_t launch_m(const MarchParams& p, const TexParams& t, int cfg, cudaStream_t s)
 {
     switch (cfg) {
-    case 1: return launch_c<DT, MODE, MULTI, 1>(p, t, s);
-    case 2: return launch_c<DT, MODE, MULTI, 2>(p, t, s);
-    case 3: return launch_c<DT, MODE, MULTI, 3>(p, t, s);
-    case 4: return launch_c<DT, MODE, MULTI, 4>(p, t, s);
-    case 5: return launch_c<DT, MODE, MULTI, 5>(p, t, s);
-    default: return launch_c<DT, MODE, MULTI, 0>(p, t, s);
+    case 1: return launch_c<DT, MODE, STACK, 1>(p, t, s);
+    case 2: return launch_c<DT, MODE, STACK, 2>(p, t, s);
+    case 3: return launch_c<DT, MODE, STACK, 3>(p, t, s);
+    case 4: return launch_c<DT, MODE, STACK, 4>(p, t, s);
+    case 5: return launch_c<DT, MODE, STACK, 5>(p, t, s);
+    default: return launch_c<DT, MODE, STACK, 0>(p, t, s);
     }
 }
 static_assert(kNumShapes == 6, "launch_m lists every shape");
@@ -112,8 +111,8 @@ static_assert(kNumShapes == 6, "launch_m lists every shape");
 template <int DT, int MODE>
 cudaError_t launch_t(const MarchParams& p, const TexParams& t, int cfg, cudaStream_t s)
 {
-    return t.n_groups > 1 ? launch_m<DT, MODE, true>(p, t, cfg, s)
-                          : launch_m<DT, MODE, false>(p, t, cfg, s);
+    return t.stack_shift > 0 ? launch_m<DT, MODE, true>(p, t, cfg, s)
+                             : launch_m<DT, MODE, false>(p, t, cfg, s);
 }
 
 template <int DT>

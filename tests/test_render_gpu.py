@@ -228,8 +228,8 @@ def test_texture_path_axis_views_and_misses():
                    what="tex axis views " + mode, tex=True)
 
 
-def test_texture_path_spans_several_layer_groups():
-    # more planes than one layered texture holds: groups overlap by a plane
+def test_texture_path_stacks_planes_of_deep_cubes():
+    # more planes than a layered texture has layers: 4 planes per layer
     dims = (6, 5, 4500)
     cube = synth.make_cube(dims, 20, ("uniform", 3.0, 8.0), 31).numpy()
     recs = [synth.axis_camera(dims, 8, 8, axis=2, spacing=(0.7, 0.6)),
@@ -260,7 +260,7 @@ def test_pair_texture_ragged_cubes(dims, step, dtype):
                    what="pair ragged %s %s %s" % (dims, dtype, mode), tex="pair")
 
 
-def test_pair_texture_spans_several_layer_groups():
+def test_pair_texture_stacks_cell_planes_of_deep_cubes():
     dims = (6, 5, 4500)
     cube = synth.make_cube(dims, 20, ("uniform", 3.0, 8.0), 31).numpy()
     recs = [synth.axis_camera(dims, 8, 8, axis=2, spacing=(0.7, 0.6)),
@@ -472,7 +472,7 @@ def _decoded(cube, dtype):
             + of.astype(np.float64)[:, None, None]).astype(np.float32)
 
 
-MASK_DIMS = [(37, 45, 70), (2, 2, 2), (6, 5, 9), (64, 3, 33)]
+MASK_DIMS = [(37, 45, 70), (2, 2, 2), (6, 5, 9), (64, 3, 33), (6, 5, 4500)]
 
 
 @pytest.mark.parametrize("dims", MASK_DIMS)
