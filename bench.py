@@ -295,46 +295,76 @@ def batched_leg(dev, reps=3):
     return res
 
 
-def serving_leg(dev, rates=(50.0, 200.0), duration=2.0):
-    """Poisson arrivals of random requests (random direction, resolution
-    512^2..1920x1080, 80 % composite, clip U[2,5] sigma) over the resident
-    cubes of the batched leg, served with continuous batching (reduced
-    precision storage, textures) and, for comparison, one request at a time
-    on the plain FP32 path."""
-    from paper_1001_2049_b300.serve import RenderJob, Server, latency_stats, run_poisson
-    lut = synth.default_lut()
-    served, plain, dims = {}, {}, {}
-    for i, (name, d, dt) in enumerate(synth.BATCH_CUBES):
-        cube = synth.batch_cube(i, dev)
-        v = Volume(cube, dt)
-        v.attach_pair_texture() if dt != "f32" else v.attach_texture()
-        v.set_transfer(lut, 3.0, 50.0, 3.0, 0.99)
-        p = Volume(cube, "f32")
-        p.attach_texture()
-        p.set_transfer(lut, 3.0, 50.0, 3.0, 0.99)
-        del cube
-        served[name], plain[name], dims[name] = v, p, d
-    names = sorted(served)
-    out = {"cubes": names, "duration_s": duration, "rates": {}}
-    for rate in rates:
-        row = {}
-        for label, vols, mb, ns in (("continuous_batching", served, 64, 2),
-                                    ("plain_f32_one_at_a_time", plain, 1, 1)):
-            rng = np.random.default_rng(synth.SERVE_SEED + int(rate))
+def _served_volume(i, dt, dev):
+    """Served cube i stored as ``dt`` with texture storage only (built slab
+    by slab through one brick buffer, which is freed afterwards)."""
+    name, dims = synth.SERVE_CUBES[i]
+    v = Volume(dims=dims, dtype=dt, device=dev)
+    for z0, slab in synth.serve_cube_slabs(i, dev):
+        v.upload(z0, slab)
+        del slab
+    v.attach_texture()
+    v.drop_bricks()
+    v.set_transfer(synth.default_lut(), 3.0, 50.0, 3.0, 0.99)
+    return v
 
-            def make(i):
-                name = names[int(rng.integers(0, len(names)))]
-                cam, w, h, mode, tf = synth.serve_request(dims[name], rng)
-                return RenderJob(name, cam, w, h, mode, 0.5, tf)
-            server = Server(vols, mem_budget=8 << 30, max_batch=mb, streams=ns)
-            done, wall, n = run_poisson(server, make, rate, duration, seed=int(rate))
-            st = latency_stats(done)
-            st["throughput_req_s"] = n / wall
-            st["launches"] = server.launches
-            row[label] = st
-        out["rates"][str(int(rate))] = row
-    for v in list(served.values()) + list(plain.values()):
+
+def _serve(vols, names, rate, duration, batched, seed):
+    from paper_1001_2049_b300.serve import RenderJob, Server, latency_stats, run_poisson
+    rng = np.random.default_rng(seed)
+    dims = {n: vols[n].dims for n in names}
+
+    def make(i):
+        name = names[int(rng.integers(0, len(names)))]
+        cam, w, h, mode, tf = synth.serve_request(dims[name], rng)
+        return RenderJob(name, cam, w, h, mode, 0.5, tf)
+    server = (Server(vols, mem_budget=8 << 30, max_batch=64, streams=2) if batched else
+              Server(vols, mem_budget=8 << 30, max_batch=1, streams=1, per_request=True))
+    done, wall, n = run_poisson(server, make, rate, duration, seed=seed)
+    st = latency_stats(done)
+    st["throughput_req_s"] = n / wall
+    st["launches"] = server.launches
+    return st
+
+
+def serving_leg(dev, rates=(50.0, 100.0, 200.0, 500.0), duration=3.0):
+    """The served workload: Poisson arrivals of random requests (a random
+    direction, a resolution from 512^2 to 1920x1080, 80 % composite, clip
+    U[2,5] sigma) over six resident cubes (four 2048x2048x4096 and two
+    1024^3, FP16, texture storage only: 146 GB of cube data), served with
+    continuous batching.  Head to head with the plain FP32 path (one
+    single-view render per request) on the cubes whose FP32 copies fit
+    together in memory (two large, two small): the same request streams on
+    those four cubes, served both ways."""
+    t0 = time.perf_counter()
+    names = [n for n, _ in synth.SERVE_CUBES]
+    sub = [names[0], names[1], names[4], names[5]]
+    vols = {n: _served_volume(i, "f16", dev) for i, n in enumerate(names)}
+    torch.cuda.synchronize()
+    build_f16 = time.perf_counter() - t0
+    out = {"cubes": names, "storage": "f16 layered textures, bricks dropped",
+           "resident_cube_bytes": sum(2 * d[0] * d[1] * d[2] for _, d in synth.SERVE_CUBES),
+           "duration_s_per_rate": duration, "build_s": build_f16, "rates": {},
+           "head_to_head": {"cubes": sub, "rates": {}}}
+    for rate in rates:
+        out["rates"][str(int(rate))] = _serve(vols, names, rate, duration, True,
+                                             synth.SERVE_SEED + int(rate))
+        out["head_to_head"]["rates"][str(int(rate))] = {
+            "continuous_batching_f16": _serve(vols, sub, rate, duration, True,
+                                              synth.SERVE_SEED + 1000 + int(rate))}
+    for v in vols.values():
         v.close()
+    del vols
+    torch.cuda.empty_cache()
+    f32 = {n: _served_volume(names.index(n), "f32", dev) for n in sub}
+    for rate in rates:
+        out["head_to_head"]["rates"][str(int(rate))]["plain_f32_per_request"] = _serve(
+            f32, sub, rate, duration, False, synth.SERVE_SEED + 1000 + int(rate))
+    for v in f32.values():
+        v.close()
+    del f32
+    torch.cuda.empty_cache()
+    out["total_s"] = time.perf_counter() - t0
     return out
 
 

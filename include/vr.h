@@ -213,6 +213,18 @@ int vr_volume_attach_pair_texture(vr_volume vol, void* stream);
  * bricks).  The caller must make sure no render using it is pending.       */
 int vr_volume_detach_texture(vr_volume vol);
 
+/* Keep only the texture storage: after this call the volume renders from
+ * its texture alone and never reads the brick buffer again, which the
+ * caller may free once the work already queued on it has completed (the
+ * call itself does no device work).  For VR_F32 and VR_F16 volumes with
+ * texture storage (int8 volumes keep their per-plane tables in the brick
+ * buffer: VR_ERR_UNSUPPORTED).  Afterwards the volume is read-only:
+ * vr_volume_upload, vr_volume_detach_texture, vr_volume_attach_masks and a
+ * change of texture format return VR_ERR_UNSUPPORTED; its empty-space masks
+ * are detached.  No counterpart in the paper: it keeps cubes resident whose
+ * bricks and texture would not both fit, e.g. several 32 GiB FP16 cubes.    */
+int vr_volume_drop_bricks(vr_volume vol);
+
 /* ---- many requests in one persistent launch ------------------------------
  * The paper's scheduler maps available tasks onto the computing resources
  * (Fig. 1 caption; §3.1 module 1).  Here the tasks are the 16 x 16 ray tiles

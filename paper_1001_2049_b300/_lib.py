@@ -36,6 +36,7 @@ SIGNATURES = {
     "vr_volume_attach_masks": (c_int, [c_void_p, c_void_p, c_size_t]),
     "vr_volume_attach_pair_texture": (c_int, [c_void_p, c_void_p]),
     "vr_volume_detach_texture": (c_int, [c_void_p]),
+    "vr_volume_drop_bricks": (c_int, [c_void_p]),
     "vr_volume_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int),
                                ctypes.POINTER(c_void_p)]),
     "vr_batch_workspace_bytes": (c_size_t, []),

@@ -89,7 +89,7 @@ def render_batch(requests, workspace: torch.Tensor | None = None, stream=None):
         shape = (rq.h, rq.w, 4) if m == VR_COMPOSITE else (rq.h, rq.w)
         out = rq.out
         if out is None:
-            out = torch.empty(shape, dtype=torch.float32, device=rq.volume.buffer.device)
+            out = torch.empty(shape, dtype=torch.float32, device=rq.volume.device)
         elif tuple(out.shape[-len(shape):]) != shape or out.numel() != int(np.prod(shape)):
             raise ValueError("request %d: out must hold %s floats" % (i, shape))
         outs.append(out)
@@ -162,6 +162,7 @@ class Volume:
         self.nbytes = volume_bytes(self.dims, dtype)
         dev = device if device is not None else (
             cube.device if cube is not None and cube.is_cuda else torch.device("cuda"))
+        self.device = torch.device(dev)
         self.buffer = torch.empty(self.nbytes, dtype=torch.uint8, device=dev)
         handle = ctypes.c_void_p(0)
         src, on_dev = None, 1
@@ -199,6 +200,15 @@ class Volume:
     def detach_texture(self):
         check(load().vr_volume_detach_texture(self._h))
 
+    def drop_bricks(self, stream=None):
+        """Keep only the texture storage and free the brick buffer (after the
+        work queued on ``stream`` has finished); the volume becomes
+        read-only."""
+        check(load().vr_volume_drop_bricks(self._h))
+        (stream or torch.cuda.current_stream(self.device)).synchronize()
+        self.buffer = None
+        self._keep = None
+
     def mask_bytes(self) -> int:
         n = ctypes.c_size_t(0)
         check(load().vr_volume_mask_bytes(self._h, ctypes.byref(n)))
@@ -209,7 +219,7 @@ class Volume:
         device buffer kept by this object): composite renders then skip the
         samples the clip makes transparent, with identical results."""
         buf = torch.empty(max(1, self.mask_bytes() // 8), dtype=torch.int64,
-                          device=self.buffer.device)
+                          device=self.device)
         check(load().vr_volume_attach_masks(self._h, buf.data_ptr(), buf.numel() * 8))
         self._masks = buf
         return buf
@@ -240,7 +250,7 @@ class Volume:
         m = MODES[mode]
         shape = (len(cams), h, w, 4) if m == VR_COMPOSITE else (len(cams), h, w)
         if out is None:
-            out = torch.empty(shape, dtype=torch.float32, device=self.buffer.device)
+            out = torch.empty(shape, dtype=torch.float32, device=self.device)
         elif tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous():
             raise ValueError("out must be a contiguous float32 tensor of shape %s" % (shape,))
         lib = load()
@@ -263,7 +273,7 @@ class Volume:
         m = MODES[mode]
         shape = (len(cams), h, w, 4) if m == VR_COMPOSITE else (len(cams), h, w)
         if out is None:
-            out = torch.empty(shape, dtype=torch.float32, device=self.buffer.device)
+            out = torch.empty(shape, dtype=torch.float32, device=self.device)
         best, ms = ctypes.c_int(0), ctypes.c_float(0)
         check(load().vr_autotune(self._h, cams.ctypes.data, len(cams), w, h, m, float(step),
                                  out.data_ptr(), _stream_ptr(stream), ctypes.byref(best),

@@ -454,6 +454,10 @@ int attach_texture(vr_volume vol, bool pair, void* stream)
     if (pair && v->dtype == VR_F32)
         return fail(VR_ERR_UNSUPPORTED, "pair textures hold FP16 or int8 storage only");
     const int format = pair ? (v->dtype == VR_F16 ? vr::kF16Pair : vr::kI8Pair) : v->dtype;
+    if (v->texture_only) {
+        if (v->tex_format == format) return VR_OK;
+        return fail(VR_ERR_UNSUPPORTED, "the volume's bricks were dropped: no new texture");
+    }
     if (v->has_tex) {
         if (v->tex_format == format) return VR_OK;
         release_texture(v);
@@ -606,6 +610,8 @@ int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* sr
     if (z0 < 0 || nplanes < 1 || z0 + nplanes > v->g.nz)
         return fail(VR_ERR_ARG, "planes [%lld, %lld) outside [0, %d)", (long long)z0,
                     (long long)(z0 + nplanes), v->g.nz);
+    if (v->texture_only)
+        return fail(VR_ERR_UNSUPPORTED, "the volume's bricks were dropped: it is read-only");
     const float* dsrc = src;
     if (src_on_device) {
         if (!is_device_ptr(src)) return fail(VR_ERR_ARG, "src is not device memory");
@@ -674,7 +680,24 @@ int vr_volume_attach_pair_texture(vr_volume vol, void* stream)
 int vr_volume_detach_texture(vr_volume vol)
 {
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
-    release_texture(reinterpret_cast<vr::Volume*>(vol));
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (v->texture_only)
+        return fail(VR_ERR_UNSUPPORTED, "the texture is the volume's only copy (bricks dropped)");
+    release_texture(v);
+    return VR_OK;
+}
+
+int vr_volume_drop_bricks(vr_volume vol)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (v->texture_only) return VR_OK;
+    if (!v->has_tex) return fail(VR_ERR_UNSUPPORTED, "the volume has no texture storage");
+    if (v->dtype == VR_I8)
+        return fail(VR_ERR_UNSUPPORTED, "int8 volumes keep their plane tables in the bricks");
+    v->texture_only = true;
+    v->bricks = nullptr;
+    v->mask = nullptr;
     return VR_OK;
 }
 
@@ -695,6 +718,8 @@ int vr_volume_attach_masks(vr_volume vol, void* buf, size_t bytes)
         v->mask = nullptr;
         return VR_OK;
     }
+    if (v->texture_only)
+        return fail(VR_ERR_UNSUPPORTED, "masks are built from the bricks, which were dropped");
     const size_t nm = mask_macrocells(v->g);
     if (nm > 0x7fffffffu) return fail(VR_ERR_UNSUPPORTED, "more than 2^31 macrocells");
     if (reinterpret_cast<uintptr_t>(buf) % 16 != 0)

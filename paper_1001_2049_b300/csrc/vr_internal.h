@@ -42,8 +42,9 @@ struct VolumeGeom {
 struct Volume {
     VolumeGeom g;
     int dtype;
-    void* bricks;           // caller-owned device buffer
+    void* bricks;           // caller-owned device buffer (null once dropped)
     size_t bytes;
+    bool texture_only;      // bricks dropped: the texture is the only copy
     float* scale;           // VR_I8: per-plane tables inside the buffer
     float* offset;
     // transfer function as set by the user

@@ -65,7 +65,7 @@ class _Launch:
     jobs: list
     stream: torch.cuda.Stream
     event: torch.cuda.Event
-    flags: torch.Tensor                 # pinned int32, one per job
+    flags: torch.Tensor | None          # pinned int32, one per job (batched launches)
     issued: float = 0.0
 
 
@@ -74,12 +74,15 @@ class Server:
 
     ``mem_budget`` bounds the bytes of output images of requests in flight;
     ``max_batch`` the requests per launch; ``streams`` the launches that can
-    be on the device at once.
+    be on the device at once.  ``per_request`` renders each request with its
+    own single-view render call (``Volume.render``) instead of batched
+    launches: the plain path the batched one is compared with.
     """
 
     def __init__(self, volumes: dict, mem_budget: int = 1 << 30, max_batch: int = 64,
-                 streams: int = 2, keep_outputs: bool = False):
+                 streams: int = 2, keep_outputs: bool = False, per_request: bool = False):
         self.volumes = volumes
+        self.per_request = per_request
         self.mem_budget = int(mem_budget)
         self.max_batch = int(max_batch)
         self.keep_outputs = keep_outputs
@@ -128,6 +131,19 @@ class Server:
         si = self.free_streams.popleft()
         stream = self.streams[si]
         jobs, self.admitted = self.admitted, []
+        if self.per_request:
+            with torch.cuda.stream(stream):
+                for job in jobs:
+                    vol = self.volumes[job.cube]
+                    if job.tf is not None:
+                        vol.set_transfer(*job.tf)
+                    job.out = vol.render(np.asarray([job.cam]), job.w, job.h, job.mode,
+                                         job.step, stream=stream)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+            self.in_flight.append(_Launch(jobs, stream, ev, None, time.monotonic()))
+            self.launches += 1
+            return True
         flags = torch.zeros(len(jobs), dtype=torch.int32).pin_memory()
         reqs = []
         with torch.cuda.stream(stream):
@@ -150,10 +166,11 @@ class Server:
         now = time.monotonic()
         still = []
         for ln in self.in_flight:
-            f = ln.flags.numpy()
-            for job in ln.jobs:
-                if job.finished == 0.0 and f[job.slot] != 0:
-                    job.finished = now
+            if ln.flags is not None:
+                f = ln.flags.numpy()
+                for job in ln.jobs:
+                    if job.finished == 0.0 and f[job.slot] != 0:
+                        job.finished = now
             if ln.event.query():
                 for job in ln.jobs:
                     if job.finished == 0.0:

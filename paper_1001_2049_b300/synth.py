@@ -307,6 +307,37 @@ def batch_views(n_views=64, seed=BATCH_SEED):
     return out
 
 
+#: The resident cubes of the served workload: four 2048 x 2048 x 4096 cubes
+#: and two 1024^3 cubes (as FP16: 4 x 32 GiB + 2 x 2 GiB = 146 GB).
+SERVE_CUBES = ([("cube2048x2048x4096_%d" % i, (2048, 2048, 4096)) for i in range(4)]
+               + [("cube1024_%d" % i, (1024, 1024, 1024)) for i in range(2)])
+
+
+def cube_slabs(dims, n_sources, snr, seed, device="cpu", planes=256):
+    """A noise + sources cube generated in z-slabs, for cubes too large to
+    hold whole in float32: yields (z0, float32 tensor (n, ny, nx)).  The
+    noise of each slab comes from its own generator (seeded from ``seed`` and
+    the slab index); sources straddling slabs are added to each part."""
+    nx, ny, nz = dims
+    srcs = draw_sources(dims, n_sources, snr, seed + 7919)
+    for i, z0 in enumerate(range(0, nz, planes)):
+        n = min(planes, nz - z0)
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed * 1000003 + i)
+        slab = torch.randn((n, ny, nx), generator=gen, device=device, dtype=torch.float32)
+        add_sources_(slab, srcs, z_offset=z0)
+        yield z0, slab
+
+
+def serve_cube_slabs(i, device="cpu", planes=256):
+    """Cube i of the served workload in z-slabs (sources at the density of
+    the 1024^3 workload, SNR log-uniform 2-50)."""
+    name, dims = SERVE_CUBES[i]
+    n_src = int(2000 * dims[0] * dims[1] * dims[2] / 1024 ** 3)
+    return cube_slabs(dims, n_src, ("loguniform", 2.0, 50.0), SERVE_SEED + 10 * i, device,
+                      planes)
+
+
 def serve_request(dims, rng):
     """One served request: a random direction around the cube, a resolution
     from {512^2, 1024^2, 1280x720, 1920x1080}, composite (80 %) or MIP, and a

@@ -457,6 +457,37 @@ def test_brick_buffer_too_small_is_rejected():
     assert volume_bytes((64, 64, 64), "f32") == 8 * 32768 * 4
 
 
+def test_texture_only_volume_after_dropping_bricks():
+    dims = (40, 36, 50)
+    cube = synth.make_cube(dims, 4, ("uniform", 3.0, 8.0), 71).numpy()
+    cams = synth.random_sphere_cameras(dims, 3, 21, 17, 9)
+    lut = synth.default_lut(32)
+    for dtype in ("f32", "f16"):
+        vol = Volume(torch.from_numpy(cube).cuda(), dtype)
+        vol.attach_texture()
+        vol.attach_masks()
+        vol.set_transfer(lut, 1.0, 8.0, 1.0, 0.95)
+        before = {m: vol.render(cams, 21, 17, m, 0.5).cpu() for m in ("composite", "mip")}
+        vol.drop_bricks()
+        assert vol.buffer is None
+        for m in ("composite", "mip"):
+            assert torch.equal(vol.render(cams, 21, 17, m, 0.5).cpu(), before[m])
+        with pytest.raises(VRError):
+            vol.upload(0, torch.from_numpy(cube[:2]).cuda())
+        with pytest.raises(VRError):
+            vol.detach_texture()
+        with pytest.raises(VRError):
+            vol.attach_masks()
+        vol.close()
+    v8 = Volume(torch.from_numpy(cube).cuda(), "i8")
+    v8.attach_texture()
+    with pytest.raises(VRError):
+        v8.drop_bricks()
+    v32 = Volume(torch.from_numpy(cube).cuda(), "f32")
+    with pytest.raises(VRError):                 # nothing to keep
+        v32.drop_bricks()
+
+
 # ---------------------------------------------------------------------------
 # empty-space masks: every cell whose bit is clear is below the clip, and
 # composite renders with the masks are identical to renders without them

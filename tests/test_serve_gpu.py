@@ -94,3 +94,19 @@ def test_poisson_serving_reports_latencies(cubes):
     assert st["n"] == n > 50
     assert 0 < st["p50_ms"] <= st["p99_ms"]
     assert all(j.finished >= j.admitted >= j.arrival for j in done)
+
+
+def test_per_request_server_gives_the_same_images(cubes):
+    # the plain path the batched one is compared with: one single-view render
+    # call per request, in arrival order
+    server = Server({k: v[0] for k, v in cubes.items()}, mem_budget=1 << 22, max_batch=1,
+                    streams=1, keep_outputs=True, per_request=True)
+    jobs = make_jobs(cubes, 24, 4)
+    for job in jobs:
+        server.submit(job)
+    server.drain()
+    assert len(server.done) == len(jobs) and server.launches == len(jobs)
+    for job in jobs:
+        assert job.out.shape[0] == 1
+        ref = alone(cubes, job)
+        assert torch.allclose(job.out[0], ref, rtol=0, atol=1e-6), (job.cube, job.mode)
