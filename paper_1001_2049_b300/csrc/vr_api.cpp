@@ -34,12 +34,12 @@ int cuda_fail(cudaError_t e, const char* what)
 int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
-// Macrocells of the empty-space masks: x and y cover gather coordinates
-// 0 .. n (cells -1 .. n - 1), z cells 0 .. nz - 2, four per macrocell.
+// Macrocells of the empty-space masks: every axis covers gather coordinates
+// 0 .. n (cells -1 .. n - 1), four per macrocell.
 size_t mask_macrocells(const vr::VolumeGeom& g)
 {
     return (size_t)((g.nx >> vr::kMacroShift) + 1) * ((g.ny >> vr::kMacroShift) + 1) *
-           (((g.nz - 2) >> vr::kMacroShift) + 1);
+           ((g.nz >> vr::kMacroShift) + 1);
 }
 
 size_t elem_size(int dtype) { return dtype == VR_F32 ? 4 : dtype == VR_F16 ? 2 : 1; }
@@ -187,12 +187,14 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
     tp->tex = v->tex;
     tp->stack_shift = v->stack_shift;
     tp->stack_pitch = v->stack_pitch;
+    tp->nz = v->g.nz;
     tp->scale = v->scale;
     tp->offset = v->offset;
     tp->k_max = (int)(diag / step) + 2;
     p->mask = v->mask;
     p->mnx = v->mnx;
     p->mny = v->mny;
+    p->mlast = v->mask ? v->mnx * v->mny * v->mnz - 1 : 0;
     return VR_OK;
 }
 
@@ -313,6 +315,7 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
             T.tex = v->tex;
             T.stack_shift = v->stack_shift;
             T.stack_pitch = v->stack_pitch;
+            T.nz = v->g.nz;
             T.format = v->tex_format;
             T.scale = v->scale;
             T.offset = v->offset;
@@ -425,12 +428,14 @@ void release_texture(vr::Volume* v)
 // cell planes whose texels include one of those planes).
 int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
 {
+    // slices holding planes [z0, z1): plain slice s holds plane s - 1 (slices
+    // 0 and nz + 1 repeat the edge planes); pair slice s holds planes s - 1
+    // and s (clamped)
     const bool pair = v->tex_format == vr::kF16Pair || v->tex_format == vr::kI8Pair;
-    if (pair) {
-        z0 = std::max<int64_t>(z0 - 1, 0);     // cell z0 - 1 holds plane z0
-        z1 = std::min<int64_t>(z1, v->g.nz - 1);
-    }
-    if (z0 >= z1) return VR_OK;
+    const int64_t last = pair ? v->g.nz : v->g.nz + 1;
+    int64_t s0 = z0 == 0 ? 0 : z0 + (pair ? 0 : 1);
+    int64_t s1 = z1 == v->g.nz ? last + 1 : z1 + 1;
+    if (s0 >= s1) return VR_OK;
     cudaResourceDesc rd;
     std::memset(&rd, 0, sizeof rd);
     rd.resType = cudaResourceTypeArray;
@@ -438,7 +443,7 @@ int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
     cudaSurfaceObject_t surf = 0;
     cudaError_t e = cudaCreateSurfaceObject(&surf, &rd);
     if (e != cudaSuccess) return cuda_fail(e, "surface object");
-    e = vr::fill_texture(*v, surf, (int)z0, (int)z1, s);
+    e = vr::fill_texture(*v, surf, (int)s0, (int)s1, s);
     // the surface object may only be destroyed after the fill ran: wait
     cudaError_t e2 = cudaStreamSynchronize(s);
     cudaDestroySurfaceObject(surf);
@@ -469,9 +474,10 @@ int attach_texture(vr_volume vol, bool pair, void* stream)
     cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, dev);
     cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, dev);
     maxl = std::min(maxl, vr::kMaxLayers);
-    // slices: planes (plain) or cell planes (pair), stacked 2^shift per layer
-    // (each with a copy of its edge rows) when they outnumber the layers
-    const int slices = pair ? v->g.nz - 1 : v->g.nz;
+    // slices: planes (plain, nz + 2 with the edge planes repeated) or cells
+    // (pair, nz + 1), stacked 2^shift per layer (each with a copy of its edge
+    // rows) when they outnumber the layers
+    const int slices = pair ? v->g.nz + 1 : v->g.nz + 2;
     int shift = 0;
     while (((slices + (1 << shift) - 1) >> shift) > maxl) ++shift;
     const int pitch = shift > 0 ? v->g.ny + 2 : v->g.ny;
@@ -732,7 +738,7 @@ int vr_volume_attach_masks(vr_volume vol, void* buf, size_t bytes)
     v->mask_clip = NAN;                       // built by the next composite render
     v->mnx = (v->g.nx >> vr::kMacroShift) + 1;
     v->mny = (v->g.ny >> vr::kMacroShift) + 1;
-    v->mnz = ((v->g.nz - 2) >> vr::kMacroShift) + 1;
+    v->mnz = (v->g.nz >> vr::kMacroShift) + 1;
     return VR_OK;
 }
 

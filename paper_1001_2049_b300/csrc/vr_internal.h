@@ -25,10 +25,9 @@ constexpr int kF16Pair = 3;
 constexpr int kI8Pair = 4;
 // Empty-space masks: per macrocell of 4 x 4 x 4 cells, a 64-bit mask of the
 // cells that a clip level leaves visible (bit (x & 3) | (y & 3) << 2 |
-// (z & 3) << 4).  Cells are indexed by their gather coordinates: x and y run
-// over cells -1 .. n - 1 stored at x + 1 (the outermost ones are positions a
-// rounding error outside the box, which read the edge voxels), z over cells
-// 0 .. nz - 2.
+// (z & 3) << 4).  Cells are indexed by their gather coordinates: on every
+// axis cells -1 .. n - 1 stored at cell + 1 (the outermost ones hold
+// positions a rounding error outside the box, which read the edge voxels).
 constexpr int kMacroShift = 2;
 constexpr int kMacro = 1 << kMacroShift;
 
@@ -60,7 +59,7 @@ struct Volume {
     // 2^stack_shift slices stacked per layer
     bool has_tex;
     int tex_format;         // VR_F32 / VR_F16 / VR_I8, or kF16Pair / kI8Pair
-    cudaArray_t array;
+    cudaArray_t array;      // nz + 2 slices (plain) or nz + 1 (pair), see vr_ray.cuh
     cudaTextureObject_t tex;
     int stack_shift;        // 0: a layer per slice
     int stack_pitch;        // rows per stacked slice (ny + 2) when stacked
@@ -75,6 +74,7 @@ struct Volume {
 struct TexParams {
     cudaTextureObject_t tex;
     int stack_shift, stack_pitch;   // see Volume
+    int nz;
     const float* scale;     // VR_I8 only
     const float* offset;
     int k_max;
@@ -99,7 +99,7 @@ struct MarchParams {
     float* out;             // first view of this launch
     unsigned long long* samples;   // may be null
     const unsigned long long* mask;   // empty-space masks for `clip` (COMPOSITE), or null
-    int mnx, mny;
+    int mnx, mny, mlast;              // macrocells along x, y; last macrocell index
     vr_camera cams[kMaxViewsPerLaunch];
     float4 lut[VR_MAX_LUT];
 };
@@ -115,6 +115,7 @@ constexpr int kBatchWords = 1 + kMaxBatch;
 struct BatchTex {
     cudaTextureObject_t tex;
     int stack_shift, stack_pitch;   // see Volume
+    int nz;
     int format;            // texel format (see kF16Pair)
     const float* scale;
     const float* offset;
@@ -194,9 +195,8 @@ cudaError_t launch_tex_i8pair(const MarchParams& p, const TexParams& t, int mode
 cudaError_t launch_masks(const Volume& v, float clip, cudaStream_t s);
 int tex_shape_count();
 void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb);
-// Copy planes (plain formats) or cell planes (pair formats) [z0, z1) from
-// the bricks into the volume's texture through surface `surf`.
-cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int z0, int z1,
+// Fill texture slices [s0, s1) from the bricks through surface `surf`.
+cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1,
                          cudaStream_t s);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
                         cudaStream_t s);

@@ -18,10 +18,10 @@
 // float32 as stored, binary16 widened exactly, int8 as fma(code, scale[z],
 // offset[z]).
 //
-// Cells are indexed by the kernels' gather coordinates: x and y from -1 to
-// n - 1 (stored at +1; the outermost cells hold positions a rounding error
-// outside the box, which read the edge voxels, so they take the bit of the
-// edge cell), z from 0 to nz - 2.
+// Cells are indexed by the kernels' gather coordinates: on every axis from
+// -1 to n - 1 (stored at +1; the outermost cells hold positions a rounding
+// error outside the box, which read the edge voxels, so they take the bit of
+// the edge cell).
 #include <cuda_fp16.h>
 
 #include "vr_internal.h"
@@ -49,13 +49,14 @@ __global__ void __launch_bounds__(64) mask_kernel(const void* __restrict__ brick
     const unsigned m = blockIdx.x;
     const int mx = (int)(m % mnx), my = (int)((m / mnx) % mny), mz = (int)(m / ((unsigned)mnx * mny));
     const int t = threadIdx.x;
-    const int gx = (mx << kMacroShift) + (t & 3);           // gather coordinate: cell + 1
+    const int gx = (mx << kMacroShift) + (t & 3);           // gather coordinates: cell + 1
     const int gy = (my << kMacroShift) + ((t >> 2) & 3);
-    const int cz = (mz << kMacroShift) + (t >> 4);
+    const int gz = (mz << kMacroShift) + (t >> 4);
     bool need = false;
-    if (gx <= g.nx && gy <= g.ny && cz <= g.nz - 2) {
+    if (gx <= g.nx && gy <= g.ny && gz <= g.nz) {
         const int cx = min(max(gx - 1, 0), g.nx - 2);
         const int cy = min(max(gy - 1, 0), g.ny - 2);
+        const int cz = min(max(gz - 1, 0), g.nz - 2);
         float hi = -INFINITY, mag = 0.0f;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {

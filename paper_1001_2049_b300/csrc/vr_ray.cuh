@@ -118,12 +118,15 @@ __device__ __forceinline__ Ray setup_ray(const PP& P, const vr_camera& c, int px
     return r;
 }
 
-// Decode int8 codes of plane z (scale/offset); identity for float storage.
-// TT supplies tex, stack_shift, stack_pitch, scale and offset.
+// Decode int8 codes of texture slice `slice` (plane slice - 1, clamped: the
+// first and last slices repeat the edge planes) with its plane's scale and
+// offset; identity for float storage.  TT supplies tex, stack_shift,
+// stack_pitch, nz, scale and offset.
 template <int DT, typename TT>
-__device__ __forceinline__ float4 decode(const TT& T, float4 q, int z)
+__device__ __forceinline__ float4 decode(const TT& T, float4 q, int slice)
 {
     if (DT != VR_I8) return q;
+    const int z = min(max(slice - 1, 0), T.nz - 1);
     const float s = __ldg(T.scale + z), o = __ldg(T.offset + z);
     return make_float4(fmaf(q.x, s, o), fmaf(q.y, s, o), fmaf(q.z, s, o), fmaf(q.w, s, o));
 }
@@ -148,9 +151,15 @@ __device__ __forceinline__ float code_hi(unsigned b)
     return (float)(signed char)((b >> 8) & 0xffu);
 }
 
-// Layer and row offset of plane z (plain formats) or cell plane z (pair
-// formats) of a volume's texture.  Unstacked (a layer per plane): layer z,
-// rows as stored.  Stacked: 2^shift planes per layer, plane z at sub-plane
+// Texture slices.  Plain formats: slice s holds plane s - 1, and slices 0
+// and nz + 1 repeat planes 0 and nz - 1.  Pair formats: slice s holds the
+// cell between planes s - 1 and s (clamped to [0, nz - 1]), s in [0, nz].
+// A sample at height pz therefore reads slices floor(pz) + 1 (and + 2),
+// with no clamping for positions a rounding error outside the z faces: the
+// repeated edge planes give the edge value exactly.
+//
+// Layer and row offset of slice z.  Unstacked (a layer per slice): layer z,
+// rows as stored.  Stacked: 2^shift slices per layer, slice z at sub-slice
 // z & (2^shift - 1) of layer z >> shift, whose ny data rows start at row
 // sub * pitch + 1 (rows sub * pitch and sub * pitch + ny + 1 copy its first
 // and last rows, so a gather one row outside the data reads the edge row as
@@ -167,8 +176,9 @@ __device__ __forceinline__ int plane_layer(const TT& T, int z, float y, float& y
     return z >> T.stack_shift;
 }
 
-// The two planes z and z + 1 of the cell whose x/y corner is texel (x-1, y-1).
-// Pair formats: one gather of cell plane z holds both planes.
+// The two planes of the cell at slice z (planes z - 1 and z, see above)
+// whose x/y corner is texel (x-1, y-1).  Pair formats: one gather of slice z
+// holds both planes.
 template <int DT, bool STACK, typename TT>
 __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z, float x,
                                      float y, float4& q0, float4& q1)
@@ -182,8 +192,9 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
             q1 = make_float4(half_bits(p.x >> 16), half_bits(p.y >> 16), half_bits(p.z >> 16),
                              half_bits(p.w >> 16));
         } else {
-            const float s0 = __ldg(T.scale + z), o0 = __ldg(T.offset + z);
-            const float s1 = __ldg(T.scale + z + 1), o1 = __ldg(T.offset + z + 1);
+            const int z0 = min(max(z - 1, 0), T.nz - 1), z1 = min(z, T.nz - 1);
+            const float s0 = __ldg(T.scale + z0), o0 = __ldg(T.offset + z0);
+            const float s1 = __ldg(T.scale + z1), o1 = __ldg(T.offset + z1);
             q0 = make_float4(fmaf(code_lo(p.x), s0, o0), fmaf(code_lo(p.y), s0, o0),
                              fmaf(code_lo(p.z), s0, o0), fmaf(code_lo(p.w), s0, o0));
             q1 = make_float4(fmaf(code_hi(p.x), s1, o1), fmaf(code_hi(p.y), s1, o1),
@@ -198,14 +209,50 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
 }
 
 // Corners of the cell of sample geometry `n` given the cell `c` whose corners
-// (c0, c1) are held: nothing is fetched when the cell is the same; with plain
-// texels, one plane when only z moved by one, both planes otherwise.  The
-// texture return path is what bounds this kernel, so every gather saved
-// counts.
+// (c0, c1) are held: nothing is fetched when the cell is the same.  Pair
+// formats fetch the cell in one gather.  Plain formats fetch the lower and
+// the upper plane in two gather slots that every lane of a warp shares, each
+// skipped by the lanes that hold that plane already (the lower one when z
+// rose by one, the upper one when z fell by one): whatever mix of moves the
+// lanes make, a warp issues at most two gathers per sample.
 template <int DT, bool STACK, typename TT, typename G>
 __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, const G& c,
                                           const float4& c0, const float4& c1, const G& n,
                                           float4& n0, float4& n1)
+{
+    const bool xy = n.gx == c.gx && n.gy == c.gy;
+    const int dz = n.iz - c.iz;
+    if (xy && dz == 0) {
+        n0 = c0;
+        n1 = c1;
+        return;
+    }
+    if constexpr (DT == kF16Pair || DT == kI8Pair) {
+        cell<DT, STACK>(T, t0, n.iz, n.gx, n.gy, n0, n1);
+    } else {
+        float yt;
+        if (xy && dz == 1) {
+            n0 = c1;
+        } else {
+            const int l = plane_layer<STACK>(T, n.iz, n.gy, yt);
+            n0 = decode<DT>(T, gather<DT>(t0, l, n.gx, yt), n.iz);
+        }
+        if (xy && dz == -1) {
+            n1 = c0;
+        } else {
+            const int l = plane_layer<STACK>(T, n.iz + 1, n.gy, yt);
+            n1 = decode<DT>(T, gather<DT>(t0, l, n.gx, yt), n.iz + 1);
+        }
+    }
+}
+
+// next_cell for the lockstep march (march_tex_lock), where a lane gathers
+// only for the samples it needs: one plane when only z rose by one, both
+// planes otherwise (measured faster there than the shared-slot form).
+template <int DT, bool STACK, typename TT, typename G>
+__device__ __forceinline__ void next_cell_up(const TT& T, cudaTextureObject_t t0, const G& c,
+                                             const float4& c0, const float4& c1, const G& n,
+                                             float4& n0, float4& n1)
 {
     if (n.gx == c.gx && n.gy == c.gy) {
         if (n.iz == c.iz) {
@@ -227,15 +274,14 @@ __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, c
 }
 
 // Per-sample geometry: the gather coordinates of the cell and the weights.
-// x and y are not clamped to the box: a position just outside a face (by
+// Nothing is clamped to the box: a position just outside an x or y face (by
 // rounding) has both its corners clamped to the edge texel by the texture
-// unit, which gives the edge value exactly as clamping the position would.
-// z is the layer index and is clamped explicitly (cell in [0, nz - 2],
-// weight in [0, 1]).
+// unit, and one just outside a z face reads a repeated edge plane, which
+// gives the edge value exactly as clamping the position would.
 struct Geo {
     float gx, gy;     // gather coordinates (cell corner + 1)
     float fx, fy, fz;
-    int iz;
+    int iz;           // texture slice of the cell's lower plane (cell + 1)
 };
 
 template <typename PP>
@@ -244,14 +290,13 @@ __device__ __forceinline__ Geo geo(const PP& P, const Ray& r, float kf)
     Geo g;
     const float t = fmaf(kf, P.step, r.te);
     const float px = fmaf(t, r.dx, r.ox), py = fmaf(t, r.dy, r.oy), pz = fmaf(t, r.dz, r.oz);
-    const float flx = floorf(px), fly = floorf(py);
-    const float flz = fminf(fmaxf(floorf(pz), 0.0f), P.hiz - 1.0f);
+    const float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
     g.gx = flx + 1.0f;
     g.gy = fly + 1.0f;
     g.fx = px - flx;
     g.fy = py - fly;
-    g.fz = fminf(fmaxf(pz - flz, 0.0f), 1.0f);
-    g.iz = (int)flz;
+    g.fz = pz - flz;
+    g.iz = (int)flz + 1;
     return g;
 }
 
@@ -306,14 +351,17 @@ struct Acc {
 
 // ---- empty-space skipping ----
 // A sample's macrocell and its cell's bit there, from the gather coordinates
-// (x, y: cell + 1, in [0, n] for positions inside the box up to rounding;
-// z: the clamped cell).
+// (cell + 1 on every axis: in [0, n] for positions inside the box up to
+// rounding).  The index is clamped to the mask array: the look-ahead samples
+// past a ray's end, and positions of cameras so far away that rounding
+// moves them by a voxel, may lie outside, and their bits are never used.
 template <typename PP>
 __device__ __forceinline__ int macro_of(const PP& P, const Geo& g, int& bit)
 {
     const int x = (int)g.gx, y = (int)g.gy, z = g.iz;
     bit = (x & 3) | ((y & 3) << 2) | ((z & 3) << 4);
-    return ((z >> kMacroShift) * P.mny + (y >> kMacroShift)) * P.mnx + (x >> kMacroShift);
+    const int i = ((z >> kMacroShift) * P.mny + (y >> kMacroShift)) * P.mnx + (x >> kMacroShift);
+    return (int)min((unsigned)i, (unsigned)P.mlast);
 }
 
 // march_tex with empty-space skipping in lockstep (COMPOSITE): every lane
@@ -355,7 +403,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
         const bool n1 = acc.need(rX, b1);
         if (n1) {
             if (n0)
-                next_cell<DT, STACK>(T, t0, g0, a0, a1, g1, c0, c1);
+                next_cell_up<DT, STACK>(T, t0, g0, a0, a1, g1, c0, c1);
             else
                 cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
         }
@@ -371,7 +419,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
         const bool n2 = acc.need(rY, b2);
         if (n2) {
             if (n1)
-                next_cell<DT, STACK>(T, t0, g1, c0, c1, g2, a0, a1);
+                next_cell_up<DT, STACK>(T, t0, g1, c0, c1, g2, a0, a1);
             else
                 cell<DT, STACK>(T, t0, g2.iz, g2.gx, g2.gy, a0, a1);
         }

@@ -14,8 +14,8 @@
 namespace vr {
 namespace {
 
-// Plane (plain formats) or cell plane (pair formats) z of the texture is 2-D
-// slice z & (2^shift - 1) of layer z >> shift.  Unstacked (shift 0) a slice
+// Slice z of the texture (see vr_ray.cuh for what the slices hold) is 2-D
+// sub-slice z & (2^shift - 1) of layer z >> shift.  Unstacked (shift 0) a slice
 // is the ny rows of data; stacked, a slice spans `pitch` = ny + 2 rows: a
 // copy of data row 0, the ny data rows, a copy of data row ny - 1, so a
 // gather one row outside the data reads the edge row exactly as the
@@ -35,28 +35,30 @@ __device__ __forceinline__ void write_slice_row(cudaSurfaceObject_t surf, W v, i
     if (y == ny - 1) surf2DLayeredwrite(v, surf, x * (int)sizeof(W), base + ny, layer);
 }
 
-// Plain formats: planes [z0, z1) of the bricks into the texture.
+// Plain formats: slices [s0, s1) of the texture; slice s holds plane s - 1,
+// slices 0 and nz + 1 repeat the edge planes.
 template <typename T>
 __global__ void __launch_bounds__(256) fill_kernel(const T* __restrict__ bricks, VolumeGeom g,
-                                                   cudaSurfaceObject_t surf, int z0, int z1,
+                                                   cudaSurfaceObject_t surf, int s0, int s1,
                                                    int shift, int pitch)
 {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (x >= g.nx || y >= g.ny) return;
-    for (int z = z0 + blockIdx.z; z < z1; z += gridDim.z) {
+    for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z) {
+        const int z = min(max(sl - 1, 0), g.nz - 1);
         const size_t brick = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) * g.nbx +
                              (x >> kBrickShift);
         const T v = bricks[brick * kBrickVoxels + ((z & 31) << 10) + ((y & 31) << 5) + (x & 31)];
-        write_slice_row(surf, v, x, y, z, g.ny, shift, pitch);
+        write_slice_row(surf, v, x, y, sl, g.ny, shift, pitch);
     }
 }
 
-// Pair formats: cell planes [c0, c1), each texel the voxels of planes c and
-// c + 1 packed (low bits plane c).
+// Pair formats: slices [s0, s1); slice s holds the voxels of planes s - 1 and
+// s (clamped to the cube) packed in one texel, low bits plane s - 1.
 template <typename T, typename W>
 __global__ void __launch_bounds__(256) fill_pair_kernel(const T* __restrict__ bricks, VolumeGeom g,
-                                                        cudaSurfaceObject_t surf, int c0, int c1,
+                                                        cudaSurfaceObject_t surf, int s0, int s1,
                                                         int shift, int pitch)
 {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -65,14 +67,14 @@ __global__ void __launch_bounds__(256) fill_pair_kernel(const T* __restrict__ br
     const size_t row = ((size_t)(y >> kBrickShift) * g.nbx + (x >> kBrickShift)) * kBrickVoxels +
                        ((y & 31) << 5) + (x & 31);
     const size_t slab = (size_t)g.nbx * g.nby * kBrickVoxels;
-    for (int c = c0 + blockIdx.z; c < c1; c += gridDim.z) {
-        const T lo = bricks[(size_t)(c >> kBrickShift) * slab + row + ((c & 31) << 10)];
-        const int c_ = c + 1;
-        const T hi = bricks[(size_t)(c_ >> kBrickShift) * slab + row + ((c_ & 31) << 10)];
+    for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z) {
+        const int za = min(max(sl - 1, 0), g.nz - 1), zb = min(sl, g.nz - 1);
+        const T lo = bricks[(size_t)(za >> kBrickShift) * slab + row + ((za & 31) << 10)];
+        const T hi = bricks[(size_t)(zb >> kBrickShift) * slab + row + ((zb & 31) << 10)];
         const W packed = (W)((W)(unsigned)(typename std::make_unsigned<T>::type)lo |
                              ((W)(unsigned)(typename std::make_unsigned<T>::type)hi
                               << (8 * sizeof(T))));
-        write_slice_row(surf, packed, x, y, c, g.ny, shift, pitch);
+        write_slice_row(surf, packed, x, y, sl, g.ny, shift, pitch);
     }
 }
 

@@ -514,12 +514,11 @@ def test_masks_mark_every_cell_that_can_reach_the_clip(dims, dtype):
     vol.attach_texture()
     vol.attach_masks()
     nx, ny, nz = dims
-    mnx, mny, mnz = (nx >> 2) + 1, (ny >> 2) + 1, ((nz - 2) >> 2) + 1
+    mnx, mny, mnz = (nx >> 2) + 1, (ny >> 2) + 1, (nz >> 2) + 1
     assert vol.mask_bytes() == 8 * mnx * mny * mnz
     dec = _decoded(cube, dtype).astype(np.float64)
-    # bound of each cell's eight corners, for gather coordinates x, y in
-    # [0, n] (cells -1 .. n - 1, the outermost reading the edge cell) and z
-    # in [0, nz - 2]
+    # bound of each cell's eight corners, for gather coordinates in [0, n]
+    # on every axis (cells -1 .. n - 1, the outermost reading the edge cell)
     hi = np.full((nz - 1, ny - 1, nx - 1), -np.inf)
     mag = np.zeros_like(hi)
     for c in range(8):
@@ -530,9 +529,11 @@ def test_masks_mark_every_cell_that_can_reach_the_clip(dims, dtype):
     bound = hi + 2.0 ** -19 * mag
     gx = np.clip(np.arange(nx + 1) - 1, 0, nx - 2)
     gy = np.clip(np.arange(ny + 1) - 1, 0, ny - 2)
-    bound = bound[:, gy][:, :, gx]                       # (nz - 1, ny + 1, nx + 1)
+    gz = np.clip(np.arange(nz + 1) - 1, 0, nz - 2)
+    bound = bound[gz][:, gy][:, :, gx]                   # (nz + 1, ny + 1, nx + 1)
+    hi = hi[gz][:, gy][:, :, gx]
     cams = synth.random_sphere_cameras(dims, 1, 4, 4, 3)
-    z, y, x = np.meshgrid(np.arange(nz - 1), np.arange(ny + 1), np.arange(nx + 1),
+    z, y, x = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1),
                           indexing="ij")
     bit = ((x & 3) | ((y & 3) << 2) | ((z & 3) << 4)).astype(np.uint64)
     for clip in (2.0, 4.5):
@@ -546,7 +547,7 @@ def test_masks_mark_every_cell_that_can_reach_the_clip(dims, dtype):
         clear = np.abs(bound - clip) > 1e-5 * max(1.0, abs(clip))   # not a rounding tie
         assert (got == want)[clear].all(), (dtype, dims, clip)
         # a clear bit never hides a corner at or above the clip
-        assert not (~got & (hi[:, gy][:, :, gx] >= clip)).any()
+        assert not (~got & (hi >= clip)).any()
 
 
 def _skip_cases(dims, seed):
