@@ -113,6 +113,16 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # algorithmic bytes: storage bytes of every voxel some sample's corners touch
 # ---------------------------------------------------------------------------
+# DRAM bytes (read + write) per algorithmic byte of the two render launches,
+# from one ncu capture of the same kernels and launch shapes on the 512^3 /
+# 4-view case (profiles/tex_kernel_f32_cube1024_orbit32.md): MIP
+# 2.0245 GB for 2.1307 GB; composite with the empty-space masks 0.4184 GB for
+# 2.1533 GB.  The cube exceeds L2 in both cases, so every view re-reads it
+# and the traffic of the full launch scales with touched voxels x views.
+TRAFFIC_PER_ALGORITHMIC_BYTE = {"mip": 2.024333e9 / 2.130716e9,
+                                "composite_masks": 0.418379e9 / 2.153293e9}
+
+
 def touched_voxels(cam, dims, step, w, h, device):
     """Number of distinct voxels referenced by the eight corners of every
     sample of one view (float64 geometry; measurement only)."""
@@ -386,6 +396,8 @@ def main():
                     help="profiling captures only: smaller cube, same framing")
     ap.add_argument("--views", type=int, default=32)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--shapes", default=None,
+                    help="launch shapes C,M (composite, MIP) instead of the autotuner's")
     ap.add_argument("--no-masks", action="store_true",
                     help="composite without the empty-space masks")
     ap.add_argument("--no-extra", action="store_true",
@@ -423,7 +435,11 @@ def main():
 
     # launch shapes chosen by the autotuner on these very views (untimed)
     tuned = {}
-    if args.storage == "texture" and not args.no_tune:
+    if args.storage == "texture" and args.shapes:
+        for mode, cfg in zip(("composite", "mip"), (int(c) for c in args.shapes.split(","))):
+            vol.set_launch_config(mode, cfg)
+            tuned[mode] = {"config": cfg, "shape": list(launch_shapes()[cfg]), "ms": None}
+    elif args.storage == "texture" and not args.no_tune:
         for mode, out in (("composite", comp), ("mip", mip)):
             cfg, ms = vol.autotune(cams, W, H, mode, wl.step, out=out)
             tuned[mode] = {"config": cfg, "shape": list(launch_shapes()[cfg]), "ms": ms}
@@ -520,6 +536,12 @@ def main():
         dom_ms, dom_bytes, dom = (comp_ms, comp_bytes, "composite") if comp_ms >= mip_ms else \
             (mip_ms, mip_bytes, "mip")
         achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
+        masks_on = args.storage == "texture" and not args.no_masks
+        ratio = {"mip": TRAFFIC_PER_ALGORITHMIC_BYTE["mip"],
+                 "composite": (TRAFFIC_PER_ALGORITHMIC_BYTE["composite_masks"] if masks_on
+                               else None)}
+        traffic = (ratio[dom] * dom_bytes if args.storage == "texture" and ratio[dom] else None)
+        comp_traffic = ratio["composite"] * comp_bytes if ratio["composite"] else None
         value = samples_step * args.steps * world / elapsed
         fps = 2 * n_views * args.steps * world / elapsed
         cpu = None
@@ -556,13 +578,22 @@ def main():
                 "without_masks": no_masks,
                 "autotuned": tuned,
                 "l2": "inputs larger than L2 (4 GiB cube per view pass)"},
-            "roofline": {"bound": "hbm", "kernel": ("tex_kernel" if args.storage == "texture"
-                                                     else "march kernel") + " composite f32",
+            "roofline": {"bound": "hbm",
+                         "kernel": ("tex_kernel" if args.storage == "texture"
+                                    else "march kernel") + " %s f32" % dom,
                          "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                           "on the 512^3 / 4-view case, scaled by algorithmic "
+                                           "bytes" if traffic else None,
                          "algorithmic_bytes_per_launch": dom_bytes, "dominant": dom,
-                         "touched_voxels_per_view": touched},
+                         "touched_voxels_per_view": touched,
+                         "composite": {"achieved": comp_bytes / (comp_ms / 1000.0) / 1e9,
+                                       "frac": comp_bytes / (comp_ms / 1000.0) / 1e9 / peak,
+                                       "algorithmic_bytes_per_launch": comp_bytes,
+                                       "traffic": comp_traffic,
+                                       "empty_space_masks": masks_on}},
             "cpu_baseline": cpu,
             "e2e": ({"value": samples_step / e2e_s * world, "unit": "samples/s",
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
