@@ -305,6 +305,39 @@ def batched_leg(dev, reps=3):
     return res
 
 
+def tf_edit_leg(vol, cams, W, H, wl, lut):
+    """Interactive transfer-function editing: a sequence of clip levels, each
+    set and followed by one 1080p composite view; latency from the
+    vr_set_transfer call to the finished image (host clock), with the
+    empty-space masks (rebuilt only when the clip drops below the level they
+    were built for) and without them."""
+    clips = [3.0, 3.25, 3.5, 2.75, 4.0, 2.5, 3.0, 5.0, 2.0, 3.0, 3.5, 4.5] * 3
+    out = torch.empty((1, H, W, 4), dtype=torch.float32, device=vol.device)
+    res = {}
+    for label, masks in (("with_masks", True), ("without_masks", False)):
+        if masks:
+            vol.attach_masks()
+        else:
+            vol.detach_masks()
+        lat, level, rebuilt = [], None, 0
+        for i, c in enumerate(clips):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            vol.set_transfer(lut, c, wl.v_hi, c, wl.term_alpha)
+            vol.render(cams[i % len(cams):i % len(cams) + 1], W, H, "composite", wl.step, out=out)
+            torch.cuda.synchronize()
+            lat.append(1000.0 * (time.perf_counter() - t0))
+            if masks and (level is None or c < level):
+                level, rebuilt = c, rebuilt + 1
+        lat = np.array(lat[1:])                 # the first edit also builds the first masks
+        res[label] = {"edits": int(lat.size), "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+                      "mask_builds": rebuilt if masks else 0}
+    vol.attach_masks()
+    vol.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
+    return res
+
+
 def _served_volume(i, dt, dev):
     """Served cube i stored as ``dt`` with texture storage only (built slab
     by slab through one brick buffer, which is freed afterwards)."""
@@ -552,6 +585,8 @@ def main():
                    "sample": sample, "fps": cfps}
         extra = {}
         if not args.no_extra and W == 1920:
+            if args.storage == "texture" and not args.no_masks:
+                extra["tf_edit"] = tf_edit_leg(vol, cams, W, H, wl, lut)
             del comp, mip, host_comp, host_mip
             vol.close()
             del vol, cube

@@ -35,13 +35,16 @@
  * Arithmetic is single precision with FP32 accumulation whatever the
  * storage type.
  *
- * Memory.  The caller owns all device memory: the brick buffer of each
- * volume (size from vr_volume_bytes), every source and every output buffer.
- * The library owns only the small host-side handle.  Every call that takes a
+ * Memory.  The caller owns the device memory a render reads and writes: the
+ * brick buffer of each volume (size from vr_volume_bytes), the empty-space
+ * masks, every source, output buffer and batch workspace.  The library owns
+ * the small host-side handle and, when asked for it, a volume's texture
+ * storage (vr_volume_attach_texture: the one device allocation it makes).  Every call that takes a
  * stream (a cudaStream_t passed as void*, NULL = legacy default stream) is
  * asynchronous on it: argument errors are reported synchronously; a device
  * fault surfaces at the caller's next synchronisation.  The library never
- * synchronises the device on its own and never falls back to the CPU.
+ * synchronises on its own except where a call says so (texture attach, the
+ * autotuner) and never falls back to the CPU.
  *
  * Errors.  Every function returns VR_OK (0) or a negative VR_ERR_* code;
  * vr_last_error() then gives a message (thread-local, valid until the next
@@ -176,9 +179,11 @@ int vr_volume_mask_bytes(vr_volume vol, size_t* bytes_out);
  * volume then skip the fetch and evaluation of samples whose cell cannot
  * reach the clip level (such samples are transparent: §3.1 item 3 with the
  * noise clip), with the warp's rays kept in step.  The masks depend on the
- * clip: they are (re)built on the render's stream by the first COMPOSITE
- * render (or autotune) after this call, a vr_set_transfer that changes the
- * clip, or a vr_volume_upload.  Images and sample counts are identical to
+ * clip: they are built on the render's stream by the first COMPOSITE render
+ * (or autotune) after this call or after a vr_volume_upload, and rebuilt
+ * when vr_set_transfer lowers the clip below the level they were built for
+ * (masks for a lower clip stay valid, only less tight, when the clip rises:
+ * attach again to rebuild them tight).  Images and sample counts are identical to
  * those without masks; only the work differs.  MIP, SUM, brick-gather and
  * batched renders do not use them.  buf = NULL detaches.  No device work
  * here.  The paper describes no such structure.                            */

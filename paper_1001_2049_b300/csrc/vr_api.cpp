@@ -198,11 +198,14 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
     return VR_OK;
 }
 
-// Composite renders with empty-space masks use the masks of the volume's clip
-// level: rebuild them (on the render's stream) when the clip has changed.
+// Composite renders with empty-space masks need masks built for a clip level
+// at or below the volume's clip (a cell that can reach the clip can reach
+// any lower one, so masks for a lower clip are conservative): rebuild them
+// (on the render's stream) when the clip has dropped below it.
 int ensure_masks(vr::Volume* v, int mode, cudaStream_t s)
 {
-    if (!v->mask || mode != VR_COMPOSITE || v->mask_clip == v->clip) return VR_OK;
+    if (!v->mask || mode != VR_COMPOSITE) return VR_OK;
+    if (!std::isnan(v->mask_clip) && !(v->clip < v->mask_clip)) return VR_OK;
     cudaError_t e = vr::launch_masks(*v, v->clip, s);
     if (e != cudaSuccess) return cuda_fail(e, "mask launch");
     v->mask_clip = v->clip;
@@ -727,7 +730,8 @@ int vr_volume_attach_masks(vr_volume vol, void* buf, size_t bytes)
     if (v->texture_only)
         return fail(VR_ERR_UNSUPPORTED, "masks are built from the bricks, which were dropped");
     const size_t nm = mask_macrocells(v->g);
-    if (nm > 0x7fffffffu) return fail(VR_ERR_UNSUPPORTED, "more than 2^31 macrocells");
+    if (nm > 0x7fffffffu || (v->g.ny >> vr::kMacroShift) + 1 > 65535)
+        return fail(VR_ERR_UNSUPPORTED, "cube too large for empty-space masks");
     if (reinterpret_cast<uintptr_t>(buf) % 16 != 0)
         return fail(VR_ERR_ARG, "mask buffer must be 16-byte aligned");
     if (bytes < nm * sizeof(unsigned long long))

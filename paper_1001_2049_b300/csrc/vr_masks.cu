@@ -37,62 +37,101 @@ __device__ __forceinline__ float voxel(const void* __restrict__ b, size_t i)
     return (float)__ldg(static_cast<const signed char*>(b) + i);
 }
 
-// One block of 64 threads per macrocell, thread t the cell
-// (t & 3, (t >> 2) & 3, t >> 4) of it.
+// One block of 16 warps per column of 8 x 1 macrocells (walked along z):
+// for each macrocell row, warp w takes cell
+// row (y, z) = (w & 3, w >> 2) of the macrocells, lane l the cell at gather
+// coordinate x = 32 bx + l.  The block's corner voxels (33 x 5 x 5, indices
+// clamped to the cube) are staged once in shared memory, decoded.
+// A warp's ballot holds 4 x-bits of each of the 8 macrocells for its (y, z);
+// eight threads assemble the masks from the 16 ballots.
+constexpr int kMaskWarps = 16;
+constexpr int kTileX = 33, kTileYZ = 5;
+
 template <int DT>
-__global__ void __launch_bounds__(64) mask_kernel(const void* __restrict__ bricks,
-                                                  const float* __restrict__ scale,
-                                                  const float* __restrict__ offset,
-                                                  VolumeGeom g, unsigned* __restrict__ out,
-                                                  int mnx, int mny, float clip)
+__global__ void __launch_bounds__(32 * kMaskWarps) mask_kernel(
+    const void* __restrict__ bricks, const float* __restrict__ scale,
+    const float* __restrict__ offset, VolumeGeom g, unsigned long long* __restrict__ out,
+    int mnx, int mny, int mnz, float clip)
 {
-    const unsigned m = blockIdx.x;
-    const int mx = (int)(m % mnx), my = (int)((m / mnx) % mny), mz = (int)(m / ((unsigned)mnx * mny));
-    const int t = threadIdx.x;
-    const int gx = (mx << kMacroShift) + (t & 3);           // gather coordinates: cell + 1
-    const int gy = (my << kMacroShift) + ((t >> 2) & 3);
-    const int gz = (mz << kMacroShift) + (t >> 4);
-    bool need = false;
-    if (gx <= g.nx && gy <= g.ny && gz <= g.nz) {
-        const int cx = min(max(gx - 1, 0), g.nx - 2);
-        const int cy = min(max(gy - 1, 0), g.ny - 2);
-        const int cz = min(max(gz - 1, 0), g.nz - 2);
-        float hi = -INFINITY, mag = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int x = cx + (c & 1), y = cy + ((c >> 1) & 1), z = cz + (c >> 2);
-            const size_t brick =
-                ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) * g.nbx + (x >> kBrickShift);
+    __shared__ float s_v[kTileYZ][kTileYZ][kTileX];
+    __shared__ unsigned s_ballot[kMaskWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // tile origin: the block's first cell, clamped like every cell (the
+    // clamped cells of the block then lie in [origin, origin + 31] along x
+    // and [origin, origin + 3] along y and z, clamping being 1-Lipschitz)
+    const int x0 = min(max((int)blockIdx.x * 32 - 1, 0), g.nx - 2);
+    const int y0 = min(max((int)blockIdx.y * 4 - 1, 0), g.ny - 2);
+    const int gx = blockIdx.x * 32 + lane;                      // gather coordinates: cell + 1
+    const int gy = blockIdx.y * 4 + (w & 3);
+    // one row of macrocells along z after the other (the block walks its
+    // column, so the launch has few blocks)
+    for (int bz = 0; bz < mnz; ++bz) {
+        const int z0 = min(max(bz * 4 - 1, 0), g.nz - 2);
+        __syncthreads();                 // the previous row's tile and ballots are used up
+        for (int i = threadIdx.x; i < kTileX * kTileYZ * kTileYZ; i += 32 * kMaskWarps) {
+            const int tx = i % kTileX, ty = (i / kTileX) % kTileYZ, tz = i / (kTileX * kTileYZ);
+            const int x = min(x0 + tx, g.nx - 1);
+            const int y = min(y0 + ty, g.ny - 1);
+            const int z = min(z0 + tz, g.nz - 1);
+            const size_t brick = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) * g.nbx +
+                                 (x >> kBrickShift);
             float v = voxel<DT>(bricks, brick * kBrickVoxels + ((z & 31) << 10) + ((y & 31) << 5) +
                                             (x & 31));
             if (DT == VR_I8) v = fmaf(v, __ldg(scale + z), __ldg(offset + z));
-            hi = fmaxf(hi, v);
-            mag = fmaxf(mag, fabsf(v));
+            s_v[tz][ty][tx] = v;
         }
-        need = !(fmaf(mag, 0x1p-19f, hi) < clip);
+        __syncthreads();
+        const int gz = bz * 4 + (w >> 2);
+        bool need = false;
+        if (gx <= g.nx && gy <= g.ny && gz <= g.nz) {
+            // the cell's corners, as tile indices (cells clamped to the cube)
+            const int cx = min(max(gx - 1, 0), g.nx - 2) - x0;
+            const int cy = min(max(gy - 1, 0), g.ny - 2) - y0;
+            const int cz = min(max(gz - 1, 0), g.nz - 2) - z0;
+            float hi = -INFINITY, mag = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float v = s_v[cz + (c >> 2)][cy + ((c >> 1) & 1)][cx + (c & 1)];
+                hi = fmaxf(hi, v);
+                mag = fmaxf(mag, fabsf(v));
+            }
+            need = !(fmaf(mag, 0x1p-19f, hi) < clip);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, need);
+        if (lane == 0) s_ballot[w] = b;
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            const int mx = blockIdx.x * 8 + threadIdx.x;
+            if (mx < mnx) {
+                unsigned long long m = 0;
+#pragma unroll
+                for (int i = 0; i < kMaskWarps; ++i) {
+                    const unsigned long long nib = (s_ballot[i] >> (4 * threadIdx.x)) & 0xfu;
+                    m |= nib << (4 * (i & 3) + 16 * (i >> 2));      // bit x | y << 2 | z << 4
+                }
+                out[((size_t)bz * mny + blockIdx.y) * mnx + mx] = m;
+            }
+        }
     }
-    const unsigned word = __ballot_sync(0xffffffffu, need);
-    if ((t & 31) == 0) out[2 * (size_t)m + (t >> 5)] = word;
 }
 
 }  // namespace
 
 cudaError_t launch_masks(const Volume& v, float clip, cudaStream_t s)
 {
-    const unsigned nm = (unsigned)v.mnx * v.mny * v.mnz;
-    unsigned* out = reinterpret_cast<unsigned*>(v.mask);
+    const dim3 grid((unsigned)((v.mnx + 7) / 8), (unsigned)v.mny);
     switch (v.dtype) {
     case VR_F32:
-        mask_kernel<VR_F32><<<nm, 64, 0, s>>>(v.bricks, v.scale, v.offset, v.g, out, v.mnx, v.mny,
-                                              clip);
+        mask_kernel<VR_F32><<<grid, 32 * kMaskWarps, 0, s>>>(v.bricks, v.scale, v.offset, v.g,
+                                                             v.mask, v.mnx, v.mny, v.mnz, clip);
         break;
     case VR_F16:
-        mask_kernel<VR_F16><<<nm, 64, 0, s>>>(v.bricks, v.scale, v.offset, v.g, out, v.mnx, v.mny,
-                                              clip);
+        mask_kernel<VR_F16><<<grid, 32 * kMaskWarps, 0, s>>>(v.bricks, v.scale, v.offset, v.g,
+                                                             v.mask, v.mnx, v.mny, v.mnz, clip);
         break;
     default:
-        mask_kernel<VR_I8><<<nm, 64, 0, s>>>(v.bricks, v.scale, v.offset, v.g, out, v.mnx, v.mny,
-                                             clip);
+        mask_kernel<VR_I8><<<grid, 32 * kMaskWarps, 0, s>>>(v.bricks, v.scale, v.offset, v.g,
+                                                            v.mask, v.mnx, v.mny, v.mnz, clip);
         break;
     }
     return cudaGetLastError();

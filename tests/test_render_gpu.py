@@ -536,18 +536,28 @@ def test_masks_mark_every_cell_that_can_reach_the_clip(dims, dtype):
     z, y, x = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1),
                           indexing="ij")
     bit = ((x & 3) | ((y & 3) << 2) | ((z & 3) << 4)).astype(np.uint64)
-    for clip in (2.0, 4.5):
+    def bits(clip):
         vol.set_transfer(synth.default_lut(16), clip, 9.0, clip, 1.0)
-        vol.render(cams, 4, 4, "composite", 0.5)     # builds the masks for this clip
+        vol.render(cams, 4, 4, "composite", 0.5)     # builds the masks when needed
         torch.cuda.synchronize()
         words = vol._masks.cpu().numpy().view(np.uint64)[:mnx * mny * mnz]
         words = words.reshape(mnz, mny, mnx)
-        got = ((words[z >> 2, y >> 2, x >> 2] >> bit) & np.uint64(1)).astype(bool)
+        return ((words[z >> 2, y >> 2, x >> 2] >> bit) & np.uint64(1)).astype(bool)
+
+    def check(got, clip):
         want = bound >= clip
         clear = np.abs(bound - clip) > 1e-5 * max(1.0, abs(clip))   # not a rounding tie
         assert (got == want)[clear].all(), (dtype, dims, clip)
         # a clear bit never hides a corner at or above the clip
         assert not (~got & (hi >= clip)).any()
+
+    for clip in (2.0, 4.5):                 # fresh masks are exact for their clip
+        vol.attach_masks()
+        check(bits(clip), clip)
+    low = bits(2.0)                         # lowering the clip rebuilds them
+    check(low, 2.0)
+    assert (bits(4.5) == low).all()         # raising it keeps them (conservative)
+    check(bits(1.5), 1.5)
 
 
 def _skip_cases(dims, seed):
