@@ -230,6 +230,47 @@ int vr_volume_detach_texture(vr_volume vol);
  * bricks and texture would not both fit, e.g. several 32 GiB FP16 cubes.    */
 int vr_volume_drop_bricks(vr_volume vol);
 
+/* ---- cubes larger than the device: rendering part by part ---------------
+ * The paper's pipeline partitions the cube into sub-cubes, renders each into
+ * an image and composites the images (§3.1 items 1, 4, 5; abstract: data
+ * larger than GPU memory).  Here a part is an ordinary volume holding planes
+ * [z_first, z_first + nz) of the whole cube (with texture storage), and
+ * vr_render_part continues images from the state they hold: each ray of the
+ * whole cube takes, in order, its samples whose cell (floor of the sample
+ * height) lies in [cell_lo, cell_hi), each sample computed exactly as the
+ * one-pass vr_render computes it, so rendering every part in the rays' order
+ * gives the one-pass images bit for bit.  Rays going up in z (sweep +1)
+ * must see the parts in ascending order, rays going down (sweep -1) in
+ * descending order: a caller renders the ascending sweep with sweep = +1
+ * and the descending sweep with sweep = -1 (one of them is empty when every
+ * ray of the views goes the same way; MIP needs no order but takes the same
+ * calls).                                                                  */
+
+/* Fill n_views images of w x h pixels with the empty state of `mode` (0 for
+ * COMPOSITE and SUM, -inf for MIP) before the first vr_render_part.  out as
+ * in vr_render.                                                            */
+int vr_render_init(float* out, int n_views, int w, int h, int mode, void* stream);
+
+/* Continue the images in `out` with the part's samples (see above).
+ *   part         volume of planes [z_first, z_first + nz_part) of the cube,
+ *                with texture storage; its transfer function is used.
+ *   full_dims    the whole cube's nx, ny (equal to the part's), nz.
+ *   cell_lo, cell_hi  cells [cell_lo, cell_hi) (the cell between planes c
+ *                and c + 1 is cell c), within the part's planes:
+ *                z_first <= cell_lo <= cell_hi <= z_first + nz_part - 1.
+ *                cell_lo = 0 also takes positions a rounding error below
+ *                plane 0, cell_hi = nz - 1 those above the top plane.  The
+ *                parts' ranges must tile [0, nz - 1).
+ *   sweep        +1: rays with dz >= 0; -1: rays with dz < 0.
+ *   out          images as left by vr_render_init or earlier parts.
+ *   d_samples    optional count of evaluated samples (added to).
+ * Other arguments as in vr_render.  COMPOSITE rays that terminated in an
+ * earlier part are left as they are.                                       */
+int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
+                   int64_t cell_lo, int64_t cell_hi, const vr_camera* cams, int n_views,
+                   int w, int h, int mode, float step, int sweep, float* out,
+                   unsigned long long* d_samples, void* stream);
+
 /* ---- many requests in one persistent launch ------------------------------
  * The paper's scheduler maps available tasks onto the computing resources
  * (Fig. 1 caption; §3.1 module 1).  Here the tasks are the 16 x 16 ray tiles

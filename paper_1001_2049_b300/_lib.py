@@ -37,6 +37,10 @@ SIGNATURES = {
     "vr_volume_attach_pair_texture": (c_int, [c_void_p, c_void_p]),
     "vr_volume_detach_texture": (c_int, [c_void_p]),
     "vr_volume_drop_bricks": (c_int, [c_void_p]),
+    "vr_render_init": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p]),
+    "vr_render_part": (c_int, [c_void_p, ctypes.POINTER(c_int64), c_int64, c_int64, c_int64,
+                               c_void_p, c_int, c_int, c_int, c_int, c_float, c_int, c_void_p,
+                               c_void_p, c_void_p]),
     "vr_volume_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int),
                                ctypes.POINTER(c_void_p)]),
     "vr_batch_workspace_bytes": (c_size_t, []),

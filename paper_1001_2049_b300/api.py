@@ -73,6 +73,17 @@ class Request:
     done_value: int = 1
 
 
+def render_init(out: torch.Tensor, mode: str, stream=None) -> torch.Tensor:
+    """Fill images (views, h, w[, 4]) with the empty state of ``mode`` (0, or
+    -inf for MIP) before rendering a cube part by part."""
+    m = MODES[mode]
+    if out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
+        raise ValueError("out must be a contiguous float32 CUDA tensor")
+    views, h, w = out.shape[:3]
+    check(load().vr_render_init(out.data_ptr(), views, w, h, m, _stream_ptr(stream)))
+    return out
+
+
 def batch_workspace(device=None) -> torch.Tensor:
     n = load().vr_batch_workspace_bytes()
     return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
@@ -263,6 +274,27 @@ class Volume:
             check(lib.vr_render_counted(self._h, cams.ctypes.data, len(cams), w, h, m,
                                         float(step), out.data_ptr(), count.data_ptr(),
                                         _stream_ptr(stream)))
+        return out
+
+    def render_part(self, full_dims, z_first: int, cell_lo: int, cell_hi: int, cams: np.ndarray,
+                    w: int, h: int, mode: str, step: float, sweep: int, out: torch.Tensor,
+                    count: torch.Tensor | None = None, stream=None):
+        """This volume holds planes [z_first, z_first + nz) of a cube of
+        ``full_dims``: continue ``out`` (from render_init or earlier parts)
+        with the samples of cells [cell_lo, cell_hi) of the rays going up
+        (sweep +1) or down (sweep -1)."""
+        cams = np.ascontiguousarray(cams)
+        m = MODES[mode]
+        shape = (len(cams), h, w, 4) if m == VR_COMPOSITE else (len(cams), h, w)
+        if tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 tensor of shape %s" % (shape,))
+        if count is not None and (count.dtype != torch.int64 or not count.is_cuda):
+            raise ValueError("count must be an int64 CUDA tensor")
+        check(load().vr_render_part(self._h, _dims_arr(full_dims), int(z_first), int(cell_lo),
+                                    int(cell_hi), cams.ctypes.data, len(cams), w, h, m,
+                                    float(step), int(sweep), out.data_ptr(),
+                                    count.data_ptr() if count is not None else None,
+                                    _stream_ptr(stream)))
         return out
 
     def autotune(self, cams: np.ndarray, w: int, h: int, mode: str = "composite",

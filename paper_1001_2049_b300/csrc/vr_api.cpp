@@ -2,6 +2,7 @@
 // validation, volume handles, transfer-function preparation and launch
 // planning.  No device memory is allocated here; all of it is the caller's.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -707,6 +708,69 @@ int vr_volume_drop_bricks(vr_volume vol)
     v->texture_only = true;
     v->bricks = nullptr;
     v->mask = nullptr;
+    return VR_OK;
+}
+
+int vr_render_init(float* out, int n_views, int w, int h, int mode, void* stream)
+{
+    if (!out) return fail(VR_ERR_ARG, "out is NULL");
+    if (n_views < 1 || w < 1 || h < 1) return fail(VR_ERR_ARG, "empty image set");
+    if (mode != VR_MIP && mode != VR_COMPOSITE && mode != VR_SUM)
+        return fail(VR_ERR_ARG, "unknown mode %d", mode);
+    if (reinterpret_cast<uintptr_t>(out) % 16 != 0)
+        return fail(VR_ERR_ARG, "out must be 16-byte aligned");
+    if (!is_device_ptr(out)) return fail(VR_ERR_ARG, "out is not device memory of this device");
+    cudaError_t e = vr::launch_render_init(out, (size_t)n_views * w * h, mode,
+                                           static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? VR_OK : cuda_fail(e, "init launch");
+}
+
+int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
+                   int64_t cell_lo, int64_t cell_hi, const vr_camera* cams, int n_views,
+                   int w, int h, int mode, float step, int sweep, float* out,
+                   unsigned long long* d_samples, void* stream)
+{
+    if (!part) return fail(VR_ERR_ARG, "volume is NULL");
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(part);
+    if (!full_dims) return fail(VR_ERR_ARG, "full_dims is NULL");
+    if (!v->has_tex) return fail(VR_ERR_UNSUPPORTED, "part rendering needs texture storage");
+    if (full_dims[0] != v->g.nx || full_dims[1] != v->g.ny)
+        return fail(VR_ERR_ARG, "the part's nx, ny differ from the cube's");
+    if (z_first < 0 || z_first + v->g.nz > full_dims[2] || full_dims[2] > (1 << 20))
+        return fail(VR_ERR_ARG, "part planes [%lld, %lld) outside the cube's %lld",
+                    (long long)z_first, (long long)(z_first + v->g.nz), (long long)full_dims[2]);
+    if (cell_lo < z_first || cell_hi > z_first + v->g.nz - 1 || cell_lo > cell_hi)
+        return fail(VR_ERR_ARG, "cells [%lld, %lld) are not within the part's planes [%lld, %lld]",
+                    (long long)cell_lo, (long long)cell_hi, (long long)z_first,
+                    (long long)(z_first + v->g.nz - 1));
+    if (sweep != 1 && sweep != -1) return fail(VR_ERR_ARG, "sweep must be +1 or -1");
+    vr::MarchParams p;
+    vr::TexParams tp;
+    int rc = prepare(part, cams, n_views, w, h, mode, step, out, d_samples, &p, &tp);
+    if (rc) return rc;
+    // the whole cube's box and sample bound; the part's cells and slices
+    const double hz = full_dims[2] - 1.0;
+    const double hx = v->g.nx - 1.0, hy = v->g.ny - 1.0;
+    const double diag = std::sqrt(hx * hx + hy * hy + hz * hz);
+    if (diag / step + 2.0 >= 16777216.0)
+        return fail(VR_ERR_ARG, "step %g too small: a ray could take 2^24 samples", (double)step);
+    p.hiz = (float)hz;
+    tp.k_max = (int)(diag / step) + 2;
+    p.part_lo = cell_lo == 0 ? INT_MIN : (int)cell_lo;
+    p.part_hi = cell_hi == full_dims[2] - 1 ? INT_MAX : (int)cell_hi;
+    p.slice_base = (int)z_first;
+    p.sweep = sweep;
+    p.mask = nullptr;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t per_view = (size_t)w * h * (mode == VR_COMPOSITE ? 4 : 1);
+    for (int v0 = 0; v0 < n_views; v0 += vr::kMaxViewsPerLaunch) {
+        const int nv = std::min(vr::kMaxViewsPerLaunch, n_views - v0);
+        p.n_views = nv;
+        std::memcpy(p.cams, cams + v0, sizeof(vr_camera) * nv);
+        p.out = out + per_view * v0;
+        cudaError_t e = vr::launch_part(p, tp, v->tex_format, mode, s);
+        if (e != cudaSuccess) return cuda_fail(e, "part launch");
+    }
     return VR_OK;
 }
 

@@ -100,6 +100,9 @@ struct MarchParams {
     unsigned long long* samples;   // may be null
     const unsigned long long* mask;   // empty-space masks for `clip` (COMPOSITE), or null
     int mnx, mny, mlast;              // macrocells along x, y; last macrocell index
+    // rendering one part of a larger cube (vr_render_part): the cells of the
+    // part, the part's first plane, which rays (+1 going up, -1 going down)
+    int part_lo, part_hi, slice_base, sweep;
     vr_camera cams[kMaxViewsPerLaunch];
     float4 lut[VR_MAX_LUT];
 };
@@ -180,6 +183,18 @@ size_t slab_window_elems(const SlabConfig& c);
 bool plan_slab(const MarchParams& p, SlabConfig* c);
 cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int format, int mode, int cfg,
                        cudaStream_t s);
+// Render one part of a larger cube, continuing the images in p.out.
+cudaError_t launch_part(const MarchParams& p, const TexParams& t, int format, int mode,
+                        cudaStream_t s);
+cudaError_t launch_part_f32(const MarchParams& p, const TexParams& t, int mode, cudaStream_t s);
+cudaError_t launch_part_f16(const MarchParams& p, const TexParams& t, int mode, cudaStream_t s);
+cudaError_t launch_part_i8(const MarchParams& p, const TexParams& t, int mode, cudaStream_t s);
+cudaError_t launch_part_f16pair(const MarchParams& p, const TexParams& t, int mode,
+                                cudaStream_t s);
+cudaError_t launch_part_i8pair(const MarchParams& p, const TexParams& t, int mode,
+                               cudaStream_t s);
+// Fill n_pixels images with the empty state of `mode` (0 / -inf / 0).
+cudaError_t launch_render_init(float* out, size_t n_pixels, int mode, cudaStream_t s);
 // One texel format each (vr_tex_<format>.cu).
 cudaError_t launch_tex_f32(const MarchParams& p, const TexParams& t, int mode, int cfg,
                            cudaStream_t s);

@@ -465,6 +465,86 @@ __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4*
     return k;
 }
 
+// ---- rendering a cube part by part ----
+// A part holds planes [base, base + n) of a larger cube (its slices are the
+// part's own: local slice = global slice - base).  Rendering a part marches,
+// of each ray of the whole cube, the samples whose cell (floor of the sample
+// height) lies in [lo, hi): cells whose two planes are both in the part (the
+// first part also takes the cells below plane 0, the last those above the
+// top plane, positions a rounding error outside the box).  Sample heights
+// are monotone in k, so those samples are one range of k, found by bisection
+// with the march's own position arithmetic.
+
+// Cell (floor of the height) of sample k.
+template <typename PP>
+__device__ __forceinline__ float sample_cell(const PP& P, const Ray& r, int k)
+{
+    return floorf(fmaf(fmaf((float)k, P.step, r.te), r.dz, r.oz));
+}
+
+// First k in [0, K] whose cell satisfies `past` (false before it, true from
+// it on: the predicate is monotone in k).
+template <typename PP, typename F>
+__device__ __forceinline__ int first_k(const PP& P, const Ray& r, F past)
+{
+    int a = 0, b = r.K;
+    while (a < b) {
+        const int m = (a + b) >> 1;
+        if (past(sample_cell(P, r, m)))
+            b = m;
+        else
+            a = m + 1;
+    }
+    return a;
+}
+
+// Samples [k0, k1) of the part's cells, for a ray going up (dz >= 0) or down.
+template <typename PP>
+__device__ __forceinline__ void part_range(const PP& P, const Ray& r, int& k0, int& k1)
+{
+    const float lo = (float)P.part_lo, hi = (float)P.part_hi;
+    if (r.dz >= 0.0f) {
+        k0 = first_k(P, r, [&](float c) { return c >= lo; });
+        k1 = first_k(P, r, [&](float c) { return c >= hi; });
+    } else {
+        k0 = first_k(P, r, [&](float c) { return c < hi; });
+        k1 = first_k(P, r, [&](float c) { return c < lo; });
+    }
+}
+
+// march_tex over samples [k0, k1) of a part, continuing `acc`; slices are
+// shifted to the part's own.  Returns the number of samples evaluated.
+template <int DT, int MODE, bool STACK, typename PP, typename TT>
+__device__ __forceinline__ int march_part(const PP& P, const TT& T,
+                                          const float4* __restrict__ lut, const Ray& r,
+                                          Acc<MODE>& acc, int k0, int k1)
+{
+    if (k0 >= k1) return 0;
+    const cudaTextureObject_t t0 = T.tex;
+    int k = k0;
+    float kf = (float)k0;
+    Geo ga = geo(P, r, kf), gb;
+    ga.iz -= P.slice_base;
+    float4 a0, a1, b0, b1;
+    cell<DT, STACK>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
+    kf += 1.0f;
+    for (;;) {
+        gb = geo(P, r, kf);
+        gb.iz -= P.slice_base;
+        next_cell<DT, STACK>(T, t0, ga, a0, a1, gb, b0, b1);
+        ++k;
+        if (acc.add(P, lut, interp(a0, a1, ga)) || k >= k1) break;
+        kf += 1.0f;
+        ga = geo(P, r, kf);
+        ga.iz -= P.slice_base;
+        next_cell<DT, STACK>(T, t0, gb, b0, b1, ga, a0, a1);
+        ++k;
+        if (acc.add(P, lut, interp(b0, b1, gb)) || k >= k1) break;
+        kf += 1.0f;
+    }
+    return k - k0;
+}
+
 template <int DT>
 __device__ __forceinline__ float load_voxel(const void* b, size_t i)
 {

@@ -4,6 +4,7 @@
 //
 // Layers: a layered texture holds at most kMaxLayers layers, so deeper cubes
 // stack 2^shift planes per layer (see write_slice_row).
+#include <algorithm>
 #include <type_traits>
 
 #include <cuda_fp16.h>
@@ -91,6 +92,35 @@ cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int format, int
     case kI8Pair: return launch_tex_i8pair(p, t, mode, cfg, s);
     default: return launch_tex_i8(p, t, mode, cfg, s);
     }
+}
+
+cudaError_t launch_part(const MarchParams& p, const TexParams& t, int format, int mode,
+                        cudaStream_t s)
+{
+    switch (format) {
+    case VR_F32: return launch_part_f32(p, t, mode, s);
+    case VR_F16: return launch_part_f16(p, t, mode, s);
+    case kF16Pair: return launch_part_f16pair(p, t, mode, s);
+    case kI8Pair: return launch_part_i8pair(p, t, mode, s);
+    default: return launch_part_i8(p, t, mode, s);
+    }
+}
+
+namespace {
+__global__ void __launch_bounds__(256) init_kernel(float* __restrict__ out, size_t n, float v)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = v;
+}
+}  // namespace
+
+cudaError_t launch_render_init(float* out, size_t n_pixels, int mode, cudaStream_t s)
+{
+    const size_t n = n_pixels * (mode == VR_COMPOSITE ? 4 : 1);
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 148 * 32);
+    init_kernel<<<blocks, 256, 0, s>>>(out, n, mode == VR_MIP ? -INFINITY : 0.0f);
+    return cudaGetLastError();
 }
 
 int tex_shape_count() { return tex::kNumShapes; }

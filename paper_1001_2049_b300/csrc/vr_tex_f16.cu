@@ -1,5 +1,5 @@
-// vr_tex_f16.cu -- the texture-gather march instantiated for one texel
-// format (see vr_tex_kernel.cuh).
+// vr_tex_f16.cu -- the texture-gather kernels (whole cube and cube part)
+// instantiated for one texel format (see vr_tex_kernel.cuh).
 #include "vr_tex_kernel.cuh"
 
 namespace vr {
@@ -8,6 +8,12 @@ cudaError_t launch_tex_f16(const MarchParams& p, const TexParams& t, int mode, i
                            cudaStream_t s)
 {
     return tex::launch_dt<VR_F16>(p, t, mode, cfg, s);
+}
+
+cudaError_t launch_part_f16(const MarchParams& p, const TexParams& t, int mode,
+                            cudaStream_t s)
+{
+    return tex::launch_part_dt<VR_F16>(p, t, mode, s);
 }
 
 }  // namespace vr

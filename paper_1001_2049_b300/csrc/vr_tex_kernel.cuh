@@ -126,5 +126,81 @@ cudaError_t launch_dt(const MarchParams& p, const TexParams& t, int mode, int cf
     }
 }
 
+// One part of a larger cube (vr_render_part): each ray of the whole cube
+// whose direction matches the sweep continues from the state in `out` with
+// the samples of the part's cells (the same samples, in the same order, as
+// the one-pass render takes there), then writes the state back.
+template <int DT, int MODE, bool STACK>
+__global__ void __launch_bounds__(256) part_kernel(const __grid_constant__ MarchParams P,
+                                                   const __grid_constant__ TexParams T)
+{
+    __shared__ float4 s_lut[VR_MAX_LUT];
+    if (MODE == VR_COMPOSITE) {
+        for (int i = threadIdx.x; i < P.n_lut; i += blockDim.x) s_lut[i] = P.lut[i];
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * 16 + (warp >> 1) * 4 + (lane >> 3);
+    const int view = blockIdx.z;
+    unsigned count = 0;
+    if (px < P.w && py < P.h) {
+        const ray::Ray r = ray::setup_ray(P, P.cams[view], px, py, T.k_max);
+        const bool mine = P.sweep > 0 ? r.dz >= 0.0f : r.dz < 0.0f;
+        if (r.K > 0 && mine) {
+            const size_t pix = ((size_t)view * P.h + py) * P.w + px;
+            ray::Acc<MODE> acc;
+            bool done = false;
+            if (MODE == VR_COMPOSITE) {
+                const float4 c = reinterpret_cast<const float4*>(P.out)[pix];
+                acc.r = c.x;
+                acc.g = c.y;
+                acc.b = c.z;
+                acc.A = c.w;
+                done = acc.A >= P.term_alpha;          // the ray stopped in an earlier part
+            } else {
+                acc.m = P.out[pix];
+            }
+            if (!done) {
+                int k0, k1;
+                ray::part_range(P, r, k0, k1);
+                count = (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r, acc, k0, k1);
+                if (MODE == VR_COMPOSITE)
+                    reinterpret_cast<float4*>(P.out)[pix] =
+                        make_float4(acc.r, acc.g, acc.b, acc.A);
+                else
+                    P.out[pix] = acc.m;
+            }
+        }
+    }
+    if (P.samples) {
+        const unsigned tot = __reduce_add_sync(0xffffffffu, count);
+        if (lane == 0 && tot) atomicAdd(P.samples, (unsigned long long)tot);
+    }
+}
+
+template <int DT>
+cudaError_t launch_part_dt(const MarchParams& p, const TexParams& t, int mode, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((p.w + 15) / 16), (unsigned)((p.h + 15) / 16),
+                    (unsigned)p.n_views);
+    const bool st = t.stack_shift > 0;
+    switch (mode) {
+    case VR_MIP:
+        st ? part_kernel<DT, VR_MIP, true><<<grid, 256, 0, s>>>(p, t)
+           : part_kernel<DT, VR_MIP, false><<<grid, 256, 0, s>>>(p, t);
+        break;
+    case VR_COMPOSITE:
+        st ? part_kernel<DT, VR_COMPOSITE, true><<<grid, 256, 0, s>>>(p, t)
+           : part_kernel<DT, VR_COMPOSITE, false><<<grid, 256, 0, s>>>(p, t);
+        break;
+    default:
+        st ? part_kernel<DT, VR_SUM, true><<<grid, 256, 0, s>>>(p, t)
+           : part_kernel<DT, VR_SUM, false><<<grid, 256, 0, s>>>(p, t);
+        break;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace tex
 }  // namespace vr

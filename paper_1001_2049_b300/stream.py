@@ -1,0 +1,144 @@
+"""Rendering a cube part by part, for cubes larger than the device.
+
+The paper's pipeline splits the cube into sub-cubes, renders each and
+combines the images (§3.1 items 1, 4, 5), and aims at data larger than GPU
+memory (abstract).  Here the cube stays with its source (page-locked host
+memory, or a generator) and passes through two part volumes on the device:
+while one part renders on the compute stream, the next is packed into the
+other (and its texture filled) on a copy stream.  Each part continues the
+images from the state the earlier parts left (``vr_render_part``), so the
+images are those of a one-pass render of the whole cube, bit for bit.
+
+Rays going up in z take the parts in ascending order and rays going down
+in descending order: a view set whose rays go both ways is rendered in two
+sweeps (the turning part is not loaded twice).  All rendering runs in the
+library's kernels; this module is host-side control.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from .api import MODES, Volume, render_init
+from ._lib import VR_COMPOSITE
+
+
+def sweeps(cams: np.ndarray, w: int, h: int):
+    """The sweeps a view set needs: +1 when some ray may go up in z (or be
+    level), -1 when some ray may go down.  The height component of a ray's
+    direction is an affine function of the pixel position, so its extremes
+    are at the image corners; a margin keeps near-level rays in both."""
+    need_up = need_down = False
+    for c in np.asarray(cams):
+        fz = float(c["fwd"][2])
+        if int(c["proj"]) == 0:
+            dz = [fz]
+        else:
+            dz = [fz + u * float(c["du"][2]) + v * float(c["dv"][2])
+                  for u in (0.5 - w / 2.0, w / 2.0 - 0.5) for v in (0.5 - h / 2.0, h / 2.0 - 0.5)]
+        scale = max(1e-30, max(abs(x) for x in dz), float(np.abs(c["fwd"]).max()))
+        need_up |= max(dz) >= -1e-5 * scale
+        need_down |= min(dz) < 1e-5 * scale
+    return ([1] if need_up else []) + ([-1] if need_down else [])
+
+
+@dataclass
+class Part:
+    z_first: int
+    cell_lo: int
+    cell_hi: int
+
+
+class PartStream:
+    """A cube of ``dims`` (nx, ny, nz) rendered in parts of ``part_planes``
+    planes.  ``source(z0, n)`` returns planes [z0, z0 + n) as a float32
+    tensor (n, ny, nx) on the device or in page-locked host memory; it is
+    called on the copy stream.  ``dtype`` is the parts' storage, ``pair``
+    selects pair-texel texture storage (FP16 / int8)."""
+
+    def __init__(self, dims, dtype: str, source, part_planes: int, device=None,
+                 pair: bool = False):
+        nx, ny, nz = (int(d) for d in dims)
+        if not 2 <= part_planes:
+            raise ValueError("a part needs at least two planes")
+        self.dims = (nx, ny, nz)
+        self.source = source
+        self.planes = min(part_planes, nz)
+        cells = self.planes - 1
+        self.parts = []
+        for lo in range(0, nz - 1, cells):
+            hi = min(lo + cells, nz - 1)
+            self.parts.append(Part(min(lo, nz - self.planes), lo, hi))
+        self.device = torch.device(device) if device is not None else torch.device("cuda")
+        self.vols = []
+        for _ in range(2 if len(self.parts) > 1 else 1):
+            v = Volume(dims=(nx, ny, self.planes), dtype=dtype, device=self.device)
+            v.attach_pair_texture() if pair else v.attach_texture()
+            self.vols.append(v)
+        self.holds = [None] * len(self.vols)        # z_first of the part each volume holds
+        # device staging for parts that come from host memory: one DMA copy
+        # per part, then packing from device memory
+        self.staging = [None] * len(self.vols)
+        self.copy = torch.cuda.Stream(self.device)
+        self.done = [torch.cuda.Event() for _ in self.vols]
+        self.bytes_loaded = 0
+
+    def set_transfer(self, lut, v_lo, v_hi, clip, term_alpha=1.0):
+        for v in self.vols:
+            v.set_transfer(lut, v_lo, v_hi, clip, term_alpha)
+
+    def _load(self, i: int, part: Part):
+        v = self.vols[i]
+        if self.holds[i] == part.z_first:
+            return
+        self.copy.wait_event(self.done[i])           # its last render has finished
+        with torch.cuda.stream(self.copy):
+            planes = self.source(part.z_first, self.planes)
+            if not planes.is_cuda:
+                if self.staging[i] is None or self.staging[i].shape != planes.shape:
+                    self.staging[i] = torch.empty(planes.shape, dtype=torch.float32,
+                                                  device=self.device)
+                self.staging[i].copy_(planes, non_blocking=True)
+                planes = self.staging[i]
+            v.upload(0, planes, stream=self.copy)    # packs and refreshes the texture
+        self.bytes_loaded += planes.numel() * planes.element_size()
+        self.holds[i] = part.z_first
+
+    def render(self, cams: np.ndarray, w: int, h: int, targets, step: float = 0.5,
+               count: torch.Tensor | None = None, stream=None):
+        """Render the views into every target: a list of (mode, out) pairs,
+        out a float32 tensor (views, h, w) or (views, h, w, 4); each part is
+        loaded once per sweep for all targets."""
+        stream = stream or torch.cuda.current_stream(self.device)
+        cams = np.ascontiguousarray(cams)
+        for mode, out in targets:
+            render_init(out, mode, stream)
+        step_order = []
+        for sw in sweeps(cams, w, h):
+            order = self.parts if sw > 0 else self.parts[::-1]
+            step_order += [(sw, p) for p in order]
+        slot = 0
+        for n, (sw, part) in enumerate(step_order):
+            held = [i for i, z in enumerate(self.holds) if z == part.z_first]
+            if held:
+                i = held[0]
+            else:
+                i = slot
+                slot = (slot + 1) % len(self.vols)
+                self._load(i, part)
+            loaded = torch.cuda.Event()
+            loaded.record(self.copy)
+            stream.wait_event(loaded)
+            for mode, out in targets:
+                self.vols[i].render_part(self.dims, part.z_first, part.cell_lo, part.cell_hi,
+                                         cams, w, h, mode, step, sw, out, count=count,
+                                         stream=stream)
+            self.done[i].record(stream)
+        return targets
+
+    def close(self):
+        for v in self.vols:
+            v.close()
+        self.vols = []

@@ -1,0 +1,103 @@
+"""Rendering a cube part by part (vr_render_part through stream.PartStream)
+gives the one-pass images and sample counts bit for bit: every sample is
+computed as the one-pass render computes it, in the same order along each
+ray, the parts continuing the images the earlier parts left."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1001_2049_b300 import Volume, VRError, render_init, synth
+from paper_1001_2049_b300.stream import PartStream, sweeps
+
+pytestmark = pytest.mark.gpu
+
+MODES = ("composite", "mip", "sum")
+
+
+def _case(dims, seed, w=29, h=19):
+    cube = synth.make_cube(dims, 3, ("uniform", 3.0, 8.0), seed)
+    cams = synth.random_sphere_cameras(dims, 4, w, h, seed, fov_deg=70.0)
+    c = np.array([(d - 1) / 2.0 for d in dims])
+    recs = [synth.look_at_camera(c + 0.3, c + np.array([5.0, -3.0, 2.0]), w, h, 90.0)]
+    recs += [synth.axis_camera(dims, w, h, axis=a, sign=sg) for a in range(3) for sg in (1, -1)]
+    cams = np.concatenate([cams, synth.cameras(recs).astype(cams.dtype)])
+    return cube, cams
+
+
+def _one_pass(cube, dtype, pair, cams, w, h, step, lut, tf):
+    vol = Volume(cube.cuda(), dtype)
+    vol.attach_pair_texture() if pair else vol.attach_texture()
+    vol.set_transfer(lut, *tf)
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    imgs = {m: vol.render(cams, w, h, m, step, count=n) for m in MODES}
+    torch.cuda.synchronize()
+    return imgs, int(n.item())
+
+
+@pytest.mark.parametrize("store", ["f32", "f16-pair", "i8", "i8-pair"])
+@pytest.mark.parametrize("dims,part_planes", [((37, 45, 70), 2), ((37, 45, 70), 9),
+                                              ((37, 45, 70), 16), ((20, 17, 9), 64),
+                                              ((6, 5, 4500), 700)])
+def test_parts_give_the_one_pass_images(store, dims, part_planes):
+    dtype, _, pair = store.partition("-")
+    cube, cams = _case(dims, 80 + part_planes)
+    w, h, step = 29, 19, 0.37
+    lut = synth.default_lut(64)
+    tf = (1.0, 8.0, 1.0, 0.95)
+    ref, n_ref = _one_pass(cube, dtype, bool(pair), cams, w, h, step, lut, tf)
+    dev = cube.cuda()
+    ps = PartStream(dims, dtype, lambda z0, n: dev[z0:z0 + n], part_planes, pair=bool(pair))
+    ps.set_transfer(lut, *tf)
+    outs = [(m, torch.empty(ref[m].shape, dtype=torch.float32, device="cuda")) for m in MODES]
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ps.render(cams, w, h, outs, step, count=n)
+    torch.cuda.synchronize()
+    for m, out in outs:
+        assert torch.equal(out, ref[m]), (store, dims, part_planes, m)
+    assert int(n.item()) == n_ref
+    ps.close()
+
+
+def test_parts_from_pinned_host_memory_and_one_way_views():
+    dims = (48, 40, 96)
+    cube = synth.make_cube(dims, 4, ("uniform", 3.0, 8.0), 91).pin_memory()
+    w, h = 32, 24
+    # orthographic views along -z and +z: one sweep each
+    down = synth.cameras([synth.axis_camera(dims, w, h, axis=2, sign=-1)])
+    up = synth.cameras([synth.axis_camera(dims, w, h, axis=2, sign=1)])
+    assert sweeps(down, w, h) == [-1] and sweeps(up, w, h) == [1]
+    lut = synth.default_lut(32)
+    for cams in (down, up, np.concatenate([down, up])):
+        ref, n_ref = _one_pass(cube, "f32", False, cams, w, h, 0.5, lut, (1.0, 8.0, 1.0, 0.9))
+        ps = PartStream(dims, "f32", lambda z0, n: cube[z0:z0 + n], 17)
+        ps.set_transfer(lut, 1.0, 8.0, 1.0, 0.9)
+        out = torch.empty(ref["composite"].shape, dtype=torch.float32, device="cuda")
+        n = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ps.render(cams, w, h, [("composite", out)], 0.5, count=n)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref["composite"])
+        # each part is loaded once per sweep, except that the second sweep
+        # starts with the parts the two part volumes still hold
+        n_sweeps = len(sweeps(cams, w, h))
+        loads = len(ps.parts) * n_sweeps - (n_sweeps - 1) * min(len(ps.vols), len(ps.parts))
+        assert ps.bytes_loaded == loads * 17 * 40 * 48 * 4
+        ps.close()
+
+
+def test_part_arguments_are_checked():
+    dims = (16, 16, 40)
+    cube = synth.make_cube(dims, 2, ("uniform", 3.0, 8.0), 5).cuda()
+    part = Volume(cube[10:20].contiguous(), "f32")
+    cams = synth.random_sphere_cameras(dims, 1, 8, 8, 1)
+    out = render_init(torch.empty((1, 8, 8), device="cuda"), "mip")
+    assert torch.isinf(out).all() and (out < 0).all()
+    with pytest.raises(VRError):          # no texture storage
+        part.render_part(dims, 10, 10, 19, cams, 8, 8, "mip", 0.5, 1, out)
+    part.attach_texture()
+    with pytest.raises(VRError):          # cells beyond the part's planes
+        part.render_part(dims, 10, 10, 20, cams, 8, 8, "mip", 0.5, 1, out)
+    with pytest.raises(VRError):          # planes beyond the cube
+        part.render_part((16, 16, 15), 10, 10, 14, cams, 8, 8, "mip", 0.5, 1, out)
+    with pytest.raises(VRError):
+        part.render_part(dims, 10, 10, 19, cams, 8, 8, "mip", 0.5, 0, out)
+    part.render_part(dims, 10, 10, 19, cams, 8, 8, "mip", 0.5, 1, out)
