@@ -197,6 +197,73 @@ def oracle_throughput(host_cube, cams, wl, budget_s, seed=5, w=W, h=H):
     return samples / secs, fps, oracle.num_threads(), sample
 
 
+def precision_leg(cube, cams, W, H, wl, lut, pixels, reps=3):
+    """The same cube and views stored as FP16 and as int8 with per-plane
+    scale and offset (pair-texel texture storage, empty-space masks for the
+    composite launch): launch times, and the images' values at ``pixels``
+    for the error against the oracle (evaluated in the CPU leg)."""
+    out, values = {}, {}
+    stream = torch.cuda.current_stream()
+    comp = torch.empty((len(cams), H, W, 4), dtype=torch.float32, device=cube.device)
+    mip = torch.empty((len(cams), H, W), dtype=torch.float32, device=cube.device)
+    idx = torch.from_numpy(pixels.astype(np.int64)).to(cube.device)
+    for dt in ("f16", "i8"):
+        v = Volume(cube, dt)
+        v.attach_pair_texture()
+        v.attach_masks()
+        v.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
+        row = {"storage": dt + " pair-texel texture"}
+        for mode, img in (("composite", comp), ("mip", mip)):
+            cfg, _ = v.autotune(cams, W, H, mode, wl.step, out=img)
+            ms = event_ms(lambda: v.render(cams, W, H, mode, wl.step, out=img), reps, stream)
+            row[mode + "_ms_per_launch"] = ms
+            row[mode + "_shape"] = cfg
+            values[(dt, mode)] = img[idx[:, 0], idx[:, 2], idx[:, 1]].cpu().numpy()
+        out[dt] = row
+        v.close()
+    return out, values
+
+
+def oracle_errors(host_cube, cams, wl, pixels, values, w=W, h=H):
+    """The oracle at ``pixels`` (view, px, py) on the float32 source cube and
+    on each storage's decoded cube; the largest error of each GPU image there
+    against the oracle's acceptance set (max abs per channel; MIP divided by
+    the cube's max - min), and how many pixels exceed the stated tolerance."""
+    import oracle
+    from oracle import quantize
+    eye = float(np.abs(np.asarray(cams["eye"], dtype=np.float64)).max())
+    t_scale = eye + math.sqrt(sum((d - 1.0) ** 2 for d in wl.dims)) + max(wl.dims)
+    ulp = 2.0 ** -23
+    bands = oracle.Bands(band_k=2e-3 + 64 * ulp * t_scale / wl.step,
+                         band_pos=16 * ulp * max(1.0, t_scale), band_clip=1e-4, band_a=1e-4)
+    tf = oracle.TF(synth.default_lut(), wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
+    vols = {"f32": oracle.Volume(host_cube)}
+    if any(dt == "f16" for dt, _ in values):
+        vols["f16"] = oracle.Volume(quantize.to_f16(host_cube))
+    if any(dt == "i8" for dt, _ in values):
+        vols["i8"] = oracle.Volume(*quantize.quantize_i8(host_cube))
+    tol = {"f32": 1e-4, "f16": 2e-3, "i8": 1e-2}
+    mip_scale = float(host_cube.max() - host_cube.min())
+    res = {}
+    for mode_name, mode in (("composite", oracle.COMPOSITE), ("mip", oracle.MIP)):
+        ch = 4 if mode == oracle.COMPOSITE else 1
+        scale = 1.0 if mode == oracle.COMPOSITE else mip_scale
+        ref = {k: oracle.render(vol, cams, w, h, mode, wl.step, tf, pixels=pixels, bands=bands)
+               for k, vol in vols.items()}
+        for (dt, m), got in values.items():
+            if m != mode_name:
+                continue
+            row = res.setdefault(dt, {}).setdefault(mode_name, {})
+            for against in ("f32", dt) if dt != "f32" else ("f32",):
+                t = 1e-4 if against == dt else tol[dt]
+                ok, err = oracle.match(ref[against], got.reshape(-1, ch), t, ch, scale)
+                fin = err[np.isfinite(err)]
+                key = "vs_float32_source" if against == "f32" else "vs_decoded_storage"
+                row[key] = {"max_err": float(fin.max()) if fin.size else 0.0, "tol": t,
+                            "pixels_over_tol": int((~ok).sum())}
+    return {"pixels": int(len(pixels)), "errors": res}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -615,12 +682,35 @@ def main():
         comp_traffic = ratio["composite"] * comp_bytes if ratio["composite"] else None
         value = samples_step * args.steps * world / elapsed
         fps = 2 * n_views * args.steps * world / elapsed
+        # precision variants of the same cube and views (FP16, int8), and the
+        # f32 images' values at the pixels where the oracle checks them
+        rng = np.random.default_rng(synth.LARGE.seed + 7)
+        pixels = np.stack([rng.integers(0, n_views, 20000), rng.integers(0, W, 20000),
+                           rng.integers(0, H, 20000)], axis=1).astype(np.int32)
+        prec, values = None, {}
+        if args.storage == "texture" and not args.no_extra and W == 1920:
+            idx = torch.from_numpy(pixels.astype(np.int64)).to(dev)
+            values[("f32", "composite")] = comp[idx[:, 0], idx[:, 2], idx[:, 1]].cpu().numpy()
+            values[("f32", "mip")] = mip[idx[:, 0], idx[:, 2], idx[:, 1]].cpu().numpy()
+            prec, pv = precision_leg(cube, cams, W, H, wl, lut, pixels)
+            values.update(pv)
+            for dt, row in prec.items():
+                ms = row["composite_ms_per_launch"] + row["mip_ms_per_launch"]
+                row["fps"] = 2 * n_views / (ms / 1000.0)
+                row["fps_vs_f32"] = (comp_ms + mip_ms) / ms
         cpu = None
         if args.cpu_budget > 0:
-            sps, cfps, threads, sample = oracle_throughput(cube.cpu().numpy(), cams, wl,
+            host_cube = cube.cpu().numpy()
+            sps, cfps, threads, sample = oracle_throughput(host_cube, cams, wl,
                                                            args.cpu_budget, w=W, h=H)
             cpu = {"value": sps, "unit": "samples/s", "cores": threads, "kind": "oracle",
                    "sample": sample, "fps": cfps}
+            if values:
+                # the oracle's results at the checked pixels also give the
+                # error of every storage's images against FP64
+                cpu["errors_at_checked_pixels"] = oracle_errors(host_cube, cams, wl, pixels,
+                                                                values, w=W, h=H)
+            del host_cube
         extra = {}
         if not args.no_extra and W == 1920:
             if args.storage == "texture" and not args.no_masks:
@@ -680,6 +770,8 @@ def main():
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
         }
+        if prec is not None:
+            result["precision"] = prec
         result.update(extra)
         print(json.dumps(result))
     if dist:
