@@ -298,6 +298,21 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # batched and served legs (reported beside the headline number)
 # ---------------------------------------------------------------------------
+def aggregate_ranks(samples, elapsed, dist=None, device=None):
+    """Whole-job figures of a timed region run by every rank: the samples of
+    all ranks (sum) and the slowest rank's time (max), after which the ranks
+    meet at a barrier.  One rank: the figures as given."""
+    if dist is None:
+        return samples, elapsed
+    t = torch.tensor([float(samples), float(elapsed)], dtype=torch.float64, device=device)
+    s = t[:1].clone()
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    e = t[1:].clone()
+    dist.all_reduce(e, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(s.item()), float(e.item())
+
+
 def event_ms(fn, reps, stream):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -618,11 +633,7 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     elapsed = t0.elapsed_time(t1) / 1000.0
-    if dist:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
-        dist.barrier()
+    total_samples, elapsed = aggregate_ranks(samples_step * args.steps, elapsed, dist, dev)
     comp_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     mip_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
 
@@ -680,7 +691,7 @@ def main():
                                else None)}
         traffic = (ratio[dom] * dom_bytes if args.storage == "texture" and ratio[dom] else None)
         comp_traffic = ratio["composite"] * comp_bytes if ratio["composite"] else None
-        value = samples_step * args.steps * world / elapsed
+        value = total_samples / elapsed
         fps = 2 * n_views * args.steps * world / elapsed
         # precision variants of the same cube and views (FP16, int8), and the
         # f32 images' values at the pixels where the oracle checks them

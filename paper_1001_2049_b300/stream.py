@@ -51,6 +51,18 @@ class Part:
     cell_hi: int
 
 
+def plan_parts(nz: int, planes: int):
+    """Parts of ``planes`` planes (at most nz) whose cell ranges tile the
+    cells [0, nz - 1) in order; the last part is moved down so it has as
+    many planes as the others."""
+    planes = min(planes, nz)
+    if planes < 2:
+        raise ValueError("a part needs at least two planes")
+    cells = planes - 1
+    return [Part(min(lo, nz - planes), lo, min(lo + cells, nz - 1))
+            for lo in range(0, nz - 1, cells)]
+
+
 class PartStream:
     """A cube of ``dims`` (nx, ny, nz) rendered in parts of ``part_planes``
     planes.  ``source(z0, n)`` returns planes [z0, z0 + n) as a float32
@@ -61,16 +73,10 @@ class PartStream:
     def __init__(self, dims, dtype: str, source, part_planes: int, device=None,
                  pair: bool = False):
         nx, ny, nz = (int(d) for d in dims)
-        if not 2 <= part_planes:
-            raise ValueError("a part needs at least two planes")
         self.dims = (nx, ny, nz)
         self.source = source
+        self.parts = plan_parts(nz, part_planes)
         self.planes = min(part_planes, nz)
-        cells = self.planes - 1
-        self.parts = []
-        for lo in range(0, nz - 1, cells):
-            hi = min(lo + cells, nz - 1)
-            self.parts.append(Part(min(lo, nz - self.planes), lo, hi))
         self.device = torch.device(device) if device is not None else torch.device("cuda")
         self.vols = []
         for _ in range(2 if len(self.parts) > 1 else 1):
