@@ -113,14 +113,16 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # algorithmic bytes: storage bytes of every voxel some sample's corners touch
 # ---------------------------------------------------------------------------
-# DRAM bytes (read + write) per algorithmic byte of the two render launches,
-# from one ncu capture of the same kernels and launch shapes on the 512^3 /
-# 4-view case (profiles/tex_kernel_f32_cube1024_orbit32.md): MIP
-# 2.0245 GB for 2.1307 GB; composite with the empty-space masks 0.4184 GB for
-# 2.1533 GB.  The cube exceeds L2 in both cases, so every view re-reads it
-# and the traffic of the full launch scales with touched voxels x views.
-TRAFFIC_PER_ALGORITHMIC_BYTE = {"mip": 2.024333e9 / 2.130716e9,
-                                "composite_masks": 0.418379e9 / 2.153293e9}
+# DRAM bytes (read + write) of one launch of the two render launches of the
+# 1024^3 / 32-view workload, from one ncu capture of the full-size launches
+# (one pass: dram__bytes_read.sum + dram__bytes_write.sum; launch shapes
+# 5 and 2; profiles/tex_kernel_f32_cube1024_orbit32.md): MIP 149.48 GB read
+# + 0.42 GB written; composite with the empty-space masks 32.05 + 1.37 GB.
+# Other workloads (the --cube-edge/--views cases) report them scaled by their
+# algorithmic bytes.
+MEASURED_TRAFFIC = {"mip": 149.479612e9 + 0.416618e9,
+                    "composite_masks": 32.046386e9 + 1.374209e9}
+MEASURED_ALGORITHMIC = {"mip": 136229959936.0, "composite_masks": 136433374037.6}
 
 
 def touched_voxels(cam, dims, step, w, h, device):
@@ -686,11 +688,14 @@ def main():
             (mip_ms, mip_bytes, "mip")
         achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
         masks_on = args.storage == "texture" and not args.no_masks
-        ratio = {"mip": TRAFFIC_PER_ALGORITHMIC_BYTE["mip"],
-                 "composite": (TRAFFIC_PER_ALGORITHMIC_BYTE["composite_masks"] if masks_on
-                               else None)}
-        traffic = (ratio[dom] * dom_bytes if args.storage == "texture" and ratio[dom] else None)
-        comp_traffic = ratio["composite"] * comp_bytes if ratio["composite"] else None
+
+        def measured(kind, alg):
+            if args.storage != "texture" or kind is None:
+                return None
+            return MEASURED_TRAFFIC[kind] * alg / MEASURED_ALGORITHMIC[kind]
+        kinds = {"mip": "mip", "composite": "composite_masks" if masks_on else None}
+        traffic = measured(kinds[dom], dom_bytes)
+        comp_traffic = measured(kinds["composite"], comp_bytes)
         value = total_samples / elapsed
         fps = 2 * n_views * args.steps * world / elapsed
         # precision variants of the same cube and views (FP16, int8), and the
@@ -765,8 +770,8 @@ def main():
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum "
-                                           "on the 512^3 / 4-view case, scaled by algorithmic "
-                                           "bytes" if traffic else None,
+                                           "of the full-size launch (one pass)"
+                                           if traffic else None,
                          "algorithmic_bytes_per_launch": dom_bytes, "dominant": dom,
                          "touched_voxels_per_view": touched,
                          "composite": {"achieved": comp_bytes / (comp_ms / 1000.0) / 1e9,
