@@ -350,27 +350,13 @@ struct Acc {
 };
 
 // ---- empty-space skipping ----
-// A sample's macrocell and its cell's bit there, from the gather coordinates
-// (cell + 1 on every axis: in [0, n] for positions inside the box up to
-// rounding).  The index is clamped to the mask array: the look-ahead samples
-// past a ray's end, and positions of cameras so far away that rounding
-// moves them by a voxel, may lie outside, and their bits are never used.
-template <typename PP>
-__device__ __forceinline__ int macro_of(const PP& P, const Geo& g, int& bit)
-{
-    const int x = (int)g.gx, y = (int)g.gy, z = g.iz;
-    bit = (x & 3) | ((y & 3) << 2) | ((z & 3) << 4);
-    const int i = ((z >> kMacroShift) * P.mny + (y >> kMacroShift)) * P.mnx + (x >> kMacroShift);
-    return (int)min((unsigned)i, (unsigned)P.mlast);
-}
-
 // march_tex with empty-space skipping in lockstep (COMPOSITE): every lane
 // steps through its samples at the same pace as without skipping (the
 // warp's rays stay side by side, so their gathers share cache lines), but a
 // lane fetches and evaluates a sample only when its cell's mask bit says the
 // clip can leave it visible; when no lane of the warp needs its sample, the
-// step costs the geometry alone.  Masks are loaded one sample ahead of the
-// gathers, gathers one sample ahead of the interpolation.  The result and
+// step costs the sample's cell alone.  Masks are loaded one sample ahead of
+// the gathers, gathers one sample ahead of the interpolation.  The result and
 // the sample count are those of march_tex.
 template <int DT, int MODE, bool STACK, typename PP, typename TT>
 __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
@@ -381,27 +367,45 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
     using Rec = unsigned long long;
     if (r.K <= 0) return 0;
     const cudaTextureObject_t t0 = T.tex;
+    // the mask test needs only a sample's cell (integer floors of its
+    // position); the full geometry (weights, gather coordinates) is computed
+    // for the samples a lane needs, one sample ahead of their interpolation.
+    // mcell: the macrocell of sample kf and its cell's bit there, from the
+    // gather coordinates (cell + 1 on every axis: in [0, n] for positions
+    // inside the box up to rounding).  The index is clamped to the mask
+    // array: the look-ahead samples past a ray's end, and positions of
+    // cameras so far away that rounding moves them by a voxel, may lie
+    // outside, and their bits are never used.
+    auto mcell = [&](float kf, int& bit) {
+        const float t = fmaf(kf, P.step, r.te);
+        const int x = __float2int_rd(fmaf(t, r.dx, r.ox)) + 1;
+        const int y = __float2int_rd(fmaf(t, r.dy, r.oy)) + 1;
+        const int z = __float2int_rd(fmaf(t, r.dz, r.oz)) + 1;
+        bit = (x & 3) | ((y & 3) << 2) | ((z & 3) << 4);
+        const int i = ((z >> kMacroShift) * P.mny + (y >> kMacroShift)) * P.mnx + (x >> kMacroShift);
+        return (int)min((unsigned)i, (unsigned)P.mlast);
+    };
     int k = 0;
-    // g0: sample k (corners a, present iff n0); g1: sample k + 1 (record rX,
-    // macrocell mX, cell bit b1)
-    Geo g0 = geo(P, r, 0.0f), g1 = geo(P, r, 1.0f);
-    int b0, b1;
-    const int m0 = macro_of(P, g0, b0);
-    int mX = macro_of(P, g1, b1);
+    int b0, b1, b2;
+    const int m0 = mcell(0.0f, b0);
+    int m1 = mcell(1.0f, b1), m2;
     const Rec r0 = __ldg(P.mask + m0);
-    Rec rX = (mX == m0) ? r0 : __ldg(P.mask + mX), rY;
-    bool n0 = acc.need(r0, b0);
+    Rec r1 = (m1 == m0) ? r0 : __ldg(P.mask + m1), r2;
+    bool n0 = acc.need(r0, b0), n1;
+    Geo g0, g1;
     float4 a0, a1, c0, c1;
-    if (n0) cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
-    float kf = 2.0f;
+    if (n0) {
+        g0 = geo(P, r, 0.0f);
+        cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
+    }
+    float kf = 0.0f;
     for (;;) {
-        // sample k + 2: geometry and record; sample k + 1: gathers; sample k
-        Geo g2 = geo(P, r, kf);
-        int b2;
-        const int m2 = macro_of(P, g2, b2);
-        rY = (m2 == mX) ? rX : __ldg(P.mask + m2);
-        const bool n1 = acc.need(rX, b1);
+        // sample k + 2: cell and mask word; sample k + 1: geometry, gathers
+        m2 = mcell(kf + 2.0f, b2);
+        r2 = (m2 == m1) ? r1 : __ldg(P.mask + m2);
+        n1 = acc.need(r1, b1);
         if (n1) {
+            g1 = geo(P, r, kf + 1.0f);
             if (n0)
                 next_cell_up<DT, STACK>(T, t0, g0, a0, a1, g1, c0, c1);
             else
@@ -410,26 +414,20 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
         ++k;
         if ((n0 && acc.add(P, lut, interp(a0, a1, g0))) || k >= r.K) break;
         kf += 1.0f;
-        // the same one sample further on, the two register sets swapped
-        const Geo g3 = geo(P, r, kf);
-        int b3;
-        const int m3 = macro_of(P, g3, b3);
-        rX = (m3 == m2) ? rY : __ldg(P.mask + m3);
-        mX = m3;
-        const bool n2 = acc.need(rY, b2);
-        if (n2) {
+        // the same one sample further on, the register sets swapped
+        m1 = mcell(kf + 2.0f, b1);
+        r1 = (m1 == m2) ? r2 : __ldg(P.mask + m1);
+        n0 = acc.need(r2, b2);
+        if (n0) {
+            g0 = geo(P, r, kf + 1.0f);
             if (n1)
-                next_cell_up<DT, STACK>(T, t0, g1, c0, c1, g2, a0, a1);
+                next_cell_up<DT, STACK>(T, t0, g1, c0, c1, g0, a0, a1);
             else
-                cell<DT, STACK>(T, t0, g2.iz, g2.gx, g2.gy, a0, a1);
+                cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
         }
         ++k;
         if ((n1 && acc.add(P, lut, interp(c0, c1, g1))) || k >= r.K) break;
         kf += 1.0f;
-        g0 = g2;
-        g1 = g3;
-        b1 = b3;
-        n0 = n2;
     }
     return k;
 }
