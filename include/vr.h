@@ -307,9 +307,9 @@ size_t vr_batch_workspace_bytes(void);
  * modes and transfer functions -- with one persistent kernel launch per
  * VR_BATCH_MAX requests (also split when a launch would need more than 8
  * textured volumes or 2 distinct opacity-corrected tables; requests on
- * volumes without texture storage, with texture storage in one layered
- * texture, and with plain texture storage spanning several layer groups
- * (more than 2049 planes) go to separate launches).  Each
+ * volumes without texture storage and on volumes with it go to separate
+ * launches).  Every request is checked before anything is enqueued, so an
+ * argument error leaves the stream untouched.  Each
  * block takes the next ray tile from a work counter in `workspace`
  * (caller-owned device memory of vr_batch_workspace_bytes(), 16-byte
  * aligned; zeroed on the stream by this call) and renders it with the same

@@ -245,28 +245,18 @@ int render_impl(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
                         static_cast<cudaStream_t>(stream));
 }
 
-// Fill the kernel record of one request; tables and textured volumes are
-// looked up in (or added to) the launch's slots.  Returns VR_OK, a negative
-// error, or 1 when the launch has no free slot left (start a new launch).
-int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_tex,
-                  vr::Volume** tex_vols, int* n_lut, float* lut_steps, int* lut_ns)
+// Every argument check of one request (the view as vr_render checks it, the
+// completion word, the request's own transfer function).
+int check_request(const vr_request& rq, int index)
 {
     if (!rq.vol) return fail(VR_ERR_ARG, "request %d: volume is NULL", index);
-    vr::Volume* v = reinterpret_cast<vr::Volume*>(rq.vol);
     vr::MarchParams mp;
     vr::TexParams tp;
-    // validation of the view as vr_render does it (one camera)
     int rc = prepare(rq.vol, &rq.cam, 1, rq.w, rq.h, rq.mode, rq.step, rq.out, rq.samples, &mp,
                      &tp);
     if (rc) return rc;
     if (rq.done && reinterpret_cast<uintptr_t>(rq.done) % 4 != 0)
         return fail(VR_ERR_ARG, "request %d: done must be 4-byte aligned", index);
-    vr::BatchReq& q = B->req[B->n];
-    std::memset(&q, 0, sizeof q);
-    // transfer function: the request's own or the volume's
-    const float* raw = &v->lut_raw[0][0];
-    int nl = v->n_lut;
-    float v_lo = v->v_lo, v_hi = v->v_hi, clip = v->clip, ta = v->term_alpha;
     if (rq.tf) {
         const vr_transfer& t = *rq.tf;
         if (!t.rgba_lut || t.n < 2 || t.n > VR_MAX_LUT)
@@ -278,6 +268,28 @@ int batch_request(const vr_request& rq, int index, vr::BatchParams* B, int* n_te
             if (!std::isfinite(t.rgba_lut[i]) || ((i & 3) == 3 && (t.rgba_lut[i] < 0.0f ||
                                                                    t.rgba_lut[i] > 1.0f)))
                 return fail(VR_ERR_ARG, "request %d: bad transfer table entry", index);
+    }
+    return VR_OK;
+}
+
+// Fill the kernel record of one (checked) request; tables and textured
+// volumes are looked up in (or added to) the launch's slots.  Returns VR_OK
+// or 1 when the launch has no free slot left (start a new launch).
+int batch_request(const vr_request& rq, vr::BatchParams* B, int* n_tex, vr::Volume** tex_vols,
+                  int* n_lut, float* lut_steps, int* lut_ns)
+{
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(rq.vol);
+    vr::MarchParams mp;
+    vr::TexParams tp;
+    prepare(rq.vol, &rq.cam, 1, rq.w, rq.h, rq.mode, rq.step, rq.out, rq.samples, &mp, &tp);
+    vr::BatchReq& q = B->req[B->n];
+    std::memset(&q, 0, sizeof q);
+    // transfer function: the request's own or the volume's
+    const float* raw = &v->lut_raw[0][0];
+    int nl = v->n_lut;
+    float v_lo = v->v_lo, v_hi = v->v_hi, clip = v->clip, ta = v->term_alpha;
+    if (rq.tf) {
+        const vr_transfer& t = *rq.tf;
         raw = t.rgba_lut;
         nl = t.n;
         v_lo = t.v_lo;
@@ -379,6 +391,12 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
         if (sms < 1) sms = 1;
         for (int c = 0; c < 2; ++c) grid[c] = sms * vr::batch_blocks_per_sm(c);
     }
+    // every request is checked before anything is enqueued, so an argument
+    // error leaves the stream untouched
+    for (int i = 0; i < n; ++i) {
+        const int rc = check_request(reqs[i], i);
+        if (rc) return rc;
+    }
     vr::BatchParams* B = new (std::nothrow) vr::BatchParams;
     if (!B) return fail(VR_ERR_OOM, "out of host memory");
     int rc = VR_OK;
@@ -400,12 +418,8 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
                     ++i;
                     continue;
                 }
-                const int r = batch_request(reqs[i], i, B, &n_tex, tex_vols, &n_lut, lut_steps,
+                const int r = batch_request(reqs[i], B, &n_tex, tex_vols, &n_lut, lut_steps,
                                             lut_ns);
-                if (r < 0) {
-                    rc = r;
-                    break;
-                }
                 if (r == 1) break;       // slots full: launch what we have
                 ++i;
             }

@@ -154,3 +154,14 @@ def test_batch_argument_errors(scene):
     small = torch.empty(8, dtype=torch.uint8, device="cuda")
     with pytest.raises(VRError):
         render_batch([Request(v, cam, 8, 8, "mip", 0.5)], workspace=small)
+    # a bad request after good ones of another launch class: nothing is
+    # enqueued (the good request's image keeps its old contents)
+    good = torch.full((8, 8), float("nan"), device="cuda")
+    bricks_vol = scene[1][0]                       # no texture storage: a later launch
+    cam1 = synth.random_sphere_cameras(scene[1][2], 1, 8, 8, 2)[0]
+    bad_tf = (synth.default_lut(), 5.0, 1.0, 5.0, 1.0)       # v_lo > v_hi
+    with pytest.raises(VRError):
+        render_batch([Request(v, cam, 8, 8, "mip", 0.5, out=good),
+                      Request(bricks_vol, cam1, 8, 8, "composite", 0.5, tf=bad_tf)])
+    torch.cuda.synchronize()
+    assert torch.isnan(good).all()
