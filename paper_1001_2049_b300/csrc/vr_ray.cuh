@@ -222,23 +222,27 @@ __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, c
 {
     const bool xy = n.gx == c.gx && n.gy == c.gy;
     const int dz = n.iz - c.iz;
-    if (xy && dz == 0) {
-        n0 = c0;
-        n1 = c1;
-        return;
-    }
     if constexpr (DT == kF16Pair || DT == kI8Pair) {
-        cell<DT, STACK>(T, t0, n.iz, n.gx, n.gy, n0, n1);
+        if (xy && dz == 0) {
+            n0 = c0;
+            n1 = c1;
+        } else {
+            cell<DT, STACK>(T, t0, n.iz, n.gx, n.gy, n0, n1);
+        }
     } else {
+        // lower plane: held as c0 (same cell) or c1 (z rose by one); upper
+        // plane: held as c1 (same cell) or c0 (z fell by one)
+        const bool keep0 = xy && (dz == 0 || dz == 1);
+        const bool keep1 = xy && (dz == 0 || dz == -1);
         float yt;
-        if (xy && dz == 1) {
-            n0 = c1;
+        if (keep0) {
+            n0 = dz == 0 ? c0 : c1;
         } else {
             const int l = plane_layer<STACK>(T, n.iz, n.gy, yt);
             n0 = decode<DT>(T, gather<DT>(t0, l, n.gx, yt), n.iz);
         }
-        if (xy && dz == -1) {
-            n1 = c0;
+        if (keep1) {
+            n1 = dz == 0 ? c1 : c0;
         } else {
             const int l = plane_layer<STACK>(T, n.iz + 1, n.gy, yt);
             n1 = decode<DT>(T, gather<DT>(t0, l, n.gx, yt), n.iz + 1);
@@ -441,26 +445,24 @@ template <int DT, int MODE, bool STACK, typename PP, typename TT>
 __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4* __restrict__ lut,
                                          const Ray& r, Acc<MODE>& acc)
 {
-    int k = 0;
     if (r.K <= 0) return 0;
     const cudaTextureObject_t t0 = T.tex;
+    const float Kf = (float)r.K;
     Geo ga = geo(P, r, 0.0f), gb;
     float4 a0, a1, b0, b1;
     cell<DT, STACK>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
-    float kf = 1.0f;
+    float kf = 1.0f;            // samples evaluated once the current one is
     for (;;) {
         gb = geo(P, r, kf);
         next_cell<DT, STACK>(T, t0, ga, a0, a1, gb, b0, b1);
-        ++k;
-        if (acc.add(P, lut, interp(a0, a1, ga)) || k >= r.K) break;
+        if (acc.add(P, lut, interp(a0, a1, ga)) || kf >= Kf) break;
         kf += 1.0f;
         ga = geo(P, r, kf);
         next_cell<DT, STACK>(T, t0, gb, b0, b1, ga, a0, a1);
-        ++k;
-        if (acc.add(P, lut, interp(b0, b1, gb)) || k >= r.K) break;
+        if (acc.add(P, lut, interp(b0, b1, gb)) || kf >= Kf) break;
         kf += 1.0f;
     }
-    return k;
+    return (int)kf;
 }
 
 // ---- rendering a cube part by part ----
