@@ -197,7 +197,8 @@ int vr_volume_attach_masks(vr_volume vol, void* buf, size_t bytes);
  * cell per plane with the texture unit's four-texel gather (unfiltered
  * texels; the interpolation stays the kernel's own FP32 lerps).  This is the
  * one place the library allocates device memory: about
- * nx*ny*nz*sizeof(storage) bytes, owned by the volume and released by
+ * nx*ny*nz*sizeof(storage) bytes (for VR_I8 also 8 or 16 bytes per slice:
+ * the planes' scales and offsets), owned by the volume and released by
  * vr_volume_detach_texture or vr_volume_destroy.  The call synchronises
  * `stream` (the fill must finish before its surface object is released).
  * Returns VR_ERR_UNSUPPORTED when nx or the stacked height exceeds the
@@ -221,9 +222,9 @@ int vr_volume_detach_texture(vr_volume vol);
 /* Keep only the texture storage: after this call the volume renders from
  * its texture alone and never reads the brick buffer again, which the
  * caller may free once the work already queued on it has completed (the
- * call itself does no device work).  For VR_F32 and VR_F16 volumes with
- * texture storage (int8 volumes keep their per-plane tables in the brick
- * buffer: VR_ERR_UNSUPPORTED).  Afterwards the volume is read-only:
+ * call itself does no device work).  For volumes with texture storage
+ * (an int8 texture carries its planes' scales and offsets).  Afterwards the
+ * volume is read-only:
  * vr_volume_upload, vr_volume_detach_texture, vr_volume_attach_masks and a
  * change of texture format return VR_ERR_UNSUPPORTED; its empty-space masks
  * are detached.  No counterpart in the paper: it keeps cubes resident whose

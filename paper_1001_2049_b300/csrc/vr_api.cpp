@@ -188,9 +188,7 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
     tp->tex = v->tex;
     tp->stack_shift = v->stack_shift;
     tp->stack_pitch = v->stack_pitch;
-    tp->nz = v->g.nz;
-    tp->scale = v->scale;
-    tp->offset = v->offset;
+    tp->dec = v->dec;
     tp->k_max = (int)(diag / step) + 2;
     p->mask = v->mask;
     p->mnx = v->mnx;
@@ -331,10 +329,8 @@ int batch_request(const vr_request& rq, vr::BatchParams* B, int* n_tex, vr::Volu
             T.tex = v->tex;
             T.stack_shift = v->stack_shift;
             T.stack_pitch = v->stack_pitch;
-            T.nz = v->g.nz;
             T.format = v->tex_format;
-            T.scale = v->scale;
-            T.offset = v->offset;
+            T.dec = v->dec;
         }
     }
     q.cam = rq.cam;
@@ -437,8 +433,10 @@ void release_texture(vr::Volume* v)
 {
     if (v->tex) cudaDestroyTextureObject(v->tex);
     if (v->array) cudaFreeArray(v->array);
+    if (v->dec) cudaFree(v->dec);
     v->tex = 0;
     v->array = nullptr;
+    v->dec = nullptr;
     v->has_tex = false;
 }
 
@@ -462,6 +460,7 @@ int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
     cudaError_t e = cudaCreateSurfaceObject(&surf, &rd);
     if (e != cudaSuccess) return cuda_fail(e, "surface object");
     e = vr::fill_texture(*v, surf, (int)s0, (int)s1, s);
+    if (e == cudaSuccess && v->dec) e = vr::fill_decode_records(*v, s);   // planes rescaled
     // the surface object may only be destroyed after the fill ran: wait
     cudaError_t e2 = cudaStreamSynchronize(s);
     cudaDestroySurfaceObject(surf);
@@ -522,6 +521,16 @@ int attach_texture(vr_volume vol, bool pair, void* stream)
     v->tex_format = format;
     v->stack_shift = shift;
     v->stack_pitch = pitch;
+    if (v->dtype == VR_I8) {
+        // per-slice decode records (float2 plain, float4 pair)
+        e = cudaMalloc(&v->dec, (size_t)slices * (pair ? 16 : 8));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            v->dec = nullptr;
+            release_texture(v);
+            return fail(VR_ERR_OOM, "texture decode records: %s", cudaGetErrorString(e));
+        }
+    }
     cudaResourceDesc rd;
     std::memset(&rd, 0, sizeof rd);
     rd.resType = cudaResourceTypeArray;
@@ -717,8 +726,6 @@ int vr_volume_drop_bricks(vr_volume vol)
     vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
     if (v->texture_only) return VR_OK;
     if (!v->has_tex) return fail(VR_ERR_UNSUPPORTED, "the volume has no texture storage");
-    if (v->dtype == VR_I8)
-        return fail(VR_ERR_UNSUPPORTED, "int8 volumes keep their plane tables in the bricks");
     v->texture_only = true;
     v->bricks = nullptr;
     v->mask = nullptr;

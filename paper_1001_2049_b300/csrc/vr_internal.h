@@ -63,6 +63,7 @@ struct Volume {
     cudaTextureObject_t tex;
     int stack_shift;        // 0: a layer per slice
     int stack_pitch;        // rows per stacked slice (ny + 2) when stacked
+    void* dec;              // VR_I8: per-slice decode records (library-owned)
     int cfg[3];             // texture-kernel launch shape per mode (autotuned)
     // optional empty-space masks (caller-owned device buffer)
     unsigned long long* mask;   // valid for clip level mask_clip
@@ -71,12 +72,14 @@ struct Volume {
 };
 
 // Texture storage as the texture kernels see it.
+// int8 texture storage decodes a code as fma(code, scale, offset) with its
+// plane's scale and offset, read per texture slice from one record: plain
+// int8 slice s -> {scale, offset} of plane s - 1 (clamped); pair slice s ->
+// {scale, offset} of planes s - 1 and s (clamped).
 struct TexParams {
     cudaTextureObject_t tex;
     int stack_shift, stack_pitch;   // see Volume
-    int nz;
-    const float* scale;     // VR_I8 only
-    const float* offset;
+    const void* dec;        // VR_I8 / kI8Pair: float2 / float4 per slice
     int k_max;
 };
 
@@ -118,10 +121,8 @@ constexpr int kBatchWords = 1 + kMaxBatch;
 struct BatchTex {
     cudaTextureObject_t tex;
     int stack_shift, stack_pitch;   // see Volume
-    int nz;
     int format;            // texel format (see kF16Pair)
-    const float* scale;
-    const float* offset;
+    const void* dec;       // as TexParams::dec
 };
 
 // One request as the batched kernel sees it (field names shared with
@@ -210,6 +211,8 @@ cudaError_t launch_tex_i8pair(const MarchParams& p, const TexParams& t, int mode
 cudaError_t launch_masks(const Volume& v, float clip, cudaStream_t s);
 int tex_shape_count();
 void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb);
+// Per-slice int8 decode records of the volume's texture (see TexParams).
+cudaError_t fill_decode_records(const Volume& v, cudaStream_t s);
 // Fill texture slices [s0, s1) from the bricks through surface `surf`.
 cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1,
                          cudaStream_t s);

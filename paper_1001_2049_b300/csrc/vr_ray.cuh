@@ -120,15 +120,15 @@ __device__ __forceinline__ Ray setup_ray(const PP& P, const vr_camera& c, int px
 
 // Decode int8 codes of texture slice `slice` (plane slice - 1, clamped: the
 // first and last slices repeat the edge planes) with its plane's scale and
-// offset; identity for float storage.  TT supplies tex, stack_shift,
-// stack_pitch, nz, scale and offset.
+// offset (one record per slice); identity for float storage.  TT supplies
+// tex, stack_shift, stack_pitch and dec.
 template <int DT, typename TT>
 __device__ __forceinline__ float4 decode(const TT& T, float4 q, int slice)
 {
     if (DT != VR_I8) return q;
-    const int z = min(max(slice - 1, 0), T.nz - 1);
-    const float s = __ldg(T.scale + z), o = __ldg(T.offset + z);
-    return make_float4(fmaf(q.x, s, o), fmaf(q.y, s, o), fmaf(q.z, s, o), fmaf(q.w, s, o));
+    const float2 d = __ldg(static_cast<const float2*>(T.dec) + slice);   // {scale, offset}
+    return make_float4(fmaf(q.x, d.x, d.y), fmaf(q.y, d.x, d.y), fmaf(q.z, d.x, d.y),
+                       fmaf(q.w, d.x, d.y));
 }
 
 __device__ __forceinline__ uint4 gather_u32(cudaTextureObject_t t, int layer, float x, float y)
@@ -192,9 +192,9 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
             q1 = make_float4(half_bits(p.x >> 16), half_bits(p.y >> 16), half_bits(p.z >> 16),
                              half_bits(p.w >> 16));
         } else {
-            const int z0 = min(max(z - 1, 0), T.nz - 1), z1 = min(z, T.nz - 1);
-            const float s0 = __ldg(T.scale + z0), o0 = __ldg(T.offset + z0);
-            const float s1 = __ldg(T.scale + z1), o1 = __ldg(T.offset + z1);
+            // {scale, offset} of the slice's two planes
+            const float4 d = __ldg(static_cast<const float4*>(T.dec) + z);
+            const float s0 = d.x, o0 = d.y, s1 = d.z, o1 = d.w;
             q0 = make_float4(fmaf(code_lo(p.x), s0, o0), fmaf(code_lo(p.y), s0, o0),
                              fmaf(code_lo(p.z), s0, o0), fmaf(code_lo(p.w), s0, o0));
             q1 = make_float4(fmaf(code_hi(p.x), s1, o1), fmaf(code_hi(p.y), s1, o1),

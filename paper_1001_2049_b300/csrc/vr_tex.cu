@@ -107,6 +107,19 @@ cudaError_t launch_part(const MarchParams& p, const TexParams& t, int format, in
 }
 
 namespace {
+__global__ void __launch_bounds__(256) dec_kernel(const float* __restrict__ scale,
+                                                  const float* __restrict__ offset, int nz,
+                                                  bool pair, void* __restrict__ out, int n)
+{
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= n) return;
+    const int z0 = min(max(sl - 1, 0), nz - 1), z1 = min(sl, nz - 1);
+    if (pair)
+        static_cast<float4*>(out)[sl] = make_float4(scale[z0], offset[z0], scale[z1], offset[z1]);
+    else
+        static_cast<float2*>(out)[sl] = make_float2(scale[z0], offset[z0]);
+}
+
 __global__ void __launch_bounds__(256) init_kernel(float* __restrict__ out, size_t n, float v)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -114,6 +127,14 @@ __global__ void __launch_bounds__(256) init_kernel(float* __restrict__ out, size
         out[i] = v;
 }
 }  // namespace
+
+cudaError_t fill_decode_records(const Volume& v, cudaStream_t s)
+{
+    const bool pair = v.tex_format == kI8Pair;
+    const int n = pair ? v.g.nz + 1 : v.g.nz + 2;
+    dec_kernel<<<(n + 255) / 256, 256, 0, s>>>(v.scale, v.offset, v.g.nz, pair, v.dec, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_render_init(float* out, size_t n_pixels, int mode, cudaStream_t s)
 {

@@ -462,9 +462,9 @@ def test_texture_only_volume_after_dropping_bricks():
     cube = synth.make_cube(dims, 4, ("uniform", 3.0, 8.0), 71).numpy()
     cams = synth.random_sphere_cameras(dims, 3, 21, 17, 9)
     lut = synth.default_lut(32)
-    for dtype in ("f32", "f16"):
+    for dtype, pair in (("f32", False), ("f16", False), ("i8", False), ("i8", True)):
         vol = Volume(torch.from_numpy(cube).cuda(), dtype)
-        vol.attach_texture()
+        vol.attach_pair_texture() if pair else vol.attach_texture()
         vol.attach_masks()
         vol.set_transfer(lut, 1.0, 8.0, 1.0, 0.95)
         before = {m: vol.render(cams, 21, 17, m, 0.5).cpu() for m in ("composite", "mip")}
@@ -479,10 +479,6 @@ def test_texture_only_volume_after_dropping_bricks():
         with pytest.raises(VRError):
             vol.attach_masks()
         vol.close()
-    v8 = Volume(torch.from_numpy(cube).cuda(), "i8")
-    v8.attach_texture()
-    with pytest.raises(VRError):
-        v8.drop_bricks()
     v32 = Volume(torch.from_numpy(cube).cuda(), "f32")
     with pytest.raises(VRError):                 # nothing to keep
         v32.drop_bricks()
