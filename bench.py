@@ -118,11 +118,14 @@ class Clocks:
 # (one pass: dram__bytes_read.sum + dram__bytes_write.sum; launch shapes
 # 5 and 2; profiles/tex_kernel_f32_cube1024_orbit32.md): MIP 150.31 GB read
 # + 0.42 GB written; composite with the empty-space masks 31.97 + 1.30 GB.
+# MIP with the binary16 MIP bounds: None (not yet captured: reported as null).
 # Other workloads (the --cube-edge/--views cases) report them scaled by their
 # algorithmic bytes.
 MEASURED_TRAFFIC = {"mip": 150.305302e9 + 0.415848e9,
+                    "mip_bounds": None,
                     "composite_masks": 31.974443e9 + 1.297023e9}
-MEASURED_ALGORITHMIC = {"mip": 136229959936.0, "composite_masks": 136433374037.6}
+MEASURED_ALGORITHMIC = {"mip": 136229959936.0, "mip_bounds": 136229959936.0,
+                        "composite_masks": 136433374037.6}
 
 
 def touched_voxels(cam, dims, step, w, h, device):
@@ -557,6 +560,8 @@ def main():
                     help="launch shapes C,M (composite, MIP) instead of the autotuner's")
     ap.add_argument("--no-masks", action="store_true",
                     help="composite without the empty-space masks")
+    ap.add_argument("--no-bounds", action="store_true",
+                    help="MIP without the binary16 MIP bounds")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and served legs")
     ap.add_argument("--storage", default="texture", choices=["texture", "bricks"],
@@ -585,6 +590,10 @@ def main():
         vol.attach_texture()
         if not args.no_masks:
             vol.attach_masks()
+        if not args.no_bounds:
+            vol.attach_mip_bounds()
+    masks_on = args.storage == "texture" and not args.no_masks
+    bounds_on = args.storage == "texture" and not args.no_bounds
     vol.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
     comp = torch.empty((n_views, H, W, 4), dtype=torch.float32, device=dev)
     mip = torch.empty((n_views, H, W), dtype=torch.float32, device=dev)
@@ -642,21 +651,24 @@ def main():
     mip_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
 
     # context only (outside the timed region): the composite launch without
-    # the empty-space masks
-    no_masks = None
-    if args.storage == "texture" and not args.no_masks:
+    # the empty-space masks, the MIP launch without the MIP bounds
+    def one_launch_ms(mode, out):
+        vol.render(cams, W, H, mode, wl.step, out=out)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        vol.render(cams, W, H, mode, wl.step, out=out)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1])
+    no_masks = no_bounds = None
+    if masks_on:
         vol.detach_masks()
-        nb = []
-        for mode, out in (("composite", comp),):
-            vol.render(cams, W, H, mode, wl.step, out=out)
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            e[0].record(stream)
-            vol.render(cams, W, H, mode, wl.step, out=out)
-            e[1].record(stream)
-            torch.cuda.synchronize()
-            nb.append(e[0].elapsed_time(e[1]))
-        no_masks = {"composite_ms_per_launch": nb[0]}
+        no_masks = {"composite_ms_per_launch": one_launch_ms("composite", comp)}
         vol.attach_masks()
+    if bounds_on:
+        vol.detach_mip_bounds()
+        no_bounds = {"mip_ms_per_launch": one_launch_ms("mip", mip)}
+        vol.attach_mip_bounds()
 
     # end to end through the public API: cameras in, images back to pinned host
     host_comp = torch.empty(comp.shape, dtype=torch.float32, pin_memory=True)
@@ -689,13 +701,13 @@ def main():
         dom_ms, dom_bytes, dom = (comp_ms, comp_bytes, "composite") if comp_ms >= mip_ms else \
             (mip_ms, mip_bytes, "mip")
         achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
-        masks_on = args.storage == "texture" and not args.no_masks
 
         def measured(kind, alg):
-            if args.storage != "texture" or kind is None:
+            if args.storage != "texture" or kind is None or MEASURED_TRAFFIC.get(kind) is None:
                 return None
             return MEASURED_TRAFFIC[kind] * alg / MEASURED_ALGORITHMIC[kind]
-        kinds = {"mip": "mip", "composite": "composite_masks" if masks_on else None}
+        kinds = {"mip": "mip_bounds" if bounds_on else "mip",
+                 "composite": "composite_masks" if masks_on else None}
         traffic = measured(kinds[dom], dom_bytes)
         comp_traffic = measured(kinds["composite"], comp_bytes)
         value = total_samples / elapsed
@@ -761,13 +773,17 @@ def main():
                 "samples_per_step": samples_step, "samples_composite": samples_comp,
                 "samples_mip": samples_mip, "composite_ms_per_launch": comp_ms,
                 "mip_ms_per_launch": mip_ms, "parallelism": "replica per GPU (views)",
-                "empty_space_masks": args.storage == "texture" and not args.no_masks,
+                "empty_space_masks": masks_on,
                 "without_masks": no_masks,
+                "mip_bounds": bounds_on,
+                "without_bounds": no_bounds,
                 "autotuned": tuned,
                 "l2": "inputs larger than L2 (4 GiB cube per view pass)"},
             "roofline": {"bound": "hbm",
                          "kernel": ("tex_kernel" if args.storage == "texture"
-                                    else "march kernel") + " %s f32" % dom,
+                                    else "march kernel") + " %s f32" % dom
+                                   + (" (binary16 MIP bounds)" if dom == "mip" and bounds_on
+                                      else ""),
                          "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -216,8 +216,31 @@ int vr_volume_attach_texture(vr_volume vol, void* stream);
 int vr_volume_attach_pair_texture(vr_volume vol, void* stream);
 
 /* Release the texture storage (renders fall back to gathering from the
- * bricks).  The caller must make sure no render using it is pending.       */
+ * bricks) and its MIP bounds.  The caller must make sure no render using it
+ * is pending.                                                               */
 int vr_volume_detach_texture(vr_volume vol);
+
+/* MIP bounds for a VR_F32 volume with (plain) texture storage: a second
+ * layered texture of the same slices holding every voxel rounded toward
+ * +infinity to binary16 (2 bytes per voxel, library-owned).  A MIP render
+ * (the maximum of the samples, §3.1 process item 3) then marches the bounds:
+ * their trilinear value is an upper bound of the sample's value up to the
+ * FP32 rounding of the two interpolations, which a margin of 2^-19 times the
+ * largest |voxel| covers, so a sample is read from the FP32 texture only when
+ * it could raise the ray's running maximum.  MIP images and sample counts
+ * are those without bounds bit for bit (voxels above 65504, infinite or NaN
+ * give bounds that never exclude a sample).  No effect on COMPOSITE and SUM
+ * renders, on vr_render_part or on the batched launch.  Uploads refresh the
+ * bounds with the texture.  VR_ERR_UNSUPPORTED for other storage types,
+ * without texture storage, or after vr_volume_drop_bricks; VR_ERR_OOM when
+ * the allocation fails.  The call synchronises `stream`.  No counterpart in
+ * the paper.                                                                */
+int vr_volume_attach_mip_bounds(vr_volume vol, void* stream);
+
+/* Release the MIP bounds (MIP renders read the FP32 texture at every
+ * sample again).  The caller must make sure no render using them is
+ * pending.                                                                   */
+int vr_volume_detach_mip_bounds(vr_volume vol);
 
 /* Keep only the texture storage: after this call the volume renders from
  * its texture alone and never reads the brick buffer again, which the

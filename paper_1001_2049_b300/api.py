@@ -211,6 +211,16 @@ class Volume:
     def detach_texture(self):
         check(load().vr_volume_detach_texture(self._h))
 
+    def attach_mip_bounds(self, stream=None):
+        """FP32 volumes with texture storage: binary16 upper bounds of the
+        voxels (library-owned, 2 bytes per voxel); MIP renders then read
+        the FP32 texels only where a sample could raise the maximum, with
+        identical images."""
+        check(load().vr_volume_attach_mip_bounds(self._h, _stream_ptr(stream)))
+
+    def detach_mip_bounds(self):
+        check(load().vr_volume_detach_mip_bounds(self._h))
+
     def drop_bricks(self, stream=None):
         """Keep only the texture storage and free the brick buffer (after the
         work queued on ``stream`` has finished); the volume becomes

@@ -190,6 +190,8 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
     tp->stack_pitch = v->stack_pitch;
     tp->dec = v->dec;
     tp->k_max = (int)(diag / step) + 2;
+    tp->bound = v->bound_tex;
+    tp->bound_delta = v->bound_delta;
     p->mask = v->mask;
     p->mnx = v->mnx;
     p->mny = v->mny;
@@ -429,8 +431,45 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
     return rc;
 }
 
+void release_bounds(vr::Volume* v)
+{
+    if (v->bound_tex) cudaDestroyTextureObject(v->bound_tex);
+    if (v->bound_array) cudaFreeArray(v->bound_array);
+    if (v->bound_vmax) cudaFree(v->bound_vmax);
+    v->bound_tex = 0;
+    v->bound_array = nullptr;
+    v->bound_vmax = nullptr;
+    v->bound_delta = 0.0f;
+}
+
+// Fill MIP-bound slices [s0, s1) and update the rounding margin from the
+// largest |voxel| the fills have seen (2^-19 of it, at least the smallest
+// normal float so that subnormal rounding is covered; +inf if a voxel is).
+// The maximum only grows, so after uploads the margin stays conservative.
+int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
+{
+    cudaResourceDesc rd;
+    std::memset(&rd, 0, sizeof rd);
+    rd.resType = cudaResourceTypeArray;
+    rd.res.array.array = v->bound_array;
+    cudaSurfaceObject_t surf = 0;
+    cudaError_t e = cudaCreateSurfaceObject(&surf, &rd);
+    if (e != cudaSuccess) return cuda_fail(e, "surface object");
+    e = vr::fill_bounds(*v, surf, (int)s0, (int)s1, v->bound_vmax, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaDestroySurfaceObject(surf);
+    if (e != cudaSuccess) return cuda_fail(e, "bound fill");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "bound fill");
+    float vmax = 0.0f;
+    e = cudaMemcpy(&vmax, v->bound_vmax, sizeof vmax, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "bound maximum");
+    v->bound_delta = std::max(std::ldexp(vmax, -19), std::ldexp(1.0f, -126));
+    return VR_OK;
+}
+
 void release_texture(vr::Volume* v)
 {
+    release_bounds(v);
     if (v->tex) cudaDestroyTextureObject(v->tex);
     if (v->array) cudaFreeArray(v->array);
     if (v->dec) cudaFree(v->dec);
@@ -466,7 +505,59 @@ int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
     cudaDestroySurfaceObject(surf);
     if (e != cudaSuccess) return cuda_fail(e, "texture fill");
     if (e2 != cudaSuccess) return cuda_fail(e2, "texture fill");
+    if (v->bound_array) return fill_bound_slices(v, s0, s1, s);   // same slices
     return VR_OK;
+}
+
+int attach_bounds(vr::Volume* v, cudaStream_t s)
+{
+    if (v->dtype != VR_F32)
+        return fail(VR_ERR_UNSUPPORTED, "MIP bounds are for FP32 storage (binary16 bounds)");
+    if (!v->has_tex || v->tex_format != VR_F32)
+        return fail(VR_ERR_UNSUPPORTED, "MIP bounds need texture storage (attach it first)");
+    if (v->bound_array) return VR_OK;
+    if (v->texture_only)
+        return fail(VR_ERR_UNSUPPORTED, "the volume's bricks were dropped: no new bounds");
+    // the texture's slices and stacking (vr_ray.cuh), in binary16
+    const int slices = v->g.nz + 2;
+    const int layers = (slices + (1 << v->stack_shift) - 1) >> v->stack_shift;
+    cudaChannelFormatDesc desc = cudaCreateChannelDescHalf();
+    cudaError_t e = cudaMalloc3DArray(
+        &v->bound_array, &desc,
+        make_cudaExtent(v->g.nx, (size_t)v->stack_pitch << v->stack_shift, layers),
+        cudaArrayLayered | cudaArraySurfaceLoadStore);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        v->bound_array = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA,
+                    "MIP bound storage: %s", cudaGetErrorString(e));
+    }
+    e = cudaMalloc(&v->bound_vmax, sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(v->bound_vmax, 0, sizeof(float));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release_bounds(v);
+        return fail(VR_ERR_OOM, "MIP bound maximum: %s", cudaGetErrorString(e));
+    }
+    cudaResourceDesc rd;
+    std::memset(&rd, 0, sizeof rd);
+    rd.resType = cudaResourceTypeArray;
+    rd.res.array.array = v->bound_array;
+    cudaTextureDesc td;
+    std::memset(&td, 0, sizeof td);
+    td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+    td.filterMode = cudaFilterModePoint;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    e = cudaCreateTextureObject(&v->bound_tex, &rd, &td, nullptr);
+    if (e != cudaSuccess) {
+        v->bound_tex = 0;
+        release_bounds(v);
+        return cuda_fail(e, "MIP bound texture object");
+    }
+    int rc = fill_bound_slices(v, 0, slices, s);
+    if (rc) release_bounds(v);
+    return rc;
 }
 
 int attach_texture(vr_volume vol, bool pair, void* stream)
@@ -708,6 +799,19 @@ int vr_volume_attach_texture(vr_volume vol, void* stream)
 int vr_volume_attach_pair_texture(vr_volume vol, void* stream)
 {
     return attach_texture(vol, true, stream);
+}
+
+int vr_volume_attach_mip_bounds(vr_volume vol, void* stream)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    return attach_bounds(reinterpret_cast<vr::Volume*>(vol), static_cast<cudaStream_t>(stream));
+}
+
+int vr_volume_detach_mip_bounds(vr_volume vol)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    release_bounds(reinterpret_cast<vr::Volume*>(vol));
+    return VR_OK;
 }
 
 int vr_volume_detach_texture(vr_volume vol)

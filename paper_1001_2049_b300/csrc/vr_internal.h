@@ -64,6 +64,12 @@ struct Volume {
     int stack_shift;        // 0: a layer per slice
     int stack_pitch;        // rows per stacked slice (ny + 2) when stacked
     void* dec;              // VR_I8: per-slice decode records (library-owned)
+    // optional MIP bounds (VR_F32 with texture storage, library-owned): the
+    // same slices, every voxel rounded toward +infinity to binary16
+    cudaArray_t bound_array;
+    cudaTextureObject_t bound_tex;
+    float* bound_vmax;      // device word: largest |voxel| seen by the fills
+    float bound_delta;      // margin for FP32 rounding, 2^-19 * that maximum
     int cfg[3];             // texture-kernel launch shape per mode (autotuned)
     // optional empty-space masks (caller-owned device buffer)
     unsigned long long* mask;   // valid for clip level mask_clip
@@ -81,6 +87,11 @@ struct TexParams {
     int stack_shift, stack_pitch;   // see Volume
     const void* dec;        // VR_I8 / kI8Pair: float2 / float4 per slice
     int k_max;
+    // MIP bounds (0: none): binary16 texels rounded up from the FP32 voxels,
+    // laid out as `tex`; a sample whose bound plus bound_delta stays below
+    // the ray's running maximum cannot raise it (see march_tex_bound)
+    cudaTextureObject_t bound;
+    float bound_delta;
 };
 
 size_t brick_bytes(const VolumeGeom& g, int dtype);   // voxel part only
@@ -216,6 +227,10 @@ cudaError_t fill_decode_records(const Volume& v, cudaStream_t s);
 // Fill texture slices [s0, s1) from the bricks through surface `surf`.
 cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1,
                          cudaStream_t s);
+// Fill MIP-bound slices [s0, s1) (VR_F32 bricks, binary16 rounded up)
+// through `surf`, raising *vmax to the largest |voxel| of those planes.
+cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1, float* vmax,
+                        cudaStream_t s);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
                         cudaStream_t s);
 

@@ -465,6 +465,50 @@ __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4*
     return (int)kf;
 }
 
+// MIP over FP32 texture storage with MIP bounds attached: the march of
+// march_tex runs over the bound texels (binary16, each voxel rounded toward
+// +infinity), whose trilinear value u is never below the sample's value v
+// by more than the FP32 rounding of the two interpolations (at most
+// 9 * 2^-24 of the largest |corner| each; bound_delta = 2^-19 of the largest
+// |voxel| covers both).  A sample is evaluated from the FP32 texture only
+// when u + bound_delta is not below the running maximum, i.e. when it could
+// raise it; a NaN or infinite bound is never below.  Every sample that can
+// change the maximum is evaluated with march_tex's arithmetic, so the result
+// and the sample count are march_tex's bit for bit, while the march moves
+// half the texel bytes.
+template <bool STACK, typename PP, typename TT>
+__device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const Ray& r,
+                                               Acc<VR_MIP>& acc)
+{
+    if (r.K <= 0) return 0;
+    const cudaTextureObject_t tb = T.bound, tf = T.tex;
+    const float Kf = (float)r.K;
+    auto take = [&](const Geo& g, const float4& u0, const float4& u1) {
+        if (!(interp(u0, u1, g) + T.bound_delta < acc.m)) {
+            float4 e0, e1;
+            cell<VR_F32, STACK>(T, tf, g.iz, g.gx, g.gy, e0, e1);
+            acc.m = fmaxf(acc.m, interp(e0, e1, g));
+        }
+    };
+    Geo ga = geo(P, r, 0.0f), gb;
+    float4 a0, a1, b0, b1;
+    cell<VR_F16, STACK>(T, tb, ga.iz, ga.gx, ga.gy, a0, a1);
+    float kf = 1.0f;
+    for (;;) {
+        gb = geo(P, r, kf);
+        next_cell<VR_F16, STACK>(T, tb, ga, a0, a1, gb, b0, b1);
+        take(ga, a0, a1);
+        if (kf >= Kf) break;
+        kf += 1.0f;
+        ga = geo(P, r, kf);
+        next_cell<VR_F16, STACK>(T, tb, gb, b0, b1, ga, a0, a1);
+        take(gb, b0, b1);
+        if (kf >= Kf) break;
+        kf += 1.0f;
+    }
+    return (int)kf;
+}
+
 // ---- rendering a cube part by part ----
 // A part holds planes [base, base + n) of a larger cube (its slices are the
 // part's own: local slice = global slice - base).  Rendering a part marches,

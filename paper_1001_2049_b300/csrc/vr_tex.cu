@@ -55,6 +55,35 @@ __global__ void __launch_bounds__(256) fill_kernel(const T* __restrict__ bricks,
     }
 }
 
+// MIP bounds: slices [s0, s1) laid out as fill_kernel lays out the FP32
+// texture, each voxel rounded toward +infinity to binary16 (never below the
+// voxel; +inf above 65504).  Also raises *vmax to the largest |voxel| read
+// (NaN ignored): |voxel| >= 0, so its bit pattern orders as an integer.
+__global__ void __launch_bounds__(256) fill_bound_kernel(const float* __restrict__ bricks,
+                                                         VolumeGeom g, cudaSurfaceObject_t surf,
+                                                         int s0, int s1, int shift, int pitch,
+                                                         float* __restrict__ vmax)
+{
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    float m = 0.0f;
+    if (x < g.nx && y < g.ny) {
+        for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z) {
+            const int z = min(max(sl - 1, 0), g.nz - 1);
+            const size_t brick = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) *
+                                     g.nbx + (x >> kBrickShift);
+            const float v =
+                bricks[brick * kBrickVoxels + ((z & 31) << 10) + ((y & 31) << 5) + (x & 31)];
+            m = fmaxf(m, fabsf(v));
+            write_slice_row(surf, __half_as_ushort(__float2half_ru(v)), x, y, sl, g.ny, shift,
+                            pitch);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(vmax), __float_as_int(m));
+}
+
 // Pair formats: slices [s0, s1); slice s holds the voxels of planes s - 1 and
 // s (clamped to the cube) packed in one texel, low bits plane s - 1.
 template <typename T, typename W>
@@ -154,6 +183,17 @@ void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb)
     *px = sh.px;
     *py = sh.py;
     *minb = sh.minb;
+}
+
+cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int z0, int z1, float* vmax,
+                        cudaStream_t s)
+{
+    if (z1 <= z0) return cudaSuccess;
+    dim3 grid((unsigned)((v.g.nx + 31) / 32), (unsigned)((v.g.ny + 7) / 8),
+              (unsigned)((z1 - z0) < 1024 ? (z1 - z0) : 1024));
+    fill_bound_kernel<<<grid, 256, 0, s>>>((const float*)v.bricks, v.g, surf, z0, z1,
+                                           v.stack_shift, v.stack_pitch, vmax);
+    return cudaGetLastError();
 }
 
 cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int z0, int z1, cudaStream_t s)

@@ -16,7 +16,10 @@
 // The gathers of the next sample are issued before the current sample is
 // interpolated, which hides the texture latency behind the arithmetic.
 // With empty-space masks attached (SKIP, COMPOSITE), samples whose cell the
-// clip makes transparent are not fetched (vr_ray.cuh, march_tex_lock).
+// clip makes transparent are not fetched (vr_ray.cuh, march_tex_lock); with
+// MIP bounds attached (SKIP, MIP, FP32) the march reads binary16 upper
+// bounds and fetches the FP32 corners only where a sample could raise the
+// maximum (march_tex_bound).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -59,7 +62,9 @@ __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG
     if (valid) {
         const ray::Ray r = ray::setup_ray(P, P.cams[view], px, py, T.k_max);
         ray::Acc<MODE> acc;
-        if constexpr (SKIP)
+        if constexpr (SKIP && MODE == VR_MIP)
+            count = (unsigned)ray::march_tex_bound<STACK>(P, T, r, acc);
+        else if constexpr (SKIP)
             count = (unsigned)ray::march_tex_lock<DT, MODE, STACK>(P, T, s_lut, r, acc);
         else
             count = (unsigned)ray::march_tex<DT, MODE, STACK>(P, T, s_lut, r, acc);
@@ -78,16 +83,19 @@ __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG
 template <int DT, int MODE, bool STACK, int CFG>
 cudaError_t launch_c(const MarchParams& p, const TexParams& t, cudaStream_t s)
 {
-    // skipping is for COMPOSITE (the clip makes most cells transparent); a
-    // MIP sample could only be passed over when no corner of its cell
-    // exceeds the ray's running maximum of interpolated values, and on noise
-    // about a quarter of the cells have such a corner: nearly every warp
-    // step would have a lane needing its sample, so MIP marches every sample
-    constexpr bool kCanSkip = MODE == VR_COMPOSITE;
+    // SKIP: COMPOSITE with empty-space masks (cells the clip makes
+    // transparent are not fetched); MIP on FP32 storage with MIP bounds (the
+    // march reads the binary16 bounds and fetches the FP32 corners only of
+    // samples that could raise the maximum).  Passing over MIP samples by
+    // their cells' corner maxima would not pay: on noise about a quarter of
+    // the cells have a corner above a ray's running maximum, so nearly every
+    // warp step would have a lane needing its sample.
+    constexpr bool kCanSkip = MODE == VR_COMPOSITE || (MODE == VR_MIP && DT == VR_F32);
     constexpr Shape S = kShapes[CFG];
     dim3 grid((unsigned)((p.w + S.bx - 1) / S.bx), (unsigned)((p.h + S.by - 1) / S.by),
               (unsigned)p.n_views);
-    if (kCanSkip && p.mask != nullptr)
+    const bool skip = MODE == VR_COMPOSITE ? p.mask != nullptr : t.bound != 0;
+    if (kCanSkip && skip)
         tex_kernel<DT, MODE, STACK, CFG, kCanSkip><<<grid, S.bx * S.by, 0, s>>>(p, t);
     else
         tex_kernel<DT, MODE, STACK, CFG, false><<<grid, S.bx * S.by, 0, s>>>(p, t);

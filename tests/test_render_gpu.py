@@ -32,7 +32,7 @@ def oracle_volume(cube: np.ndarray, dtype: str) -> oracle.Volume:
 
 
 def gpu_images(cube_t, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, count=None,
-               tex=False, masks=False):
+               tex=False, masks=False, bounds=False):
     vol = Volume(cube_t.cuda(), dtype)
     if tex == "pair":
         vol.attach_pair_texture()
@@ -40,6 +40,8 @@ def gpu_images(cube_t, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta,
         vol.attach_texture()
     if masks:
         vol.attach_masks()
+    if bounds:
+        vol.attach_mip_bounds()
     vol.set_transfer(lut, v_lo, v_hi, clip, ta)
     out = vol.render(cams, w, h, mode, step, count=count)
     torch.cuda.synchronize()
@@ -56,13 +58,13 @@ def scale_for(mode, cube, got):
 
 
 def run_parity(cube, dtype, cams, w, h, mode, step, lut, v_lo, v_hi, clip, ta, tol=TOL_FP32,
-               reference="decoded", pixels=None, what="", tex=False, masks=False):
+               reference="decoded", pixels=None, what="", tex=False, masks=False, bounds=False):
     """Render on the GPU (bricks, or texture storage with tex=True, with the
-    empty-space masks with masks=True) and compare with the oracle (on the
-    decoded storage values, or on the float32 source with
-    reference="source")."""
+    empty-space masks with masks=True, with MIP bounds with bounds=True) and
+    compare with the oracle (on the decoded storage values, or on the float32
+    source with reference="source")."""
     got = gpu_images(torch.from_numpy(cube), dtype, cams, w, h, mode, step, lut, v_lo, v_hi,
-                     clip, ta, tex=tex, masks=masks)
+                     clip, ta, tex=tex, masks=masks, bounds=bounds)
     ovol = oracle_volume(cube, dtype if reference == "decoded" else "f32")
     tf = oracle.TF(lut, v_lo, v_hi, clip, ta)
     nz, ny, nx = cube.shape
@@ -327,14 +329,18 @@ def test_every_launch_shape_gives_identical_images():
     cams = synth.random_sphere_cameras(dims, 3, 45, 29, 7)
     shapes = launch_shapes()
     assert len(shapes) >= 4
-    for mode in ("composite", "mip"):
-        ref = None
+    refs = {}
+    for case in ("composite", "mip", "mip bounds"):
+        mode = case.split()[0]
+        if case == "mip bounds":              # the same images as without bounds
+            vol.attach_mip_bounds()
+        ref = refs.get(mode)
         for cfg in range(len(shapes)):
             vol.set_launch_config(mode, cfg)
             img = vol.render(cams, 45, 29, mode, 0.5)
             if ref is None:
-                ref = img.clone()
-            assert torch.equal(img, ref), (mode, cfg, shapes[cfg])
+                ref = refs[mode] = img.clone()
+            assert torch.equal(img, ref), (case, cfg, shapes[cfg])
         best, ms = vol.autotune(cams, 45, 29, mode, 0.5)
         assert 0 <= best < len(shapes) and ms > 0
         assert torch.equal(vol.render(cams, 45, 29, mode, 0.5), ref)
@@ -646,6 +652,114 @@ def test_masks_ragged_cubes(dims, step, dtype):
 
 
 # ---------------------------------------------------------------------------
+# MIP bounds: binary16 upper bounds decide which samples read the FP32 texels
+# ---------------------------------------------------------------------------
+def _mip_with_and_without_bounds(vol, cams, w, h, step):
+    outs = []
+    for bounds in (False, True):
+        if bounds:
+            vol.attach_mip_bounds()
+        n = torch.zeros(1, dtype=torch.int64, device="cuda")
+        img = vol.render(cams, w, h, "mip", step, count=n)
+        torch.cuda.synchronize()
+        outs.append((img.cpu(), int(n.item())))
+        vol.detach_mip_bounds()
+    return outs
+
+
+@pytest.mark.parametrize("dims", MASK_DIMS)
+def test_mip_bounds_leave_images_and_counts_unchanged(dims):
+    cube, cams = _skip_cases(dims, 70 + dims[2])
+    vol = Volume(torch.from_numpy(cube).cuda(), "f32")
+    vol.attach_texture()
+    (a, na), (b, nb) = _mip_with_and_without_bounds(vol, cams, 29, 19, 0.37)
+    assert torch.equal(a, b), dims
+    assert na == nb
+
+
+def test_mip_bounds_with_values_binary16_cannot_hold():
+    # voxels above 65504 (bound +inf), hugely negative (bound -65504), NaN
+    # and infinite voxels, tiny and subnormal values: identical images
+    dims = (23, 19, 31)
+    cube, cams = _skip_cases(dims, 77)
+    rng = np.random.default_rng(5)
+    flat = cube.reshape(-1)
+    idx = rng.choice(flat.size, 60, replace=False)
+    flat[idx[:10]] = 7.0e4
+    flat[idx[10:20]] = -3.0e6
+    flat[idx[20:25]] = np.nan
+    flat[idx[25:28]] = np.inf
+    flat[idx[28:31]] = -np.inf
+    flat[idx[31:45]] = 1.0e-30
+    flat[idx[45:60]] = 3.0e-41
+    vol = Volume(torch.from_numpy(cube).cuda(), "f32")
+    vol.attach_texture()
+    (a, na), (b, nb) = _mip_with_and_without_bounds(vol, cams, 29, 19, 0.5)
+    assert torch.equal(a, b) or torch.equal(torch.nan_to_num(a), torch.nan_to_num(b))
+    assert na == nb
+    # a cube of subnormal values only: the margin covers their rounding
+    tiny = (np.abs(cube) * 1e-40).astype(np.float32)
+    vol = Volume(torch.from_numpy(np.nan_to_num(tiny, posinf=0.0)).cuda(), "f32")
+    vol.attach_texture()
+    (a, _), (b, _) = _mip_with_and_without_bounds(vol, cams, 29, 19, 0.5)
+    assert torch.equal(a, b)
+
+
+def test_mip_bounds_small_workload_against_the_oracle(small):
+    wl, cube, lut, cams = small
+    run_parity(cube, "f32", cams, 256, 256, "mip", wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+               wl.term_alpha, what="small mip bounds", tex=True, bounds=True)
+
+
+@pytest.mark.parametrize("dims,step", RAGGED)
+def test_mip_bounds_ragged_cubes(dims, step):
+    cube, cams, lut = ragged_case(dims, 29 + dims[0])
+    run_parity(cube, "f32", cams, 23, 17, "mip", step, lut, 1.0, 8.0, 3.0, 0.95,
+               what="mip bounds ragged %s" % (dims,), tex=True, bounds=True)
+
+
+def test_mip_bounds_follow_uploads_and_survive_dropping_bricks():
+    dims = (40, 36, 50)
+    cube = synth.make_cube(dims, 4, ("uniform", 3.0, 8.0), 62).numpy()
+    cams = synth.random_sphere_cameras(dims, 3, 21, 21, 6)
+    vol = Volume(torch.from_numpy(cube).cuda(), "f32")
+    vol.attach_texture()
+    vol.attach_mip_bounds()
+    ref = Volume(torch.from_numpy(cube).cuda(), "f32")
+    ref.attach_texture()
+    assert torch.equal(vol.render(cams, 21, 21, "mip", 0.5), ref.render(cams, 21, 21, "mip", 0.5))
+    # new planes with a larger maximum: the bounds and their margin follow
+    cube2 = cube.copy()
+    cube2[20:30] = cube2[20:30] * 40.0 + 3.0
+    for v in (vol, ref):
+        v.upload(20, torch.from_numpy(cube2[20:30]).cuda())
+    assert torch.equal(vol.render(cams, 21, 21, "mip", 0.5), ref.render(cams, 21, 21, "mip", 0.5))
+    vol.drop_bricks()
+    assert torch.equal(vol.render(cams, 21, 21, "mip", 0.5), ref.render(cams, 21, 21, "mip", 0.5))
+    vol.detach_mip_bounds()
+    with pytest.raises(VRError):                  # the bricks are gone: no new bounds
+        vol.attach_mip_bounds()
+
+
+def test_mip_bounds_are_refused_where_they_do_not_apply():
+    cube = synth.make_cube((16, 16, 16), 2, ("uniform", 3.0, 8.0), 63)
+    for dtype in ("f16", "i8"):
+        v = Volume(cube.cuda(), dtype)
+        v.attach_texture()
+        with pytest.raises(VRError):
+            v.attach_mip_bounds()
+    v = Volume(cube.cuda(), "f32")
+    with pytest.raises(VRError):                  # no texture storage
+        v.attach_mip_bounds()
+    v.attach_texture()
+    v.attach_mip_bounds()
+    v.attach_mip_bounds()                         # attaching twice is a no-op
+    v.detach_texture()                            # releases the bounds too
+    with pytest.raises(VRError):
+        v.attach_mip_bounds()
+
+
+# ---------------------------------------------------------------------------
 # the 1024^3 workload at full size, in the benchmark's launch configuration
 # (32 orbiting 1920x1080 views in one call), checked on sampled pixels
 # ---------------------------------------------------------------------------
@@ -692,6 +806,16 @@ def test_large_workload_sampled_pixels(large, dtype, tex):
             vol.detach_masks()
             torch.cuda.synchronize()
             assert torch.equal(img, img1), "large %s %s: masks change the image" % (dtype, mode)
+            assert int(n0.item()) == int(n1.item())
+            img = img1
+        if tex and dtype == "f32" and mode == "mip":
+            # with the MIP bounds (the benchmark's configuration) likewise
+            vol.attach_mip_bounds()
+            n1 = torch.zeros(1, dtype=torch.int64, device="cuda")
+            img1 = vol.render(cams, w, h, mode, wl.step, count=n1)
+            vol.detach_mip_bounds()
+            torch.cuda.synchronize()
+            assert torch.equal(img, img1), "large mip: bounds change the image"
             assert int(n0.item()) == int(n1.item())
             img = img1
         torch.cuda.synchronize()
