@@ -764,7 +764,8 @@ def main():
             "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {
-                "workload": wl.name, "cube": "1024^3 float32, 2000 sources, sigma=1 noise",
+                "workload": wl.name,
+                "cube": "%dx%dx%d float32, %d sources, sigma=1 noise" % (wl.dims + (wl.n_sources,)),
                 "storage": "f32 32^3 bricks" + (" + layered textures" if args.storage == "texture"
                                                 else ""),
                 "views": n_views, "resolution": "%dx%d" % (W, H),
