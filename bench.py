@@ -279,21 +279,25 @@ def run_reference(args):
     cams = synth.large_cameras()
     cube = wl.cube("cuda" if torch.cuda.is_available() else "cpu").cpu().numpy()
     per_step = []
-    total_samples, total_secs = 0.0, 0.0
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         sps, fps, threads, sample = oracle_throughput(cube, cams, wl, args.ref_budget, seed=i)
         if i >= args.warmup:
-            per_step.append((sps, fps))
-    sps = statistics.mean(s for s, _ in per_step)
-    fps = statistics.mean(f for _, f in per_step)
+            per_step.append((sps, fps, time.perf_counter() - t0))
+    sps = statistics.mean(s for s, _, _ in per_step)
+    fps = statistics.mean(f for _, f, _ in per_step)
     line = {
         "impl": "reference", "metric": METRIC, "value": sps, "unit": "samples/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * 64 / fps if fps else None, "higher_is_better": True,
+        # each step is a bounded sample of the workload: its measured time;
+        # the whole 64-frame step at this rate is in config
+        "ms_per_step": 1000.0 * statistics.mean(t for _, _, t in per_step),
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "cube": "1024^3 float32", "views": 32,
                    "resolution": "1920x1080", "modes": ["composite", "mip"], "step": wl.step,
-                   "fps": fps},
+                   "fps": fps,
+                   "projected_ms_per_full_step": 1000.0 * 64 / fps if fps else None},
         "cpu_baseline": {"value": sps, "unit": "samples/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": sps, "unit": "samples/s", "h2d_bytes_per_step": 0,
