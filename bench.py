@@ -339,9 +339,12 @@ def event_ms(fn, reps, stream):
 def batched_leg(dev, reps=3):
     """64 mixed views of four resident cubes (f32, f16, f16, int8; texture
     storage, pair texels for f16 and int8): one persistent launch (replayed
-    from a CUDA graph) against the plain FP32 path (the same views as 64
-    per-request renders of FP32 copies with texture storage)."""
-    from paper_1001_2049_b300 import Request, batch_workspace, render_batch
+    from a CUDA graph, tile and packet shape from the batch autotuner)
+    against the plain FP32 path (the same views as 64 per-request renders of
+    FP32 copies with texture storage, launch shapes from the per-view
+    autotuner)."""
+    from paper_1001_2049_b300 import (Request, batch_autotune, batch_shapes, batch_workspace,
+                                      render_batch)
     lut = synth.default_lut()
     vols, f32 = [], []
     for i, (name, dims, dt) in enumerate(synth.BATCH_CUBES):
@@ -368,6 +371,17 @@ def batched_leg(dev, reps=3):
     samples = int(cnt.item())
     for r in reqs:
         r.samples = None
+    # tile and ray-packet shape of the batched launch, by the batch autotuner
+    # on this very batch; the plain path's launch shapes by the per-view
+    # autotuner, per cube and mode on that cube's largest view
+    cfg, tune_ms = batch_autotune(reqs, ws)
+    for c, p in enumerate(f32):
+        for mode in ("composite", "mip"):
+            mine = [(w * h, cam, w, h) for (cc, cam, w, h, m) in views if cc == c and m == mode]
+            if mine:
+                _, cam, w, h = max(mine, key=lambda x: x[0])
+                p.autotune(np.asarray([cam]), w, h, mode, 0.5)
+    torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
@@ -391,6 +405,8 @@ def batched_leg(dev, reps=3):
            "batched_graph_ms": batch_ms, "batched_fps": n / (batch_ms / 1000.0),
            "batched_samples_per_s": samples / (batch_ms / 1000.0),
            "batched_launch_ms": launch_ms,
+           "batch_shape": {"config": cfg, "tile_and_packet": list(batch_shapes()[cfg]),
+                           "ms": tune_ms},
            "plain_f32_per_request_ms": plain_ms, "plain_f32_fps": n / (plain_ms / 1000.0),
            "speedup_vs_plain_f32": plain_ms / batch_ms}
     for v in vols + f32:

@@ -297,8 +297,9 @@ int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
 
 /* ---- many requests in one persistent launch ------------------------------
  * The paper's scheduler maps available tasks onto the computing resources
- * (Fig. 1 caption; §3.1 module 1).  Here the tasks are the 16 x 16 ray tiles
- * of every request and the resources are the SMs of one GPU.             */
+ * (Fig. 1 caption; §3.1 module 1).  Here the tasks are the ray tiles (256
+ * rays each, in the shape vr_batch_autotune chose) of every request and the
+ * resources are the SMs of one GPU.                                         */
 
 #define VR_BATCH_MAX 64          /* requests per kernel launch (more are split) */
 
@@ -362,6 +363,29 @@ int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_by
  *   GPU (different streams, or devices sharing nothing but this array) race
  *   and must be ordered by the caller.                                       */
 int vr_render_batch_noalloc(const vr_request* reqs, int n, void* stream);
+
+/* Tile and ray-packet shapes of the batched launch (the batch autotuner's
+ * search space): configuration cfg in [0, vr_batch_tune_count()) splits
+ * every image into tiles of tile_x x tile_y rays (256, one block each) whose
+ * warps hold packet_x x packet_y neighbouring rays.  Any output pointer may
+ * be NULL.  Images do not depend on the shape.                             */
+int vr_batch_tune_count(void);
+int vr_batch_tune_describe(int cfg, int* tile_x, int* tile_y, int* packet_x, int* packet_y);
+
+/* The shape every later vr_render_batch and vr_render_batch_noalloc call of
+ * this process uses (initially 0; a process-wide setting, so callers on
+ * several threads share it).  vr_get_batch_config returns it.              */
+int vr_set_batch_config(int cfg);
+int vr_get_batch_config(void);
+
+/* Time every batch shape on these requests (arguments as vr_render_batch;
+ * the images are written to the requests' outputs, each shape's run
+ * overwriting the last) and keep the fastest as the process-wide shape.  A
+ * tuning call, not a render call: it records events on `stream` and waits
+ * for them, so it must not be captured into a CUDA graph.  n = 0 sets
+ * *best_ms to -1 and changes nothing.                                        */
+int vr_batch_autotune(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,
+                      void* stream, int* best_cfg, float* best_ms);
 
 /* Launch shapes of the texture-gather kernel (the autotuner's search space):
  * configuration cfg in [0, vr_tune_count()) renders blocks of block_x x

@@ -8,6 +8,7 @@ the seeded synthetic inputs (``synth``) and host-side control: the
 continuous-batching server (``serve``) and part-by-part streaming of cubes
 larger than the device (``stream``).
 """
-from .api import (CAMERA_DTYPE, DTYPES, MODES, Request, Volume, batch_workspace,  # noqa: F401
-                  render_batch, render_init, volume_bytes)
+from .api import (CAMERA_DTYPE, DTYPES, MODES, Request, Volume, batch_autotune,  # noqa: F401
+                  batch_shapes, batch_workspace, get_batch_config, render_batch, render_init,
+                  set_batch_config, volume_bytes)
 from ._lib import VRError, load  # noqa: F401

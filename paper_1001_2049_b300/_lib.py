@@ -48,6 +48,12 @@ SIGNATURES = {
     "vr_batch_workspace_bytes": (c_size_t, []),
     "vr_render_batch": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_void_p]),
     "vr_render_batch_noalloc": (c_int, [c_void_p, c_int, c_void_p]),
+    "vr_batch_tune_count": (c_int, []),
+    "vr_batch_tune_describe": (c_int, [c_int] + [ctypes.POINTER(c_int)] * 4),
+    "vr_set_batch_config": (c_int, [c_int]),
+    "vr_get_batch_config": (c_int, []),
+    "vr_batch_autotune": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_void_p,
+                                  ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float)]),
     "vr_tune_count": (c_int, []),
     "vr_tune_describe": (c_int, [c_int] + [ctypes.POINTER(c_int)] * 5),
     "vr_autotune": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_void_p,

@@ -89,9 +89,9 @@ def batch_workspace(device=None) -> torch.Tensor:
     return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
 
 
-def render_batch(requests, workspace: torch.Tensor | None = None, stream=None):
-    """Render every request with the batched persistent kernel; returns the
-    output tensors (allocated here when a request has none)."""
+def _batch_args(requests):
+    """The vr_request array of ``requests`` (outputs allocated where a
+    request has none), the objects it points into, and the outputs."""
     n = len(requests)
     arr = (_Request * max(n, 1))()
     keep, outs = [], []
@@ -122,12 +122,53 @@ def render_batch(requests, workspace: torch.Tensor | None = None, stream=None):
             flags, idx = rq.done
             r.done = flags.data_ptr() + 4 * int(idx)
             r.done_value = int(rq.done_value)
+    return arr, keep, outs
+
+
+def render_batch(requests, workspace: torch.Tensor | None = None, stream=None):
+    """Render every request with the batched persistent kernel; returns the
+    output tensors (allocated here when a request has none)."""
+    arr, keep, outs = _batch_args(requests)
     if workspace is None:
         workspace = batch_workspace(outs[0].device if outs else None)
-    check(load().vr_render_batch(arr, n, workspace.data_ptr(), workspace.numel(),
+    check(load().vr_render_batch(arr, len(requests), workspace.data_ptr(), workspace.numel(),
                                  _stream_ptr(stream)))
     del keep
     return outs
+
+
+def batch_shapes():
+    """The batched launch's tile and ray-packet shapes: (tile_x, tile_y,
+    packet_x, packet_y) per configuration index."""
+    lib = load()
+    out = []
+    for c in range(lib.vr_batch_tune_count()):
+        v = [ctypes.c_int(0) for _ in range(4)]
+        check(lib.vr_batch_tune_describe(c, *[ctypes.byref(x) for x in v]))
+        out.append(tuple(x.value for x in v))
+    return out
+
+
+def set_batch_config(cfg: int):
+    """Use batch shape ``cfg`` for every later batched render of the process."""
+    check(load().vr_set_batch_config(int(cfg)))
+
+
+def get_batch_config() -> int:
+    return int(load().vr_get_batch_config())
+
+
+def batch_autotune(requests, workspace: torch.Tensor | None = None, stream=None):
+    """Time every batch shape on these requests (their images are written)
+    and keep the fastest for the process; returns (config, ms)."""
+    arr, keep, outs = _batch_args(requests)
+    if workspace is None:
+        workspace = batch_workspace(outs[0].device if outs else None)
+    best, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+    check(load().vr_batch_autotune(arr, len(requests), workspace.data_ptr(), workspace.numel(),
+                                   _stream_ptr(stream), ctypes.byref(best), ctypes.byref(ms)))
+    del keep
+    return int(best.value), float(ms.value)
 
 
 def launch_shapes():

@@ -2,6 +2,7 @@
 // validation, volume handles, transfer-function preparation and launch
 // planning.  No device memory is allocated here; all of it is the caller's.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -276,7 +277,7 @@ int check_request(const vr_request& rq, int index)
 // volumes are looked up in (or added to) the launch's slots.  Returns VR_OK
 // or 1 when the launch has no free slot left (start a new launch).
 int batch_request(const vr_request& rq, vr::BatchParams* B, int* n_tex, vr::Volume** tex_vols,
-                  int* n_lut, float* lut_steps, int* lut_ns)
+                  int* n_lut, float* lut_steps, int* lut_ns, int cfg)
 {
     vr::Volume* v = reinterpret_cast<vr::Volume*>(rq.vol);
     vr::MarchParams mp;
@@ -362,8 +363,9 @@ int batch_request(const vr_request& rq, vr::BatchParams* B, int* n_tex, vr::Volu
     q.dtype = v->dtype;
     q.tex_slot = tex_slot;
     q.lut_slot = lut_slot;
-    q.tiles_x = (rq.w + 15) / 16;
-    q.n_tiles = q.tiles_x * ((rq.h + 15) / 16);
+    const vr::BatchShape& S = vr::kBatchShapes[cfg];
+    q.tiles_x = (rq.w + S.tx - 1) / S.tx;
+    q.n_tiles = q.tiles_x * ((rq.h + S.ty - 1) / S.ty);
     q.first_item = B->total_items;
     B->total_items += q.n_tiles;
     B->n++;
@@ -379,15 +381,25 @@ int batch_class(const vr_request& r)
     return v && v->has_tex ? vr::kBatchTex : vr::kBatchBricks;
 }
 
-int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
+// Tile and ray-packet shape of the batched launches (process-wide; set by
+// vr_set_batch_config or vr_batch_autotune).
+std::atomic<int> g_batch_cfg{0};
+
+int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s, int cfg)
 {
-    static int grid[2] = {0, 0};
-    if (grid[0] == 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-        for (int c = 0; c < 2; ++c) grid[c] = sms * vr::batch_blocks_per_sm(c);
+    // persistent grid: as many blocks as fit on the device at once
+    static std::atomic<int> grid[2][vr::kNumBatchShapes];
+    int g[2];
+    for (int c = 0; c < 2; ++c) {
+        g[c] = grid[c][cfg].load();
+        if (g[c] == 0) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (sms < 1) sms = 1;
+            g[c] = sms * vr::batch_blocks_per_sm(c, cfg);
+            grid[c][cfg].store(g[c]);
+        }
     }
     // every request is checked before anything is enqueued, so an argument
     // error leaves the stream untouched
@@ -417,12 +429,12 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s)
                     continue;
                 }
                 const int r = batch_request(reqs[i], B, &n_tex, tex_vols, &n_lut, lut_steps,
-                                            lut_ns);
+                                            lut_ns, cfg);
                 if (r == 1) break;       // slots full: launch what we have
                 ++i;
             }
             if (rc == VR_OK && B->n > 0) {
-                cudaError_t e = vr::launch_batch(*B, ws, grid[cls], cls, s);
+                cudaError_t e = vr::launch_batch(*B, ws, g[cls], cls, cfg, s);
                 if (e != cudaSuccess) rc = cuda_fail(e, "batch launch");
             }
         }
@@ -650,7 +662,7 @@ namespace vr {
 // launch a batch on counters the caller supplies, and record an error.
 int batch_with_counters(const vr_request* reqs, int n, unsigned* counters, cudaStream_t s)
 {
-    return batch_impl(reqs, n, counters, s);
+    return batch_impl(reqs, n, counters, s, g_batch_cfg.load());
 }
 
 int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -940,8 +952,9 @@ size_t vr_batch_workspace_bytes(void)
     return align_up(sizeof(unsigned) * vr::kBatchWords, 256);
 }
 
-int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,
-                    void* stream)
+namespace {
+
+int check_batch_args(const vr_request* reqs, int n, void* workspace, size_t ws_bytes)
 {
     if (n < 0) return fail(VR_ERR_ARG, "n = %d < 0", n);
     if (n == 0) return VR_OK;
@@ -953,8 +966,88 @@ int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_by
         return fail(VR_ERR_OOM, "workspace has %zu bytes, %zu needed", ws_bytes,
                     vr_batch_workspace_bytes());
     if (!is_device_ptr(workspace)) return fail(VR_ERR_ARG, "workspace is not device memory");
+    return VR_OK;
+}
+
+}  // namespace
+
+int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,
+                    void* stream)
+{
+    const int rc = check_batch_args(reqs, n, workspace, ws_bytes);
+    if (rc || n == 0) return rc;
     return batch_impl(reqs, n, static_cast<unsigned*>(workspace),
-                      static_cast<cudaStream_t>(stream));
+                      static_cast<cudaStream_t>(stream), g_batch_cfg.load());
+}
+
+int vr_batch_tune_count(void) { return vr::kNumBatchShapes; }
+
+int vr_batch_tune_describe(int cfg, int* tile_x, int* tile_y, int* packet_x, int* packet_y)
+{
+    if (cfg < 0 || cfg >= vr::kNumBatchShapes)
+        return fail(VR_ERR_ARG, "batch configuration %d out of range", cfg);
+    const vr::BatchShape& S = vr::kBatchShapes[cfg];
+    if (tile_x) *tile_x = S.tx;
+    if (tile_y) *tile_y = S.ty;
+    if (packet_x) *packet_x = S.px;
+    if (packet_y) *packet_y = S.py;
+    return VR_OK;
+}
+
+int vr_set_batch_config(int cfg)
+{
+    if (cfg < 0 || cfg >= vr::kNumBatchShapes)
+        return fail(VR_ERR_ARG, "batch configuration %d out of range", cfg);
+    g_batch_cfg.store(cfg);
+    return VR_OK;
+}
+
+int vr_get_batch_config(void) { return g_batch_cfg.load(); }
+
+int vr_batch_autotune(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,
+                      void* stream, int* best_cfg, float* best_ms)
+{
+    int rc = check_batch_args(reqs, n, workspace, ws_bytes);
+    if (rc) return rc;
+    if (n == 0) {
+        if (best_cfg) *best_cfg = g_batch_cfg.load();
+        if (best_ms) *best_ms = -1.0f;
+        return VR_OK;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned* ws = static_cast<unsigned*>(workspace);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "event");
+    }
+    int best = -1;
+    float best_t = 0.0f;
+    for (int c = 0; c < vr::kNumBatchShapes && rc == VR_OK; ++c) {
+        float t = 1e30f;
+        for (int it = 0; it < 3 && rc == VR_OK; ++it) {    // first run warms up
+            cudaEventRecord(e0, s);
+            rc = batch_impl(reqs, n, ws, s, c);
+            cudaEventRecord(e1, s);
+            const cudaError_t e = cudaEventSynchronize(e1);
+            if (rc == VR_OK && e != cudaSuccess) rc = cuda_fail(e, "batch autotune");
+            float ms = 0.0f;
+            if (rc == VR_OK) cudaEventElapsedTime(&ms, e0, e1);
+            if (it > 0 && ms < t) t = ms;
+        }
+        if (rc == VR_OK && (best < 0 || t < best_t)) {
+            best = c;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    g_batch_cfg.store(best);
+    if (best_cfg) *best_cfg = best;
+    if (best_ms) *best_ms = best_t;
+    return VR_OK;
 }
 
 int vr_tune_count(void) { return vr::tex_shape_count(); }

@@ -3,7 +3,8 @@
 //
 // The paper's scheduling module maps the available tasks onto the computing
 // resources (Fig. 1 caption, §3.1 module 1); on one GPU the tasks are the
-// 16 x 16 ray tiles of every requested view and the resources are the SMs.
+// ray tiles (256 rays, in one of kBatchShapes) of every requested view and
+// the resources are the SMs.
 // The launch puts about as many blocks as fit on the device at once; each
 // block repeatedly takes the next tile from a work counter in the caller's
 // workspace (an atomic add, no waiting on anything), renders it with the
@@ -18,8 +19,7 @@
 namespace vr {
 namespace {
 
-constexpr int kTile = 16;
-constexpr int kThreads = kTile * kTile;
+constexpr int kThreads = 256;             // one ray per thread, a tile per block
 #ifndef VR_BATCH_MIN_BLOCKS
 #define VR_BATCH_MIN_BLOCKS 4     // resident blocks per SM the registers must allow
 #endif
@@ -146,11 +146,17 @@ __device__ __forceinline__ unsigned tex_pixel_any(const BatchReq& q, const Batch
 
 // CLS (BatchClass): every request of the launch is of one class, so each
 // kernel instance compiles one fetch path: bricks (run-time storage type) or
-// texture (specialised per kind).
-template <int CLS>
+// texture (specialised per kind).  CFG: the tile and ray-packet shape
+// (kBatchShapes), chosen by vr_batch_autotune.
+template <int CLS, int CFG>
 __global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(const __grid_constant__ BatchParams B,
                                                          unsigned* __restrict__ ws)
 {
+    constexpr BatchShape S = kBatchShapes[CFG];
+    constexpr int wpr = S.tx / S.px;               // warps per row of packets
+    static_assert(S.tx * S.ty == kThreads && S.px * S.py == 32 && S.tx % S.px == 0 &&
+                      S.ty % S.py == 0,
+                  "a tile is 256 rays in warp packets");
     __shared__ float4 s_lut[VR_MAX_LUT];
     __shared__ int s_item;
     __shared__ int s_lut_slot;
@@ -175,8 +181,8 @@ __global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(co
         }
         const int t = item - q.first_item;
         const int tx = t % q.tiles_x, ty = t / q.tiles_x;
-        const int px = tx * kTile + (warp & 1) * 8 + (lane & 7);
-        const int py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+        const int px = tx * S.tx + (warp % wpr) * S.px + (lane % S.px);
+        const int py = ty * S.ty + (warp / wpr) * S.py + (lane / S.px);
         unsigned count = 0;
         if (px < q.w && py < q.h) {
             if constexpr (CLS == kBatchTex) {
@@ -212,26 +218,47 @@ __global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(co
 
 }  // namespace
 
-cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, int cls, cudaStream_t s)
+namespace {
+
+// The kernel instance of a (class, shape) pair.
+template <int CFG>
+const void* kernel_of_shape(int cls)
+{
+    return cls == kBatchTex ? reinterpret_cast<const void*>(batch_kernel<kBatchTex, CFG>)
+                            : reinterpret_cast<const void*>(batch_kernel<kBatchBricks, CFG>);
+}
+
+const void* batch_kernel_of(int cls, int cfg)
+{
+    switch (cfg) {
+    case 1: return kernel_of_shape<1>(cls);
+    case 2: return kernel_of_shape<2>(cls);
+    case 3: return kernel_of_shape<3>(cls);
+    case 4: return kernel_of_shape<4>(cls);
+    case 5: return kernel_of_shape<5>(cls);
+    default: return kernel_of_shape<0>(cls);
+    }
+}
+static_assert(kNumBatchShapes == 6, "batch_kernel_of lists every shape");
+
+}  // namespace
+
+cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, int cls, int cfg,
+                         cudaStream_t s)
 {
     // the counters start at zero for every launch (stream-ordered, capturable)
     cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned) * (1 + b.n), s);
     if (e != cudaSuccess) return e;
-    switch (cls) {
-    case kBatchTex: batch_kernel<kBatchTex><<<grid, kThreads, 0, s>>>(b, ws); break;
-    default: batch_kernel<kBatchBricks><<<grid, kThreads, 0, s>>>(b, ws); break;
-    }
-    return cudaGetLastError();
+    void* args[] = {const_cast<BatchParams*>(&b), &ws};
+    return cudaLaunchKernel(batch_kernel_of(cls, cfg), dim3((unsigned)grid), dim3(kThreads),
+                            args, 0, s);
 }
 
-int batch_blocks_per_sm(int cls)
+int batch_blocks_per_sm(int cls, int cfg)
 {
     int n = 0;
-    cudaError_t e =
-        cls == kBatchTex
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<kBatchTex>, kThreads, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<kBatchBricks>,
-                                                            kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel_of(cls, cfg),
+                                                                  kThreads, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;

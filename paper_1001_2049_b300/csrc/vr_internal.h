@@ -168,8 +168,19 @@ struct BatchParams {
 // Launch classes of the batched kernel: requests on volumes without texture
 // storage and on volumes with it, each compiled as its own kernel.
 enum BatchClass { kBatchBricks = 0, kBatchTex = 1 };
-cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, int cls, cudaStream_t s);
-int batch_blocks_per_sm(int cls);
+// Tile and ray-packet shapes of the batched kernel (the batch autotuner's
+// search space): a tile of tx x ty rays (one block of 256 threads) whose
+// warps hold px x py packets of neighbouring rays.
+struct BatchShape {
+    int tx, ty, px, py;
+};
+constexpr BatchShape kBatchShapes[] = {
+    {16, 16, 8, 4}, {16, 16, 16, 2}, {16, 16, 4, 8}, {32, 8, 8, 4}, {32, 8, 16, 2}, {64, 4, 16, 2},
+};
+constexpr int kNumBatchShapes = sizeof(kBatchShapes) / sizeof(kBatchShapes[0]);
+cudaError_t launch_batch(const BatchParams& b, unsigned* ws, int grid, int cls, int cfg,
+                         cudaStream_t s);
+int batch_blocks_per_sm(int cls, int cfg);
 int batch_with_counters(const vr_request* reqs, int n, unsigned* counters, cudaStream_t s);
 int record_error(int code, const char* msg);
 

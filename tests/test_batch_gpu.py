@@ -165,3 +165,37 @@ def test_batch_argument_errors(scene):
                       Request(bricks_vol, cam1, 8, 8, "composite", 0.5, tf=bad_tf)])
     torch.cuda.synchronize()
     assert torch.isnan(good).all()
+
+
+def test_every_batch_shape_gives_identical_images(scene):
+    # tile and ray-packet shapes only change which block renders which ray
+    from paper_1001_2049_b300 import (batch_autotune, batch_shapes, get_batch_config,
+                                      set_batch_config)
+    shapes = batch_shapes()
+    assert len(shapes) >= 4
+    for tx, ty, px, py in shapes:
+        assert tx * ty == 256 and px * py == 32
+    reqs = requests_for(scene, 24, 7)
+    saved = get_batch_config()
+    try:
+        ref = None
+        for cfg in range(len(shapes)):
+            set_batch_config(cfg)
+            assert get_batch_config() == cfg
+            outs = [o.clone() for o in render_batch(reqs)]
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = outs
+            for a, b in zip(ref, outs):
+                assert torch.equal(torch.nan_to_num(a), torch.nan_to_num(b)), shapes[cfg]
+        best, ms = batch_autotune(reqs)
+        assert 0 <= best < len(shapes) and ms > 0
+        assert get_batch_config() == best
+        outs = render_batch(reqs)
+        torch.cuda.synchronize()
+        for a, b in zip(ref, outs):
+            assert torch.equal(torch.nan_to_num(a), torch.nan_to_num(b))
+        with pytest.raises(Exception):
+            set_batch_config(len(shapes))
+    finally:
+        set_batch_config(saved)
