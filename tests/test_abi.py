@@ -76,3 +76,25 @@ def test_null_arguments_are_rejected_synchronously():
     dims = (ctypes.c_int64 * 3)(8, 8, 8)
     assert lib.vr_volume_create(dims, 7, None, 1, None, 0, None, ctypes.byref(h)) == _lib.VR_ERR_ARG
     assert b"dtype" in lib.vr_last_error()
+
+
+def test_batch_shapes_and_config_host_only():
+    lib = _lib.load()
+    n = lib.vr_batch_tune_count()
+    assert n >= 4
+    seen = set()
+    for c in range(n):
+        v = [ctypes.c_int(0) for _ in range(4)]
+        assert lib.vr_batch_tune_describe(c, *[ctypes.byref(x) for x in v]) == 0
+        tx, ty, px, py = (x.value for x in v)
+        assert tx * ty == 256 and px * py == 32 and tx % px == 0 and ty % py == 0
+        seen.add((tx, ty, px, py))
+    assert len(seen) == n                      # no shape listed twice
+    assert lib.vr_batch_tune_describe(n, None, None, None, None) != 0
+    assert lib.vr_batch_tune_describe(-1, None, None, None, None) != 0
+    saved = lib.vr_get_batch_config()
+    try:
+        assert lib.vr_set_batch_config(n - 1) == 0 and lib.vr_get_batch_config() == n - 1
+        assert lib.vr_set_batch_config(n) != 0 and lib.vr_get_batch_config() == n - 1
+    finally:
+        lib.vr_set_batch_config(saved)
