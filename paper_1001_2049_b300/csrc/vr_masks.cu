@@ -37,15 +37,23 @@ __device__ __forceinline__ float voxel(const void* __restrict__ b, size_t i)
     return (float)__ldg(static_cast<const signed char*>(b) + i);
 }
 
-// One block of 16 warps per column of 8 x 1 macrocells (walked along z):
-// for each macrocell row, warp w takes cell
-// row (y, z) = (w & 3, w >> 2) of the macrocells, lane l the cell at gather
-// coordinate x = 32 bx + l.  The block's corner voxels (33 x 5 x 5, indices
-// clamped to the cube) are staged once in shared memory, decoded.
-// A warp's ballot holds 4 x-bits of each of the 8 macrocells for its (y, z);
-// eight threads assemble the masks from the 16 ballots.
-constexpr int kMaskWarps = 16;
-constexpr int kTileX = 33, kTileYZ = 5;
+// One block of 4 warps per column of 8 x 1 macrocells (32 x 4 cells across),
+// walked along z in chunks of kRows macrocell rows.  The chunk's corner voxels
+// (33 x 5 x (4 kRows + 1), indices clamped to the cube) are staged in shared
+// memory, decoded: every thread issues all its loads of the chunk before
+// storing any (about 22 loads in flight per thread, which HBM latency
+// needs), then decodes and stores them.  Thread (lane, warp)
+// owns the cell column at gather coordinates x = 32 bx + lane, y = 4 by +
+// warp and walks it along z: the largest value and the largest |value| of a
+// plane's 2 x 2 corners are computed once and serve the two cells that
+// plane bounds, so a step reads the four corners of one new plane.  A warp's
+// ballot holds 4 x-bits of each of the 8 macrocells for its (y, z); after
+// the chunk, 8 x kRows threads assemble the masks from the ballots.
+constexpr int kMaskWarps = 4;
+constexpr int kRows = 4;
+constexpr int kTileX = 33, kTileY = 5, kTileZ = 4 * kRows + 1;
+constexpr int kTileElems = kTileX * kTileY * kTileZ;
+constexpr int kPerThread = (kTileElems + 32 * kMaskWarps - 1) / (32 * kMaskWarps);
 
 template <int DT>
 __global__ void __launch_bounds__(32 * kMaskWarps) mask_kernel(
@@ -53,61 +61,99 @@ __global__ void __launch_bounds__(32 * kMaskWarps) mask_kernel(
     const float* __restrict__ offset, VolumeGeom g, unsigned long long* __restrict__ out,
     int mnx, int mny, int mnz, float clip)
 {
-    __shared__ float s_v[kTileYZ][kTileYZ][kTileX];
-    __shared__ unsigned s_ballot[kMaskWarps];
+    __shared__ float s_v[kTileZ][kTileY][kTileX];
+    __shared__ unsigned s_ballot[4 * kRows][kMaskWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // tile origin: the block's first cell, clamped like every cell (the
-    // clamped cells of the block then lie in [origin, origin + 31] along x
-    // and [origin, origin + 3] along y and z, clamping being 1-Lipschitz)
+    // tile origin: the block's first cell (the chunk's along z), clamped
+    // like every cell (the clamped cells then lie in [origin, origin + 31]
+    // along x, [origin, origin + 3] along y and [origin, origin + 4 kRows -
+    // 1] along z, clamping being 1-Lipschitz)
     const int x0 = min(max((int)blockIdx.x * 32 - 1, 0), g.nx - 2);
     const int y0 = min(max((int)blockIdx.y * 4 - 1, 0), g.ny - 2);
     const int gx = blockIdx.x * 32 + lane;                      // gather coordinates: cell + 1
-    const int gy = blockIdx.y * 4 + (w & 3);
-    // one row of macrocells along z after the other (the block walks its
-    // column, so the launch has few blocks)
-    for (int bz = 0; bz < mnz; ++bz) {
-        const int z0 = min(max(bz * 4 - 1, 0), g.nz - 2);
-        __syncthreads();                 // the previous row's tile and ballots are used up
-        for (int i = threadIdx.x; i < kTileX * kTileYZ * kTileYZ; i += 32 * kMaskWarps) {
-            const int tx = i % kTileX, ty = (i / kTileX) % kTileYZ, tz = i / (kTileX * kTileYZ);
-            const int x = min(x0 + tx, g.nx - 1);
-            const int y = min(y0 + ty, g.ny - 1);
-            const int z = min(z0 + tz, g.nz - 1);
-            const size_t brick = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) * g.nbx +
-                                 (x >> kBrickShift);
-            float v = voxel<DT>(bricks, brick * kBrickVoxels + ((z & 31) << 10) + ((y & 31) << 5) +
-                                            (x & 31));
-            if (DT == VR_I8) v = fmaf(v, __ldg(scale + z), __ldg(offset + z));
-            s_v[tz][ty][tx] = v;
-        }
-        __syncthreads();
-        const int gz = bz * 4 + (w >> 2);
-        bool need = false;
-        if (gx <= g.nx && gy <= g.ny && gz <= g.nz) {
-            // the cell's corners, as tile indices (cells clamped to the cube)
-            const int cx = min(max(gx - 1, 0), g.nx - 2) - x0;
-            const int cy = min(max(gy - 1, 0), g.ny - 2) - y0;
-            const int cz = min(max(gz - 1, 0), g.nz - 2) - z0;
-            float hi = -INFINITY, mag = 0.0f;
+    const int gy = blockIdx.y * 4 + w;
+    const bool in_xy = gx <= g.nx && gy <= g.ny;
+    // the cell's corner columns and rows, as tile indices (cells clamped)
+    const int cx = min(max(gx - 1, 0), g.nx - 2) - x0;
+    const int cy = min(max(gy - 1, 0), g.ny - 2) - y0;
+    for (int bz0 = 0; bz0 < mnz; bz0 += kRows) {
+        const int z0 = min(max(bz0 * 4 - 1, 0), g.nz - 2);
+        // stage: tile element i = (tz * 5 + ty) * 33 + tx; all loads first
+        float vals[kPerThread];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float v = s_v[cz + (c >> 2)][cy + ((c >> 1) & 1)][cx + (c & 1)];
-                hi = fmaxf(hi, v);
-                mag = fmaxf(mag, fabsf(v));
+        for (int k = 0; k < kPerThread; ++k) {
+            const int i = threadIdx.x + k * 32 * kMaskWarps;
+            if (i < kTileElems) {
+                const int row = i / kTileX, tx = i - row * kTileX;
+                const int tz = row / kTileY, ty = row - tz * kTileY;
+                const int x = min(x0 + tx, g.nx - 1);
+                const int y = min(y0 + ty, g.ny - 1);
+                const int z = min(z0 + tz, g.nz - 1);
+                const size_t brick =
+                    ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) * g.nbx +
+                    (x >> kBrickShift);
+                vals[k] = voxel<DT>(bricks, brick * kBrickVoxels + ((z & 31) << 10) +
+                                                ((y & 31) << 5) + (x & 31));
             }
-            need = !(fmaf(mag, 0x1p-19f, hi) < clip);
         }
-        const unsigned b = __ballot_sync(0xffffffffu, need);
-        if (lane == 0) s_ballot[w] = b;
+        __syncthreads();                 // the previous chunk's tile and ballots are used up
+        float* s_flat = &s_v[0][0][0];
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
+            const int i = threadIdx.x + k * 32 * kMaskWarps;
+            if (i < kTileElems) {
+                float v = vals[k];
+                if (DT == VR_I8) {
+                    const int z = min(z0 + i / (kTileX * kTileY), g.nz - 1);
+                    v = fmaf(v, __ldg(scale + z), __ldg(offset + z));
+                }
+                s_flat[i] = v;
+            }
+        }
         __syncthreads();
-        if (threadIdx.x < 8) {
-            const int mx = blockIdx.x * 8 + threadIdx.x;
-            if (mx < mnx) {
+        // walk the chunk's cells along z; a plane's corner bounds serve the
+        // cell below and the cell above it
+        int have = -1;                   // tile plane whose bounds are in hi1 / mag1
+        float hi0 = 0.0f, mag0 = 0.0f, hi1 = 0.0f, mag1 = 0.0f;
+        auto plane_bounds = [&](int pz, float& hi, float& mag) {
+            const float a = s_v[pz][cy][cx], b = s_v[pz][cy][cx + 1];
+            const float c = s_v[pz][cy + 1][cx], d = s_v[pz][cy + 1][cx + 1];
+            // (fmaxf ignores NaN; the -inf and 0 keep a plane of NaN corners
+            // from giving a NaN bound)
+            hi = fmaxf(fmaxf(fmaxf(a, b), fmaxf(c, d)), -INFINITY);
+            mag = fmaxf(fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(c), fabsf(d))), 0.0f);
+        };
+        for (int c = 0; c < 4 * kRows; ++c) {
+            const int gz = bz0 * 4 + c;
+            // block-uniform: the cell's lower plane in the tile
+            const int cz = min(max(gz - 1, 0), g.nz - 2) - z0;
+            if (cz == have) {            // the next plane up: its lower plane is held
+                hi0 = hi1;
+                mag0 = mag1;
+                plane_bounds(cz + 1, hi1, mag1);
+                have = cz + 1;
+            } else if (cz + 1 != have) { // first cell of the chunk
+                plane_bounds(cz, hi0, mag0);
+                plane_bounds(cz + 1, hi1, mag1);
+                have = cz + 1;
+            }                            // else: the same cell again (clamped at an edge)
+            const bool need = in_xy && gz <= g.nz &&
+                              !(fmaf(fmaxf(mag0, mag1), 0x1p-19f, fmaxf(hi0, hi1)) < clip);
+            const unsigned b = __ballot_sync(0xffffffffu, need);
+            if (lane == 0) s_ballot[c][w] = b;
+        }
+        __syncthreads();
+        // masks of the chunk's 8 x kRows macrocells
+        if (threadIdx.x < 8 * kRows) {
+            const int mx = blockIdx.x * 8 + (threadIdx.x & 7);
+            const int bz = bz0 + (threadIdx.x >> 3);
+            if (mx < mnx && bz < mnz) {
+                const int c0 = (threadIdx.x >> 3) * 4, sh = 4 * (threadIdx.x & 7);
                 unsigned long long m = 0;
 #pragma unroll
-                for (int i = 0; i < kMaskWarps; ++i) {
-                    const unsigned long long nib = (s_ballot[i] >> (4 * threadIdx.x)) & 0xfu;
-                    m |= nib << (4 * (i & 3) + 16 * (i >> 2));      // bit x | y << 2 | z << 4
+                for (int i = 0; i < 16; ++i) {   // cell row y = i & 3, z = i >> 2
+                    const unsigned long long nib = (s_ballot[c0 + (i >> 2)][i & 3] >> sh) & 0xfu;
+                    m |= nib << (4 * i);                        // bit x | y << 2 | z << 4
                 }
                 out[((size_t)bz * mny + blockIdx.y) * mnx + mx] = m;
             }
@@ -119,7 +165,7 @@ __global__ void __launch_bounds__(32 * kMaskWarps) mask_kernel(
 
 cudaError_t launch_masks(const Volume& v, float clip, cudaStream_t s)
 {
-    const dim3 grid((unsigned)((v.mnx + 7) / 8), (unsigned)v.mny);
+    const dim3 grid((unsigned)((v.mnx + 7) / 8), (unsigned)v.mny);   // 32 x 4 cells each
     switch (v.dtype) {
     case VR_F32:
         mask_kernel<VR_F32><<<grid, 32 * kMaskWarps, 0, s>>>(v.bricks, v.scale, v.offset, v.g,
