@@ -40,28 +40,56 @@ __device__ __forceinline__ float voxel(const void* __restrict__ b, size_t i)
 // One block of 4 warps per column of 8 x 1 macrocells (32 x 4 cells across),
 // walked along z in chunks of kRows macrocell rows.  The chunk's corner voxels
 // (33 x 5 x (4 kRows + 1), indices clamped to the cube) are staged in shared
-// memory, decoded: every thread issues all its loads of the chunk before
-// storing any (about 22 loads in flight per thread, which HBM latency
-// needs), then decodes and stores them.  Thread (lane, warp)
-// owns the cell column at gather coordinates x = 32 bx + lane, y = 4 by +
-// warp and walks it along z: the largest value and the largest |value| of a
-// plane's 2 x 2 corners are computed once and serve the two cells that
-// plane bounds, so a step reads the four corners of one new plane.  A warp's
-// ballot holds 4 x-bits of each of the 8 macrocells for its (y, z); after
-// the chunk, 8 x kRows threads assemble the masks from the ballots.
+// memory, decoded.  FP32 cubes stage with asynchronous 4-byte copies into two
+// buffers, the next chunk's copies in flight while the current chunk is
+// tested; FP16 and int8 cubes (elements too small for those copies) issue all
+// of a chunk's loads before storing any (about 22 in flight per thread), then
+// decode and store them.  Thread (lane, warp) owns the cell column at gather
+// coordinates x = 32 bx + lane, y = 4 by + warp and walks it along z: the
+// largest value and the largest |value| of a plane's 2 x 2 corners are
+// computed once and serve the two cells that plane bounds, so a step reads
+// the four corners of one new plane.  A warp's ballot holds 4 x-bits of each
+// of the 8 macrocells for its (y, z); after the chunk, 8 x kRows threads
+// assemble the masks from the ballots.
 constexpr int kMaskWarps = 4;
 constexpr int kRows = 4;
 constexpr int kTileX = 33, kTileY = 5, kTileZ = 4 * kRows + 1;
 constexpr int kTileElems = kTileX * kTileY * kTileZ;
-constexpr int kPerThread = (kTileElems + 32 * kMaskWarps - 1) / (32 * kMaskWarps);
+constexpr int kMaskThreads = 32 * kMaskWarps;
+constexpr int kPerThread = (kTileElems + kMaskThreads - 1) / kMaskThreads;
+
+// Brick-layout index of tile element i of the chunk whose tile origin is
+// (x0, y0, z0); element i = (tz * 5 + ty) * 33 + tx, indices clamped.
+__device__ __forceinline__ size_t tile_voxel(const VolumeGeom& g, int x0, int y0, int z0, int i,
+                                             int* zout)
+{
+    const int row = i / kTileX, tx = i - row * kTileX;
+    const int tz = row / kTileY, ty = row - tz * kTileY;
+    const int x = min(x0 + tx, g.nx - 1);
+    const int y = min(y0 + ty, g.ny - 1);
+    const int z = min(z0 + tz, g.nz - 1);
+    *zout = z;
+    const size_t brick = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) * g.nbx +
+                         (x >> kBrickShift);
+    return brick * kBrickVoxels + ((z & 31) << 10) + ((y & 31) << 5) + (x & 31);
+}
+
+__device__ __forceinline__ void copy_async4(float* dst, const float* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
 
 template <int DT>
-__global__ void __launch_bounds__(32 * kMaskWarps) mask_kernel(
+__global__ void __launch_bounds__(kMaskThreads) mask_kernel(
     const void* __restrict__ bricks, const float* __restrict__ scale,
     const float* __restrict__ offset, VolumeGeom g, unsigned long long* __restrict__ out,
     int mnx, int mny, int mnz, float clip)
 {
-    __shared__ float s_v[kTileZ][kTileY][kTileX];
+    constexpr int kBufs = DT == VR_F32 ? 2 : 1;
+    __shared__ float s_v[kBufs][kTileZ][kTileY][kTileX];
     __shared__ unsigned s_ballot[4 * kRows][kMaskWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // tile origin: the block's first cell (the chunk's along z), clamped
@@ -76,52 +104,77 @@ __global__ void __launch_bounds__(32 * kMaskWarps) mask_kernel(
     // the cell's corner columns and rows, as tile indices (cells clamped)
     const int cx = min(max(gx - 1, 0), g.nx - 2) - x0;
     const int cy = min(max(gy - 1, 0), g.ny - 2) - y0;
-    for (int bz0 = 0; bz0 < mnz; bz0 += kRows) {
-        const int z0 = min(max(bz0 * 4 - 1, 0), g.nz - 2);
-        // stage: tile element i = (tz * 5 + ty) * 33 + tx; all loads first
-        float vals[kPerThread];
-#pragma unroll
-        for (int k = 0; k < kPerThread; ++k) {
-            const int i = threadIdx.x + k * 32 * kMaskWarps;
-            if (i < kTileElems) {
-                const int row = i / kTileX, tx = i - row * kTileX;
-                const int tz = row / kTileY, ty = row - tz * kTileY;
-                const int x = min(x0 + tx, g.nx - 1);
-                const int y = min(y0 + ty, g.ny - 1);
-                const int z = min(z0 + tz, g.nz - 1);
-                const size_t brick =
-                    ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) * g.nbx +
-                    (x >> kBrickShift);
-                vals[k] = voxel<DT>(bricks, brick * kBrickVoxels + ((z & 31) << 10) +
-                                                ((y & 31) << 5) + (x & 31));
-            }
+    auto chunk_z0 = [&](int bz0) { return min(max(bz0 * 4 - 1, 0), g.nz - 2); };
+    // FP32: copies of chunk bz0 into buffer b (one commit group), a tile row
+    // (fixed y, z) per warp step: lane l copies column l, lane 0 also column
+    // 32; a column's offset inside a brick row is the same for every row
+    const int col_a = min(x0 + lane, g.nx - 1), col_b = min(x0 + 32, g.nx - 1);
+    const size_t off_a = (size_t)(col_a >> kBrickShift) * kBrickVoxels + (col_a & 31);
+    const size_t off_b = (size_t)(col_b >> kBrickShift) * kBrickVoxels + (col_b & 31);
+    auto stage_async = [&](int b, int bz0) {
+        const int z0 = chunk_z0(bz0);
+        float* dst = &s_v[b][0][0][0];
+        const float* src = static_cast<const float*>(bricks);
+        for (int r = w; r < kTileZ * kTileY; r += kMaskWarps) {
+            const int tz = r / kTileY, ty = r - tz * kTileY;
+            const int y = min(y0 + ty, g.ny - 1);
+            const int z = min(z0 + tz, g.nz - 1);
+            const size_t row = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) *
+                                   g.nbx * kBrickVoxels +
+                               ((z & 31) << 10) + ((y & 31) << 5);
+            copy_async4(dst + r * kTileX + lane, src + row + off_a);
+            if (lane == 0) copy_async4(dst + r * kTileX + 32, src + row + off_b);
         }
-        __syncthreads();                 // the previous chunk's tile and ballots are used up
-        float* s_flat = &s_v[0][0][0];
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if constexpr (DT == VR_F32) stage_async(0, 0);
+    for (int bz0 = 0, j = 0; bz0 < mnz; bz0 += kRows, ++j) {
+        const int z0 = chunk_z0(bz0);
+        const int b = kBufs == 2 ? (j & 1) : 0;
+        if constexpr (DT == VR_F32) {
+            // the next chunk's copies go to the other buffer (free: its last
+            // use ended before the barrier closing the previous chunk); then
+            // wait for this chunk's
+            if (bz0 + kRows < mnz) {
+                stage_async(b ^ 1, bz0 + kRows);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncthreads();
+        } else {
+            // all loads first, then decode and store
+            float vals[kPerThread];
+            int zs[kPerThread];
 #pragma unroll
-        for (int k = 0; k < kPerThread; ++k) {
-            const int i = threadIdx.x + k * 32 * kMaskWarps;
-            if (i < kTileElems) {
-                float v = vals[k];
-                if (DT == VR_I8) {
-                    const int z = min(z0 + i / (kTileX * kTileY), g.nz - 1);
-                    v = fmaf(v, __ldg(scale + z), __ldg(offset + z));
+            for (int k = 0; k < kPerThread; ++k) {
+                const int i = threadIdx.x + k * kMaskThreads;
+                if (i < kTileElems) vals[k] = voxel<DT>(bricks, tile_voxel(g, x0, y0, z0, i, &zs[k]));
+            }
+            __syncthreads();             // the previous chunk's tile and ballots are used up
+            float* s_flat = &s_v[0][0][0][0];
+#pragma unroll
+            for (int k = 0; k < kPerThread; ++k) {
+                const int i = threadIdx.x + k * kMaskThreads;
+                if (i < kTileElems) {
+                    float v = vals[k];
+                    if (DT == VR_I8) v = fmaf(v, __ldg(scale + zs[k]), __ldg(offset + zs[k]));
+                    s_flat[i] = v;
                 }
-                s_flat[i] = v;
             }
+            __syncthreads();
         }
-        __syncthreads();
         // walk the chunk's cells along z; a plane's corner bounds serve the
         // cell below and the cell above it
         int have = -1;                   // tile plane whose bounds are in hi1 / mag1
         float hi0 = 0.0f, mag0 = 0.0f, hi1 = 0.0f, mag1 = 0.0f;
         auto plane_bounds = [&](int pz, float& hi, float& mag) {
-            const float a = s_v[pz][cy][cx], b = s_v[pz][cy][cx + 1];
-            const float c = s_v[pz][cy + 1][cx], d = s_v[pz][cy + 1][cx + 1];
+            const float a = s_v[b][pz][cy][cx], bb = s_v[b][pz][cy][cx + 1];
+            const float c = s_v[b][pz][cy + 1][cx], d = s_v[b][pz][cy + 1][cx + 1];
             // (fmaxf ignores NaN; the -inf and 0 keep a plane of NaN corners
             // from giving a NaN bound)
-            hi = fmaxf(fmaxf(fmaxf(a, b), fmaxf(c, d)), -INFINITY);
-            mag = fmaxf(fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(c), fabsf(d))), 0.0f);
+            hi = fmaxf(fmaxf(fmaxf(a, bb), fmaxf(c, d)), -INFINITY);
+            mag = fmaxf(fmaxf(fmaxf(fabsf(a), fabsf(bb)), fmaxf(fabsf(c), fabsf(d))), 0.0f);
         };
         for (int c = 0; c < 4 * kRows; ++c) {
             const int gz = bz0 * 4 + c;
@@ -139,8 +192,8 @@ __global__ void __launch_bounds__(32 * kMaskWarps) mask_kernel(
             }                            // else: the same cell again (clamped at an edge)
             const bool need = in_xy && gz <= g.nz &&
                               !(fmaf(fmaxf(mag0, mag1), 0x1p-19f, fmaxf(hi0, hi1)) < clip);
-            const unsigned b = __ballot_sync(0xffffffffu, need);
-            if (lane == 0) s_ballot[c][w] = b;
+            const unsigned bal = __ballot_sync(0xffffffffu, need);
+            if (lane == 0) s_ballot[c][w] = bal;
         }
         __syncthreads();
         // masks of the chunk's 8 x kRows macrocells
@@ -158,6 +211,7 @@ __global__ void __launch_bounds__(32 * kMaskWarps) mask_kernel(
                 out[((size_t)bz * mny + blockIdx.y) * mnx + mx] = m;
             }
         }
+        __syncthreads();                 // this chunk's buffer and ballots are used up
     }
 }
 
