@@ -39,6 +39,7 @@ struct Shape {
 constexpr Shape kShapes[] = {
     {16, 16, 8, 4, 1}, {16, 16, 8, 4, 6}, {32, 8, 8, 4, 5}, {16, 16, 16, 2, 5},
     {16, 16, 4, 8, 5}, {8, 8, 8, 4, 16},
+    {16, 8, 8, 4, 8}, {8, 16, 8, 4, 8}, {16, 16, 8, 4, 4},
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -111,10 +112,13 @@ cudaError_t launch_m(const MarchParams& p, const TexParams& t, int cfg, cudaStre
     case 3: return launch_c<DT, MODE, STACK, 3>(p, t, s);
     case 4: return launch_c<DT, MODE, STACK, 4>(p, t, s);
     case 5: return launch_c<DT, MODE, STACK, 5>(p, t, s);
+    case 6: return launch_c<DT, MODE, STACK, 6>(p, t, s);
+    case 7: return launch_c<DT, MODE, STACK, 7>(p, t, s);
+    case 8: return launch_c<DT, MODE, STACK, 8>(p, t, s);
     default: return launch_c<DT, MODE, STACK, 0>(p, t, s);
     }
 }
-static_assert(kNumShapes == 6, "launch_m lists every shape");
+static_assert(kNumShapes == 9, "launch_m lists every shape");
 
 template <int DT, int MODE>
 cudaError_t launch_t(const MarchParams& p, const TexParams& t, int cfg, cudaStream_t s)
