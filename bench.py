@@ -115,15 +115,16 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # DRAM bytes (read + write) of one launch of the two render launches of the
 # 1024^3 / 32-view workload, from one ncu capture of the full-size launches
-# (one pass: dram__bytes_read.sum + dram__bytes_write.sum; launch shapes
-# 5 and 2; profiles/tex_kernel_f32_cube1024_orbit32.md): MIP 150.31 GB read
-# + 0.42 GB written; MIP with the binary16 MIP bounds (shape 4) 92.05 + 0.27
-# GB; composite with the empty-space masks 31.97 + 1.30 GB.
+# (one pass: dram__bytes_read.sum + dram__bytes_write.sum;
+# profiles/tex_kernel_f32_cube1024_orbit32.md): MIP at launch shape 2 150.31
+# GB read + 0.42 GB written; MIP with the binary16 MIP bounds at shape 4
+# 92.04 + 0.27 GB; composite with the empty-space masks at shape 7 31.99 +
+# 1.29 GB.
 # Other workloads (the --cube-edge/--views cases) report them scaled by their
 # algorithmic bytes.
 MEASURED_TRAFFIC = {"mip": 150.305302e9 + 0.415848e9,
-                    "mip_bounds": 92.051239e9 + 0.269526e9,
-                    "composite_masks": 31.974443e9 + 1.297023e9}
+                    "mip_bounds": 92.041213e9 + 0.269872e9,
+                    "composite_masks": 31.987687e9 + 1.288413e9}
 MEASURED_ALGORITHMIC = {"mip": 136229959936.0, "mip_bounds": 136229959936.0,
                         "composite_masks": 136433374037.6}
 
