@@ -448,15 +448,18 @@ def tf_edit_leg(vol, cams, W, H, wl, lut):
     return res
 
 
-def out_of_core_leg(cube, cams, W, H, wl, lut, comp_ref, mip_ref, part_planes=129, reps=2):
+def out_of_core_leg(cube, cams, W, H, wl, lut, comp_ref, mip_ref, part_planes=129, cache_parts=4,
+                    reps=2):
     """The 1024^3 workload rendered part by part from page-locked host memory
-    (the cube never resident on the device: two part volumes of
-    ``part_planes`` planes), composite and MIP in one pass over the parts per
-    sweep; the images are compared with the resident render's."""
+    (the cube never resident on the device: a cache of ``cache_parts`` part
+    volumes of ``part_planes`` planes sharing one brick buffer), composite and
+    MIP in one pass over the parts per sweep; the images are compared with the
+    resident render's."""
     from paper_1001_2049_b300.stream import PartStream, sweeps
     host = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
     host.copy_(cube)
-    ps = PartStream(wl.dims, "f32", lambda z0, n: host[z0:z0 + n], part_planes)
+    ps = PartStream(wl.dims, "f32", lambda z0, n: host[z0:z0 + n], part_planes,
+                    cache_parts=cache_parts)
     ps.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
     comp = torch.empty_like(comp_ref)
     mip = torch.empty_like(mip_ref)
@@ -464,22 +467,22 @@ def out_of_core_leg(cube, cams, W, H, wl, lut, comp_ref, mip_ref, part_planes=12
     ps.render(cams, W, H, targets, wl.step)
     torch.cuda.synchronize()
     same = bool(torch.equal(comp, comp_ref) and torch.equal(mip, mip_ref))
-    times, loaded = [], []
+    times, loaded, parts = [], [], []
     for _ in range(reps):
-        b0 = ps.bytes_loaded
+        b0, p0 = ps.bytes_loaded, ps.parts_loaded
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ps.render(cams, W, H, targets, wl.step)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
         loaded.append(ps.bytes_loaded - b0)
-    # per part volume: its bricks, its texture (nz + 2 f32 slices) and the
-    # device staging of its planes
-    dev_bytes = sum(v.nbytes + v.dims[0] * v.dims[1] * (2 * v.dims[2] + 2) * 4 for v in ps.vols)
+        parts.append(ps.parts_loaded - p0)
     res = {"parts": len(ps.parts), "planes_per_part": ps.planes,
+           "cache_parts": len(ps.vols),
            "sweeps": len(sweeps(cams, W, H)), "ms_per_step": 1000.0 * min(times),
+           "part_loads_per_step": parts[-1],
            "host_bytes_read_per_step": loaded[-1],
-           "device_bytes_for_the_cube": dev_bytes,
+           "device_bytes_for_the_cube": ps.device_bytes(),
            "cube_bytes": cube.numel() * 4, "images_identical_to_resident": same}
     ps.close()
     del host

@@ -195,11 +195,15 @@ class Volume:
     ``cube`` is a float32 tensor of shape (nz, ny, nx) (x = RA fastest, z =
     frequency slowest) on the current CUDA device or in pinned host memory;
     ``dtype`` is the storage type ("f32", "f16" or "i8").  The brick buffer
-    is a torch allocation owned by this object.
+    is a torch allocation owned by this object, or ``buffer`` (a uint8
+    device tensor of at least volume_bytes(dims, dtype)).  Volumes may share
+    one buffer, as the part volumes of stream.PartStream do: an upload
+    repacks the buffer and refreshes only its own volume's texture, so such
+    volumes render from their textures and must not upload concurrently.
     """
 
     def __init__(self, cube: torch.Tensor | None = None, dtype: str = "f32", dims=None,
-                 stream=None, device=None):
+                 stream=None, device=None, buffer: torch.Tensor | None = None):
         lib = load()
         if cube is not None:
             if cube.dtype != torch.float32 or cube.dim() != 3:
@@ -212,10 +216,17 @@ class Volume:
         self.dims = tuple(int(d) for d in dims)
         self.dtype = dtype
         self.nbytes = volume_bytes(self.dims, dtype)
-        dev = device if device is not None else (
-            cube.device if cube is not None and cube.is_cuda else torch.device("cuda"))
+        if buffer is not None:
+            if buffer.dtype != torch.uint8 or not buffer.is_cuda or buffer.numel() < self.nbytes:
+                raise ValueError("buffer must be a uint8 CUDA tensor of at least %d bytes"
+                                 % self.nbytes)
+            dev = buffer.device
+        else:
+            dev = device if device is not None else (
+                cube.device if cube is not None and cube.is_cuda else torch.device("cuda"))
         self.device = torch.device(dev)
-        self.buffer = torch.empty(self.nbytes, dtype=torch.uint8, device=dev)
+        self.buffer = buffer if buffer is not None else torch.empty(self.nbytes, dtype=torch.uint8,
+                                                                    device=dev)
         handle = ctypes.c_void_p(0)
         src, on_dev = None, 1
         if cube is not None:

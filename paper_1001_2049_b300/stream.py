@@ -3,9 +3,11 @@
 The paper's pipeline splits the cube into sub-cubes, renders each and
 combines the images (§3.1 items 1, 4, 5), and aims at data larger than GPU
 memory (abstract).  Here the cube stays with its source (page-locked host
-memory, or a generator) and passes through two part volumes on the device:
-while one part renders on the compute stream, the next is packed into the
-other (and its texture filled) on a copy stream.  Each part continues the
+memory, or a generator) and passes through a cache of part volumes on the
+device: while one part renders on the compute stream, the next is packed
+(into one brick buffer the part volumes share) and copied into a free part
+volume's texture on a copy stream; the part volume used least recently makes
+room.  Each part continues the
 images from the state the earlier parts left (``vr_render_part``), so the
 images are those of a one-pass render of the whole cube, bit for bit.
 
@@ -68,28 +70,53 @@ class PartStream:
     planes.  ``source(z0, n)`` returns planes [z0, z0 + n) as a float32
     tensor (n, ny, nx) on the device or in page-locked host memory; it is
     called on the copy stream.  ``dtype`` is the parts' storage, ``pair``
-    selects pair-texel texture storage (FP16 / int8)."""
+    selects pair-texel texture storage (FP16 / int8).  ``cache_parts`` part
+    volumes (at least two, at most one per part) stay on the device; with
+    the sweeps' order (ascending, then descending, then ascending again) a
+    render loads 2 (parts - cache_parts) parts once the cache is warm.
+    Device memory: one brick buffer and one staging buffer of a part, and
+    ``cache_parts`` textures of a part."""
 
     def __init__(self, dims, dtype: str, source, part_planes: int, device=None,
-                 pair: bool = False):
+                 pair: bool = False, cache_parts: int = 2):
         nx, ny, nz = (int(d) for d in dims)
         self.dims = (nx, ny, nz)
         self.source = source
         self.parts = plan_parts(nz, part_planes)
         self.planes = min(part_planes, nz)
         self.device = torch.device(device) if device is not None else torch.device("cuda")
+        self.dtype, self.pair = dtype, bool(pair)
+        n_vols = min(max(2, int(cache_parts)), len(self.parts))
+        from .api import volume_bytes
+        self.bricks = torch.empty(volume_bytes((nx, ny, self.planes), dtype), dtype=torch.uint8,
+                                  device=self.device)
         self.vols = []
-        for _ in range(2 if len(self.parts) > 1 else 1):
-            v = Volume(dims=(nx, ny, self.planes), dtype=dtype, device=self.device)
+        for _ in range(n_vols):
+            v = Volume(dims=(nx, ny, self.planes), dtype=dtype, buffer=self.bricks)
             v.attach_pair_texture() if pair else v.attach_texture()
             self.vols.append(v)
         self.holds = [None] * len(self.vols)        # z_first of the part each volume holds
+        self.last_use = [-1] * len(self.vols)       # when each volume last rendered
+        self.uses = 0
         # device staging for parts that come from host memory: one DMA copy
-        # per part, then packing from device memory
-        self.staging = [None] * len(self.vols)
+        # per part, then packing from device memory (uploads are serialised
+        # on the copy stream, so one staging buffer serves every volume)
+        self.staging = None
         self.copy = torch.cuda.Stream(self.device)
         self.done = [torch.cuda.Event() for _ in self.vols]
         self.bytes_loaded = 0
+        self.parts_loaded = 0
+
+    def device_bytes(self) -> int:
+        """Device memory the stream holds for the cube: the shared brick
+        buffer, the staging buffer and the part volumes' textures."""
+        nx, ny, _ = self.dims
+        tex_slices = self.planes + 2                 # plain formats; pair: planes + 1
+        texel = {"f32": 4, "f16": 2, "i8": 1}[self.dtype]
+        if self.pair:
+            tex_slices, texel = self.planes + 1, 2 * texel
+        staging = nx * ny * self.planes * 4
+        return self.bricks.numel() + staging + len(self.vols) * nx * ny * tex_slices * texel
 
     def set_transfer(self, lut, v_lo, v_hi, clip, term_alpha=1.0):
         for v in self.vols:
@@ -103,13 +130,17 @@ class PartStream:
         with torch.cuda.stream(self.copy):
             planes = self.source(part.z_first, self.planes)
             if not planes.is_cuda:
-                if self.staging[i] is None or self.staging[i].shape != planes.shape:
-                    self.staging[i] = torch.empty(planes.shape, dtype=torch.float32,
-                                                  device=self.device)
-                self.staging[i].copy_(planes, non_blocking=True)
-                planes = self.staging[i]
-            v.upload(0, planes, stream=self.copy)    # packs and refreshes the texture
+                if self.staging is None or self.staging.shape != planes.shape:
+                    self.staging = torch.empty(planes.shape, dtype=torch.float32,
+                                               device=self.device)
+                self.staging.copy_(planes, non_blocking=True)
+                planes = self.staging
+            # packs into the shared bricks and refreshes this volume's texture
+            # (the call waits for the copy stream, so the next load can reuse
+            # the staging and brick buffers)
+            v.upload(0, planes, stream=self.copy)
         self.bytes_loaded += planes.numel() * planes.element_size()
+        self.parts_loaded += 1
         self.holds[i] = part.z_first
 
     def render(self, cams: np.ndarray, w: int, h: int, targets, step: float = 0.5,
@@ -125,15 +156,16 @@ class PartStream:
         for sw in sweeps(cams, w, h):
             order = self.parts if sw > 0 else self.parts[::-1]
             step_order += [(sw, p) for p in order]
-        slot = 0
         for n, (sw, part) in enumerate(step_order):
             held = [i for i, z in enumerate(self.holds) if z == part.z_first]
             if held:
                 i = held[0]
             else:
-                i = slot
-                slot = (slot + 1) % len(self.vols)
+                # the volume used least recently (never the one just queued)
+                i = min(range(len(self.vols)), key=lambda j: self.last_use[j])
                 self._load(i, part)
+            self.uses += 1
+            self.last_use[i] = self.uses
             loaded = torch.cuda.Event()
             loaded.record(self.copy)
             stream.wait_event(loaded)

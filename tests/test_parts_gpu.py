@@ -58,6 +58,44 @@ def test_parts_give_the_one_pass_images(store, dims, part_planes):
     ps.close()
 
 
+@pytest.mark.parametrize("store", ["f32", "i8", "f16-pair"])
+@pytest.mark.parametrize("cache", [3, 5, 12])
+def test_part_cache_keeps_parts_resident_between_renders(store, cache):
+    # the part volumes share one brick buffer; the least recently used one
+    # takes the next part; the images stay those of one pass, render after
+    # render, and a warm cache loads 2 (parts - cache) parts per render
+    dtype, _, pair = store.partition("-")
+    dims = (33, 29, 90)
+    cube, cams = _case(dims, 97 + cache)
+    w, h, step = 29, 19, 0.5
+    lut = synth.default_lut(64)
+    tf = (1.0, 8.0, 1.0, 0.95)
+    ref, n_ref = _one_pass(cube, dtype, bool(pair), cams, w, h, step, lut, tf)
+    host = cube.pin_memory()
+    ps = PartStream(dims, dtype, lambda z0, n: host[z0:z0 + n], 12, pair=bool(pair),
+                    cache_parts=cache)
+    n_parts = len(ps.parts)
+    assert len(ps.vols) == min(max(2, cache), n_parts)
+    assert len(sweeps(cams, w, h)) == 2
+    ps.set_transfer(lut, *tf)
+    outs = [(m, torch.empty(ref[m].shape, dtype=torch.float32, device="cuda")) for m in MODES]
+    for r in range(3):
+        before = ps.parts_loaded
+        n = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ps.render(cams, w, h, outs, step, count=n)
+        torch.cuda.synchronize()
+        for m, out in outs:
+            assert torch.equal(out, ref[m]), (store, cache, r, m)
+        assert int(n.item()) == n_ref
+        loads = ps.parts_loaded - before
+        c = len(ps.vols)
+        if r == 0:
+            assert loads == 2 * n_parts - c
+        else:
+            assert loads == 2 * max(0, n_parts - c)
+    ps.close()
+
+
 def test_parts_from_pinned_host_memory_and_one_way_views():
     dims = (48, 40, 96)
     cube = synth.make_cube(dims, 4, ("uniform", 3.0, 8.0), 91).pin_memory()
