@@ -468,13 +468,16 @@ int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
     cudaError_t e = cudaCreateSurfaceObject(&surf, &rd);
     if (e != cudaSuccess) return cuda_fail(e, "surface object");
     e = vr::fill_bounds(*v, surf, (int)s0, (int)s1, v->bound_vmax, s);
+    // the maximum comes back on the same stream (not the legacy stream, which
+    // would wait for other streams' work), then the stream is waited for: the
+    // surface object may only be destroyed after the fill ran
+    float vmax = 0.0f;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&vmax, v->bound_vmax, sizeof vmax, cudaMemcpyDeviceToHost, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     cudaDestroySurfaceObject(surf);
     if (e != cudaSuccess) return cuda_fail(e, "bound fill");
     if (e2 != cudaSuccess) return cuda_fail(e2, "bound fill");
-    float vmax = 0.0f;
-    e = cudaMemcpy(&vmax, v->bound_vmax, sizeof vmax, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(e, "bound maximum");
     v->bound_delta = std::max(std::ldexp(vmax, -19), std::ldexp(1.0f, -126));
     return VR_OK;
 }
@@ -518,6 +521,35 @@ int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
     if (e != cudaSuccess) return cuda_fail(e, "texture fill");
     if (e2 != cudaSuccess) return cuda_fail(e2, "texture fill");
     if (v->bound_array) return fill_bound_slices(v, s0, s1, s);   // same slices
+    return VR_OK;
+}
+
+// FP32 texture storage without stacked slices holds the planes exactly as
+// given: the uploaded planes [z0, z0 + n) are copied into their slices
+// (slice z + 1), and the edge planes also into slices 0 and nz + 1 when the
+// upload includes them; stream-ordered, like the fill it replaces.
+int copy_texture_planes(vr::Volume* v, int64_t z0, int64_t n, const float* src, cudaStream_t s)
+{
+    const int nx = v->g.nx, ny = v->g.ny, nz = v->g.nz;
+    auto copy = [&](int64_t plane, int64_t slice, int64_t depth) {
+        cudaMemcpy3DParms p;
+        std::memset(&p, 0, sizeof p);
+        p.srcPtr = make_cudaPitchedPtr(const_cast<float*>(src), (size_t)nx * sizeof(float), nx, ny);
+        p.srcPos = make_cudaPos(0, 0, (size_t)(plane - z0));
+        p.dstArray = v->array;
+        p.dstPos = make_cudaPos(0, 0, (size_t)slice);
+        p.extent = make_cudaExtent(nx, ny, (size_t)depth);
+        p.kind = cudaMemcpyDefault;
+        return cudaMemcpy3DAsync(&p, s);
+    };
+    cudaError_t e = copy(z0, z0 + 1, n);
+    if (e == cudaSuccess && z0 == 0) e = copy(0, 0, 1);
+    if (e == cudaSuccess && z0 + n == nz) e = copy(nz - 1, nz + 1, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "texture copy");
+    if (v->bound_array) {
+        const int64_t s0 = z0 == 0 ? 0 : z0 + 1, s1 = z0 + n == nz ? nz + 2 : z0 + n + 1;
+        return fill_bound_slices(v, s0, s1, s);
+    }
     return VR_OK;
 }
 
@@ -758,6 +790,8 @@ int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* sr
     cudaError_t e = vr::launch_pack(*v, z0, nplanes, dsrc, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "pack launch");
     v->mask_clip = NAN;               // masks are rebuilt by the next composite render
+    if (v->has_tex && v->tex_format == VR_F32 && v->stack_shift == 0)
+        return copy_texture_planes(v, z0, nplanes, dsrc, static_cast<cudaStream_t>(stream));
     if (v->has_tex)
         return refresh_texture(v, z0, z0 + nplanes, static_cast<cudaStream_t>(stream));
     return VR_OK;

@@ -135,9 +135,9 @@ class PartStream:
                                                device=self.device)
                 self.staging.copy_(planes, non_blocking=True)
                 planes = self.staging
-            # packs into the shared bricks and refreshes this volume's texture
-            # (the call waits for the copy stream, so the next load can reuse
-            # the staging and brick buffers)
+            # packs into the shared bricks and refreshes this volume's texture;
+            # the next load reuses the staging and brick buffers after it, in
+            # the copy stream's order
             v.upload(0, planes, stream=self.copy)
         self.bytes_loaded += planes.numel() * planes.element_size()
         self.parts_loaded += 1
