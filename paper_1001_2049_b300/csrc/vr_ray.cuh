@@ -589,6 +589,46 @@ __device__ __forceinline__ int march_part(const PP& P, const TT& T,
     return k - k0;
 }
 
+// march_tex_bound over samples [k0, k1) of a part (MIP over FP32 texture
+// storage with MIP bounds), continuing `acc`; slices shifted to the part's
+// own.  The result is march_part's bit for bit (see march_tex_bound).
+template <bool STACK, typename PP, typename TT>
+__device__ __forceinline__ int march_part_bound(const PP& P, const TT& T, const Ray& r,
+                                                Acc<VR_MIP>& acc, int k0, int k1)
+{
+    if (k0 >= k1) return 0;
+    const cudaTextureObject_t tb = T.bound, tf = T.tex;
+    auto take = [&](const Geo& g, const float4& u0, const float4& u1) {
+        if (!(interp(u0, u1, g) + T.bound_delta < acc.m)) {
+            float4 e0, e1;
+            cell<VR_F32, STACK>(T, tf, g.iz, g.gx, g.gy, e0, e1);
+            acc.m = fmaxf(acc.m, interp(e0, e1, g));
+        }
+    };
+    int k = k0;
+    float kf = (float)k0;
+    Geo ga = geo(P, r, kf), gb;
+    ga.iz -= P.slice_base;
+    float4 a0, a1, b0, b1;
+    cell<VR_F16, STACK>(T, tb, ga.iz, ga.gx, ga.gy, a0, a1);
+    kf += 1.0f;
+    for (;;) {
+        gb = geo(P, r, kf);
+        gb.iz -= P.slice_base;
+        next_cell<VR_F16, STACK>(T, tb, ga, a0, a1, gb, b0, b1);
+        take(ga, a0, a1);
+        if (++k >= k1) break;
+        kf += 1.0f;
+        ga = geo(P, r, kf);
+        ga.iz -= P.slice_base;
+        next_cell<VR_F16, STACK>(T, tb, gb, b0, b1, ga, a0, a1);
+        take(gb, b0, b1);
+        if (++k >= k1) break;
+        kf += 1.0f;
+    }
+    return k - k0;
+}
+
 template <int DT>
 __device__ __forceinline__ float load_voxel(const void* b, size_t i)
 {

@@ -176,7 +176,15 @@ __global__ void __launch_bounds__(256) part_kernel(const __grid_constant__ March
             if (!done) {
                 int k0, k1;
                 ray::part_range(P, r, k0, k1);
-                count = (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r, acc, k0, k1);
+                if constexpr (MODE == VR_MIP && DT == VR_F32) {
+                    // with MIP bounds (block-uniform), as the one-pass render
+                    count = T.bound ? (unsigned)ray::march_part_bound<STACK>(P, T, r, acc, k0, k1)
+                                    : (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r,
+                                                                                 acc, k0, k1);
+                } else {
+                    count = (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r, acc, k0,
+                                                                      k1);
+                }
                 if (MODE == VR_COMPOSITE)
                     reinterpret_cast<float4*>(P.out)[pix] =
                         make_float4(acc.r, acc.g, acc.b, acc.A);

@@ -70,7 +70,9 @@ class PartStream:
     planes.  ``source(z0, n)`` returns planes [z0, z0 + n) as a float32
     tensor (n, ny, nx) on the device or in page-locked host memory; it is
     called on the copy stream.  ``dtype`` is the parts' storage, ``pair``
-    selects pair-texel texture storage (FP16 / int8).  ``cache_parts`` part
+    selects pair-texel texture storage (FP16 / int8), ``bounds`` gives FP32
+    part volumes MIP bounds (vr_volume_attach_mip_bounds: faster MIP, the
+    same images).  ``cache_parts`` part
     volumes (at least two, at most one per part) stay on the device; with
     the sweeps' order (ascending, then descending, then ascending again) a
     render loads 2 (parts - cache_parts) parts once the cache is warm.
@@ -78,7 +80,7 @@ class PartStream:
     ``cache_parts`` textures of a part."""
 
     def __init__(self, dims, dtype: str, source, part_planes: int, device=None,
-                 pair: bool = False, cache_parts: int = 2):
+                 pair: bool = False, cache_parts: int = 2, bounds: bool = False):
         nx, ny, nz = (int(d) for d in dims)
         self.dims = (nx, ny, nz)
         self.source = source
@@ -88,12 +90,17 @@ class PartStream:
         self.dtype, self.pair = dtype, bool(pair)
         n_vols = min(max(2, int(cache_parts)), len(self.parts))
         from .api import volume_bytes
-        self.bricks = torch.empty(volume_bytes((nx, ny, self.planes), dtype), dtype=torch.uint8,
+        # zeroed: the MIP bounds' rounding margin follows the largest |voxel|
+        # their fills have seen, from the first (empty) fill on
+        self.bricks = torch.zeros(volume_bytes((nx, ny, self.planes), dtype), dtype=torch.uint8,
                                   device=self.device)
+        self.bounds = bool(bounds) and dtype == "f32" and not pair
         self.vols = []
         for _ in range(n_vols):
             v = Volume(dims=(nx, ny, self.planes), dtype=dtype, buffer=self.bricks)
             v.attach_pair_texture() if pair else v.attach_texture()
+            if self.bounds:
+                v.attach_mip_bounds()
             self.vols.append(v)
         self.holds = [None] * len(self.vols)        # z_first of the part each volume holds
         self.last_use = [-1] * len(self.vols)       # when each volume last rendered
@@ -116,7 +123,9 @@ class PartStream:
         if self.pair:
             tex_slices, texel = self.planes + 1, 2 * texel
         staging = nx * ny * self.planes * 4
-        return self.bricks.numel() + staging + len(self.vols) * nx * ny * tex_slices * texel
+        bounds = nx * ny * (self.planes + 2) * 2 if self.bounds else 0
+        return (self.bricks.numel() + staging
+                + len(self.vols) * (nx * ny * tex_slices * texel + bounds))
 
     def set_transfer(self, lut, v_lo, v_hi, clip, term_alpha=1.0):
         for v in self.vols:

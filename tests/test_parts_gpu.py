@@ -96,6 +96,33 @@ def test_part_cache_keeps_parts_resident_between_renders(store, cache):
     ps.close()
 
 
+@pytest.mark.parametrize("dims,part_planes,cache", [((33, 29, 90), 12, 3), ((37, 45, 70), 2, 2),
+                                                    ((6, 5, 4500), 700, 4)])
+def test_parts_with_mip_bounds_give_the_one_pass_images(dims, part_planes, cache):
+    # FP32 part volumes with MIP bounds (filled from the shared bricks at each
+    # part's upload): the one-pass images and counts, render after render
+    cube, cams = _case(dims, 120 + part_planes)
+    w, h, step = 29, 19, 0.37
+    lut = synth.default_lut(64)
+    tf = (1.0, 8.0, 1.0, 0.95)
+    ref, n_ref = _one_pass(cube, "f32", False, cams, w, h, step, lut, tf)
+    host = cube.pin_memory()
+    dev = cube.cuda()
+    for source in (lambda z0, n: host[z0:z0 + n], lambda z0, n: dev[z0:z0 + n]):
+        ps = PartStream(dims, "f32", source, part_planes, cache_parts=cache, bounds=True)
+        assert ps.bounds
+        ps.set_transfer(lut, *tf)
+        outs = [(m, torch.empty(ref[m].shape, dtype=torch.float32, device="cuda")) for m in MODES]
+        for r in range(2):
+            n = torch.zeros(1, dtype=torch.int64, device="cuda")
+            ps.render(cams, w, h, outs, step, count=n)
+            torch.cuda.synchronize()
+            for m, out in outs:
+                assert torch.equal(out, ref[m]), (dims, part_planes, r, m)
+            assert int(n.item()) == n_ref
+        ps.close()
+
+
 def test_parts_from_pinned_host_memory_and_one_way_views():
     dims = (48, 40, 96)
     cube = synth.make_cube(dims, 4, ("uniform", 3.0, 8.0), 91).pin_memory()
