@@ -189,6 +189,15 @@ int vr_volume_mask_bytes(vr_volume vol, size_t* bytes_out);
  * here.  The paper describes no such structure.                            */
 int vr_volume_attach_masks(vr_volume vol, void* buf, size_t bytes);
 
+/* Build the attached masks now, for the current clip, from the bricks, on
+ * `stream` (attached masks are otherwise built by the next composite render
+ * that needs them).  For volumes whose brick buffer is about to hold other
+ * data, such as part volumes sharing one buffer (a later build would read
+ * whatever the buffer then holds).  vr_render_part uses a part's masks only
+ * while they hold for its clip and never rebuilds them.  VR_ERR_UNSUPPORTED
+ * without attached masks or after vr_volume_drop_bricks.                    */
+int vr_volume_build_masks(vr_volume vol, void* stream);
+
 /* Give the volume texture storage: a copy of the cube in one layered 2-D
  * texture, one 2-D slice per frequency plane, filled from the bricks on
  * `stream`.  A layered texture has at most 2048 layers: deeper cubes stack

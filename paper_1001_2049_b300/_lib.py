@@ -37,6 +37,7 @@ SIGNATURES = {
     "vr_volume_attach_pair_texture": (c_int, [c_void_p, c_void_p]),
     "vr_volume_detach_texture": (c_int, [c_void_p]),
     "vr_volume_attach_mip_bounds": (c_int, [c_void_p, c_void_p]),
+    "vr_volume_build_masks": (c_int, [c_void_p, c_void_p]),
     "vr_volume_detach_mip_bounds": (c_int, [c_void_p]),
     "vr_volume_drop_bricks": (c_int, [c_void_p]),
     "vr_render_init": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p]),

@@ -301,6 +301,11 @@ class Volume:
         check(load().vr_volume_attach_masks(self._h, None, 0))
         self._masks = None
 
+    def build_masks(self, stream=None):
+        """Build the attached masks now, for the current clip, on ``stream``
+        (for volumes whose brick buffer will soon hold other data)."""
+        check(load().vr_volume_build_masks(self._h, _stream_ptr(stream)))
+
     def set_transfer(self, lut, v_lo: float, v_hi: float, clip: float, term_alpha: float = 1.0):
         """RGBA table (n, 4) with alpha per unit voxel length over [v_lo, v_hi];
         samples below ``clip`` are transparent; rays stop at ``term_alpha``."""

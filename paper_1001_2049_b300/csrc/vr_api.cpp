@@ -931,7 +931,11 @@ int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
     p.part_hi = cell_hi == full_dims[2] - 1 ? INT_MAX : (int)cell_hi;
     p.slice_base = (int)z_first;
     p.sweep = sweep;
-    p.mask = nullptr;
+    // masks only where they hold for the clip: nothing rebuilds them here
+    // (a part's bricks may already hold another part; see
+    // vr_volume_build_masks)
+    const bool masks_valid = v->mask && !std::isnan(v->mask_clip) && !(v->clip < v->mask_clip);
+    if (mode != VR_COMPOSITE || !masks_valid) p.mask = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t per_view = (size_t)w * h * (mode == VR_COMPOSITE ? 4 : 1);
     for (int v0 = 0; v0 < n_views; v0 += vr::kMaxViewsPerLaunch) {
@@ -942,6 +946,19 @@ int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
         cudaError_t e = vr::launch_part(p, tp, v->tex_format, mode, s);
         if (e != cudaSuccess) return cuda_fail(e, "part launch");
     }
+    return VR_OK;
+}
+
+int vr_volume_build_masks(vr_volume vol, void* stream)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (!v->mask) return fail(VR_ERR_UNSUPPORTED, "no masks are attached");
+    if (v->texture_only)
+        return fail(VR_ERR_UNSUPPORTED, "masks are built from the bricks, which were dropped");
+    cudaError_t e = vr::launch_masks(*v, v->clip, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "mask launch");
+    v->mask_clip = v->clip;
     return VR_OK;
 }
 

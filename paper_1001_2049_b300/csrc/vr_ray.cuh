@@ -542,6 +542,17 @@ __device__ __forceinline__ int first_k(const PP& P, const Ray& r, F past)
     return a;
 }
 
+// Whether any sample of the ray can lie in the part's cells: sample cells
+// are monotone in k, so those of the first and last samples bound them all.
+template <typename PP>
+__device__ __forceinline__ bool may_cross_part(const PP& P, const Ray& r)
+{
+    const float lo = (float)P.part_lo, hi = (float)P.part_hi;
+    const float c0 = sample_cell(P, r, 0), c1 = sample_cell(P, r, r.K - 1);
+    const float cmin = fminf(c0, c1), cmax = fmaxf(c0, c1);
+    return cmax >= lo && cmin < hi;
+}
+
 // Samples [k0, k1) of the part's cells, for a ray going up (dz >= 0) or down.
 template <typename PP>
 __device__ __forceinline__ void part_range(const PP& P, const Ray& r, int& k0, int& k1)
@@ -584,6 +595,80 @@ __device__ __forceinline__ int march_part(const PP& P, const TT& T,
         next_cell<DT, STACK>(T, t0, gb, b0, b1, ga, a0, a1);
         ++k;
         if (acc.add(P, lut, interp(b0, b1, gb)) || k >= k1) break;
+        kf += 1.0f;
+    }
+    return k - k0;
+}
+
+// march_tex_lock over samples [k0, k1) of a part (COMPOSITE with the part
+// volume's empty-space masks), continuing `acc`: texture slices and mask
+// macrocells are the part's own (height coordinates shifted by the part's
+// first plane).  The result and the sample count are march_part's.
+template <int DT, bool STACK, typename PP, typename TT>
+__device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
+                                               const float4* __restrict__ lut, const Ray& r,
+                                               Acc<VR_COMPOSITE>& acc, int k0, int k1)
+{
+    using Rec = unsigned long long;
+    if (k0 >= k1) return 0;
+    const cudaTextureObject_t t0 = T.tex;
+    // the macrocell of sample kf and its cell's bit there, in the part's
+    // gather coordinates (clamped to the mask array: look-ahead samples past
+    // the range lie outside the part)
+    auto mcell = [&](float kf, int& bit) {
+        const float t = fmaf(kf, P.step, r.te);
+        const int x = __float2int_rd(fmaf(t, r.dx, r.ox)) + 1;
+        const int y = __float2int_rd(fmaf(t, r.dy, r.oy)) + 1;
+        const int z = __float2int_rd(fmaf(t, r.dz, r.oz)) + 1 - P.slice_base;
+        bit = (x & 3) | ((y & 3) << 2) | ((z & 3) << 4);
+        const int i = ((z >> kMacroShift) * P.mny + (y >> kMacroShift)) * P.mnx + (x >> kMacroShift);
+        return (int)min((unsigned)i, (unsigned)P.mlast);
+    };
+    auto part_geo = [&](float kf) {
+        Geo g = geo(P, r, kf);
+        g.iz -= P.slice_base;
+        return g;
+    };
+    int k = k0;
+    float kf = (float)k0;
+    int b0, b1, b2;
+    const int m0 = mcell(kf, b0);
+    int m1 = mcell(kf + 1.0f, b1), m2;
+    const Rec r0 = __ldg(P.mask + m0);
+    Rec r1 = (m1 == m0) ? r0 : __ldg(P.mask + m1), r2;
+    bool n0 = acc.need(r0, b0), n1;
+    Geo g0, g1;
+    float4 a0, a1, c0, c1;
+    if (n0) {
+        g0 = part_geo(kf);
+        cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
+    }
+    for (;;) {
+        m2 = mcell(kf + 2.0f, b2);
+        r2 = (m2 == m1) ? r1 : __ldg(P.mask + m2);
+        n1 = acc.need(r1, b1);
+        if (n1) {
+            g1 = part_geo(kf + 1.0f);
+            if (n0)
+                next_cell_up<DT, STACK>(T, t0, g0, a0, a1, g1, c0, c1);
+            else
+                cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
+        }
+        ++k;
+        if ((n0 && acc.add(P, lut, interp(a0, a1, g0))) || k >= k1) break;
+        kf += 1.0f;
+        m1 = mcell(kf + 2.0f, b1);
+        r1 = (m1 == m2) ? r2 : __ldg(P.mask + m1);
+        n0 = acc.need(r2, b2);
+        if (n0) {
+            g0 = part_geo(kf + 1.0f);
+            if (n1)
+                next_cell_up<DT, STACK>(T, t0, g1, c0, c1, g0, a0, a1);
+            else
+                cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
+        }
+        ++k;
+        if ((n1 && acc.add(P, lut, interp(c0, c1, g1))) || k >= k1) break;
         kf += 1.0f;
     }
     return k - k0;

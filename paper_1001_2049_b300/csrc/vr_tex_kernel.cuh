@@ -142,26 +142,32 @@ cudaError_t launch_dt(const MarchParams& p, const TexParams& t, int mode, int cf
 // whose direction matches the sweep continues from the state in `out` with
 // the samples of the part's cells (the same samples, in the same order, as
 // the one-pass render takes there), then writes the state back.
-template <int DT, int MODE, bool STACK>
-__global__ void __launch_bounds__(256) part_kernel(const __grid_constant__ MarchParams P,
-                                                   const __grid_constant__ TexParams T)
+// MASKED (COMPOSITE with the part's empty-space masks): 16 x 8 blocks at 64
+// registers, the shape at which the lockstep march runs fastest; otherwise
+// 16 x 16 blocks at up to 51 registers (five blocks per SM).  Warps hold
+// 8 x 4 packets either way.
+template <int DT, int MODE, bool STACK, bool MASKED>
+__global__ void __launch_bounds__(MASKED ? 128 : 256, MASKED ? 8 : 5)
+    part_kernel(const __grid_constant__ MarchParams P, const __grid_constant__ TexParams T)
 {
+    constexpr int kRowsY = MASKED ? 8 : 16;
     __shared__ float4 s_lut[VR_MAX_LUT];
-    if (MODE == VR_COMPOSITE) {
-        for (int i = threadIdx.x; i < P.n_lut; i += blockDim.x) s_lut[i] = P.lut[i];
-        __syncthreads();
-    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    const int py = blockIdx.y * 16 + (warp >> 1) * 4 + (lane >> 3);
+    const int py = blockIdx.y * kRowsY + (warp >> 1) * 4 + (lane >> 3);
     const int view = blockIdx.z;
-    unsigned count = 0;
+    // the ray, its state and its samples in this part (most rays of a view
+    // cross a few parts only: a test of its first and last samples' cells
+    // spares the others the bisection)
+    ray::Ray r;
+    ray::Acc<MODE> acc;
+    size_t pix = 0;
+    int k0 = 0, k1 = 0;
     if (px < P.w && py < P.h) {
-        const ray::Ray r = ray::setup_ray(P, P.cams[view], px, py, T.k_max);
+        r = ray::setup_ray(P, P.cams[view], px, py, T.k_max);
         const bool mine = P.sweep > 0 ? r.dz >= 0.0f : r.dz < 0.0f;
-        if (r.K > 0 && mine) {
-            const size_t pix = ((size_t)view * P.h + py) * P.w + px;
-            ray::Acc<MODE> acc;
+        if (r.K > 0 && mine && ray::may_cross_part(P, r)) {
+            pix = ((size_t)view * P.h + py) * P.w + px;
             bool done = false;
             if (MODE == VR_COMPOSITE) {
                 const float4 c = reinterpret_cast<const float4*>(P.out)[pix];
@@ -173,25 +179,37 @@ __global__ void __launch_bounds__(256) part_kernel(const __grid_constant__ March
             } else {
                 acc.m = P.out[pix];
             }
-            if (!done) {
-                int k0, k1;
-                ray::part_range(P, r, k0, k1);
-                if constexpr (MODE == VR_MIP && DT == VR_F32) {
-                    // with MIP bounds (block-uniform), as the one-pass render
-                    count = T.bound ? (unsigned)ray::march_part_bound<STACK>(P, T, r, acc, k0, k1)
-                                    : (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r,
-                                                                                 acc, k0, k1);
-                } else {
-                    count = (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r, acc, k0,
-                                                                      k1);
-                }
-                if (MODE == VR_COMPOSITE)
-                    reinterpret_cast<float4*>(P.out)[pix] =
-                        make_float4(acc.r, acc.g, acc.b, acc.A);
-                else
-                    P.out[pix] = acc.m;
-            }
+            if (!done) ray::part_range(P, r, k0, k1);
         }
+    }
+    // a ray without samples here keeps its state (nothing to write); blocks
+    // whose rays all have none leave before staging the table
+    const bool work = k0 < k1;
+    if (!__syncthreads_or(work)) return;
+    if (MODE == VR_COMPOSITE) {
+        for (int i = threadIdx.x; i < P.n_lut; i += blockDim.x) s_lut[i] = P.lut[i];
+        __syncthreads();
+    }
+    unsigned count = 0;
+    if (work) {
+        if constexpr (MODE == VR_MIP && DT == VR_F32) {
+            // with MIP bounds (block-uniform), as the one-pass render
+            count = T.bound ? (unsigned)ray::march_part_bound<STACK>(P, T, r, acc, k0, k1)
+                            : (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r,
+                                                                         acc, k0, k1);
+        } else if constexpr (MODE == VR_COMPOSITE && MASKED) {
+            // with empty-space masks, as the one-pass render
+            count = (unsigned)ray::march_part_lock<DT, STACK>(P, T, s_lut, r, acc, k0,
+                                                              k1);
+        } else {
+            count = (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r, acc, k0,
+                                                              k1);
+        }
+        if (MODE == VR_COMPOSITE)
+            reinterpret_cast<float4*>(P.out)[pix] =
+                make_float4(acc.r, acc.g, acc.b, acc.A);
+        else
+            P.out[pix] = acc.m;
     }
     if (P.samples) {
         const unsigned tot = __reduce_add_sync(0xffffffffu, count);
@@ -207,16 +225,23 @@ cudaError_t launch_part_dt(const MarchParams& p, const TexParams& t, int mode, c
     const bool st = t.stack_shift > 0;
     switch (mode) {
     case VR_MIP:
-        st ? part_kernel<DT, VR_MIP, true><<<grid, 256, 0, s>>>(p, t)
-           : part_kernel<DT, VR_MIP, false><<<grid, 256, 0, s>>>(p, t);
+        st ? part_kernel<DT, VR_MIP, true, false><<<grid, 256, 0, s>>>(p, t)
+           : part_kernel<DT, VR_MIP, false, false><<<grid, 256, 0, s>>>(p, t);
         break;
     case VR_COMPOSITE:
-        st ? part_kernel<DT, VR_COMPOSITE, true><<<grid, 256, 0, s>>>(p, t)
-           : part_kernel<DT, VR_COMPOSITE, false><<<grid, 256, 0, s>>>(p, t);
+        if (p.mask) {
+            const dim3 g8((unsigned)((p.w + 15) / 16), (unsigned)((p.h + 7) / 8),
+                          (unsigned)p.n_views);
+            st ? part_kernel<DT, VR_COMPOSITE, true, true><<<g8, 128, 0, s>>>(p, t)
+               : part_kernel<DT, VR_COMPOSITE, false, true><<<g8, 128, 0, s>>>(p, t);
+        } else {
+            st ? part_kernel<DT, VR_COMPOSITE, true, false><<<grid, 256, 0, s>>>(p, t)
+               : part_kernel<DT, VR_COMPOSITE, false, false><<<grid, 256, 0, s>>>(p, t);
+        }
         break;
     default:
-        st ? part_kernel<DT, VR_SUM, true><<<grid, 256, 0, s>>>(p, t)
-           : part_kernel<DT, VR_SUM, false><<<grid, 256, 0, s>>>(p, t);
+        st ? part_kernel<DT, VR_SUM, true, false><<<grid, 256, 0, s>>>(p, t)
+           : part_kernel<DT, VR_SUM, false, false><<<grid, 256, 0, s>>>(p, t);
         break;
     }
     return cudaGetLastError();

@@ -72,7 +72,9 @@ class PartStream:
     called on the copy stream.  ``dtype`` is the parts' storage, ``pair``
     selects pair-texel texture storage (FP16 / int8), ``bounds`` gives FP32
     part volumes MIP bounds (vr_volume_attach_mip_bounds: faster MIP, the
-    same images).  ``cache_parts`` part
+    same images) and ``masks`` empty-space masks, built for the clip at each
+    part's upload (faster compositing, the same images; a lower clip later
+    reloads the parts).  ``cache_parts`` part
     volumes (at least two, at most one per part) stay on the device; with
     the sweeps' order (ascending, then descending, then ascending again) a
     render loads 2 (parts - cache_parts) parts once the cache is warm.
@@ -80,7 +82,8 @@ class PartStream:
     ``cache_parts`` textures of a part."""
 
     def __init__(self, dims, dtype: str, source, part_planes: int, device=None,
-                 pair: bool = False, cache_parts: int = 2, bounds: bool = False):
+                 pair: bool = False, cache_parts: int = 2, bounds: bool = False,
+                 masks: bool = False):
         nx, ny, nz = (int(d) for d in dims)
         self.dims = (nx, ny, nz)
         self.source = source
@@ -101,7 +104,11 @@ class PartStream:
             v.attach_pair_texture() if pair else v.attach_texture()
             if self.bounds:
                 v.attach_mip_bounds()
+            if masks:
+                v.attach_masks()
             self.vols.append(v)
+        self.masks = bool(masks)
+        self.clip = None
         self.holds = [None] * len(self.vols)        # z_first of the part each volume holds
         self.last_use = [-1] * len(self.vols)       # when each volume last rendered
         self.uses = 0
@@ -124,12 +131,18 @@ class PartStream:
             tex_slices, texel = self.planes + 1, 2 * texel
         staging = nx * ny * self.planes * 4
         bounds = nx * ny * (self.planes + 2) * 2 if self.bounds else 0
+        masks = self.vols[0].mask_bytes() if self.masks else 0
         return (self.bricks.numel() + staging
-                + len(self.vols) * (nx * ny * tex_slices * texel + bounds))
+                + len(self.vols) * (nx * ny * tex_slices * texel + bounds + masks))
 
     def set_transfer(self, lut, v_lo, v_hi, clip, term_alpha=1.0):
         for v in self.vols:
             v.set_transfer(lut, v_lo, v_hi, clip, term_alpha)
+        # masks hold for clips at or above the one they were built for: a
+        # lower clip reloads the parts (their bricks are gone)
+        if self.masks and self.clip is not None and clip < self.clip:
+            self.holds = [None] * len(self.vols)
+        self.clip = clip
 
     def _load(self, i: int, part: Part):
         v = self.vols[i]
@@ -148,6 +161,8 @@ class PartStream:
             # the next load reuses the staging and brick buffers after it, in
             # the copy stream's order
             v.upload(0, planes, stream=self.copy)
+            if self.masks:                           # while the bricks hold this part
+                v.build_masks(stream=self.copy)
         self.bytes_loaded += planes.numel() * planes.element_size()
         self.parts_loaded += 1
         self.holds[i] = part.z_first

@@ -123,6 +123,35 @@ def test_parts_with_mip_bounds_give_the_one_pass_images(dims, part_planes, cache
         ps.close()
 
 
+@pytest.mark.parametrize("store", ["f32", "i8", "f16-pair"])
+@pytest.mark.parametrize("dims,part_planes,cache", [((33, 29, 90), 12, 3), ((37, 45, 70), 2, 2),
+                                                    ((6, 5, 4500), 700, 4)])
+def test_parts_with_masks_give_the_one_pass_images(store, dims, part_planes, cache):
+    # part volumes with empty-space masks built at each part's upload (and,
+    # for FP32, MIP bounds): the one-pass images and counts at every clip,
+    # a lower clip reloading the parts
+    dtype, _, pair = store.partition("-")
+    cube, cams = _case(dims, 140 + part_planes)
+    w, h, step = 29, 19, 0.37
+    lut = synth.default_lut(64)
+    host = cube.pin_memory()
+    ps = PartStream(dims, dtype, lambda z0, n: host[z0:z0 + n], part_planes, pair=bool(pair),
+                    cache_parts=cache, masks=True, bounds=dtype == "f32")
+    outs = [(m, torch.empty((len(cams), h, w, 4) if m == "composite" else (len(cams), h, w),
+                            dtype=torch.float32, device="cuda")) for m in MODES]
+    for clip in (1.0, 3.0, 0.5):
+        tf = (min(clip, 1.0), 8.0, clip, 0.95)
+        ref, n_ref = _one_pass(cube, dtype, bool(pair), cams, w, h, step, lut, tf)
+        ps.set_transfer(lut, *tf)
+        n = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ps.render(cams, w, h, outs, step, count=n)
+        torch.cuda.synchronize()
+        for m, out in outs:
+            assert torch.equal(out, ref[m]), (store, dims, part_planes, clip, m)
+        assert int(n.item()) == n_ref
+    ps.close()
+
+
 def test_parts_from_pinned_host_memory_and_one_way_views():
     dims = (48, 40, 96)
     cube = synth.make_cube(dims, 4, ("uniform", 3.0, 8.0), 91).pin_memory()
