@@ -16,7 +16,10 @@
 // 10u max|corner|.  The bit is clear when max + 2^-19 max|corner| (32u,
 // rounded once by an fma) is below the clip.  Decoding is the kernels' own:
 // float32 as stored, binary16 widened exactly, int8 as fma(code, scale[z],
-// offset[z]).
+// offset[z]).  Plain int8 textures interpolate the codes of each plane and
+// decode that (interp_t): the codes' two lerp levels err by at most 512u
+// code units (|code| <= 127), i.e. 512u |scale| once decoded, which a further
+// 2^-14 max |scale| of the cell's two planes covers.
 //
 // Cells are indexed by the kernels' gather coordinates: on every axis from
 // -1 to n - 1 (stored at +1; the outermost cells hold positions a rounding
@@ -167,14 +170,15 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(
         // walk the chunk's cells along z; a plane's corner bounds serve the
         // cell below and the cell above it
         int have = -1;                   // tile plane whose bounds are in hi1 / mag1
-        float hi0 = 0.0f, mag0 = 0.0f, hi1 = 0.0f, mag1 = 0.0f;
-        auto plane_bounds = [&](int pz, float& hi, float& mag) {
+        float hi0 = 0.0f, mag0 = 0.0f, sc0 = 0.0f, hi1 = 0.0f, mag1 = 0.0f, sc1 = 0.0f;
+        auto plane_bounds = [&](int pz, float& hi, float& mag, float& sc) {
             const float a = s_v[b][pz][cy][cx], bb = s_v[b][pz][cy][cx + 1];
             const float c = s_v[b][pz][cy + 1][cx], d = s_v[b][pz][cy + 1][cx + 1];
             // (fmaxf ignores NaN; the -inf and 0 keep a plane of NaN corners
             // from giving a NaN bound)
             hi = fmaxf(fmaxf(fmaxf(a, bb), fmaxf(c, d)), -INFINITY);
             mag = fmaxf(fmaxf(fmaxf(fabsf(a), fabsf(bb)), fmaxf(fabsf(c), fabsf(d))), 0.0f);
+            sc = DT == VR_I8 ? 0x1p-14f * fabsf(__ldg(scale + min(z0 + pz, g.nz - 1))) : 0.0f;
         };
         for (int c = 0; c < 4 * kRows; ++c) {
             const int gz = bz0 * 4 + c;
@@ -183,15 +187,17 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(
             if (cz == have) {            // the next plane up: its lower plane is held
                 hi0 = hi1;
                 mag0 = mag1;
-                plane_bounds(cz + 1, hi1, mag1);
+                sc0 = sc1;
+                plane_bounds(cz + 1, hi1, mag1, sc1);
                 have = cz + 1;
             } else if (cz + 1 != have) { // first cell of the chunk
-                plane_bounds(cz, hi0, mag0);
-                plane_bounds(cz + 1, hi1, mag1);
+                plane_bounds(cz, hi0, mag0, sc0);
+                plane_bounds(cz + 1, hi1, mag1, sc1);
                 have = cz + 1;
             }                            // else: the same cell again (clamped at an edge)
             const bool need = in_xy && gz <= g.nz &&
-                              !(fmaf(fmaxf(mag0, mag1), 0x1p-19f, fmaxf(hi0, hi1)) < clip);
+                              !(fmaf(fmaxf(mag0, mag1), 0x1p-19f,
+                                     fmaxf(hi0, hi1) + fmaxf(sc0, sc1)) < clip);
             const unsigned bal = __ballot_sync(0xffffffffu, need);
             if (lane == 0) s_ballot[c][w] = bal;
         }

@@ -118,19 +118,6 @@ __device__ __forceinline__ Ray setup_ray(const PP& P, const vr_camera& c, int px
     return r;
 }
 
-// Decode int8 codes of texture slice `slice` (plane slice - 1, clamped: the
-// first and last slices repeat the edge planes) with its plane's scale and
-// offset (one record per slice); identity for float storage.  TT supplies
-// tex, stack_shift, stack_pitch and dec.
-template <int DT, typename TT>
-__device__ __forceinline__ float4 decode(const TT& T, float4 q, int slice)
-{
-    if (DT != VR_I8) return q;
-    const float2 d = __ldg(static_cast<const float2*>(T.dec) + slice);   // {scale, offset}
-    return make_float4(fmaf(q.x, d.x, d.y), fmaf(q.y, d.x, d.y), fmaf(q.z, d.x, d.y),
-                       fmaf(q.w, d.x, d.y));
-}
-
 __device__ __forceinline__ uint4 gather_u32(cudaTextureObject_t t, int layer, float x, float y)
 {
     uint4 r;
@@ -203,8 +190,8 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
     } else {
         float yt1;
         const int l1 = plane_layer<STACK>(T, z + 1, y, yt1);
-        q0 = decode<DT>(T, gather<DT>(t0, l, x, yt), z);
-        q1 = decode<DT>(T, gather<DT>(t0, l1, x, yt1), z + 1);
+        q0 = gather<DT>(t0, l, x, yt);           // int8: codes (see interp_t)
+        q1 = gather<DT>(t0, l1, x, yt1);
     }
 }
 
@@ -239,13 +226,13 @@ __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, c
             n0 = dz == 0 ? c0 : c1;
         } else {
             const int l = plane_layer<STACK>(T, n.iz, n.gy, yt);
-            n0 = decode<DT>(T, gather<DT>(t0, l, n.gx, yt), n.iz);
+            n0 = gather<DT>(t0, l, n.gx, yt);
         }
         if (keep1) {
             n1 = dz == 0 ? c1 : c0;
         } else {
             const int l = plane_layer<STACK>(T, n.iz + 1, n.gy, yt);
-            n1 = decode<DT>(T, gather<DT>(t0, l, n.gx, yt), n.iz + 1);
+            n1 = gather<DT>(t0, l, n.gx, yt);
         }
     }
 }
@@ -269,7 +256,7 @@ __device__ __forceinline__ void next_cell_up(const TT& T, cudaTextureObject_t t0
                 float yt;
                 const int l = plane_layer<STACK>(T, n.iz + 1, n.gy, yt);
                 n0 = c1;
-                n1 = decode<DT>(T, gather<DT>(t0, l, n.gx, yt), n.iz + 1);
+                n1 = gather<DT>(t0, l, n.gx, yt);
                 return;
             }
         }
@@ -286,6 +273,7 @@ struct Geo {
     float gx, gy;     // gather coordinates (cell corner + 1)
     float fx, fy, fz;
     int iz;           // texture slice of the cell's lower plane (cell + 1)
+    float2 d0, d1;    // plain int8: the decode records of slices iz, iz + 1
 };
 
 template <typename PP>
@@ -312,6 +300,48 @@ __device__ __forceinline__ float interp(const float4& q0, const float4& q1, cons
     const float y0z1 = lerpf(q1.w, q1.z, g.fx);
     const float y1z1 = lerpf(q1.x, q1.y, g.fx);
     return lerpf(lerpf(y0z0, y1z0, g.fy), lerpf(y0z1, y1z1, g.fy), g.fz);
+}
+
+// Plain int8: fetch the sample's decode records (slices g.iz and g.iz + 1)
+// along with its geometry, a step before they are used.
+template <int DT, typename TT>
+__device__ __forceinline__ void fetch_dec(const TT& T, Geo& g)
+{
+    if constexpr (DT == VR_I8) {
+        g.d0 = __ldg(static_cast<const float2*>(T.dec) + g.iz);   // {scale, offset}
+        g.d1 = __ldg(static_cast<const float2*>(T.dec) + g.iz + 1);
+    }
+}
+
+// interp for a texel format: plain int8 texels are codes, so each plane's
+// bilinear value of the codes is decoded with that plane's scale and offset
+// (decoding is affine and the bilinear weights sum to one, so this is the
+// interpolation of the decoded corners up to rounding), from the records of
+// the cell's slices (g.iz, g.iz + 1: planes g.iz - 1 and g.iz, clamped):
+// HELD, fetched with the geometry (fetch_dec, the marches over every sample);
+// otherwise read here (the lockstep marches, whose registers are spoken
+// for).  Two decodes a sample, applied when the sample is interpolated
+// rather than when its gathers return, so no decode waits for a gather in
+// flight; the records and the arithmetic are the same either way.
+template <int DT, bool HELD, typename TT>
+__device__ __forceinline__ float interp_t(const TT& T, const float4& q0, const float4& q1,
+                                          const Geo& g)
+{
+    if constexpr (DT != VR_I8) {
+        return interp(q0, q1, g);
+    } else {
+        float2 d0, d1;
+        if constexpr (HELD) {
+            d0 = g.d0;
+            d1 = g.d1;
+        } else {
+            d0 = __ldg(static_cast<const float2*>(T.dec) + g.iz);   // {scale, offset}
+            d1 = __ldg(static_cast<const float2*>(T.dec) + g.iz + 1);
+        }
+        const float b0 = lerpf(lerpf(q0.w, q0.z, g.fx), lerpf(q0.x, q0.y, g.fx), g.fy);
+        const float b1 = lerpf(lerpf(q1.w, q1.z, g.fx), lerpf(q1.x, q1.y, g.fx), g.fy);
+        return lerpf(fmaf(b0, d0.x, d0.y), fmaf(b1, d1.x, d1.y), g.fz);
+    }
 }
 
 // Accumulate one sample; returns true when the ray terminates.
@@ -416,7 +446,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
                 cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
         }
         ++k;
-        if ((n0 && acc.add(P, lut, interp(a0, a1, g0))) || k >= r.K) break;
+        if ((n0 && acc.add(P, lut, interp_t<DT, false>(T, a0, a1, g0))) || k >= r.K) break;
         kf += 1.0f;
         // the same one sample further on, the register sets swapped
         m1 = mcell(kf + 2.0f, b1);
@@ -430,7 +460,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
                 cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
         }
         ++k;
-        if ((n1 && acc.add(P, lut, interp(c0, c1, g1))) || k >= r.K) break;
+        if ((n1 && acc.add(P, lut, interp_t<DT, false>(T, c0, c1, g1))) || k >= r.K) break;
         kf += 1.0f;
     }
     return k;
@@ -449,17 +479,20 @@ __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4*
     const cudaTextureObject_t t0 = T.tex;
     const float Kf = (float)r.K;
     Geo ga = geo(P, r, 0.0f), gb;
+    fetch_dec<DT>(T, ga);
     float4 a0, a1, b0, b1;
     cell<DT, STACK>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
     float kf = 1.0f;            // samples evaluated once the current one is
     for (;;) {
         gb = geo(P, r, kf);
+        fetch_dec<DT>(T, gb);
         next_cell<DT, STACK>(T, t0, ga, a0, a1, gb, b0, b1);
-        if (acc.add(P, lut, interp(a0, a1, ga)) || kf >= Kf) break;
+        if (acc.add(P, lut, interp_t<DT, true>(T, a0, a1, ga)) || kf >= Kf) break;
         kf += 1.0f;
         ga = geo(P, r, kf);
+        fetch_dec<DT>(T, ga);
         next_cell<DT, STACK>(T, t0, gb, b0, b1, ga, a0, a1);
-        if (acc.add(P, lut, interp(b0, b1, gb)) || kf >= Kf) break;
+        if (acc.add(P, lut, interp_t<DT, true>(T, b0, b1, gb)) || kf >= Kf) break;
         kf += 1.0f;
     }
     return (int)kf;
@@ -580,21 +613,24 @@ __device__ __forceinline__ int march_part(const PP& P, const TT& T,
     float kf = (float)k0;
     Geo ga = geo(P, r, kf), gb;
     ga.iz -= P.slice_base;
+    fetch_dec<DT>(T, ga);
     float4 a0, a1, b0, b1;
     cell<DT, STACK>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
     kf += 1.0f;
     for (;;) {
         gb = geo(P, r, kf);
         gb.iz -= P.slice_base;
+        fetch_dec<DT>(T, gb);
         next_cell<DT, STACK>(T, t0, ga, a0, a1, gb, b0, b1);
         ++k;
-        if (acc.add(P, lut, interp(a0, a1, ga)) || k >= k1) break;
+        if (acc.add(P, lut, interp_t<DT, true>(T, a0, a1, ga)) || k >= k1) break;
         kf += 1.0f;
         ga = geo(P, r, kf);
         ga.iz -= P.slice_base;
+        fetch_dec<DT>(T, ga);
         next_cell<DT, STACK>(T, t0, gb, b0, b1, ga, a0, a1);
         ++k;
-        if (acc.add(P, lut, interp(b0, b1, gb)) || k >= k1) break;
+        if (acc.add(P, lut, interp_t<DT, true>(T, b0, b1, gb)) || k >= k1) break;
         kf += 1.0f;
     }
     return k - k0;
@@ -655,7 +691,7 @@ __device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
                 cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
         }
         ++k;
-        if ((n0 && acc.add(P, lut, interp(a0, a1, g0))) || k >= k1) break;
+        if ((n0 && acc.add(P, lut, interp_t<DT, false>(T, a0, a1, g0))) || k >= k1) break;
         kf += 1.0f;
         m1 = mcell(kf + 2.0f, b1);
         r1 = (m1 == m2) ? r2 : __ldg(P.mask + m1);
@@ -668,7 +704,7 @@ __device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
                 cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
         }
         ++k;
-        if ((n1 && acc.add(P, lut, interp(c0, c1, g1))) || k >= k1) break;
+        if ((n1 && acc.add(P, lut, interp_t<DT, false>(T, c0, c1, g1))) || k >= k1) break;
         kf += 1.0f;
     }
     return k - k0;
