@@ -16,7 +16,7 @@
 // 10u max|corner|.  The bit is clear when max + 2^-19 max|corner| (32u,
 // rounded once by an fma) is below the clip.  Decoding is the kernels' own:
 // float32 as stored, binary16 widened exactly, int8 as fma(code, scale[z],
-// offset[z]).  Plain int8 textures interpolate the codes of each plane and
+// offset[z]).  int8 textures interpolate the codes of each plane and
 // decode that (interp_t): the codes' two lerp levels err by at most 512u
 // code units (|code| <= 127), i.e. 512u |scale| once decoded, which a further
 // 2^-14 max |scale| of the cell's two planes covers.

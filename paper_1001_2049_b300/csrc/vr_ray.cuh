@@ -179,13 +179,9 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
             q1 = make_float4(half_bits(p.x >> 16), half_bits(p.y >> 16), half_bits(p.z >> 16),
                              half_bits(p.w >> 16));
         } else {
-            // {scale, offset} of the slice's two planes
-            const float4 d = __ldg(static_cast<const float4*>(T.dec) + z);
-            const float s0 = d.x, o0 = d.y, s1 = d.z, o1 = d.w;
-            q0 = make_float4(fmaf(code_lo(p.x), s0, o0), fmaf(code_lo(p.y), s0, o0),
-                             fmaf(code_lo(p.z), s0, o0), fmaf(code_lo(p.w), s0, o0));
-            q1 = make_float4(fmaf(code_hi(p.x), s1, o1), fmaf(code_hi(p.y), s1, o1),
-                             fmaf(code_hi(p.z), s1, o1), fmaf(code_hi(p.w), s1, o1));
+            // the two planes' codes (decoded after the interpolation, interp_t)
+            q0 = make_float4(code_lo(p.x), code_lo(p.y), code_lo(p.z), code_lo(p.w));
+            q1 = make_float4(code_hi(p.x), code_hi(p.y), code_hi(p.z), code_hi(p.w));
         }
     } else {
         float yt1;
@@ -302,18 +298,23 @@ __device__ __forceinline__ float interp(const float4& q0, const float4& q1, cons
     return lerpf(lerpf(y0z0, y1z0, g.fy), lerpf(y0z1, y1z1, g.fy), g.fz);
 }
 
-// Plain int8: fetch the sample's decode records (slices g.iz and g.iz + 1)
-// along with its geometry, a step before they are used.
+// int8: fetch the sample's decode records (plain: slices g.iz and g.iz + 1;
+// pair: the one record of slice g.iz) along with its geometry, a step before
+// they are used.
 template <int DT, typename TT>
 __device__ __forceinline__ void fetch_dec(const TT& T, Geo& g)
 {
     if constexpr (DT == VR_I8) {
         g.d0 = __ldg(static_cast<const float2*>(T.dec) + g.iz);   // {scale, offset}
         g.d1 = __ldg(static_cast<const float2*>(T.dec) + g.iz + 1);
+    } else if constexpr (DT == kI8Pair) {
+        const float4 d = __ldg(static_cast<const float4*>(T.dec) + g.iz);   // both planes
+        g.d0 = make_float2(d.x, d.y);
+        g.d1 = make_float2(d.z, d.w);
     }
 }
 
-// interp for a texel format: plain int8 texels are codes, so each plane's
+// interp for a texel format: int8 texels (plain and pair) are codes, so each plane's
 // bilinear value of the codes is decoded with that plane's scale and offset
 // (decoding is affine and the bilinear weights sum to one, so this is the
 // interpolation of the decoded corners up to rounding), from the records of
@@ -327,16 +328,20 @@ template <int DT, bool HELD, typename TT>
 __device__ __forceinline__ float interp_t(const TT& T, const float4& q0, const float4& q1,
                                           const Geo& g)
 {
-    if constexpr (DT != VR_I8) {
+    if constexpr (DT != VR_I8 && DT != kI8Pair) {
         return interp(q0, q1, g);
     } else {
         float2 d0, d1;
         if constexpr (HELD) {
             d0 = g.d0;
             d1 = g.d1;
-        } else {
+        } else if constexpr (DT == VR_I8) {
             d0 = __ldg(static_cast<const float2*>(T.dec) + g.iz);   // {scale, offset}
             d1 = __ldg(static_cast<const float2*>(T.dec) + g.iz + 1);
+        } else {
+            const float4 d = __ldg(static_cast<const float4*>(T.dec) + g.iz);   // both planes
+            d0 = make_float2(d.x, d.y);
+            d1 = make_float2(d.z, d.w);
         }
         const float b0 = lerpf(lerpf(q0.w, q0.z, g.fx), lerpf(q0.x, q0.y, g.fx), g.fy);
         const float b1 = lerpf(lerpf(q1.w, q1.z, g.fx), lerpf(q1.x, q1.y, g.fx), g.fy);
