@@ -173,16 +173,13 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
     float yt;
     const int l = plane_layer<STACK>(T, z, y, yt);
     if constexpr (DT == kF16Pair || DT == kI8Pair) {
+        // the packed texels as they are (their bits carried in q0; q1 unused):
+        // unpacked when the sample is interpolated (interp_t), not when the
+        // gather returns
         const uint4 p = gather_u32(t0, l, x, yt);
-        if constexpr (DT == kF16Pair) {
-            q0 = make_float4(half_bits(p.x), half_bits(p.y), half_bits(p.z), half_bits(p.w));
-            q1 = make_float4(half_bits(p.x >> 16), half_bits(p.y >> 16), half_bits(p.z >> 16),
-                             half_bits(p.w >> 16));
-        } else {
-            // the two planes' codes (decoded after the interpolation, interp_t)
-            q0 = make_float4(code_lo(p.x), code_lo(p.y), code_lo(p.z), code_lo(p.w));
-            q1 = make_float4(code_hi(p.x), code_hi(p.y), code_hi(p.z), code_hi(p.w));
-        }
+        q0 = make_float4(__uint_as_float(p.x), __uint_as_float(p.y), __uint_as_float(p.z),
+                         __uint_as_float(p.w));
+        q1 = q0;
     } else {
         float yt1;
         const int l1 = plane_layer<STACK>(T, z + 1, y, yt1);
@@ -328,7 +325,15 @@ template <int DT, bool HELD, typename TT>
 __device__ __forceinline__ float interp_t(const TT& T, const float4& q0, const float4& q1,
                                           const Geo& g)
 {
-    if constexpr (DT != VR_I8 && DT != kI8Pair) {
+    if constexpr (DT == kF16Pair) {
+        // q0 carries the packed texels: plane g.iz - 1 in the low halves
+        const unsigned px = __float_as_uint(q0.x), py = __float_as_uint(q0.y),
+                       pz = __float_as_uint(q0.z), pw = __float_as_uint(q0.w);
+        return interp(make_float4(half_bits(px), half_bits(py), half_bits(pz), half_bits(pw)),
+                      make_float4(half_bits(px >> 16), half_bits(py >> 16), half_bits(pz >> 16),
+                                  half_bits(pw >> 16)),
+                      g);
+    } else if constexpr (DT != VR_I8 && DT != kI8Pair) {
         return interp(q0, q1, g);
     } else {
         float2 d0, d1;
@@ -343,8 +348,15 @@ __device__ __forceinline__ float interp_t(const TT& T, const float4& q0, const f
             d0 = make_float2(d.x, d.y);
             d1 = make_float2(d.z, d.w);
         }
-        const float b0 = lerpf(lerpf(q0.w, q0.z, g.fx), lerpf(q0.x, q0.y, g.fx), g.fy);
-        const float b1 = lerpf(lerpf(q1.w, q1.z, g.fx), lerpf(q1.x, q1.y, g.fx), g.fy);
+        float4 c0 = q0, c1 = q1;             // plain int8: the two planes' codes
+        if constexpr (DT == kI8Pair) {       // packed: plane g.iz - 1 in the low bytes
+            const unsigned px = __float_as_uint(q0.x), py = __float_as_uint(q0.y),
+                           pz = __float_as_uint(q0.z), pw = __float_as_uint(q0.w);
+            c0 = make_float4(code_lo(px), code_lo(py), code_lo(pz), code_lo(pw));
+            c1 = make_float4(code_hi(px), code_hi(py), code_hi(pz), code_hi(pw));
+        }
+        const float b0 = lerpf(lerpf(c0.w, c0.z, g.fx), lerpf(c0.x, c0.y, g.fx), g.fy);
+        const float b1 = lerpf(lerpf(c1.w, c1.z, g.fx), lerpf(c1.x, c1.y, g.fx), g.fy);
         return lerpf(fmaf(b0, d0.x, d0.y), fmaf(b1, d1.x, d1.y), g.fz);
     }
 }

@@ -262,6 +262,30 @@ def test_pair_texture_ragged_cubes(dims, step, dtype):
                    what="pair ragged %s %s %s" % (dims, dtype, mode), tex="pair")
 
 
+@pytest.mark.parametrize("dtype", ["f16", "i8"])
+def test_pair_texels_give_the_plain_texels_images(dtype):
+    # the packed pair texels travel through the march as raw bits and are
+    # unpacked at interpolation: the images are those of one texel per voxel
+    # bit for bit, also where halves of a texel are zero or tiny (bit
+    # patterns that read as subnormal floats)
+    dims = (29, 23, 41)
+    cube = synth.make_cube(dims, 3, ("uniform", 3.0, 8.0), 66).numpy()
+    rng = np.random.default_rng(8)
+    m = rng.random(cube.shape)
+    cube[m < 0.3] = 0.0
+    cube[(m >= 0.3) & (m < 0.4)] = 1e-6
+    cube[(m >= 0.4) & (m < 0.45)] *= -1.0
+    cams = synth.random_sphere_cameras(dims, 3, 27, 21, 4)
+    imgs = {}
+    for pair in (False, True):
+        vol = Volume(torch.from_numpy(cube).cuda(), dtype)
+        vol.attach_pair_texture() if pair else vol.attach_texture()
+        vol.set_transfer(synth.default_lut(32), -1.0, 8.0, -1.0, 0.97)
+        imgs[pair] = {mode: vol.render(cams, 27, 21, mode, 0.37).cpu() for mode in MODES}
+    for mode in MODES:
+        assert torch.equal(imgs[False][mode], imgs[True][mode]), (dtype, mode)
+
+
 def test_pair_texture_stacks_cell_planes_of_deep_cubes():
     dims = (6, 5, 4500)
     cube = synth.make_cube(dims, 20, ("uniform", 3.0, 8.0), 31).numpy()
