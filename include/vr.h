@@ -109,7 +109,10 @@ int vr_volume_bytes(const int64_t dims[3], int dtype, size_t* bytes_out);
  *                scale = (hi - lo)/254, offset = (hi + lo)/2, code =
  *                clamp(rint((v - offset)/scale), -127, 127); a constant
  *                plane gets scale 1 and code 0).  Decoding is
- *                code * scale + offset, before interpolation.
+ *                code * scale + offset; a sample is the trilinear value
+ *                of the decoded voxels (texture storage interpolates each
+ *                plane's codes and decodes that: the same value up to
+ *                FP32 rounding, as decoding is affine).
  *   src          float32 cube, linear, x fastest (nz*ny*nx values), or NULL
  *                to bind without data (fill later with vr_volume_upload).
  *   src_on_device 1: src is device memory.  0: src is page-locked host memory
