@@ -387,18 +387,21 @@ std::atomic<int> g_batch_cfg{0};
 
 int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s, int cfg)
 {
-    // persistent grid: as many blocks as fit on the device at once
-    static std::atomic<int> grid[2][vr::kNumBatchShapes];
+    // persistent grid: as many blocks as fit on the current device at once
+    // (cached per device, class and shape)
+    constexpr int kDevices = 64;
+    static std::atomic<int> grid[kDevices][2][vr::kNumBatchShapes];
+    int dev = 0;
+    cudaGetDevice(&dev);
     int g[2];
     for (int c = 0; c < 2; ++c) {
-        g[c] = grid[c][cfg].load();
+        g[c] = dev >= 0 && dev < kDevices ? grid[dev][c][cfg].load() : 0;
         if (g[c] == 0) {
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
+            int sms = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (sms < 1) sms = 1;
             g[c] = sms * vr::batch_blocks_per_sm(c, cfg);
-            grid[c][cfg].store(g[c]);
+            if (dev >= 0 && dev < kDevices) grid[dev][c][cfg].store(g[c]);
         }
     }
     // every request is checked before anything is enqueued, so an argument

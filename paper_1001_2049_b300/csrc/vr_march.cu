@@ -252,11 +252,14 @@ cudaError_t launch_dt(const MarchParams& p, int mode, cudaStream_t s, int k_max)
 
 }  // namespace
 
-static int env_int(const char* name, int dflt)
-{
-    const char* v = getenv(name);
-    return (v && *v) ? atoi(v) : dflt;
-}
+// Slab window plan (measured on the 1024^3 orbit views): 4 cells per slab,
+// a one-voxel margin, slabs along y or z when that direction component is at
+// least 0.25, the window grown 10 % over the reach of a tile, at most 50 KB.
+constexpr int kSlabCells = 4;
+constexpr int kSlabMargin = 1;
+constexpr float kSlabMinAxis = 0.25f;
+constexpr double kSlabGrow = 1.10;
+constexpr int kSlabWindowKB = 50;
 
 bool plan_slab(const MarchParams& p, SlabConfig* c)
 {
@@ -285,17 +288,17 @@ bool plan_slab(const MarchParams& p, SlabConfig* c)
         }
         if (s > sp) sp = s;
     }
-    c->S = env_int("VR_SLAB_S", 4);
-    c->margin = env_int("VR_SLAB_MARGIN", 1);
-    c->min_axis = env_int("VR_SLAB_MIN_AXIS_PCT", 25) / 100.0f;
+    c->S = kSlabCells;
+    c->margin = kSlabMargin;
+    c->min_axis = kSlabMinAxis;
     c->ea_pitch = (c->S + 1) | 1;
     // one window buffer: the bigger of the plane footprint a 16 x 16 tile can
     // reach (ray spacing, slant across the slab, margins) and a floor, within
     // a budget that keeps two blocks per SM
-    const double grow = env_int("VR_SLAB_GROW_PCT", 110) / 100.0;
+    const double grow = kSlabGrow;
     const double side = 16.0 * sp * grow + 3.0 * (c->S + 1) + 2.0 * c->margin + 8.0;
     const double want = side * side * (c->S + 1);
-    const int budget = env_int("VR_SLAB_WIN_KB", 50) * 1024 / 4;
+    const int budget = kSlabWindowKB * 1024 / 4;
     int elems = (int)(want < budget ? want : budget);
     if (elems < 4096) elems = 4096;
     c->win_elems = (elems + 3) & ~3;
@@ -304,7 +307,6 @@ bool plan_slab(const MarchParams& p, SlabConfig* c)
     const double diag = sqrt((double)p.hix * p.hix + (double)p.hiy * p.hiy + (double)p.hiz * p.hiz);
     c->k_max = (int)(diag / p.step) + 2;
     c->smem_bytes = slab_smem_bytes(*c);
-    if (env_int("VR_SLAB_DISABLE", 0)) return false;
     return c->S >= 1 && c->S <= 7 && c->smem_bytes <= 220 * 1024;
 }
 
