@@ -581,7 +581,8 @@ def main():
                     help="seconds of oracle work for the CPU baseline (0: skip)")
     ap.add_argument("--ref-budget", type=float, default=10.0,
                     help="seconds of oracle work per step of the reference arm")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end leg (default: --steps)")
     ap.add_argument("--cube-edge", type=int, default=1024,
                     help="profiling captures only: smaller cube, same framing")
     ap.add_argument("--views", type=int, default=32)
@@ -598,6 +599,8 @@ def main():
                     help="render from layered textures (default) or gather from the bricks")
     ap.add_argument("--res", default=None, help="WxH (default scales with the cube)")
     args = ap.parse_args()
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
     if args.impl == "reference":
         return run_reference(args)
 
