@@ -458,14 +458,14 @@ def out_of_core_leg(cube, cams, W, H, wl, lut, comp_ref, mip_ref, part_planes=12
                     reps=2):
     """The 1024^3 workload rendered part by part from page-locked host memory
     (the cube never resident on the device: a cache of ``cache_parts`` part
-    volumes of ``part_planes`` planes sharing one brick buffer), composite and
-    MIP in one pass over the parts per sweep; the images are compared with the
-    resident render's."""
+    volumes of ``part_planes`` planes sharing one brick buffer, each with MIP
+    bounds filled as it loads), composite and MIP in one pass over the parts
+    per sweep; the images are compared with the resident render's."""
     from paper_1001_2049_b300.stream import PartStream, sweeps
     host = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
     host.copy_(cube)
     ps = PartStream(wl.dims, "f32", lambda z0, n: host[z0:z0 + n], part_planes,
-                    cache_parts=cache_parts)
+                    cache_parts=cache_parts, bounds=True)
     ps.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
     comp = torch.empty_like(comp_ref)
     mip = torch.empty_like(mip_ref)
@@ -484,7 +484,7 @@ def out_of_core_leg(cube, cams, W, H, wl, lut, comp_ref, mip_ref, part_planes=12
         loaded.append(ps.bytes_loaded - b0)
         parts.append(ps.parts_loaded - p0)
     res = {"parts": len(ps.parts), "planes_per_part": ps.planes,
-           "cache_parts": len(ps.vols),
+           "cache_parts": len(ps.vols), "mip_bounds": True,
            "sweeps": len(sweeps(cams, W, H)), "ms_per_step": 1000.0 * min(times),
            "part_loads_per_step": parts[-1],
            "host_bytes_read_per_step": loaded[-1],

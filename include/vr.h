@@ -38,13 +38,15 @@
  * Memory.  The caller owns the device memory a render reads and writes: the
  * brick buffer of each volume (size from vr_volume_bytes), the empty-space
  * masks, every source, output buffer and batch workspace.  The library owns
- * the small host-side handle and, when asked for it, a volume's texture
- * storage (vr_volume_attach_texture: the one device allocation it makes).  Every call that takes a
- * stream (a cudaStream_t passed as void*, NULL = legacy default stream) is
- * asynchronous on it: argument errors are reported synchronously; a device
- * fault surfaces at the caller's next synchronisation.  The library never
- * synchronises on its own except where a call says so (texture attach, the
- * autotuner) and never falls back to the CPU.
+ * the small host-side handle and, when asked for them, a volume's texture
+ * storage and MIP bounds (vr_volume_attach_texture,
+ * vr_volume_attach_mip_bounds: the device allocations it makes, besides a
+ * stream-ordered scratch buffer while bounds are filled).  Every call that
+ * takes a stream (a cudaStream_t passed as void*, NULL = legacy default
+ * stream) is asynchronous on it: argument errors are reported synchronously;
+ * a device fault surfaces at the caller's next synchronisation.  The library
+ * never synchronises on its own except where a call says so (texture attach,
+ * stacked MIP bounds, the autotuners) and never falls back to the CPU.
  *
  * Errors.  Every function returns VR_OK (0) or a negative VR_ERR_* code;
  * vr_last_error() then gives a message (thread-local, valid until the next
@@ -133,7 +135,10 @@ int vr_volume_create(const int64_t dims[3], int dtype, const float* src,
 /* Pack planes [z0, z0 + nplanes) of the cube from a float32 source holding
  * exactly those planes (nplanes*ny*nx values, x fastest).  Lets a cube be
  * filled in slabs of frequency channels.  src_on_device and stream as in
- * vr_volume_create.                                                        */
+ * vr_volume_create.  With texture storage the planes' slices of the texture
+ * (and of the MIP bounds) are refreshed too: stream-ordered for an FP32
+ * texture without stacked slices; otherwise through a surface, the call
+ * then waiting for `stream`.                                               */
 int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* src,
                      int src_on_device, void* stream);
 
@@ -239,14 +244,18 @@ int vr_volume_detach_texture(vr_volume vol);
  * their trilinear value is an upper bound of the sample's value up to the
  * FP32 rounding of the two interpolations, which a margin of 2^-19 times the
  * largest |voxel| covers, so a sample is read from the FP32 texture only when
- * it could raise the ray's running maximum.  MIP images and sample counts
- * are those without bounds bit for bit (voxels above 65504, infinite or NaN
- * give bounds that never exclude a sample).  No effect on COMPOSITE and SUM
- * renders, on vr_render_part or on the batched launch.  Uploads refresh the
+ * it could raise the ray's running maximum (the largest |voxel| is kept in
+ * device memory, raised by every fill, and the kernels read it there).  MIP
+ * images and sample counts are those without bounds bit for bit (voxels
+ * above 65504, infinite or NaN give bounds that never exclude a sample).
+ * MIP renders through vr_render_part use a part's bounds too; no effect on
+ * COMPOSITE and SUM renders or on the batched launch.  Uploads refresh the
  * bounds with the texture.  VR_ERR_UNSUPPORTED for other storage types,
  * without texture storage, or after vr_volume_drop_bricks; VR_ERR_OOM when
- * the allocation fails.  The call synchronises `stream`.  No counterpart in
- * the paper.                                                                */
+ * an allocation fails.  The fill is queued on `stream` and the call returns
+ * without waiting for it, except for cubes deep enough that the texture
+ * stacks slices, where it waits for `stream`.  No counterpart in the
+ * paper.                                                                    */
 int vr_volume_attach_mip_bounds(vr_volume vol, void* stream);
 
 /* Release the MIP bounds (MIP renders read the FP32 texture at every

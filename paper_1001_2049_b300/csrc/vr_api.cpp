@@ -192,7 +192,7 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
     tp->dec = v->dec;
     tp->k_max = (int)(diag / step) + 2;
     tp->bound = v->bound_tex;
-    tp->bound_delta = v->bound_delta;
+    tp->bound_vmax = v->bound_vmax;
     p->mask = v->mask;
     p->mnx = v->mnx;
     p->mny = v->mny;
@@ -454,15 +454,48 @@ void release_bounds(vr::Volume* v)
     v->bound_tex = 0;
     v->bound_array = nullptr;
     v->bound_vmax = nullptr;
-    v->bound_delta = 0.0f;
 }
 
-// Fill MIP-bound slices [s0, s1) and update the rounding margin from the
-// largest |voxel| the fills have seen (2^-19 of it, at least the smallest
-// normal float so that subnormal rounding is covered; +inf if a voxel is).
-// The maximum only grows, so after uploads the margin stays conservative.
+// Fill MIP-bound slices [s0, s1), raising the device word of the largest
+// |voxel| the fills have seen (the kernels derive the rounding margin from
+// it, bound_margin; it only grows, so after uploads it stays conservative).
+// An unstacked bound texture is written linearly to a stream-ordered scratch
+// buffer and copied into the array, chunk by chunk, with no wait; a stacked
+// one through a surface, the stream waited for before the surface object is
+// destroyed.
 int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
 {
+    if (s0 >= s1) return VR_OK;
+    const int nx = v->g.nx, ny = v->g.ny;
+    if (v->stack_shift == 0) {
+        const size_t slice = (size_t)nx * ny * sizeof(unsigned short);
+        const int64_t chunk =
+            std::max<int64_t>(1, std::min<int64_t>(s1 - s0, (int64_t)((256u << 20) / slice)));
+        unsigned short* buf = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), chunk * slice, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(VR_ERR_OOM, "MIP bound scratch: %s", cudaGetErrorString(e));
+        }
+        for (int64_t c0 = s0; c0 < s1 && e == cudaSuccess; c0 += chunk) {
+            const int64_t c1 = std::min(s1, c0 + chunk);
+            e = vr::fill_bounds_linear(*v, buf, (int)c0, (int)c1, v->bound_vmax, s);
+            if (e == cudaSuccess) {
+                cudaMemcpy3DParms p;
+                std::memset(&p, 0, sizeof p);
+                p.srcPtr = make_cudaPitchedPtr(buf, (size_t)nx * sizeof(unsigned short), nx, ny);
+                p.dstArray = v->bound_array;
+                p.dstPos = make_cudaPos(0, 0, (size_t)c0);
+                p.extent = make_cudaExtent(nx, ny, (size_t)(c1 - c0));
+                p.kind = cudaMemcpyDeviceToDevice;
+                e = cudaMemcpy3DAsync(&p, s);
+            }
+        }
+        const cudaError_t e2 = cudaFreeAsync(buf, s);
+        if (e != cudaSuccess) return cuda_fail(e, "bound fill");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "bound scratch");
+        return VR_OK;
+    }
     cudaResourceDesc rd;
     std::memset(&rd, 0, sizeof rd);
     rd.resType = cudaResourceTypeArray;
@@ -471,17 +504,10 @@ int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
     cudaError_t e = cudaCreateSurfaceObject(&surf, &rd);
     if (e != cudaSuccess) return cuda_fail(e, "surface object");
     e = vr::fill_bounds(*v, surf, (int)s0, (int)s1, v->bound_vmax, s);
-    // the maximum comes back on the same stream (not the legacy stream, which
-    // would wait for other streams' work), then the stream is waited for: the
-    // surface object may only be destroyed after the fill ran
-    float vmax = 0.0f;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&vmax, v->bound_vmax, sizeof vmax, cudaMemcpyDeviceToHost, s);
-    cudaError_t e2 = cudaStreamSynchronize(s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);   // before the surface object goes
     cudaDestroySurfaceObject(surf);
     if (e != cudaSuccess) return cuda_fail(e, "bound fill");
     if (e2 != cudaSuccess) return cuda_fail(e2, "bound fill");
-    v->bound_delta = std::max(std::ldexp(vmax, -19), std::ldexp(1.0f, -126));
     return VR_OK;
 }
 
@@ -580,7 +606,7 @@ int attach_bounds(vr::Volume* v, cudaStream_t s)
                     "MIP bound storage: %s", cudaGetErrorString(e));
     }
     e = cudaMalloc(&v->bound_vmax, sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(v->bound_vmax, 0, sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->bound_vmax, 0, sizeof(float), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         release_bounds(v);

@@ -69,7 +69,6 @@ struct Volume {
     cudaArray_t bound_array;
     cudaTextureObject_t bound_tex;
     float* bound_vmax;      // device word: largest |voxel| seen by the fills
-    float bound_delta;      // margin for FP32 rounding, 2^-19 * that maximum
     int cfg[3];             // texture-kernel launch shape per mode (autotuned)
     // optional empty-space masks (caller-owned device buffer)
     unsigned long long* mask;   // valid for clip level mask_clip
@@ -89,10 +88,11 @@ struct TexParams {
     const void* dec;        // VR_I8 / kI8Pair: float2 / float4 per slice
     int k_max;
     // MIP bounds (0: none): binary16 texels rounded up from the FP32 voxels,
-    // laid out as `tex`; a sample whose bound plus bound_delta stays below
+    // laid out as `tex`; a sample whose bound plus the rounding margin
+    // (bound_margin: from the largest |voxel|, a device word) stays below
     // the ray's running maximum cannot raise it (see march_tex_bound)
     cudaTextureObject_t bound;
-    float bound_delta;
+    const float* bound_vmax;
 };
 
 size_t brick_bytes(const VolumeGeom& g, int dtype);   // voxel part only
@@ -243,6 +243,10 @@ cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int s0, int 
 // through `surf`, raising *vmax to the largest |voxel| of those planes.
 cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1, float* vmax,
                         cudaStream_t s);
+// The same slices written linearly (x fastest, slice after slice) to `dst`,
+// for a copy into an unstacked bound texture.
+cudaError_t fill_bounds_linear(const Volume& v, unsigned short* dst, int s0, int s1, float* vmax,
+                               cudaStream_t s);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
                         cudaStream_t s);
 

@@ -515,17 +515,25 @@ __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4*
     return (int)kf;
 }
 
+// The rounding margin of MIP bounds: 2^-19 of the largest |voxel| the bound
+// fills have seen (a device word, read once per ray), at least the smallest
+// normal float so that subnormal rounding is covered; +inf when a voxel is.
+template <typename TT>
+__device__ __forceinline__ float bound_margin(const TT& T)
+{
+    return fmaxf(__ldg(T.bound_vmax) * 0x1p-19f, 0x1p-126f);
+}
+
 // MIP over FP32 texture storage with MIP bounds attached: the march of
 // march_tex runs over the bound texels (binary16, each voxel rounded toward
 // +infinity), whose trilinear value u is never below the sample's value v
 // by more than the FP32 rounding of the two interpolations (at most
-// 9 * 2^-24 of the largest |corner| each; bound_delta = 2^-19 of the largest
-// |voxel| covers both).  A sample is evaluated from the FP32 texture only
-// when u + bound_delta is not below the running maximum, i.e. when it could
-// raise it; a NaN or infinite bound is never below.  Every sample that can
-// change the maximum is evaluated with march_tex's arithmetic, so the result
-// and the sample count are march_tex's bit for bit, while the march moves
-// half the texel bytes.
+// 9 * 2^-24 of the largest |corner| each; bound_margin covers both).  A
+// sample is evaluated from the FP32 texture only when u + margin is not
+// below the running maximum, i.e. when it could raise it; a NaN or infinite
+// bound is never below.  Every sample that can change the maximum is
+// evaluated with march_tex's arithmetic, so the result and the sample count
+// are march_tex's bit for bit, while the march moves half the texel bytes.
 template <bool STACK, typename PP, typename TT>
 __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const Ray& r,
                                                Acc<VR_MIP>& acc)
@@ -533,8 +541,9 @@ __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const R
     if (r.K <= 0) return 0;
     const cudaTextureObject_t tb = T.bound, tf = T.tex;
     const float Kf = (float)r.K;
+    const float margin = bound_margin(T);
     auto take = [&](const Geo& g, const float4& u0, const float4& u1) {
-        if (!(interp(u0, u1, g) + T.bound_delta < acc.m)) {
+        if (!(interp(u0, u1, g) + margin < acc.m)) {
             float4 e0, e1;
             cell<VR_F32, STACK>(T, tf, g.iz, g.gx, g.gy, e0, e1);
             acc.m = fmaxf(acc.m, interp(e0, e1, g));
@@ -736,8 +745,9 @@ __device__ __forceinline__ int march_part_bound(const PP& P, const TT& T, const 
 {
     if (k0 >= k1) return 0;
     const cudaTextureObject_t tb = T.bound, tf = T.tex;
+    const float margin = bound_margin(T);
     auto take = [&](const Geo& g, const float4& u0, const float4& u1) {
-        if (!(interp(u0, u1, g) + T.bound_delta < acc.m)) {
+        if (!(interp(u0, u1, g) + margin < acc.m)) {
             float4 e0, e1;
             cell<VR_F32, STACK>(T, tf, g.iz, g.gx, g.gy, e0, e1);
             acc.m = fmaxf(acc.m, interp(e0, e1, g));

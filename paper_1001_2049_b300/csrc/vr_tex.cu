@@ -36,6 +36,22 @@ __device__ __forceinline__ void write_slice_row(cudaSurfaceObject_t surf, W v, i
     if (y == ny - 1) surf2DLayeredwrite(v, surf, x * (int)sizeof(W), base + ny, layer);
 }
 
+// *vmax = max(*vmax, the largest m of the block's 256 threads); one atomic per
+// block (the bit patterns of values >= 0 order as integers).  Every thread of
+// the block calls it.
+__device__ __forceinline__ void raise_max(float m, float* vmax)
+{
+    __shared__ float warp_max[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, warp_max[w]);
+        atomicMax(reinterpret_cast<int*>(vmax), __float_as_int(m));
+    }
+}
+
 // Plain formats: slices [s0, s1) of the texture; slice s holds plane s - 1,
 // slices 0 and nz + 1 repeat the edge planes.
 template <typename T>
@@ -79,9 +95,30 @@ __global__ void __launch_bounds__(256) fill_bound_kernel(const float* __restrict
                             pitch);
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(vmax), __float_as_int(m));
+    raise_max(m, vmax);
+}
+
+// fill_bound_kernel's slices written linearly: slice s0 + j at dst + j nx ny,
+// x fastest (for a copy into an unstacked bound texture).
+__global__ void __launch_bounds__(256) fill_bound_linear_kernel(
+    const float* __restrict__ bricks, VolumeGeom g, unsigned short* __restrict__ dst, int s0,
+    int s1, float* __restrict__ vmax)
+{
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    float m = 0.0f;
+    if (x < g.nx && y < g.ny) {
+        for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z) {
+            const int z = min(max(sl - 1, 0), g.nz - 1);
+            const size_t brick = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) *
+                                     g.nbx + (x >> kBrickShift);
+            const float v =
+                bricks[brick * kBrickVoxels + ((z & 31) << 10) + ((y & 31) << 5) + (x & 31)];
+            m = fmaxf(m, fabsf(v));
+            dst[((size_t)(sl - s0) * g.ny + y) * g.nx + x] = __half_as_ushort(__float2half_ru(v));
+        }
+    }
+    raise_max(m, vmax);
 }
 
 // Pair formats: slices [s0, s1); slice s holds the voxels of planes s - 1 and
@@ -185,14 +222,31 @@ void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb)
     *minb = sh.minb;
 }
 
+// The bound fills' grid: 32 x 8 voxel rows per block, at most 32 blocks along
+// the slices (each block then walks several slices), so that the maximum
+// takes a few thousand atomics on one word rather than one per warp row.
+static dim3 bound_grid(const Volume& v, int z0, int z1)
+{
+    return dim3((unsigned)((v.g.nx + 31) / 32), (unsigned)((v.g.ny + 7) / 8),
+                (unsigned)std::min(z1 - z0, 32));
+}
+
 cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int z0, int z1, float* vmax,
                         cudaStream_t s)
 {
     if (z1 <= z0) return cudaSuccess;
-    dim3 grid((unsigned)((v.g.nx + 31) / 32), (unsigned)((v.g.ny + 7) / 8),
-              (unsigned)((z1 - z0) < 1024 ? (z1 - z0) : 1024));
+    const dim3 grid = bound_grid(v, z0, z1);
     fill_bound_kernel<<<grid, 256, 0, s>>>((const float*)v.bricks, v.g, surf, z0, z1,
                                            v.stack_shift, v.stack_pitch, vmax);
+    return cudaGetLastError();
+}
+
+cudaError_t fill_bounds_linear(const Volume& v, unsigned short* dst, int z0, int z1, float* vmax,
+                               cudaStream_t s)
+{
+    if (z1 <= z0) return cudaSuccess;
+    const dim3 grid = bound_grid(v, z0, z1);
+    fill_bound_linear_kernel<<<grid, 256, 0, s>>>((const float*)v.bricks, v.g, dst, z0, z1, vmax);
     return cudaGetLastError();
 }
 
