@@ -117,13 +117,13 @@ class Clocks:
 # 1024^3 / 32-view workload, from one ncu capture of the full-size launches
 # (one pass: dram__bytes_read.sum + dram__bytes_write.sum;
 # profiles/tex_kernel_f32_cube1024_orbit32.md): MIP at launch shape 2 150.31
-# GB read + 0.42 GB written; MIP with the binary16 MIP bounds at shape 4
-# 92.04 + 0.27 GB; composite with the empty-space masks at shape 7 31.99 +
+# GB read + 0.42 GB written; MIP with the binary16 MIP bounds at shape 6
+# 88.64 + 0.27 GB; composite with the empty-space masks at shape 7 31.99 +
 # 1.29 GB.
 # Other workloads (the --cube-edge/--views cases) report them scaled by their
 # algorithmic bytes.
 MEASURED_TRAFFIC = {"mip": 150.305302e9 + 0.415848e9,
-                    "mip_bounds": 92.041213e9 + 0.269872e9,
+                    "mip_bounds": 88.642216e9 + 0.267677e9,
                     "composite_masks": 31.987687e9 + 1.288413e9}
 MEASURED_ALGORITHMIC = {"mip": 136229959936.0, "mip_bounds": 136229959936.0,
                         "composite_masks": 136433374037.6}
@@ -833,7 +833,8 @@ def main():
                 "mip_bounds": bounds_on,
                 "without_bounds": no_bounds,
                 "autotuned": tuned,
-                "l2": "inputs larger than L2 (4 GiB cube per view pass)"},
+                "l2": "inputs larger than L2 (a %.2f GiB cube per view pass, L2 126 MB)"
+                      % (4.0 * wl.dims[0] * wl.dims[1] * wl.dims[2] / 2 ** 30)},
             "roofline": {"bound": "hbm",
                          "kernel": ("tex_kernel" if args.storage == "texture"
                                     else "march kernel") + " %s f32" % dom
