@@ -5,16 +5,21 @@ combines the images (§3.1 items 1, 4, 5), and aims at data larger than GPU
 memory (abstract).  Here the cube stays with its source (page-locked host
 memory, or a generator) and passes through a cache of part volumes on the
 device: while one part renders on the compute stream, the next is packed
-(into one brick buffer the part volumes share) and copied into a free part
-volume's texture on a copy stream; the part volume used least recently makes
-room.  Each part continues the
+(into one brick buffer the part volumes share) and copied into a part
+volume's texture on a copy stream.  Each part continues the
 images from the state the earlier parts left (``vr_render_part``), so the
 images are those of a one-pass render of the whole cube, bit for bit.
 
 Rays going up in z take the parts in ascending order and rays going down
 in descending order: a view set whose rays go both ways is rendered in two
-sweeps (the turning part is not loaded twice).  All rendering runs in the
-library's kernels; this module is host-side control.
+sweeps (the turning part is not loaded twice), and a direction none of whose
+rays can enter the cube (a camera above the top plane looking down sends no
+ascending ray into it) is not swept.  The part volume that takes a part is
+the one whose part is needed again last, assuming the next render repeats
+this one's order, never the one rendered just before (whose render may still
+run): the parts a render starts with stay resident from one render to the
+next, and every load overlaps the renders of earlier parts.  All rendering
+runs in the library's kernels; this module is host-side control.
 """
 from __future__ import annotations
 
@@ -27,23 +32,64 @@ from .api import MODES, Volume, render_init
 from ._lib import VR_COMPOSITE
 
 
-def sweeps(cams: np.ndarray, w: int, h: int):
+def sweeps(cams: np.ndarray, w: int, h: int, dims=None):
     """The sweeps a view set needs: +1 when some ray may go up in z (or be
-    level), -1 when some ray may go down.  The height component of a ray's
-    direction is an affine function of the pixel position, so its extremes
-    are at the image corners; a margin keeps near-level rays in both."""
+    level), -1 when some ray may go down.  The height components of a ray's
+    direction and (orthographic views) origin are affine functions of the
+    pixel position, so their extremes are at the image corners; a margin
+    keeps near-level rays in both.  With ``dims`` (nx, ny, nz), a direction
+    is left out when every ray going that way starts beyond the box's face
+    in that direction (heights above nz - 1 going up, below 0 going down):
+    such a ray never enters the cube (the ray-box test gives it no sample)."""
     need_up = need_down = False
+    corners = [(u, v) for u in (0.5 - w / 2.0, w / 2.0 - 0.5) for v in (0.5 - h / 2.0, h / 2.0 - 0.5)]
     for c in np.asarray(cams):
-        fz = float(c["fwd"][2])
+        fz, ez = float(c["fwd"][2]), float(c["eye"][2])
+        duz, dvz = float(c["du"][2]), float(c["dv"][2])
         if int(c["proj"]) == 0:
             dz = [fz]
+            oz = [ez + u * duz + v * dvz for u, v in corners]
         else:
-            dz = [fz + u * float(c["du"][2]) + v * float(c["dv"][2])
-                  for u in (0.5 - w / 2.0, w / 2.0 - 0.5) for v in (0.5 - h / 2.0, h / 2.0 - 0.5)]
+            dz = [fz + u * duz + v * dvz for u, v in corners]
+            oz = [ez]
         scale = max(1e-30, max(abs(x) for x in dz), float(np.abs(c["fwd"]).max()))
-        need_up |= max(dz) >= -1e-5 * scale
-        need_down |= min(dz) < 1e-5 * scale
+        up = max(dz) >= -1e-5 * scale
+        down = min(dz) < 1e-5 * scale
+        if dims is not None:
+            # FP32 rounding of the origins: a relative margin of their terms
+            tol = 1e-5 * (1.0 + abs(ez) + (w / 2.0) * abs(duz) + (h / 2.0) * abs(dvz))
+            up = up and min(oz) <= float(dims[2]) - 1.0 + tol
+            down = down and max(oz) >= -tol
+        need_up |= up
+        need_down |= down
     return ([1] if need_up else []) + ([-1] if need_down else [])
+
+
+def pick_volume(holds, last_use, order, n):
+    """The part volume that takes visit ``n``'s part (``order``: the parts'
+    z_first of a render's visits, in order; ``holds``: the z_first each part
+    volume holds, or None; ``last_use``: when each was last rendered, larger
+    = later).  The volume rendered last is never taken (its render may still
+    be running, so a load into it would wait for it); of the others, an
+    empty one, else the one whose part is needed again latest: in the rest of
+    this render, then in the next, assumed to repeat this order (ties: the
+    one used least recently)."""
+    future = list(order[n + 1:]) + list(order)
+    never = len(future) + 1
+
+    def next_use(z):
+        if z is None:
+            return never + 1
+        try:
+            return future.index(z)
+        except ValueError:
+            return never
+
+    cands = list(range(len(holds)))
+    if len(cands) > 1:
+        newest = max(cands, key=lambda j: last_use[j])
+        cands.remove(newest)
+    return max(cands, key=lambda j: (next_use(holds[j]), -last_use[j]))
 
 
 @dataclass
@@ -75,9 +121,12 @@ class PartStream:
     same images) and ``masks`` empty-space masks, built for the clip at each
     part's upload (faster compositing, the same images; a lower clip later
     reloads the parts).  ``cache_parts`` part
-    volumes (at least two, at most one per part) stay on the device; with
-    the sweeps' order (ascending, then descending, then ascending again) a
-    render loads 2 (parts - cache_parts) parts once the cache is warm.
+    volumes (at least two, at most one per part) stay on the device
+    (``pick_volume`` decides which takes a part); two sweeps load
+    2 (parts - cache_parts) parts a render once the cache is warm; one sweep
+    keeps the parts it starts with and loads about parts - cache_parts + 1
+    (varying from render to render in a short cycle; all parts with two
+    volumes).
     Device memory: one brick buffer and one staging buffer of a part, and
     ``cache_parts`` textures of a part."""
 
@@ -177,16 +226,16 @@ class PartStream:
         for mode, out in targets:
             render_init(out, mode, stream)
         step_order = []
-        for sw in sweeps(cams, w, h):
+        for sw in sweeps(cams, w, h, self.dims):
             order = self.parts if sw > 0 else self.parts[::-1]
             step_order += [(sw, p) for p in order]
+        visits = [p.z_first for _, p in step_order]
         for n, (sw, part) in enumerate(step_order):
             held = [i for i, z in enumerate(self.holds) if z == part.z_first]
             if held:
                 i = held[0]
             else:
-                # the volume used least recently (never the one just queued)
-                i = min(range(len(self.vols)), key=lambda j: self.last_use[j])
+                i = pick_volume(self.holds, self.last_use, visits, n)
                 self._load(i, part)
             self.uses += 1
             self.last_use[i] = self.uses

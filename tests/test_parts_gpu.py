@@ -76,7 +76,7 @@ def test_part_cache_keeps_parts_resident_between_renders(store, cache):
                     cache_parts=cache)
     n_parts = len(ps.parts)
     assert len(ps.vols) == min(max(2, cache), n_parts)
-    assert len(sweeps(cams, w, h)) == 2
+    assert len(sweeps(cams, w, h, dims)) == 2
     ps.set_transfer(lut, *tf)
     outs = [(m, torch.empty(ref[m].shape, dtype=torch.float32, device="cuda")) for m in MODES]
     for r in range(3):
@@ -159,7 +159,7 @@ def test_parts_from_pinned_host_memory_and_one_way_views():
     # orthographic views along -z and +z: one sweep each
     down = synth.cameras([synth.axis_camera(dims, w, h, axis=2, sign=-1)])
     up = synth.cameras([synth.axis_camera(dims, w, h, axis=2, sign=1)])
-    assert sweeps(down, w, h) == [-1] and sweeps(up, w, h) == [1]
+    assert sweeps(down, w, h, dims) == [-1] and sweeps(up, w, h, dims) == [1]
     lut = synth.default_lut(32)
     for cams in (down, up, np.concatenate([down, up])):
         ref, n_ref = _one_pass(cube, "f32", False, cams, w, h, 0.5, lut, (1.0, 8.0, 1.0, 0.9))
@@ -172,7 +172,7 @@ def test_parts_from_pinned_host_memory_and_one_way_views():
         assert torch.equal(out, ref["composite"])
         # each part is loaded once per sweep, except that the second sweep
         # starts with the parts the two part volumes still hold
-        n_sweeps = len(sweeps(cams, w, h))
+        n_sweeps = len(sweeps(cams, w, h, dims))
         loads = len(ps.parts) * n_sweeps - (n_sweeps - 1) * min(len(ps.vols), len(ps.parts))
         assert ps.bytes_loaded == loads * 17 * 40 * 48 * 4
         ps.close()
