@@ -159,6 +159,7 @@ int vr_set_transfer(vr_volume vol, const float* rgba_lut, int n, float v_lo,
  * and item 4: one image per view at the output resolution).
  *   cams         host array of n_views cameras; copied, may be freed on
  *                return.
+ *   n_views, w, h  at least 1 each (VR_ERR_ARG for an empty image set).
  *   mode         VR_MIP / VR_COMPOSITE / VR_SUM.
  *   step         sample spacing in voxel lengths, > 0, and small enough
  *                that no ray takes 2^24 samples or more.
@@ -354,8 +355,9 @@ size_t vr_batch_workspace_bytes(void);
  * VR_BATCH_MAX requests (also split when a launch would need more than 8
  * textured volumes or 2 distinct opacity-corrected tables; requests on
  * volumes without texture storage and on volumes with it go to separate
- * launches).  Every request is checked before anything is enqueued, so an
- * argument error leaves the stream untouched.  Each
+ * launches); n = 0 enqueues nothing and returns VR_OK.  Every request is
+ * checked before anything is enqueued, so an argument error leaves the
+ * stream untouched.  Each
  * block takes the next ray tile from a work counter in `workspace`
  * (caller-owned device memory of vr_batch_workspace_bytes(), 16-byte
  * aligned; zeroed on the stream by this call) and renders it with the same

@@ -154,6 +154,9 @@ def test_batch_argument_errors(scene):
     small = torch.empty(8, dtype=torch.uint8, device="cuda")
     with pytest.raises(VRError):
         render_batch([Request(v, cam, 8, 8, "mip", 0.5)], workspace=small)
+    # an empty batch is no work, not an error
+    assert render_batch([]) == []
+    torch.cuda.synchronize()
     # a bad request after good ones of another launch class: nothing is
     # enqueued (the good request's image keeps its old contents)
     good = torch.full((8, 8), float("nan"), device="cuda")

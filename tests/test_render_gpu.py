@@ -473,6 +473,10 @@ def test_argument_errors_raise():
         vol.set_transfer(synth.default_lut(), 1.0, 1.0, 0)
     with pytest.raises(ValueError):
         vol.render(cams, 8, 8, "mip", 0.5, out=torch.empty(2, 8, 8, device="cuda"))
+    # an empty image set: no views, or images without pixels
+    for n, w, h in ((0, 8, 8), (1, 0, 8), (1, 8, 0)):
+        with pytest.raises(VRError):
+            vol.render(cams[:n], w, h, "composite", 0.5)
 
 
 def test_brick_buffer_too_small_is_rejected():
