@@ -178,7 +178,8 @@ int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w,
                       unsigned long long* d_samples, void* stream);
 
 /* Bytes of the volume's empty-space masks: 8 bytes per macrocell of
- * 4 x 4 x 4 cells, (nx/4 + 1) * (ny/4 + 1) * ((nz-2)/4 + 1) macrocells.
+ * 4 x 4 x 4 cells, (nx/4 + 1) * (ny/4 + 1) * (nz/4 + 1) macrocells (integer
+ * division; the gather coordinates 0 .. n of every axis, four per macrocell).
  * Host-only; no device work.                                                */
 int vr_volume_mask_bytes(vr_volume vol, size_t* bytes_out);
 
@@ -270,9 +271,12 @@ int vr_volume_detach_mip_bounds(vr_volume vol);
  * call itself does no device work).  For volumes with texture storage
  * (an int8 texture carries its planes' scales and offsets).  Afterwards the
  * volume is read-only:
- * vr_volume_upload, vr_volume_detach_texture, vr_volume_attach_masks and a
- * change of texture format return VR_ERR_UNSUPPORTED; its empty-space masks
- * are detached.  No counterpart in the paper: it keeps cubes resident whose
+ * vr_volume_upload, vr_volume_detach_texture, vr_volume_attach_masks (other
+ * than detaching) and a change of texture format return VR_ERR_UNSUPPORTED.
+ * Empty-space masks already built stay, frozen at the clip level they were
+ * built for: COMPOSITE renders at that clip or above use them, lower clips
+ * render without them (nothing can rebuild them); masks never built are
+ * detached.  No counterpart in the paper: it keeps cubes resident whose
  * bricks and texture would not both fit, e.g. several 32 GiB FP16 cubes.    */
 int vr_volume_drop_bricks(vr_volume vol);
 

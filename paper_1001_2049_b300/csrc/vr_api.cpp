@@ -203,11 +203,17 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
 // Composite renders with empty-space masks need masks built for a clip level
 // at or below the volume's clip (a cell that can reach the clip can reach
 // any lower one, so masks for a lower clip are conservative): rebuild them
-// (on the render's stream) when the clip has dropped below it.
-int ensure_masks(vr::Volume* v, int mode, cudaStream_t s)
+// (on the render's stream) when the clip has dropped below it.  A volume
+// whose bricks were dropped keeps the masks built before, frozen: a clip
+// below their level renders without them (p->mask cleared).
+int ensure_masks(vr::Volume* v, int mode, cudaStream_t s, vr::MarchParams* p)
 {
     if (!v->mask || mode != VR_COMPOSITE) return VR_OK;
     if (!std::isnan(v->mask_clip) && !(v->clip < v->mask_clip)) return VR_OK;
+    if (v->texture_only) {
+        p->mask = nullptr;
+        return VR_OK;
+    }
     cudaError_t e = vr::launch_masks(*v, v->clip, s);
     if (e != cudaSuccess) return cuda_fail(e, "mask launch");
     v->mask_clip = v->clip;
@@ -240,7 +246,7 @@ int render_impl(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
     int rc = prepare(vol, cams, n_views, w, h, mode, step, out, d_samples, &p, &tp);
     if (rc) return rc;
     vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
-    rc = ensure_masks(v, mode, static_cast<cudaStream_t>(stream));
+    rc = ensure_masks(v, mode, static_cast<cudaStream_t>(stream), &p);
     if (rc) return rc;
     return launch_views(v, p, tp, mode, v->cfg[mode], cams, n_views, out,
                         static_cast<cudaStream_t>(stream));
@@ -907,7 +913,7 @@ int vr_volume_drop_bricks(vr_volume vol)
     if (!v->has_tex) return fail(VR_ERR_UNSUPPORTED, "the volume has no texture storage");
     v->texture_only = true;
     v->bricks = nullptr;
-    v->mask = nullptr;
+    if (std::isnan(v->mask_clip)) v->mask = nullptr;   // never built: nothing to keep
     return VR_OK;
 }
 
@@ -1172,7 +1178,7 @@ int vr_autotune(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
         if (best_ms) *best_ms = -1.0f;
         return VR_OK;
     }
-    rc = ensure_masks(v, mode, s);
+    rc = ensure_masks(v, mode, s, &p);
     if (rc) return rc;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");

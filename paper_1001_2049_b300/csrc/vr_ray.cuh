@@ -401,6 +401,27 @@ struct Acc {
 };
 
 // ---- empty-space skipping ----
+// The macrocell of sample kf and its cell's bit there, from the gather
+// coordinates (cell + 1 on every axis: in [0, n] for positions inside the box
+// up to rounding).  The index is clamped to the mask array: the look-ahead
+// samples past a ray's end, and positions of cameras so far away that
+// rounding moves them by a voxel, may lie outside, and their bits are never
+// used.  (A function rather than a lambda, so that it is inlined in every
+// kernel that marches with masks, the batched one included.)
+// z_base: the first plane of a part volume (its masks cover its own planes).
+template <typename PP>
+__device__ __forceinline__ int mask_cell(const PP& P, const Ray& r, float kf, int& bit,
+                                         int z_base = 0)
+{
+    const float t = fmaf(kf, P.step, r.te);
+    const int x = __float2int_rd(fmaf(t, r.dx, r.ox)) + 1;
+    const int y = __float2int_rd(fmaf(t, r.dy, r.oy)) + 1;
+    const int z = __float2int_rd(fmaf(t, r.dz, r.oz)) + 1 - z_base;
+    bit = (x & 3) | ((y & 3) << 2) | ((z & 3) << 4);
+    const int i = ((z >> kMacroShift) * P.mny + (y >> kMacroShift)) * P.mnx + (x >> kMacroShift);
+    return (int)min((unsigned)i, (unsigned)P.mlast);
+}
+
 // march_tex with empty-space skipping in lockstep (COMPOSITE): every lane
 // steps through its samples at the same pace as without skipping (the
 // warp's rays stay side by side, so their gathers share cache lines), but a
@@ -421,25 +442,10 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
     // the mask test needs only a sample's cell (integer floors of its
     // position); the full geometry (weights, gather coordinates) is computed
     // for the samples a lane needs, one sample ahead of their interpolation.
-    // mcell: the macrocell of sample kf and its cell's bit there, from the
-    // gather coordinates (cell + 1 on every axis: in [0, n] for positions
-    // inside the box up to rounding).  The index is clamped to the mask
-    // array: the look-ahead samples past a ray's end, and positions of
-    // cameras so far away that rounding moves them by a voxel, may lie
-    // outside, and their bits are never used.
-    auto mcell = [&](float kf, int& bit) {
-        const float t = fmaf(kf, P.step, r.te);
-        const int x = __float2int_rd(fmaf(t, r.dx, r.ox)) + 1;
-        const int y = __float2int_rd(fmaf(t, r.dy, r.oy)) + 1;
-        const int z = __float2int_rd(fmaf(t, r.dz, r.oz)) + 1;
-        bit = (x & 3) | ((y & 3) << 2) | ((z & 3) << 4);
-        const int i = ((z >> kMacroShift) * P.mny + (y >> kMacroShift)) * P.mnx + (x >> kMacroShift);
-        return (int)min((unsigned)i, (unsigned)P.mlast);
-    };
     int k = 0;
     int b0, b1, b2;
-    const int m0 = mcell(0.0f, b0);
-    int m1 = mcell(1.0f, b1), m2;
+    const int m0 = mask_cell(P, r, 0.0f, b0);
+    int m1 = mask_cell(P, r, 1.0f, b1), m2;
     const Rec r0 = __ldg(P.mask + m0);
     Rec r1 = (m1 == m0) ? r0 : __ldg(P.mask + m1), r2;
     bool n0 = acc.need(r0, b0), n1;
@@ -452,7 +458,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
     float kf = 0.0f;
     for (;;) {
         // sample k + 2: cell and mask word; sample k + 1: geometry, gathers
-        m2 = mcell(kf + 2.0f, b2);
+        m2 = mask_cell(P, r, kf + 2.0f, b2);
         r2 = (m2 == m1) ? r1 : __ldg(P.mask + m2);
         n1 = acc.need(r1, b1);
         if (n1) {
@@ -466,7 +472,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
         if ((n0 && acc.add(P, lut, interp_t<DT, false>(T, a0, a1, g0))) || k >= r.K) break;
         kf += 1.0f;
         // the same one sample further on, the register sets swapped
-        m1 = mcell(kf + 2.0f, b1);
+        m1 = mask_cell(P, r, kf + 2.0f, b1);
         r1 = (m1 == m2) ? r2 : __ldg(P.mask + m1);
         n0 = acc.need(r2, b2);
         if (n0) {
@@ -674,18 +680,8 @@ __device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
     using Rec = unsigned long long;
     if (k0 >= k1) return 0;
     const cudaTextureObject_t t0 = T.tex;
-    // the macrocell of sample kf and its cell's bit there, in the part's
-    // gather coordinates (clamped to the mask array: look-ahead samples past
-    // the range lie outside the part)
-    auto mcell = [&](float kf, int& bit) {
-        const float t = fmaf(kf, P.step, r.te);
-        const int x = __float2int_rd(fmaf(t, r.dx, r.ox)) + 1;
-        const int y = __float2int_rd(fmaf(t, r.dy, r.oy)) + 1;
-        const int z = __float2int_rd(fmaf(t, r.dz, r.oz)) + 1 - P.slice_base;
-        bit = (x & 3) | ((y & 3) << 2) | ((z & 3) << 4);
-        const int i = ((z >> kMacroShift) * P.mny + (y >> kMacroShift)) * P.mnx + (x >> kMacroShift);
-        return (int)min((unsigned)i, (unsigned)P.mlast);
-    };
+    // mask_cell in the part's gather coordinates (clamped to the mask array:
+    // look-ahead samples past the range lie outside the part)
     auto part_geo = [&](float kf) {
         Geo g = geo(P, r, kf);
         g.iz -= P.slice_base;
@@ -694,8 +690,8 @@ __device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
     int k = k0;
     float kf = (float)k0;
     int b0, b1, b2;
-    const int m0 = mcell(kf, b0);
-    int m1 = mcell(kf + 1.0f, b1), m2;
+    const int m0 = mask_cell(P, r, kf, b0, P.slice_base);
+    int m1 = mask_cell(P, r, kf + 1.0f, b1, P.slice_base), m2;
     const Rec r0 = __ldg(P.mask + m0);
     Rec r1 = (m1 == m0) ? r0 : __ldg(P.mask + m1), r2;
     bool n0 = acc.need(r0, b0), n1;
@@ -706,7 +702,7 @@ __device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
         cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
     }
     for (;;) {
-        m2 = mcell(kf + 2.0f, b2);
+        m2 = mask_cell(P, r, kf + 2.0f, b2, P.slice_base);
         r2 = (m2 == m1) ? r1 : __ldg(P.mask + m2);
         n1 = acc.need(r1, b1);
         if (n1) {
@@ -719,7 +715,7 @@ __device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
         ++k;
         if ((n0 && acc.add(P, lut, interp_t<DT, false>(T, a0, a1, g0))) || k >= k1) break;
         kf += 1.0f;
-        m1 = mcell(kf + 2.0f, b1);
+        m1 = mask_cell(P, r, kf + 2.0f, b1, P.slice_base);
         r1 = (m1 == m2) ? r2 : __ldg(P.mask + m1);
         n0 = acc.need(r2, b2);
         if (n0) {

@@ -202,3 +202,41 @@ def test_every_batch_shape_gives_identical_images(scene):
             set_batch_config(len(shapes))
     finally:
         set_batch_config(saved)
+
+
+def test_batch_on_masked_volumes_equals_renders_without():
+    # batched launches march every sample (the lockstep march over the masks
+    # measured slower there); requests on volumes with built masks, at clips
+    # below, at and above the masks' level, give the images of mask-free
+    # twin volumes bit for bit, and so do the twins' per-view renders
+    specs = [((40, 36, 50), "f32", False), ((33, 45, 70), "f16", True),
+             ((30, 30, 2100), "i8", False), ((35, 30, 2200), "f16", True)]
+    lut = synth.default_lut()
+    masked, twins = [], []
+    for i, (dims, dt, pair) in enumerate(specs):
+        cube = synth.make_cube(dims, 6, ("uniform", 3.0, 9.0), 300 + i).cuda()
+        for out in (masked, twins):
+            v = Volume(cube, dt)
+            v.attach_pair_texture() if pair else v.attach_texture()
+            v.set_transfer(lut, 2.0, 9.0, 2.0, 0.97)
+            out.append((v, dims))
+        masked[-1][0].attach_masks()
+        masked[-1][0].build_masks()
+    rng = np.random.default_rng(17)
+    reqs, twin_reqs = [], []
+    for i in range(24):
+        (v, dims), (t, _) = masked[i % len(masked)], twins[i % len(twins)]
+        w, h = (int(x) for x in rng.integers(9, 48, 2))
+        cam = synth.random_sphere_cameras(dims, 1, w, h, 900 + i)[0]
+        mode = "mip" if i % 6 == 5 else "composite"
+        clip = [1.5, 2.0, 3.0, 2.5][i % 4]          # 1.5: below the masks' level
+        tf = (lut, clip, 9.0, clip, 0.95)
+        reqs.append(Request(v, cam, w, h, mode, 0.5, tf=tf))
+        twin_reqs.append(Request(t, cam, w, h, mode, 0.5, tf=tf))
+    ref = render_batch(twin_reqs)
+    got = render_batch(reqs)
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(zip(got, ref)):
+        assert torch.equal(a, b), (k, reqs[k].mode, reqs[k].tf[1])
+    for rq, img in zip(twin_reqs[:8], ref[:8]):
+        assert torch.equal(single(rq), img)

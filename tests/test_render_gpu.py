@@ -12,7 +12,7 @@ import torch
 
 import oracle
 from oracle import quantize
-from paper_1001_2049_b300 import Volume, VRError, synth
+from paper_1001_2049_b300 import Request, Volume, VRError, render_batch, synth
 from paper_1001_2049_b300.api import volume_bytes
 
 from _util import TOL_FP32, TOL_PREC, bands_for, compare, sum_scale
@@ -499,6 +499,11 @@ def test_texture_only_volume_after_dropping_bricks():
     for dtype, pair in (("f32", False), ("f16", False), ("i8", False), ("i8", True)):
         vol = Volume(torch.from_numpy(cube).cuda(), dtype)
         vol.attach_pair_texture() if pair else vol.attach_texture()
+        # a mask-free twin: the images at a clip below the masks' level
+        twin = Volume(torch.from_numpy(cube).cuda(), dtype)
+        twin.attach_pair_texture() if pair else twin.attach_texture()
+        twin.set_transfer(lut, 0.6, 8.0, 0.6, 0.95)
+        low = twin.render(cams, 21, 17, "composite", 0.5).cpu()
         vol.attach_masks()
         vol.set_transfer(lut, 1.0, 8.0, 1.0, 0.95)
         before = {m: vol.render(cams, 21, 17, m, 0.5).cpu() for m in ("composite", "mip")}
@@ -506,6 +511,18 @@ def test_texture_only_volume_after_dropping_bricks():
         assert vol.buffer is None
         for m in ("composite", "mip"):
             assert torch.equal(vol.render(cams, 21, 17, m, 0.5).cpu(), before[m])
+        # the masks built for clip 1 stay, frozen: a lower clip renders
+        # without them (they would drop its samples between 0.6 and 1), a
+        # batch too, and the clip they were built for uses them again
+        vol.set_transfer(lut, 0.6, 8.0, 0.6, 0.95)
+        assert torch.equal(vol.render(cams, 21, 17, "composite", 0.5).cpu(), low)
+        got = render_batch([Request(vol, c, 21, 17, "composite", 0.5) for c in cams])
+        assert all(torch.equal(g.cpu(), low[i]) for i, g in enumerate(got))
+        vol.set_transfer(lut, 1.0, 8.0, 1.0, 0.95)
+        assert torch.equal(vol.render(cams, 21, 17, "composite", 0.5).cpu(), before["composite"])
+        got = render_batch([Request(vol, c, 21, 17, "composite", 0.5) for c in cams])
+        assert all(torch.equal(g.cpu(), before["composite"][i]) for i, g in enumerate(got))
+        twin.close()
         with pytest.raises(VRError):
             vol.upload(0, torch.from_numpy(cube[:2]).cuda())
         with pytest.raises(VRError):
