@@ -358,8 +358,10 @@ size_t vr_batch_workspace_bytes(void);
  * modes and transfer functions -- with one persistent kernel launch per
  * VR_BATCH_MAX requests (also split when a launch would need more than 8
  * textured volumes or 2 distinct opacity-corrected tables; requests on
- * volumes without texture storage and on volumes with it go to separate
- * launches); n = 0 enqueues nothing and returns VR_OK.  Every request is
+ * volumes with pair-texel texture storage, with plain texture storage and
+ * without texture storage go to separate launches, in that order, each
+ * kernel keeping the warps resident that its registers allow); n = 0
+ * enqueues nothing and returns VR_OK.  Every request is
  * checked before anything is enqueued, so an argument error leaves the
  * stream untouched.  Each
  * block takes the next ray tile from a work counter in `workspace`

@@ -378,13 +378,16 @@ int batch_request(const vr_request& rq, vr::BatchParams* B, int* n_tex, vr::Volu
     return VR_OK;
 }
 
-// A launch holds requests of one storage kind (texture or bricks), so that
-// each kernel instance compiles one fetch path: textured requests go first,
-// then the others, each group split into launches as its slots fill.
+// A launch holds requests of one class (pair texels, plain texels, bricks),
+// so that each kernel instance compiles one fetch path and keeps the warps
+// its registers allow: the classes go in that order, each split into
+// launches as its slots fill.
 int batch_class(const vr_request& r)
 {
     const vr::Volume* v = reinterpret_cast<const vr::Volume*>(r.vol);
-    return v && v->has_tex ? vr::kBatchTex : vr::kBatchBricks;
+    if (!v || !v->has_tex) return vr::kBatchBricks;
+    const bool pair = v->tex_format == vr::kF16Pair || v->tex_format == vr::kI8Pair;
+    return pair ? vr::kBatchTexPair : vr::kBatchTex;
 }
 
 // Tile and ray-packet shape of the batched launches (process-wide; set by
@@ -396,11 +399,11 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s, int 
     // persistent grid: as many blocks as fit on the current device at once
     // (cached per device, class and shape)
     constexpr int kDevices = 64;
-    static std::atomic<int> grid[kDevices][2][vr::kNumBatchShapes];
+    static std::atomic<int> grid[kDevices][vr::kNumBatchClasses][vr::kNumBatchShapes];
     int dev = 0;
     cudaGetDevice(&dev);
-    int g[2];
-    for (int c = 0; c < 2; ++c) {
+    int g[vr::kNumBatchClasses];
+    for (int c = 0; c < vr::kNumBatchClasses; ++c) {
         g[c] = dev >= 0 && dev < kDevices ? grid[dev][c][cfg].load() : 0;
         if (g[c] == 0) {
             int sms = 0;
@@ -419,8 +422,9 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s, int 
     vr::BatchParams* B = new (std::nothrow) vr::BatchParams;
     if (!B) return fail(VR_ERR_OOM, "out of host memory");
     int rc = VR_OK;
-    const int order[2] = {vr::kBatchTex, vr::kBatchBricks};
-    for (int oi = 0; oi < 2 && rc == VR_OK; ++oi) {
+    const int order[vr::kNumBatchClasses] = {vr::kBatchTexPair, vr::kBatchTex,
+                                             vr::kBatchBricks};
+    for (int oi = 0; oi < vr::kNumBatchClasses && rc == VR_OK; ++oi) {
         const int cls = order[oi];
         int i = 0;
         while (rc == VR_OK) {

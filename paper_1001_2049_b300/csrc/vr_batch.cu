@@ -23,6 +23,12 @@ constexpr int kThreads = 256;             // one ray per thread, a tile per bloc
 #ifndef VR_BATCH_MIN_BLOCKS
 #define VR_BATCH_MIN_BLOCKS 4     // resident blocks per SM the registers must allow
 #endif
+// Pair texels hold half the corner registers: six blocks (48 warps) per SM,
+// measured faster than four for both modes (a 1024^3 FP16 pair cube, 32 views
+// of 1024^2: 65 -> 56 ms).
+#ifndef VR_BATCH_PAIR_MIN_BLOCKS
+#define VR_BATCH_PAIR_MIN_BLOCKS 6
+#endif
 
 // Find the request whose items contain `item` (first_item ascending).
 __device__ __forceinline__ int find_request(const BatchParams& B, int item)
@@ -123,33 +129,43 @@ __host__ __device__ constexpr int tex_kind(int format, int mode, bool stack)
     return (format * 3 + mode) * 2 + (stack ? 1 : 0);
 }
 
-// One switch over the kinds (uniform over the block: a tile belongs to one
-// request); each case is the specialised march of one kind.
+// One switch over the kinds of a launch class (uniform over the block: a
+// tile belongs to one request); each case is the specialised march of one
+// kind.  PAIR: the pair texel formats, else the plain ones.
+template <bool PAIR>
 __device__ __forceinline__ unsigned tex_pixel_any(const BatchReq& q, const BatchTex& T,
                                                   const float4* __restrict__ lut, int px, int py)
 {
-    switch (tex_kind(T.format, q.mode, T.stack_shift > 0)) {
 #define VR_KIND(F, M)                                                              \
     case tex_kind(F, M, false): return tex_pixel<F, M, false>(q, T, lut, px, py);  \
     case tex_kind(F, M, true): return tex_pixel<F, M, true>(q, T, lut, px, py);
 #define VR_FORMAT(F) VR_KIND(F, VR_MIP) VR_KIND(F, VR_COMPOSITE) VR_KIND(F, VR_SUM)
-        VR_FORMAT(VR_F32)
-        VR_FORMAT(VR_F16)
-        VR_FORMAT(VR_I8)
-        VR_FORMAT(kF16Pair)
-        VR_FORMAT(kI8Pair)
+    if constexpr (PAIR) {
+        switch (tex_kind(T.format, q.mode, T.stack_shift > 0)) {
+            VR_FORMAT(kF16Pair)
+            VR_FORMAT(kI8Pair)
+        default: return 0;
+        }
+    } else {
+        switch (tex_kind(T.format, q.mode, T.stack_shift > 0)) {
+            VR_FORMAT(VR_F32)
+            VR_FORMAT(VR_F16)
+            VR_FORMAT(VR_I8)
+        default: return 0;
+        }
+    }
 #undef VR_FORMAT
 #undef VR_KIND
-    default: return 0;
-    }
 }
 
 // CLS (BatchClass): every request of the launch is of one class, so each
 // kernel instance compiles one fetch path: bricks (run-time storage type) or
-// texture (specialised per kind).  CFG: the tile and ray-packet shape
+// texture (specialised per kind), plain and pair texel formats apart.  CFG: the tile and ray-packet shape
 // (kBatchShapes), chosen by vr_batch_autotune.
 template <int CLS, int CFG>
-__global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(const __grid_constant__ BatchParams B,
+__global__ void __launch_bounds__(kThreads, CLS == kBatchTexPair ? VR_BATCH_PAIR_MIN_BLOCKS
+                                                                 : VR_BATCH_MIN_BLOCKS)
+    batch_kernel(const __grid_constant__ BatchParams B,
                                                          unsigned* __restrict__ ws)
 {
     constexpr BatchShape S = kBatchShapes[CFG];
@@ -185,8 +201,8 @@ __global__ void __launch_bounds__(kThreads, VR_BATCH_MIN_BLOCKS) batch_kernel(co
         const int py = ty * S.ty + (warp / wpr) * S.py + (lane / S.px);
         unsigned count = 0;
         if (px < q.w && py < q.h) {
-            if constexpr (CLS == kBatchTex) {
-                count = tex_pixel_any(q, B.tex[q.tex_slot], s_lut, px, py);
+            if constexpr (CLS == kBatchTex || CLS == kBatchTexPair) {
+                count = tex_pixel_any<CLS == kBatchTexPair>(q, B.tex[q.tex_slot], s_lut, px, py);
             } else {
                 const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
                 AccRT acc(q.mode);
@@ -224,8 +240,9 @@ namespace {
 template <int CFG>
 const void* kernel_of_shape(int cls)
 {
-    return cls == kBatchTex ? reinterpret_cast<const void*>(batch_kernel<kBatchTex, CFG>)
-                            : reinterpret_cast<const void*>(batch_kernel<kBatchBricks, CFG>);
+    return cls == kBatchTex       ? reinterpret_cast<const void*>(batch_kernel<kBatchTex, CFG>)
+           : cls == kBatchTexPair ? reinterpret_cast<const void*>(batch_kernel<kBatchTexPair, CFG>)
+                                  : reinterpret_cast<const void*>(batch_kernel<kBatchBricks, CFG>);
 }
 
 const void* batch_kernel_of(int cls, int cfg)

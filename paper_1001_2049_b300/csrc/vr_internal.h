@@ -166,9 +166,11 @@ struct BatchParams {
     float4 lut[kMaxBatchLut][VR_MAX_LUT];
 };
 
-// Launch classes of the batched kernel: requests on volumes without texture
-// storage and on volumes with it, each compiled as its own kernel.
-enum BatchClass { kBatchBricks = 0, kBatchTex = 1 };
+// Launch classes of the batched kernel, each compiled as its own kernel:
+// requests on volumes without texture storage, on volumes with plain texel
+// formats and with pair texels (which need fewer registers, so that class
+// keeps more warps resident).
+enum BatchClass { kBatchBricks = 0, kBatchTex = 1, kBatchTexPair = 2, kNumBatchClasses = 3 };
 // Tile and ray-packet shapes of the batched kernel (the batch autotuner's
 // search space): a tile of tx x ty rays (one block of 256 threads) whose
 // warps hold px x py packets of neighbouring rays.
