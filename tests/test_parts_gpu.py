@@ -152,6 +152,60 @@ def test_parts_with_masks_give_the_one_pass_images(store, dims, part_planes, cac
     ps.close()
 
 
+@pytest.mark.parametrize("cache,masks", [(3, False), (4, True), (2, False)])
+def test_views_from_above_take_one_sweep_and_keep_the_first_parts(cache, masks):
+    # orbit cameras above the cube: their ascending rays never enter it, so
+    # one descending sweep serves them; the part volumes keep the parts a
+    # sweep starts with, so repeated renders load fewer parts than the
+    # least recently used choice would (all of them), with the images and
+    # counts of one pass every time
+    from paper_1001_2049_b300.stream import pick_volume
+    dims = (31, 27, 96)
+    cube = synth.make_cube(dims, 5, ("uniform", 3.0, 8.0), 140 + cache)
+    w, h, step = 33, 21, 0.5
+    cams = synth.orbit_cameras(dims, 6, w, h, elev_deg=20.0)
+    assert sweeps(cams, w, h) == [1, -1] and sweeps(cams, w, h, dims) == [-1]
+    lut = synth.default_lut(64)
+    tf = (1.5, 8.0, 1.5, 0.95)
+    ref, n_ref = _one_pass(cube, "f32", False, cams, w, h, step, lut, tf)
+    host = cube.pin_memory()
+    ps = PartStream(dims, "f32", lambda z0, n: host[z0:z0 + n], 13, cache_parts=cache,
+                    bounds=True, masks=masks)
+    ps.set_transfer(lut, *tf)
+    n_parts, n_vols = len(ps.parts), len(ps.vols)
+    # the host model of the volume choice over the same visits
+    visits = [p.z_first for p in ps.parts[::-1]]
+    holds, last, uses, expect = [None] * n_vols, [-1] * n_vols, 0, []
+    for _ in range(4):
+        loads = 0
+        for k, z in enumerate(visits):
+            if z in holds:
+                i = holds.index(z)
+            else:
+                i = pick_volume(holds, last, visits, k)
+                holds[i] = z
+                loads += 1
+            uses += 1
+            last[i] = uses
+        expect.append(loads)
+    outs = [(m, torch.empty(ref[m].shape, dtype=torch.float32, device="cuda")) for m in MODES]
+    got = []
+    for r in range(4):
+        before = ps.parts_loaded
+        n = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ps.render(cams, w, h, outs, step, count=n)
+        torch.cuda.synchronize()
+        for m, out in outs:
+            assert torch.equal(out, ref[m]), (cache, masks, r, m)
+        assert int(n.item()) == n_ref
+        got.append(ps.parts_loaded - before)
+    assert got == expect
+    assert got[0] == n_parts
+    if n_vols > 2:
+        assert max(got[1:]) < n_parts
+    ps.close()
+
+
 def test_parts_from_pinned_host_memory_and_one_way_views():
     dims = (48, 40, 96)
     cube = synth.make_cube(dims, 4, ("uniform", 3.0, 8.0), 91).pin_memory()
