@@ -476,6 +476,181 @@ int vro_render(const vro_volume* vol, const vro_camera* cams, int n_views, int w
     return bad ? -1 : 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* sub-cubes rendered independently, then integrated                    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The paper's pipeline splits the cube into sub-cubes, renders each into its
+ * own partial image and combines the partial images (§3.1 items 1, 4, 5;
+ * the garbled "scene integration" sentence is read as combining the partial
+ * images by the compositing operator in visibility order).  Here sub-cube i
+ * owns the cells [cell_lo[i], cell_lo[i+1]) along z (the last one up to
+ * n_z - 1); a sample belongs to the sub-cube of its cell, floor(z) of its
+ * position before clamping (the first sub-cube also takes heights below 0,
+ * the last those above).  Each sub-cube's partial result starts empty and
+ * sees only its own samples, in the ray's order; a composite partial stops
+ * once its own alpha reaches term_alpha.  The partial results are combined
+ * in the order the ray meets the sub-cubes: "over" for composite,
+ *   C += (1 - A) C_i,  A += (1 - A) A_i,
+ * max for MIP, addition for SUM.  Without termination this is the one-pass
+ * result (the operator is associative); with it, a ray may pass an opaque
+ * sub-cube's partial and keep contributions behind it, attenuated.
+ * The primary FP64 result only; flags: bit 0 K tie, bit 1 clip tie, bit 2
+ * termination tie (a partial's alpha within band_a of term_alpha), bit 4 a
+ * sample within rounding of a sub-cube boundary plane (2^-20 of the
+ * position's magnitude plus band_pos).
+ */
+static int segment_of(double z, const int64_t* cell_lo, int n_sub)
+{
+    double c = floor(z);
+    int i = 0;
+    while (i + 1 < n_sub && c >= (double)cell_lo[i + 1]) ++i;
+    return i;
+}
+
+static void render_pixel_subcubes(const vro_volume* vol, const vro_camera* cam, int w, int h,
+                                  int px, int py, int mode, double step, const vro_tf* tf,
+                                  const double* lutc, const vro_bands* b,
+                                  const int64_t* cell_lo, int n_sub, double res[4],
+                                  int* flags, double* segC, double* segA, double* segV,
+                                  int* done, int* order)
+{
+    double o[3], d[3];
+    make_ray(cam, w, h, px, py, o, d);
+    double tn, tf_, miss_dist, face_dist;
+    slab(o, d, vol->n, &tn, &tf_, &miss_dist, &face_dist);
+    double t_entry = tn > 0.0 ? tn : 0.0;
+    double q = (tf_ - t_entry) / step;
+    int hit = miss_dist == 0.0 && tf_ >= t_entry;
+    int64_t K = 0;
+    *flags = 0;
+    if (hit) {
+        double fl = floor(q);
+        K = (int64_t)fl + 1;
+        if (q - fl < b->band_k || q - fl > 1.0 - b->band_k || face_dist <= b->band_pos)
+            *flags |= 1;
+    } else if (miss_dist <= b->band_pos && q >= -b->band_k) {
+        *flags |= 1;
+    }
+    double clip_rgba[4];
+    classify(tf, lutc, tf->clip, clip_rgba);
+    int n_order = 0;
+    for (int i = 0; i < n_sub; ++i) {
+        segC[3 * i] = segC[3 * i + 1] = segC[3 * i + 2] = 0.0;
+        segA[i] = 0.0;
+        segV[i] = mode == VRO_MIP ? -INFINITY : 0.0;
+        done[i] = 0;
+    }
+    for (int64_t k = 0; k < K; ++k) {
+        double t = t_entry + (double)k * step;
+        double z = o[2] + t * d[2];
+        int i = segment_of(z, cell_lo, n_sub);
+        for (int j = 1; j < n_sub; ++j) {
+            double bz = (double)cell_lo[j];
+            if (fabs(z - bz) <= ldexp(fabs(o[2]) + fabs(t) + fabs(z) + 1.0, -20) + b->band_pos)
+                *flags |= 16;
+        }
+        if (n_order == 0 || order[n_order - 1] != i) order[n_order++] = i;
+        double s = sample(vol, o, d, t);
+        if (mode == VRO_MIP) {
+            if (s > segV[i]) segV[i] = s;
+            continue;
+        }
+        if (mode == VRO_SUM) {
+            segV[i] += s * step;
+            continue;
+        }
+        if (done[i]) continue;
+        if (clip_rgba[3] > 0.0 && fabs(s - tf->clip) <= b->band_clip * fmax(1.0, fabs(s)))
+            *flags |= 2;
+        if (s < tf->clip) continue;
+        double rgba[4];
+        classify(tf, lutc, s, rgba);
+        double wgt = (1.0 - segA[i]) * rgba[3];
+        for (int c = 0; c < 3; ++c) segC[3 * i + c] += wgt * rgba[c];
+        segA[i] += wgt;
+        if (fabs(segA[i] - tf->term_alpha) <= b->band_a) *flags |= 4;
+        if (segA[i] >= tf->term_alpha) done[i] = 1;
+    }
+    res[0] = res[1] = res[2] = res[3] = 0.0;
+    if (mode == VRO_MIP) {
+        res[0] = -INFINITY;
+        for (int a = 0; a < n_order; ++a)
+            if (segV[order[a]] > res[0]) res[0] = segV[order[a]];
+    } else if (mode == VRO_SUM) {
+        for (int a = 0; a < n_order; ++a) res[0] += segV[order[a]];
+    } else {
+        for (int a = 0; a < n_order; ++a) {
+            int i = order[a];
+            double T = 1.0 - res[3];
+            for (int c = 0; c < 3; ++c) res[c] += T * segC[3 * i + c];
+            res[3] += T * segA[i];
+        }
+    }
+}
+
+/*
+ * Render a list of pixels (as vro_render) as n_sub sub-cubes rendered
+ * independently and integrated; cell_lo[0] must be 0 and cell_lo ascending
+ * below n_z - 1.  out[i*4 + c]: channel c of pixel i (MIP and SUM: channel
+ * 0).  Returns 0, or -1 on bad arguments.
+ */
+int vro_render_subcubes(const vro_volume* vol, const vro_camera* cams, int n_views, int w,
+                        int h, int mode, double step, const vro_tf* tf,
+                        const vro_bands* bands, const int64_t* cell_lo, int n_sub,
+                        const int32_t* pix, int64_t npix, double* out, int32_t* flags,
+                        int nthreads)
+{
+    if (!vol || !cams || !tf || !bands || !cell_lo || !pix || !out || !flags) return -1;
+    if (vol->n[0] < 2 || vol->n[1] < 2 || vol->n[2] < 2 || !(step > 0.0) ||
+        tf->n_lut < 2 || w <= 0 || h <= 0 || n_views <= 0 || n_sub < 1)
+        return -1;
+    if (mode != VRO_MIP && mode != VRO_COMPOSITE && mode != VRO_SUM) return -1;
+    if (cell_lo[0] != 0) return -1;
+    for (int i = 1; i < n_sub; ++i)
+        if (!(cell_lo[i] > cell_lo[i - 1]) || cell_lo[i] >= vol->n[2] - 1) return -1;
+    double* lutc = (double*)malloc(sizeof(double) * 4 * (size_t)tf->n_lut);
+    if (!lutc) return -1;
+    correct_table(tf, step, lutc);
+    int bad = 0;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel num_threads(nt) reduction(| : bad)
+#endif
+    {
+        double* segC = (double*)malloc(sizeof(double) * 3 * (size_t)n_sub);
+        double* segA = (double*)malloc(sizeof(double) * (size_t)n_sub);
+        double* segV = (double*)malloc(sizeof(double) * (size_t)n_sub);
+        int* done = (int*)malloc(sizeof(int) * (size_t)n_sub);
+        int* order = (int*)malloc(sizeof(int) * (size_t)n_sub);
+        if (!segC || !segA || !segV || !done || !order) bad = 1;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t i = 0; i < npix; ++i) {
+            int view = pix[3 * i], px = pix[3 * i + 1], py = pix[3 * i + 2];
+            if (bad || view < 0 || view >= n_views || px < 0 || px >= w || py < 0 || py >= h) {
+                bad = 1;
+                continue;
+            }
+            int fl = 0;
+            render_pixel_subcubes(vol, &cams[view], w, h, px, py, mode, step, tf, lutc,
+                                  bands, cell_lo, n_sub, &out[4 * i], &fl, segC, segA, segV,
+                                  done, order);
+            flags[i] = fl;
+        }
+        free(segC);
+        free(segA);
+        free(segV);
+        free(done);
+        free(order);
+    }
+    (void)nthreads;
+    free(lutc);
+    return bad ? -1 : 0;
+}
+
 /* Exposed pieces for the oracle's own tests: one trilinear sample at a point
  * and the corrected table entry for a value.                             */
 double vro_sample_at(const vro_volume* vol, double x, double y, double z)
