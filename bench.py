@@ -488,6 +488,7 @@ def out_of_core_leg(cube, cams, W, H, wl, lut, comp_ref, mip_ref, part_planes=12
         loaded.append(ps.bytes_loaded - b0)
         parts.append(ps.parts_loaded - p0)
     same = same and bool(torch.equal(comp, comp_ref) and torch.equal(mip, mip_ref))
+    sub = subcube_leg(ps, cams, W, H, wl, comp, mip, comp_ref, mip_ref, reps)
     res = {"parts": len(ps.parts), "planes_per_part": ps.planes,
            "cache_parts": len(ps.vols), "mip_bounds": True, "empty_space_masks": True,
            "sweeps": len(sweeps(cams, W, H, wl.dims)),
@@ -496,10 +497,50 @@ def out_of_core_leg(cube, cams, W, H, wl, lut, comp_ref, mip_ref, part_planes=12
            "part_loads_per_step": sum(parts) / len(parts),
            "host_bytes_read_per_step": sum(loaded) / len(loaded),
            "device_bytes_for_the_cube": ps.device_bytes(),
-           "cube_bytes": cube.numel() * 4, "images_identical_to_resident": same}
+           "cube_bytes": cube.numel() * 4, "images_identical_to_resident": same,
+           "subcubes": sub}
     ps.close()
     del host
     return res
+
+
+def subcube_leg(ps, cams, W, H, wl, comp, mip, comp_ref, mip_ref, reps):
+    """The paper's own pipeline on the same part cache: every part rendered
+    on its own into partial images (any order, each loaded at most once),
+    then the partial images integrated per pixel in each ray's order.  MIP
+    is the resident image bit for bit; composite differs where a part
+    reaches the termination alpha (each part stops at its own opacity).
+    The integration kernel is also timed alone on a partial image set of
+    this size: it reads every partial image once and writes one image."""
+    from paper_1001_2049_b300 import integrate_partials
+    targets = [("composite", comp), ("mip", mip)]
+    ps.render_subcubes(cams, W, H, targets, wl.step)
+    torch.cuda.synchronize()
+    times, loads = [], []
+    for _ in range(reps):
+        p0 = ps.parts_loaded
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ps.render_subcubes(cams, W, H, targets, wl.step)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        loads.append(ps.parts_loaded - p0)
+    mip_same = bool(torch.equal(mip, mip_ref))
+    dA = float((comp[..., 3] - comp_ref[..., 3]).abs().max().item())
+    n_parts = len(ps.parts)
+    partials = torch.zeros((n_parts,) + tuple(comp.shape), device=comp.device)
+    stream = torch.cuda.current_stream()
+    integrate_partials(partials, cams, "composite", out=comp)
+    ms = event_ms(lambda: integrate_partials(partials, cams, "composite", out=comp), 5, stream)
+    nbytes = (n_parts + 1) * comp.numel() * 4
+    del partials
+    torch.cuda.empty_cache()
+    return {"ms_per_step": 1000.0 * sum(times) / len(times),
+            "part_loads_per_step": sum(loads) / len(loads),
+            "mip_identical_to_resident": mip_same,
+            "composite_max_alpha_difference_to_resident": dA,
+            "integrate_composite_ms": ms, "integrate_bytes": nbytes,
+            "integrate_gb_s": nbytes / ms / 1e6}
 
 
 def _served_volume(i, dt, dev):

@@ -163,7 +163,8 @@ int vr_set_transfer(vr_volume vol, const float* rgba_lut, int n, float v_lo,
  *   mode         VR_MIP / VR_COMPOSITE / VR_SUM.
  *   step         sample spacing in voxel lengths, > 0, and small enough
  *                that no ray takes 2^24 samples or more.
- *   out          device memory, 16-byte aligned: view-major, then row py,
+ *   out          device memory, 16-byte aligned for COMPOSITE (4-byte for
+ *                MIP and SUM): view-major, then row py,
  *                then column px; 1 float per pixel (MIP, SUM) or 4 floats
  *                (COMPOSITE: premultiplied r, g, b, A).
  *   stream       cudaStream_t as void*.                                     */
@@ -311,7 +312,9 @@ int vr_render_init(float* out, int n_views, int w, int h, int mode, void* stream
  *                cell_lo = 0 also takes positions a rounding error below
  *                plane 0, cell_hi = nz - 1 those above the top plane.  The
  *                parts' ranges must tile [0, nz - 1).
- *   sweep        +1: rays with dz >= 0; -1: rays with dz < 0.
+ *   sweep        +1: rays with dz >= 0; -1: rays with dz < 0; 0: every
+ *                ray (a sub-cube's partial image, see
+ *                vr_integrate_partials).
  *   out          images as left by vr_render_init or earlier parts.
  *   d_samples    optional count of evaluated samples (added to).
  * Other arguments as in vr_render.  COMPOSITE rays that terminated in an
@@ -320,6 +323,33 @@ int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
                    int64_t cell_lo, int64_t cell_hi, const vr_camera* cams, int n_views,
                    int w, int h, int mode, float step, int sweep, float* out,
                    unsigned long long* d_samples, void* stream);
+
+/* Scene integration (paper §3.1 items 4, 5: each sub-cube rendered into its
+ * own image, the images combined; read as the compositing operator applied
+ * in visibility order).  Each sub-cube's partial image is its part's
+ * vr_render_part with sweep 0 into images fresh from vr_render_init, so the
+ * parts can be rendered in any order, or on different streams; this call
+ * combines them, per pixel, in the order the pixel's ray meets them
+ * (ascending z when its direction's height component is >= 0, computed as
+ * vr_render computes it; descending otherwise):
+ *   COMPOSITE  C += (1 - A) C_i, A += (1 - A) A_i  (premultiplied RGBA)
+ *   MIP        the maximum;  SUM  the sum.
+ * Without early termination (term_alpha > 1) the result equals the
+ * one-pass image up to FP32 rounding (the operator is associative); with
+ * it, each sub-cube stops at its own opacity, so a ray keeps, attenuated,
+ * what lies behind an opaque sub-cube.
+ *   partials     device memory, aligned as vr_render's `out`: n_parts image sets in
+ *                sub-cube order (ascending z), each laid out as vr_render's
+ *                `out` for n_views views of w x h (1 or 4 floats a pixel).
+ *   cams         the n_views cameras the partial images were rendered with
+ *                (host, copied).
+ *   out          device memory, aligned as vr_render's `out`, one image set; it must not
+ *                overlap `partials` (VR_ERR_ARG).
+ * Asynchronous on `stream`; an HBM-bound kernel reading every partial image
+ * once.  VR_ERR_ARG for null, misaligned or non-device pointers, n_parts <
+ * 1, an empty image set, an unknown mode or a bad camera.                   */
+int vr_integrate_partials(const float* partials, int n_parts, const vr_camera* cams,
+                          int n_views, int w, int h, int mode, float* out, void* stream);
 
 /* ---- many requests in one persistent launch ------------------------------
  * The paper's scheduler maps available tasks onto the computing resources
@@ -341,7 +371,7 @@ typedef struct {
     vr_camera cam;               /* one view                                   */
     int32_t w, h, mode;          /* image size; VR_MIP / VR_COMPOSITE / VR_SUM  */
     float step;
-    float* out;                  /* device, 16-byte aligned, one view          */
+    float* out;                  /* device, aligned as vr_render's, one view   */
     const vr_transfer* tf;       /* host; NULL: the volume's transfer function */
     unsigned long long* samples; /* optional device counter (8-byte aligned):
                                     the evaluated samples are added to it      */

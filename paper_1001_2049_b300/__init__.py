@@ -9,6 +9,6 @@ continuous-batching server (``serve``) and part-by-part streaming of cubes
 larger than the device (``stream``).
 """
 from .api import (CAMERA_DTYPE, DTYPES, MODES, Request, Volume, batch_autotune,  # noqa: F401
-                  batch_shapes, batch_workspace, get_batch_config, render_batch, render_init,
-                  set_batch_config, volume_bytes)
+                  batch_shapes, batch_workspace, get_batch_config, integrate_partials,
+                  render_batch, render_init, set_batch_config, volume_bytes)
 from ._lib import VRError, load  # noqa: F401

@@ -41,6 +41,8 @@ SIGNATURES = {
     "vr_volume_detach_mip_bounds": (c_int, [c_void_p]),
     "vr_volume_drop_bricks": (c_int, [c_void_p]),
     "vr_render_init": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p]),
+    "vr_integrate_partials": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_int, c_int,
+                                      c_void_p, c_void_p]),
     "vr_render_part": (c_int, [c_void_p, ctypes.POINTER(c_int64), c_int64, c_int64, c_int64,
                                c_void_p, c_int, c_int, c_int, c_int, c_float, c_int, c_void_p,
                                c_void_p, c_void_p]),

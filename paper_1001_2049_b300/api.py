@@ -84,6 +84,30 @@ def render_init(out: torch.Tensor, mode: str, stream=None) -> torch.Tensor:
     return out
 
 
+def integrate_partials(partials: torch.Tensor, cams: np.ndarray, mode: str,
+                       out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Scene integration: ``partials`` (parts, views, h, w[, 4]), the
+    sub-cubes' partial images in ascending z, combined per pixel in the
+    order its ray meets them ("over" for composite, max for MIP, sum for
+    SUM) into ``out`` (views, h, w[, 4])."""
+    cams = np.ascontiguousarray(cams)
+    m = MODES[mode]
+    if partials.dtype != torch.float32 or not partials.is_contiguous() or not partials.is_cuda:
+        raise ValueError("partials must be a contiguous float32 CUDA tensor")
+    shape = tuple(partials.shape[1:])
+    if len(shape) != (4 if m == VR_COMPOSITE else 3) or shape[0] != len(cams):
+        raise ValueError("partials must be (parts, views, h, w%s)" % (", 4" if m == VR_COMPOSITE
+                                                                      else ""))
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=partials.device)
+    elif tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 tensor of shape %s" % (shape,))
+    views, h, w = shape[:3]
+    check(load().vr_integrate_partials(partials.data_ptr(), partials.shape[0], cams.ctypes.data,
+                                       views, w, h, m, out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
 def batch_workspace(device=None) -> torch.Tensor:
     n = load().vr_batch_workspace_bytes()
     return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
@@ -349,7 +373,8 @@ class Volume:
         """This volume holds planes [z_first, z_first + nz) of a cube of
         ``full_dims``: continue ``out`` (from render_init or earlier parts)
         with the samples of cells [cell_lo, cell_hi) of the rays going up
-        (sweep +1) or down (sweep -1)."""
+        (sweep +1), down (sweep -1) or both (0: a partial image for
+        integrate_partials)."""
         cams = np.ascontiguousarray(cams)
         m = MODES[mode]
         shape = (len(cams), h, w, 4) if m == VR_COMPOSITE else (len(cams), h, w)

@@ -92,6 +92,10 @@ const void* host_to_device_ptr(const void* p)
     return a.devicePointer;
 }
 
+// Images are written a pixel at a time: 16-byte stores of RGBA for
+// COMPOSITE, 4-byte stores for MIP and SUM.
+int out_alignment(int mode) { return mode == VR_COMPOSITE ? 16 : 4; }
+
 bool finite3(const float v[3])
 {
     return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
@@ -143,8 +147,8 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
     if (diag / step + 2.0 >= 16777216.0)
         return fail(VR_ERR_ARG, "step %g too small: a ray could take 2^24 samples", (double)step);
     if (!out) return fail(VR_ERR_ARG, "out is NULL");
-    if (reinterpret_cast<uintptr_t>(out) % 16 != 0)
-        return fail(VR_ERR_ARG, "out must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(out) % out_alignment(mode) != 0)
+        return fail(VR_ERR_ARG, "out must be %d-byte aligned", out_alignment(mode));
     if (!is_device_ptr(out)) return fail(VR_ERR_ARG, "out is not device memory of this device");
     if (d_samples) {
         if (reinterpret_cast<uintptr_t>(d_samples) % 8 != 0)
@@ -927,12 +931,58 @@ int vr_render_init(float* out, int n_views, int w, int h, int mode, void* stream
     if (n_views < 1 || w < 1 || h < 1) return fail(VR_ERR_ARG, "empty image set");
     if (mode != VR_MIP && mode != VR_COMPOSITE && mode != VR_SUM)
         return fail(VR_ERR_ARG, "unknown mode %d", mode);
-    if (reinterpret_cast<uintptr_t>(out) % 16 != 0)
-        return fail(VR_ERR_ARG, "out must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(out) % out_alignment(mode) != 0)
+        return fail(VR_ERR_ARG, "out must be %d-byte aligned", out_alignment(mode));
     if (!is_device_ptr(out)) return fail(VR_ERR_ARG, "out is not device memory of this device");
     cudaError_t e = vr::launch_render_init(out, (size_t)n_views * w * h, mode,
                                            static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? VR_OK : cuda_fail(e, "init launch");
+}
+
+int vr_integrate_partials(const float* partials, int n_parts, const vr_camera* cams,
+                          int n_views, int w, int h, int mode, float* out, void* stream)
+{
+    if (!partials || !out) return fail(VR_ERR_ARG, "partials or out is NULL");
+    if (!cams) return fail(VR_ERR_ARG, "cams is NULL");
+    if (n_parts < 1) return fail(VR_ERR_ARG, "n_parts = %d < 1", n_parts);
+    if (n_views < 1 || w < 1 || h < 1 || w > 65536 || h > 65536)
+        return fail(VR_ERR_ARG, "image set %d x %d x %d is empty or too large", n_views, w, h);
+    if (mode != VR_MIP && mode != VR_COMPOSITE && mode != VR_SUM)
+        return fail(VR_ERR_ARG, "unknown mode %d", mode);
+    if (reinterpret_cast<uintptr_t>(partials) % out_alignment(mode) != 0 ||
+        reinterpret_cast<uintptr_t>(out) % out_alignment(mode) != 0)
+        return fail(VR_ERR_ARG, "partials and out must be %d-byte aligned", out_alignment(mode));
+    if (!is_device_ptr(partials) || !is_device_ptr(out))
+        return fail(VR_ERR_ARG, "partials and out must be device memory of this device");
+    const size_t pixels = (size_t)n_views * w * h;
+    const size_t ch = mode == VR_COMPOSITE ? 4 : 1;
+    const float* p_end = partials + pixels * ch * (size_t)n_parts;
+    if (out < p_end && partials < out + pixels * ch)
+        return fail(VR_ERR_ARG, "out overlaps the partial images");
+    for (int i = 0; i < n_views; ++i) {
+        const vr_camera& c = cams[i];
+        if (c.proj != VR_ORTHO && c.proj != VR_PERSP)
+            return fail(VR_ERR_ARG, "camera %d: unknown projection %d", i, c.proj);
+        if (!finite3(c.eye) || !finite3(c.fwd) || !finite3(c.du) || !finite3(c.dv))
+            return fail(VR_ERR_ARG, "camera %d: non-finite parameters", i);
+    }
+    vr::IntegrateParams p;
+    std::memset(&p, 0, sizeof p);
+    p.n_parts = n_parts;
+    p.w = w;
+    p.h = h;
+    p.part_stride = pixels;
+    const size_t per_view = (size_t)w * h * ch;
+    for (int v0 = 0; v0 < n_views; v0 += vr::kMaxViewsPerLaunch) {
+        const int nv = std::min(vr::kMaxViewsPerLaunch, n_views - v0);
+        p.n_views = nv;
+        std::memcpy(p.cams, cams + v0, sizeof(vr_camera) * nv);
+        p.partials = partials + per_view * v0;
+        p.out = out + per_view * v0;
+        cudaError_t e = vr::launch_integrate(p, mode, static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "integration launch");
+    }
+    return VR_OK;
 }
 
 int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
@@ -953,7 +1003,8 @@ int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
         return fail(VR_ERR_ARG, "cells [%lld, %lld) are not within the part's planes [%lld, %lld]",
                     (long long)cell_lo, (long long)cell_hi, (long long)z_first,
                     (long long)(z_first + v->g.nz - 1));
-    if (sweep != 1 && sweep != -1) return fail(VR_ERR_ARG, "sweep must be +1 or -1");
+    if (sweep != 1 && sweep != -1 && sweep != 0)
+        return fail(VR_ERR_ARG, "sweep must be +1, -1 or 0");
     vr::MarchParams p;
     vr::TexParams tp;
     int rc = prepare(part, cams, n_views, w, h, mode, step, out, d_samples, &p, &tp);

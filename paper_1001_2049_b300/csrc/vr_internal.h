@@ -210,6 +210,16 @@ bool plan_slab(const MarchParams& p, SlabConfig* c);
 cudaError_t launch_tex(const MarchParams& p, const TexParams& t, int format, int mode, int cfg,
                        cudaStream_t s);
 // Render one part of a larger cube, continuing the images in p.out.
+// Scene integration of sub-cubes' partial images (vr_integrate.cu).
+struct IntegrateParams {
+    const float* partials;   // the views' first pixel in sub-cube 0's partial images
+    float* out;
+    size_t part_stride;      // pixels from one sub-cube's partial images to the next's
+    int n_parts, n_views, w, h;
+    vr_camera cams[kMaxViewsPerLaunch];
+};
+cudaError_t launch_integrate(const IntegrateParams& p, int mode, cudaStream_t s);
+
 cudaError_t launch_part(const MarchParams& p, const TexParams& t, int format, int mode,
                         cudaStream_t s);
 cudaError_t launch_part_f32(const MarchParams& p, const TexParams& t, int mode, cudaStream_t s);

@@ -61,6 +61,17 @@ struct Ray {
     int K;
 };
 
+// The height component of a pixel's ray direction before normalisation,
+// computed as setup_ray computes it: the ray goes up (or is level) exactly
+// when it is >= 0, as setup_ray's r.dz.
+__device__ __forceinline__ float ray_dz_raw(const vr_camera& c, int w, int h, int px, int py)
+{
+    if (c.proj == VR_ORTHO) return c.fwd[2];
+    const float u = ((float)px + 0.5f) - 0.5f * (float)w;
+    const float v = ((float)py + 0.5f) - 0.5f * (float)h;
+    return fmaf(v, c.dv[2], fmaf(u, c.du[2], c.fwd[2]));
+}
+
 // Camera -> ray -> box -> sample count K (0 for a miss or a degenerate
 // direction).  PP supplies w, h, hix, hiy, hiz and step.
 template <typename PP>

@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(MASKED ? 128 : 256, MASKED ? 8 : 5)
     int k0 = 0, k1 = 0;
     if (px < P.w && py < P.h) {
         r = ray::setup_ray(P, P.cams[view], px, py, T.k_max);
-        const bool mine = P.sweep > 0 ? r.dz >= 0.0f : r.dz < 0.0f;
+        // sweep 0: every ray (a partial image rendered on its own)
+        const bool mine = P.sweep == 0 || (P.sweep > 0 ? r.dz >= 0.0f : r.dz < 0.0f);
         if (r.K > 0 && mine && ray::may_cross_part(P, r)) {
             pix = ((size_t)view * P.h + py) * P.w + px;
             bool done = false;

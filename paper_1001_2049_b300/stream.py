@@ -28,7 +28,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from .api import MODES, Volume, render_init
+from .api import MODES, Volume, integrate_partials, render_init
 from ._lib import VR_COMPOSITE
 
 
@@ -247,6 +247,50 @@ class PartStream:
                                          cams, w, h, mode, step, sw, out, count=count,
                                          stream=stream)
             self.done[i].record(stream)
+        return targets
+
+    def render_subcubes(self, cams: np.ndarray, w: int, h: int, targets, step: float = 0.5,
+                        count: torch.Tensor | None = None, stream=None):
+        """The paper's sub-cube pipeline (§3.1 items 1, 4, 5): every part
+        rendered on its own into a partial image set (vr_render_part with
+        sweep 0 from an empty start, so the parts go in any order: here the
+        held ones first, each loaded at most once), then the partial images
+        integrated per pixel in the order its ray meets the parts
+        (vr_integrate_partials).  ``targets`` as in render.  Without early
+        termination the images are the one-pass ones up to FP32 rounding;
+        with it, each part stops at its own opacity.  Device memory: one
+        partial image set per part and target."""
+        stream = stream or torch.cuda.current_stream(self.device)
+        cams = np.ascontiguousarray(cams)
+        parts = sorted(range(len(self.parts)),
+                       key=lambda j: self.parts[j].z_first not in self.holds)
+        partials = []
+        for mode, out in targets:
+            pt = torch.empty((len(self.parts),) + tuple(out.shape), dtype=torch.float32,
+                             device=out.device)
+            render_init(pt.view((-1,) + tuple(out.shape[1:])), mode, stream)
+            partials.append(pt)
+        visits = [self.parts[j].z_first for j in parts]
+        for n, j in enumerate(parts):
+            part = self.parts[j]
+            held = [i for i, z in enumerate(self.holds) if z == part.z_first]
+            if held:
+                i = held[0]
+            else:
+                i = pick_volume(self.holds, self.last_use, visits, n)
+                self._load(i, part)
+            self.uses += 1
+            self.last_use[i] = self.uses
+            loaded = torch.cuda.Event()
+            loaded.record(self.copy)
+            stream.wait_event(loaded)
+            for (mode, _), pt in zip(targets, partials):
+                self.vols[i].render_part(self.dims, part.z_first, part.cell_lo, part.cell_hi,
+                                         cams, w, h, mode, step, 0, pt[j], count=count,
+                                         stream=stream)
+            self.done[i].record(stream)
+        for (mode, out), pt in zip(targets, partials):
+            integrate_partials(pt, cams, mode, out=out, stream=stream)
         return targets
 
     def close(self):

@@ -247,5 +247,5 @@ def test_part_arguments_are_checked():
     with pytest.raises(VRError):          # planes beyond the cube
         part.render_part((16, 16, 15), 10, 10, 14, cams, 8, 8, "mip", 0.5, 1, out)
     with pytest.raises(VRError):
-        part.render_part(dims, 10, 10, 19, cams, 8, 8, "mip", 0.5, 0, out)
+        part.render_part(dims, 10, 10, 19, cams, 8, 8, "mip", 0.5, 2, out)
     part.render_part(dims, 10, 10, 19, cams, 8, 8, "mip", 0.5, 1, out)
