@@ -145,3 +145,29 @@ def test_integration_arguments_are_checked():
     bad[0]["fwd"][2] = np.nan
     with pytest.raises(VRError):
         integrate_partials(parts, bad, "composite")
+
+
+def test_subcubes_with_masks_and_bounds_are_bit_identical():
+    # empty-space masks (composite) and MIP bounds (FP32 MIP) change only the
+    # work of the partial renders, so the integrated images are those of the
+    # same pipeline without them, bit for bit
+    dims = (33, 31, 65)
+    cube, cams = _case(dims, 61)
+    w, h, step = 23, 17, 0.5
+    lut = synth.default_lut(64, alpha_max=0.8)
+    tf = (2.0, 8.0, 2.0, 0.9)
+    dev = torch.from_numpy(cube).cuda()
+    imgs = []
+    for extra in (False, True):
+        ps = PartStream(dims, "f32", lambda z0, n: dev[z0:z0 + n], 17, cache_parts=2,
+                        bounds=extra, masks=extra)
+        ps.set_transfer(lut, *tf)
+        outs = [(m, torch.empty((len(cams), h, w, 4) if m == "composite" else (len(cams), h, w),
+                                device="cuda")) for m in ("composite", "mip")]
+        ps.render_subcubes(cams, w, h, outs, step)
+        ps.render_subcubes(cams, w, h, outs, step)          # with the cache warm
+        torch.cuda.synchronize()
+        imgs.append([o.clone() for _, o in outs])
+        ps.close()
+    for a, b in zip(*imgs):
+        assert torch.equal(a, b)
