@@ -118,13 +118,13 @@ class Clocks:
 # (one pass: dram__bytes_read.sum + dram__bytes_write.sum;
 # profiles/tex_kernel_f32_cube1024_orbit32.md): MIP at launch shape 2 150.31
 # GB read + 0.42 GB written; MIP with the binary16 MIP bounds at shape 6
-# 88.64 + 0.27 GB; composite with the empty-space masks at shape 7 31.99 +
+# 88.62 + 0.27 GB; composite with the empty-space masks at shape 7 32.01 +
 # 1.29 GB.
 # Other workloads (the --cube-edge/--views cases) report them scaled by their
 # algorithmic bytes.
 MEASURED_TRAFFIC = {"mip": 150.305302e9 + 0.415848e9,
-                    "mip_bounds": 88.642216e9 + 0.267677e9,
-                    "composite_masks": 31.987687e9 + 1.288413e9}
+                    "mip_bounds": 88.621030e9 + 0.267783e9,
+                    "composite_masks": 32.006811e9 + 1.289451e9}
 MEASURED_ALGORITHMIC = {"mip": 136229959936.0, "mip_bounds": 136229959936.0,
                         "composite_masks": 136433374037.6}
 
