@@ -331,6 +331,17 @@ def aggregate_ranks(samples, elapsed, dist=None, device=None):
     return float(s.item()), float(e.item())
 
 
+def run_leg(fn):
+    """One secondary leg of the line: its figures, or the error that ended
+    it (recorded in the line, so that the headline measured before it is
+    still reported)."""
+    try:
+        return fn()
+    except Exception as e:             # noqa: BLE001 -- reported, not hidden
+        torch.cuda.empty_cache()
+        return {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+
+
 def event_ms(fn, reps, stream):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -846,20 +857,20 @@ def main():
         extra = {}
         if not args.no_extra and W == 1920:
             if args.storage == "texture" and not args.no_masks:
-                extra["tf_edit"] = tf_edit_leg(vol, cams, W, H, wl, lut)
+                extra["tf_edit"] = run_leg(lambda: tf_edit_leg(vol, cams, W, H, wl, lut))
             if args.storage == "texture":
                 vol.close()
                 torch.cuda.empty_cache()
-                r = out_of_core_leg(cube, cams, W, H, wl, lut, comp, mip)
+                r = run_leg(lambda: out_of_core_leg(cube, cams, W, H, wl, lut, comp, mip))
                 r["resident_ms_per_step"] = comp_ms + mip_ms
                 extra["out_of_core"] = r
             del comp, mip, host_comp, host_mip
             vol.close()
             del vol, cube
             torch.cuda.empty_cache()
-            extra["batched"] = batched_leg(dev)
+            extra["batched"] = run_leg(lambda: batched_leg(dev))
             torch.cuda.empty_cache()
-            extra["serving"] = serving_leg(dev)
+            extra["serving"] = run_leg(lambda: serving_leg(dev))
         result = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
