@@ -171,3 +171,33 @@ def test_subcubes_with_masks_and_bounds_are_bit_identical():
         ps.close()
     for a, b in zip(*imgs):
         assert torch.equal(a, b)
+
+
+def test_integration_spans_several_launches_of_views():
+    # more views than one launch carries (64 cameras): each view's partials
+    # hold values of its own, and every view comes out in its own order
+    w, h, n = 5, 3, 70
+    dims = (8, 6, 10)
+    recs = [synth.axis_camera(dims, w, h, axis=2, sign=1 if v % 2 == 0 else -1)
+            for v in range(n)]
+    cams = synth.cameras(recs)
+    view = torch.arange(n, dtype=torch.float32, device="cuda").reshape(n, 1, 1, 1)
+    front = torch.zeros((n, h, w, 4), device="cuda")
+    front[..., 3] = 0.5
+    front[..., 0] = 0.5 * view[..., 0] / n          # premultiplied red, per view
+    back = torch.zeros((n, h, w, 4), device="cuda")
+    back[..., 3] = 1.0
+    back[..., 2] = 1.0
+    parts = torch.stack([front, back]).contiguous()
+    out = integrate_partials(parts, cams, "composite")
+    torch.cuda.synchronize()
+    for v in range(n):
+        if v % 2 == 0:                               # up: the first partial in front
+            want = torch.tensor([0.5 * v / n, 0.0, 0.5, 1.0], device="cuda")
+        else:                                        # down: the opaque one in front
+            want = torch.tensor([0.0, 0.0, 1.0, 1.0], device="cuda")
+        assert torch.allclose(out[v], want.expand_as(out[v]), atol=1e-6), v
+    m = view.reshape(1, n, 1, 1).expand(2, n, h, w) * torch.tensor(
+        [1.0, -1.0], device="cuda").reshape(2, 1, 1, 1)
+    mip = integrate_partials(m.contiguous(), cams, "mip")
+    assert torch.equal(mip, view.reshape(n, 1, 1).expand(n, h, w))
