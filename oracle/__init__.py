@@ -58,7 +58,8 @@ class _TF(ctypes.Structure):
 
 class _Bands(ctypes.Structure):
     _fields_ = [("band_k", ctypes.c_double), ("band_pos", ctypes.c_double),
-                ("band_clip", ctypes.c_double), ("band_a", ctypes.c_double)]
+                ("band_clip", ctypes.c_double), ("band_a", ctypes.c_double),
+                ("band_t", ctypes.c_double)]
 
 
 _lib = None
@@ -80,7 +81,7 @@ def lib():
             ctypes.POINTER(_Volume), ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_TF),
             ctypes.POINTER(_Bands), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
-            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         _lib.vro_maxalt.restype = ctypes.c_int
         _lib.vro_num_threads.restype = ctypes.c_int
         _lib.vro_sample_at.restype = ctypes.c_double
@@ -161,11 +162,57 @@ class TF:
 
 @dataclass
 class Bands:
-    """Widths of the tie bands around the three discontinuities."""
+    """Widths of the tie bands around the three discontinuities (see the
+    header of ``vr_oracle.c``): ``band_k`` an absolute floor of the K band,
+    ``band_pos`` the absolute error of a ray origin, ``band_clip`` the
+    relative error of an interpolated value (per unit of its largest
+    |corner|), ``band_a`` the termination band in alpha, ``band_t`` the
+    relative error of a ray parameter t (0: the K band is band_k alone)."""
     band_k: float = 2e-3
     band_pos: float = 1e-5
     band_clip: float = 1e-4
     band_a: float = 1e-4
+    band_t: float = 0.0
+
+    def _c(self):
+        return _Bands(self.band_k, self.band_pos, self.band_clip, self.band_a, self.band_t)
+
+
+#: Units of 2^-24 (half an ulp at 1) of the rounding a single-precision
+#: evaluation of the definition makes, as the bands model it:
+#:  * a ray parameter t = (plane - o_a) / d_a: the division (1), the
+#:    direction component d_a from fwd + u du + v dv in two fused steps and
+#:    the normalisation (about 3 of |d| = 1, which the oracle divides by the
+#:    deciding |d_a|), the subtraction t_exit - t_entry (1), one of slack: 6;
+#:  * an orthographic origin eye + u du + v dv in two fused steps: 2 of the
+#:    largest term, doubled: 4;
+#:  * an interpolated value: three levels of lerps fma(f, b - a, a), each
+#:    rounding b - a and the fused step (3 of the largest |corner| per
+#:    level, 9 in all), the int8 decode of each plane's value (2 more),
+#:    rounded up: 16.
+FP32_T_UNITS = 6.0
+FP32_ORIGIN_UNITS = 4.0
+FP32_VALUE_UNITS = 16.0
+
+
+def fp32_bands(dims, cams, step, w=None, h=None, band_a=1e-4) -> "Bands":
+    """Tie bands for a single-precision evaluation of these views (see the
+    header of ``vr_oracle.c`` for how each band enters the decisions).
+
+    ``band_a`` is the termination band in alpha: a result whose alpha is
+    within the image tolerance of the oracle's can take the other
+    termination decision only where the oracle's alpha is within that
+    tolerance of the threshold, so the tests pass their tolerance (1e-4)."""
+    u = 2.0 ** -24
+    half = max(w or 0, h or 0) / 2.0 if (w or h) else 2.0 * max(dims)
+    scale = 1.0            # a perspective origin is the eye itself, exactly
+    for c in np.asarray(cams):
+        if int(c["proj"]) == 0:   # orthographic: eye + u du + v dv, rounded
+            scale = max(scale, float(np.abs(c["eye"]).max()) + 1.0
+                        + half * (float(np.abs(c["du"]).max()) + float(np.abs(c["dv"]).max())))
+    origin = FP32_ORIGIN_UNITS * u * scale
+    return Bands(band_k=2.0 ** -20, band_pos=origin, band_clip=FP32_VALUE_UNITS * u,
+                 band_a=band_a, band_t=FP32_T_UNITS * u)
 
 
 @dataclass
@@ -202,7 +249,7 @@ def render(volume: Volume, cams: np.ndarray, w: int, h: int, mode: int,
     nsam = np.zeros(npix, dtype=np.int64)
     cv, keep_v = volume._c()
     ct, keep_t = tf._c()
-    cb = _Bands(bands.band_k, bands.band_pos, bands.band_clip, bands.band_a)
+    cb = bands._c()
     rc = lib().vro_render(ctypes.byref(cv), cams.ctypes.data, n_views, w, h, mode,
                           float(step), ctypes.byref(ct), ctypes.byref(cb),
                           pixels.ctypes.data, npix, out.ctypes.data,
@@ -216,14 +263,15 @@ def render(volume: Volume, cams: np.ndarray, w: int, h: int, mode: int,
 
 def render_subcubes(volume: Volume, cams: np.ndarray, w: int, h: int, mode: int,
                     step: float, tf: TF, cell_lo, pixels: np.ndarray | None = None,
-                    bands: Bands | None = None, nthreads: int = 0):
+                    bands: Bands | None = None, nthreads: int = 0) -> Result:
     """The pixels rendered as sub-cubes (sub-cube i owns the cells
     [cell_lo[i], cell_lo[i+1]) along z; cell_lo[0] = 0), each into its own
     partial result from an empty start, combined in the order each ray meets
     them ("over" for composite, max for MIP, sum for SUM): the paper's
-    sub-cube pipeline (§3.1 items 1, 4, 5).  Returns (values (npix, 4)
-    float64, flags (npix,) int32: bit 0 K tie, 1 clip tie, 2 termination tie,
-    4 a sample on a sub-cube boundary plane up to rounding)."""
+    sub-cube pipeline (§3.1 items 1, 4, 5).  Returns a Result as ``render``
+    (``nsamples`` zero): the primary FP64 result and the alternatives of the
+    tie bands; flags bit 0 K tie, 1 clip tie, 2 termination tie, 3 list
+    truncated, 4 a sample on a sub-cube boundary plane up to rounding."""
     cams = np.ascontiguousarray(cams)
     assert cams.dtype.itemsize == 64
     n_views = cams.shape[0]
@@ -235,19 +283,22 @@ def render_subcubes(volume: Volume, cams: np.ndarray, w: int, h: int, mode: int,
     npix = pixels.shape[0]
     lo = np.ascontiguousarray(cell_lo, dtype=np.int64)
     bands = bands or Bands()
-    out = np.zeros((npix, 4), dtype=np.float64)
+    m = maxalt()
+    out = np.zeros((npix, m, 4), dtype=np.float64)
+    nalt = np.zeros(npix, dtype=np.int32)
     flags = np.zeros(npix, dtype=np.int32)
     cv, keep_v = volume._c()
     ct, keep_t = tf._c()
-    cb = _Bands(bands.band_k, bands.band_pos, bands.band_clip, bands.band_a)
+    cb = bands._c()
     rc = lib().vro_render_subcubes(ctypes.byref(cv), cams.ctypes.data, n_views, w, h, mode,
                                    float(step), ctypes.byref(ct), ctypes.byref(cb),
                                    lo.ctypes.data, int(lo.size), pixels.ctypes.data, npix,
-                                   out.ctypes.data, flags.ctypes.data, int(nthreads))
+                                   out.ctypes.data, nalt.ctypes.data, flags.ctypes.data,
+                                   int(nthreads))
     del keep_v, keep_t
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
-    return out, flags
+    return Result(out, nalt, flags, np.zeros(npix, dtype=np.int64))
 
 
 def sample_at(volume: Volume, x: float, y: float, z: float) -> float:

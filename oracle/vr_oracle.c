@@ -47,17 +47,34 @@
  * legitimately land on the other side of each.  For every pixel the oracle
  * therefore returns the primary double-precision result plus the results of
  * the alternative decisions whose deciding quantity lies within a stated band
- * of its threshold (bands are inputs; the tests state them):
- *   K band      (t_exit - t_entry)/step within band_k of an integer (this also
- *               covers near-miss / grazing rays, K = 0 <-> 1, and rays lying
- *               within band_pos of a face plane they are parallel to);
- *   clip band   |s - clip| <= band_clip * max(1, |s|) where the table's alpha
- *               at the clip level is non-zero (the sample's decision is
- *               flipped alone);
+ * of its threshold.  The bands are inputs (the tests state them) and model
+ * the rounding of a single-precision evaluation of the same definition:
+ *   band_t      relative error of a ray parameter t per unit |t| (division,
+ *               subtraction, the direction's rounding);
+ *   band_pos    absolute error of the ray origin (orthographic origins are
+ *               computed from the camera), per coordinate;
+ *   band_clip   relative error of an interpolated value, per unit of its
+ *               largest |corner|;
+ *   band_k      an absolute floor of the K band;
+ *   band_a      the termination band in alpha.
+ * From them, per ray:  a slab parameter t decided by axis a is uncertain by
+ *   e(t) = (band_t |t| + band_pos) / |d_a|
+ * (t_entry is exact when the camera is inside the box, t_entry = 0), and per
+ * sample k the position by
+ *   e_p  = e(t_entry) + band_t (|t_k| + max|o| + max|p_k|) + band_pos.
+ *   K band      (t_exit - t_entry)/step within band_k + (e(t_entry) +
+ *               e(t_exit))/step of an integer (this also covers near-miss /
+ *               grazing rays, K = 0 <-> 1, and rays lying within band_pos of
+ *               a face plane they are parallel to);
+ *   clip band   |s - clip| <= band_clip max(1, max|corner|) + e_p |grad s|_1
+ *               where the table's alpha at the clip level is non-zero (the
+ *               sample's decision is flipped alone; |grad s|_1 is the sum of
+ *               the trilinear field's partial derivatives' magnitudes there);
  *   term band   every composited sample from the first with A >= ta - band_a
  *               up to the first with A >= ta + band_a is a possible stop.
  * Flags: bit 0 K tie, bit 1 clip tie, bit 2 termination tie, bit 3 the
- * alternative list was truncated at VRO_MAXALT.
+ * alternative list was truncated at VRO_MAXALT (or more clip ties than
+ * VRO_MAXCLIP were found).
  */
 #include <math.h>
 #include <stdint.h>
@@ -67,8 +84,8 @@
 #include <omp.h>
 #endif
 
-#define VRO_MAXALT 8
-#define VRO_MAXCLIP 2
+#define VRO_MAXALT 16
+#define VRO_MAXCLIP 4
 
 enum { VRO_F32 = 0, VRO_F16 = 1, VRO_I8 = 2 };
 enum { VRO_MIP = 0, VRO_COMPOSITE = 1, VRO_SUM = 2 };
@@ -95,7 +112,7 @@ typedef struct {
 } vro_tf;
 
 typedef struct {
-    double band_k, band_pos, band_clip, band_a;
+    double band_k, band_pos, band_clip, band_a, band_t;
 } vro_bands;
 
 /* ------------------------------------------------------------------ */
@@ -160,11 +177,15 @@ static void make_ray(const vro_camera* c, int w, int h, int px, int py,
  * unclamped).  For the parallel axes (d_i == 0, no division) it reports
  * *miss_dist, how far outside [0, n_i - 1] the worst excluded coordinate lies
  * (0 when none is excluded), and *face_dist, the smallest distance of an
- * included coordinate to one of its two face planes (infinity if none).   */
+ * included coordinate to one of its two face planes (infinity if none).
+ * *dn and *df are |d_a| of the axes that decide t_near and t_far.          */
 static void slab(const double o[3], const double d[3], const int64_t n[3],
-                 double* t_near, double* t_far, double* miss_dist, double* face_dist)
+                 double* t_near, double* t_far, double* miss_dist, double* face_dist,
+                 double* dn, double* df)
 {
     double tn = -INFINITY, tf = INFINITY;
+    *dn = 1.0;
+    *df = 1.0;
     *miss_dist = 0.0;
     *face_dist = INFINITY;
     for (int a = 0; a < 3; ++a) {
@@ -174,8 +195,8 @@ static void slab(const double o[3], const double d[3], const int64_t n[3],
             double tb = (hi - o[a]) / d[a];
             double lo_t = ta < tb ? ta : tb;
             double hi_t = ta < tb ? tb : ta;
-            if (lo_t > tn) tn = lo_t;
-            if (hi_t < tf) tf = hi_t;
+            if (lo_t > tn) { tn = lo_t; *dn = fabs(d[a]); }
+            if (hi_t < tf) { tf = hi_t; *df = fabs(d[a]); }
         } else if (o[a] < 0.0 || o[a] > hi) {
             double md = o[a] < 0.0 ? -o[a] : o[a] - hi;
             if (md > *miss_dist) *miss_dist = md;
@@ -190,8 +211,12 @@ static void slab(const double o[3], const double d[3], const int64_t n[3],
 
 static double lerp(double a, double b, double f) { return a + f * (b - a); }
 
-static double sample(const vro_volume* vol, const double o[3], const double d[3],
-                     double t)
+/* One trilinear sample at o + t d.  When sens is not NULL it receives what
+ * the clip band needs: sens[0] the sum of the magnitudes of the field's
+ * partial derivatives at the point (per unit length), sens[1] the largest
+ * |corner|, sens[2] the largest |coordinate| of the (unclamped) position.  */
+static double sample_sens(const vro_volume* vol, const double o[3], const double d[3],
+                          double t, double* sens)
 {
     double p[3], f[3];
     int64_t i0[3];
@@ -216,7 +241,67 @@ static double sample(const vro_volume* vol, const double o[3], const double d[3]
     double y1z1 = lerp(c[1][1][0], c[1][1][1], f[0]);
     double z0 = lerp(y0z0, y1z0, f[1]);
     double z1 = lerp(y0z1, y1z1, f[1]);
+    if (sens) {
+        double gx = lerp(lerp(c[0][0][1] - c[0][0][0], c[0][1][1] - c[0][1][0], f[1]),
+                         lerp(c[1][0][1] - c[1][0][0], c[1][1][1] - c[1][1][0], f[1]), f[2]);
+        double gy = lerp(y1z0 - y0z0, y1z1 - y0z1, f[2]);
+        double gz = z1 - z0;
+        double cm = 0.0, pm = 0.0;
+        for (int cz = 0; cz < 2; ++cz)
+            for (int cy = 0; cy < 2; ++cy)
+                for (int cx = 0; cx < 2; ++cx) cm = fmax(cm, fabs(c[cz][cy][cx]));
+        for (int a = 0; a < 3; ++a) pm = fmax(pm, fabs(o[a] + t * d[a]));
+        sens[0] = fabs(gx) + fabs(gy) + fabs(gz);
+        sens[1] = cm;
+        sens[2] = pm;
+    }
     return lerp(z0, z1, f[2]);
+}
+
+static double sample(const vro_volume* vol, const double o[3], const double d[3],
+                     double t)
+{
+    return sample_sens(vol, o, d, t, NULL);
+}
+
+/* ------------------------------------------------------------------ */
+/* rounding bands of one ray                                            */
+/* ------------------------------------------------------------------ */
+
+/* What a single-precision evaluation of the ray may get wrong (see the
+ * header): e_te, the error of t_entry; omax, max |o_i|.  */
+typedef struct {
+    double e_te, omax;
+} ray_err;
+
+/* Error of a slab parameter t decided by an axis with |d_a| = da.        */
+static double t_err(const vro_bands* b, double t, double da)
+{
+    return (b->band_t * fabs(t) + b->band_pos) / da;
+}
+
+static ray_err make_ray_err(const vro_bands* b, const double o[3], double tn, double dn)
+{
+    ray_err e;
+    double et = isfinite(tn) ? t_err(b, tn, dn) : 0.0;
+    e.e_te = tn > -et ? et : 0.0;     /* t_entry = 0 exactly when the camera is inside */
+    e.omax = fmax(fabs(o[0]), fmax(fabs(o[1]), fabs(o[2])));
+    return e;
+}
+
+/* Position error of the sample at t (see the header).                  */
+static double pos_err(const vro_bands* b, const ray_err* e, double t, double pmax)
+{
+    return e->e_te + b->band_t * (fabs(t) + e->omax + pmax) + b->band_pos;
+}
+
+/* May a single-precision evaluation put this sample on the other side of
+ * the clip?                                                              */
+static int clip_tie(const vro_bands* b, const ray_err* e, const vro_tf* tf, double s,
+                    double t, const double sens[3])
+{
+    double band = b->band_clip * fmax(1.0, sens[1]) + pos_err(b, e, t, sens[2]) * sens[0];
+    return fabs(s - tf->clip) <= band;
 }
 
 /* ------------------------------------------------------------------ */
@@ -291,7 +376,8 @@ static int64_t march_scalar(const vro_volume* vol, int mode, const double o[3],
 static int64_t march_composite(const vro_volume* vol, const vro_tf* tf,
                                const double* lutc, const double o[3], const double d[3],
                                double t_entry, int64_t K, double step, int64_t flip_k,
-                               const vro_bands* b, alts* r, int64_t* clip_k, int* n_clip)
+                               const vro_bands* b, const ray_err* e, alts* r,
+                               int64_t* clip_k, int* n_clip)
 {
     double C[3] = {0, 0, 0}, A = 0.0;
     double ta = tf->term_alpha;
@@ -304,12 +390,15 @@ static int64_t march_composite(const vro_volume* vol, const vro_tf* tf,
     int n_cand = 0;
     if (n_clip) *n_clip = 0;
     for (int64_t k = 0; k < K; ++k) {
-        double s = sample(vol, o, d, t_entry + (double)k * step);
+        double t = t_entry + (double)k * step, sens[3];
+        double s = sample_sens(vol, o, d, t, sens);
         int keep = !(s < tf->clip);
-        if (n_clip && clip_rgba[3] > 0.0 &&
-            fabs(s - tf->clip) <= b->band_clip * fmax(1.0, fabs(s)) &&
-            *n_clip < VRO_MAXCLIP)
-            clip_k[(*n_clip)++] = k;
+        if (n_clip && clip_rgba[3] > 0.0 && clip_tie(b, e, tf, s, t, sens)) {
+            if (*n_clip < VRO_MAXCLIP)
+                clip_k[(*n_clip)++] = k;
+            else
+                r->flags |= 8;
+        }
         if (k == flip_k) keep = !keep;
         if (!keep) continue;
         double rgba[4];
@@ -358,12 +447,14 @@ static void render_pixel(const vro_volume* vol, const vro_camera* cam, int w, in
     double o[3], d[3];
     make_ray(cam, w, h, px, py, o, d);
 
-    double tn, tf_, miss_dist, face_dist;
-    slab(o, d, vol->n, &tn, &tf_, &miss_dist, &face_dist);
+    double tn, tf_, miss_dist, face_dist, dn, df;
+    slab(o, d, vol->n, &tn, &tf_, &miss_dist, &face_dist, &dn, &df);
     double t_entry = tn > 0.0 ? tn : 0.0;
     double t_exit = tf_;
     double q = (t_exit - t_entry) / step;
     int hit = miss_dist == 0.0 && t_exit >= t_entry;
+    ray_err e = make_ray_err(b, o, tn, dn);
+    double wq = b->band_k + (e.e_te + t_err(b, t_exit, df)) / step;
 
     /* candidate sample counts, primary first */
     int64_t Ks[4];
@@ -372,13 +463,13 @@ static void render_pixel(const vro_volume* vol, const vro_camera* cam, int w, in
         double fl = floor(q);
         int64_t K = (int64_t)fl + 1;
         Ks[nK++] = K;
-        if (q - fl < b->band_k) Ks[nK++] = K - 1;
-        if (q - fl > 1.0 - b->band_k) Ks[nK++] = K + 1;
+        if (q - fl < wq) Ks[nK++] = K - 1;
+        if (q - fl > 1.0 - wq) Ks[nK++] = K + 1;
         if (face_dist <= b->band_pos) Ks[nK++] = 0;
     } else {
         Ks[nK++] = 0;
         /* a near miss: slightly different rounding could give a short hit */
-        if (miss_dist <= b->band_pos && q >= -b->band_k)
+        if (miss_dist <= b->band_pos && q >= -wq)
             Ks[nK++] = q < 0.0 ? 1 : (int64_t)floor(q) + 1;
     }
     if (nK > 1) r->flags |= 1;
@@ -394,12 +485,12 @@ static void render_pixel(const vro_volume* vol, const vro_camera* cam, int w, in
             }
             int64_t clip_k[VRO_MAXCLIP];
             int n_clip = 0;
-            int64_t cnt = march_composite(vol, tf, lutc, o, d, t_entry, K, step, -1, b, r,
-                                          clip_k, &n_clip);
+            int64_t cnt = march_composite(vol, tf, lutc, o, d, t_entry, K, step, -1, b, &e,
+                                          r, clip_k, &n_clip);
             if (ik == 0) *nsamples = cnt;
             for (int ic = 0; ic < n_clip; ++ic) {
                 r->flags |= 2;
-                march_composite(vol, tf, lutc, o, d, t_entry, K, step, clip_k[ic], b, r,
+                march_composite(vol, tf, lutc, o, d, t_entry, K, step, clip_k[ic], b, &e, r,
                                 NULL, NULL);
             }
         } else {
@@ -496,11 +587,18 @@ int vro_render(const vro_volume* vol, const vro_camera* cams, int n_views, int w
  * max for MIP, addition for SUM.  Without termination this is the one-pass
  * result (the operator is associative); with it, a ray may pass an opaque
  * sub-cube's partial and keep contributions behind it, attenuated.
- * The primary FP64 result only; flags: bit 0 K tie, bit 1 clip tie, bit 2
- * termination tie (a partial's alpha within band_a of term_alpha), bit 4 a
- * sample within rounding of a sub-cube boundary plane (2^-20 of the
- * position's magnitude plus band_pos).
+ * Acceptance set as for vro_render: the primary FP64 result plus the results
+ * of single decisions changed within the bands -- K - 1 or K + 1 (K band), one
+ * sample's clip decision inverted (clip band), one sample given to the
+ * sub-cube on the other side of a boundary plane it lies within rounding of
+ * (the position band), one sub-cube's partial stopped at another sample of
+ * its termination band.  Flags: bit 0 K tie, bit 1 clip tie, bit 2
+ * termination tie, bit 3 truncated (more ties than the lists hold), bit 4 a
+ * sample within rounding of a sub-cube boundary plane.
  */
+#define VRO_MAXMOVE 4
+#define VRO_MAXSTOP 8
+
 static int segment_of(double z, const int64_t* cell_lo, int n_sub)
 {
     double c = floor(z);
@@ -509,100 +607,234 @@ static int segment_of(double z, const int64_t* cell_lo, int n_sub)
     return i;
 }
 
-static void render_pixel_subcubes(const vro_volume* vol, const vro_camera* cam, int w, int h,
-                                  int px, int py, int mode, double step, const vro_tf* tf,
-                                  const double* lutc, const vro_bands* b,
-                                  const int64_t* cell_lo, int n_sub, double res[4],
-                                  int* flags, double* segC, double* segA, double* segV,
-                                  int* done, int* order)
+/* One decision of a sub-cube march changed from the primary rule.        */
+typedef struct {
+    int64_t flip_k;        /* this sample's clip decision inverted (-1: none) */
+    int64_t move_k;        /* this sample belongs to sub-cube move_to (-1: none) */
+    int move_to;
+    int stop_seg;          /* sub-cube stop_seg stops after composited sample stop_k */
+    int64_t stop_k;        /* (-1: every sub-cube stops by the threshold)          */
+} sub_variant;
+
+/* The ties a probing march finds.                                       */
+typedef struct {
+    int64_t clip_k[VRO_MAXCLIP];
+    int n_clip;
+    int64_t move_k[VRO_MAXMOVE];
+    int move_to[VRO_MAXMOVE];
+    int n_move;
+    int stop_seg[VRO_MAXSTOP];
+    int64_t stop_k[VRO_MAXSTOP];
+    int n_stop;
+    int flags;
+} sub_ties;
+
+typedef struct {
+    double *C, *A, *V;
+    int *done, *order;
+} sub_work;
+
+/* March samples 0..K-1 of a ray as n_sub independent partials and combine
+ * them in the ray's order into res.  With ties != NULL the march probes:
+ * every sub-cube composites on until its alpha reaches term_alpha + band_a,
+ * and the ties met on the way are listed (res is then not the result).   */
+static void subcube_march(const vro_volume* vol, const double o[3], const double d[3],
+                          double t_entry, int64_t K, double step, int mode,
+                          const vro_tf* tf, const double* lutc, double clip_alpha,
+                          const vro_bands* b, const ray_err* e, const int64_t* cell_lo,
+                          int n_sub, const sub_variant* var, sub_ties* ties,
+                          sub_work* wk, double res[4])
 {
-    double o[3], d[3];
-    make_ray(cam, w, h, px, py, o, d);
-    double tn, tf_, miss_dist, face_dist;
-    slab(o, d, vol->n, &tn, &tf_, &miss_dist, &face_dist);
-    double t_entry = tn > 0.0 ? tn : 0.0;
-    double q = (tf_ - t_entry) / step;
-    int hit = miss_dist == 0.0 && tf_ >= t_entry;
-    int64_t K = 0;
-    *flags = 0;
-    if (hit) {
-        double fl = floor(q);
-        K = (int64_t)fl + 1;
-        if (q - fl < b->band_k || q - fl > 1.0 - b->band_k || face_dist <= b->band_pos)
-            *flags |= 1;
-    } else if (miss_dist <= b->band_pos && q >= -b->band_k) {
-        *flags |= 1;
-    }
-    double clip_rgba[4];
-    classify(tf, lutc, tf->clip, clip_rgba);
     int n_order = 0;
+    double ta = tf->term_alpha;
     for (int i = 0; i < n_sub; ++i) {
-        segC[3 * i] = segC[3 * i + 1] = segC[3 * i + 2] = 0.0;
-        segA[i] = 0.0;
-        segV[i] = mode == VRO_MIP ? -INFINITY : 0.0;
-        done[i] = 0;
+        wk->C[3 * i] = wk->C[3 * i + 1] = wk->C[3 * i + 2] = 0.0;
+        wk->A[i] = 0.0;
+        wk->V[i] = mode == VRO_MIP ? -INFINITY : 0.0;
+        wk->done[i] = 0;
+    }
+    int64_t* first_stop = NULL;  /* probe: the primary stop of each sub-cube */
+    int64_t stops_buf[64];
+    if (ties) {
+        first_stop = n_sub <= 64 ? stops_buf : (int64_t*)malloc(sizeof(int64_t) * n_sub);
+        for (int i = 0; i < n_sub; ++i) first_stop[i] = -1;
     }
     for (int64_t k = 0; k < K; ++k) {
         double t = t_entry + (double)k * step;
         double z = o[2] + t * d[2];
         int i = segment_of(z, cell_lo, n_sub);
-        for (int j = 1; j < n_sub; ++j) {
-            double bz = (double)cell_lo[j];
-            if (fabs(z - bz) <= ldexp(fabs(o[2]) + fabs(t) + fabs(z) + 1.0, -20) + b->band_pos)
-                *flags |= 16;
+        double sens[3];
+        double s = sample_sens(vol, o, d, t, sens);
+        if (ties) {
+            double ep = pos_err(b, e, t, sens[2]) + ldexp(fabs(z) + 1.0, -22);
+            for (int j = 1; j < n_sub; ++j) {
+                double bz = (double)cell_lo[j];
+                if (fabs(z - bz) <= ep) {
+                    ties->flags |= 16;
+                    if (ties->n_move < VRO_MAXMOVE) {
+                        ties->move_k[ties->n_move] = k;
+                        ties->move_to[ties->n_move++] = i >= j ? j - 1 : j;
+                    } else {
+                        ties->flags |= 8;
+                    }
+                }
+            }
         }
-        if (n_order == 0 || order[n_order - 1] != i) order[n_order++] = i;
-        double s = sample(vol, o, d, t);
+        if (k == var->move_k) i = var->move_to;
+        if (n_order == 0 || wk->order[n_order - 1] != i) wk->order[n_order++] = i;
         if (mode == VRO_MIP) {
-            if (s > segV[i]) segV[i] = s;
+            if (s > wk->V[i]) wk->V[i] = s;
             continue;
         }
         if (mode == VRO_SUM) {
-            segV[i] += s * step;
+            wk->V[i] += s * step;
             continue;
         }
-        if (done[i]) continue;
-        if (clip_rgba[3] > 0.0 && fabs(s - tf->clip) <= b->band_clip * fmax(1.0, fabs(s)))
-            *flags |= 2;
-        if (s < tf->clip) continue;
+        if (wk->done[i]) continue;
+        int keep = !(s < tf->clip);
+        if (ties && clip_alpha > 0.0 && clip_tie(b, e, tf, s, t, sens)) {
+            ties->flags |= 2;
+            if (ties->n_clip < VRO_MAXCLIP)
+                ties->clip_k[ties->n_clip++] = k;
+            else
+                ties->flags |= 8;
+        }
+        if (k == var->flip_k) keep = !keep;
+        if (!keep) continue;
         double rgba[4];
         classify(tf, lutc, s, rgba);
-        double wgt = (1.0 - segA[i]) * rgba[3];
-        for (int c = 0; c < 3; ++c) segC[3 * i + c] += wgt * rgba[c];
-        segA[i] += wgt;
-        if (fabs(segA[i] - tf->term_alpha) <= b->band_a) *flags |= 4;
-        if (segA[i] >= tf->term_alpha) done[i] = 1;
-    }
-    res[0] = res[1] = res[2] = res[3] = 0.0;
-    if (mode == VRO_MIP) {
-        res[0] = -INFINITY;
-        for (int a = 0; a < n_order; ++a)
-            if (segV[order[a]] > res[0]) res[0] = segV[order[a]];
-    } else if (mode == VRO_SUM) {
-        for (int a = 0; a < n_order; ++a) res[0] += segV[order[a]];
-    } else {
-        for (int a = 0; a < n_order; ++a) {
-            int i = order[a];
-            double T = 1.0 - res[3];
-            for (int c = 0; c < 3; ++c) res[c] += T * segC[3 * i + c];
-            res[3] += T * segA[i];
+        double wgt = (1.0 - wk->A[i]) * rgba[3];
+        for (int c = 0; c < 3; ++c) wk->C[3 * i + c] += wgt * rgba[c];
+        wk->A[i] += wgt;
+        double A = wk->A[i];
+        if (ties) {
+            if (A >= ta - b->band_a) {
+                if (first_stop[i] < 0 && A >= ta) {
+                    first_stop[i] = k;            /* the primary stop */
+                } else {
+                    ties->flags |= 4;
+                    if (ties->n_stop < VRO_MAXSTOP) {
+                        ties->stop_seg[ties->n_stop] = i;
+                        ties->stop_k[ties->n_stop++] = k;
+                    } else {
+                        ties->flags |= 8;
+                    }
+                }
+                if (A >= ta + b->band_a) wk->done[i] = 1;
+            }
+        } else if (i == var->stop_seg) {
+            if (k == var->stop_k) wk->done[i] = 1;
+        } else if (A >= ta) {
+            wk->done[i] = 1;
         }
+    }
+    if (ties && first_stop != stops_buf) free(first_stop);
+    /* combine each partial once, in the order of the ray's first visits (a
+     * moved sample can make a ray revisit a sub-cube) */
+    res[0] = res[1] = res[2] = res[3] = 0.0;
+    if (mode == VRO_MIP) res[0] = -INFINITY;
+    for (int a = 0; a < n_order; ++a) {
+        int i = wk->order[a], seen = 0;
+        for (int a2 = 0; a2 < a; ++a2) seen |= wk->order[a2] == i;
+        if (seen) continue;
+        if (mode == VRO_MIP) {
+            if (wk->V[i] > res[0]) res[0] = wk->V[i];
+        } else if (mode == VRO_SUM) {
+            res[0] += wk->V[i];
+        } else {
+            double T = 1.0 - res[3];
+            for (int c = 0; c < 3; ++c) res[c] += T * wk->C[3 * i + c];
+            res[3] += T * wk->A[i];
+        }
+    }
+}
+
+static void render_pixel_subcubes(const vro_volume* vol, const vro_camera* cam, int w, int h,
+                                  int px, int py, int mode, double step, const vro_tf* tf,
+                                  const double* lutc, const vro_bands* b,
+                                  const int64_t* cell_lo, int n_sub, alts* r, sub_work* wk)
+{
+    double o[3], d[3];
+    make_ray(cam, w, h, px, py, o, d);
+    double tn, tf_, miss_dist, face_dist, dn, df;
+    slab(o, d, vol->n, &tn, &tf_, &miss_dist, &face_dist, &dn, &df);
+    double t_entry = tn > 0.0 ? tn : 0.0;
+    double q = (tf_ - t_entry) / step;
+    int hit = miss_dist == 0.0 && tf_ >= t_entry;
+    ray_err e = make_ray_err(b, o, tn, dn);
+    double wq = b->band_k + (e.e_te + t_err(b, tf_, df)) / step;
+    int64_t Ks[4];
+    int nK = 0;
+    if (hit) {
+        double fl = floor(q);
+        Ks[nK++] = (int64_t)fl + 1;
+        if (q - fl < wq) Ks[nK++] = (int64_t)fl;
+        if (q - fl > 1.0 - wq) Ks[nK++] = (int64_t)fl + 2;
+        if (face_dist <= b->band_pos) Ks[nK++] = 0;
+    } else {
+        Ks[nK++] = 0;
+        if (miss_dist <= b->band_pos && q >= -wq)
+            Ks[nK++] = q < 0.0 ? 1 : (int64_t)floor(q) + 1;
+    }
+    r->n = 0;
+    r->flags = nK > 1 ? 1 : 0;
+    double clip_rgba[4];
+    classify(tf, lutc, tf->clip, clip_rgba);
+    sub_variant none = {-1, -1, 0, -1, -1};
+    double res[4];
+    subcube_march(vol, o, d, t_entry, Ks[0], step, mode, tf, lutc, clip_rgba[3], b, &e,
+                  cell_lo, n_sub, &none, NULL, wk, res);
+    push(r, res);
+    for (int ik = 1; ik < nK; ++ik) {
+        subcube_march(vol, o, d, t_entry, Ks[ik], step, mode, tf, lutc, clip_rgba[3], b, &e,
+                      cell_lo, n_sub, &none, NULL, wk, res);
+        push(r, res);
+    }
+    sub_ties ties;
+    memset(&ties, 0, sizeof ties);
+    subcube_march(vol, o, d, t_entry, Ks[0], step, mode, tf, lutc, clip_rgba[3], b, &e,
+                  cell_lo, n_sub, &none, &ties, wk, res);
+    r->flags |= ties.flags;
+    for (int i = 0; i < ties.n_clip; ++i) {
+        sub_variant v = none;
+        v.flip_k = ties.clip_k[i];
+        subcube_march(vol, o, d, t_entry, Ks[0], step, mode, tf, lutc, clip_rgba[3], b, &e,
+                      cell_lo, n_sub, &v, NULL, wk, res);
+        push(r, res);
+    }
+    for (int i = 0; i < ties.n_move; ++i) {
+        sub_variant v = none;
+        v.move_k = ties.move_k[i];
+        v.move_to = ties.move_to[i];
+        subcube_march(vol, o, d, t_entry, Ks[0], step, mode, tf, lutc, clip_rgba[3], b, &e,
+                      cell_lo, n_sub, &v, NULL, wk, res);
+        push(r, res);
+    }
+    for (int i = 0; i < ties.n_stop; ++i) {
+        sub_variant v = none;
+        v.stop_seg = ties.stop_seg[i];
+        v.stop_k = ties.stop_k[i];
+        subcube_march(vol, o, d, t_entry, Ks[0], step, mode, tf, lutc, clip_rgba[3], b, &e,
+                      cell_lo, n_sub, &v, NULL, wk, res);
+        push(r, res);
     }
 }
 
 /*
  * Render a list of pixels (as vro_render) as n_sub sub-cubes rendered
  * independently and integrated; cell_lo[0] must be 0 and cell_lo ascending
- * below n_z - 1.  out[i*4 + c]: channel c of pixel i (MIP and SUM: channel
- * 0).  Returns 0, or -1 on bad arguments.
+ * below n_z - 1.  Output as vro_render's: out[i*VRO_MAXALT*4 + a*4 + c] is
+ * channel c of acceptable result a (a < nalt[i]; a = 0 the primary result;
+ * MIP and SUM use channel 0).  Returns 0, or -1 on bad arguments.
  */
 int vro_render_subcubes(const vro_volume* vol, const vro_camera* cams, int n_views, int w,
                         int h, int mode, double step, const vro_tf* tf,
                         const vro_bands* bands, const int64_t* cell_lo, int n_sub,
-                        const int32_t* pix, int64_t npix, double* out, int32_t* flags,
-                        int nthreads)
+                        const int32_t* pix, int64_t npix, double* out, int32_t* nalt,
+                        int32_t* flags, int nthreads)
 {
-    if (!vol || !cams || !tf || !bands || !cell_lo || !pix || !out || !flags) return -1;
+    if (!vol || !cams || !tf || !bands || !cell_lo || !pix || !out || !nalt || !flags)
+        return -1;
     if (vol->n[0] < 2 || vol->n[1] < 2 || vol->n[2] < 2 || !(step > 0.0) ||
         tf->n_lut < 2 || w <= 0 || h <= 0 || n_views <= 0 || n_sub < 1)
         return -1;
@@ -619,12 +851,15 @@ int vro_render_subcubes(const vro_volume* vol, const vro_camera* cams, int n_vie
 #pragma omp parallel num_threads(nt) reduction(| : bad)
 #endif
     {
-        double* segC = (double*)malloc(sizeof(double) * 3 * (size_t)n_sub);
-        double* segA = (double*)malloc(sizeof(double) * (size_t)n_sub);
-        double* segV = (double*)malloc(sizeof(double) * (size_t)n_sub);
-        int* done = (int*)malloc(sizeof(int) * (size_t)n_sub);
-        int* order = (int*)malloc(sizeof(int) * (size_t)n_sub);
-        if (!segC || !segA || !segV || !done || !order) bad = 1;
+        sub_work wk;
+        wk.C = (double*)malloc(sizeof(double) * 3 * (size_t)n_sub);
+        wk.A = (double*)malloc(sizeof(double) * (size_t)n_sub);
+        wk.V = (double*)malloc(sizeof(double) * (size_t)n_sub);
+        wk.done = (int*)malloc(sizeof(int) * (size_t)n_sub);
+        /* a ray visits each sub-cube in one run, but a moved sample can add
+         * a visit: room for twice the sub-cubes */
+        wk.order = (int*)malloc(sizeof(int) * 2 * (size_t)n_sub + 2 * sizeof(int));
+        if (!wk.C || !wk.A || !wk.V || !wk.done || !wk.order) bad = 1;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 16)
 #endif
@@ -634,17 +869,20 @@ int vro_render_subcubes(const vro_volume* vol, const vro_camera* cams, int n_vie
                 bad = 1;
                 continue;
             }
-            int fl = 0;
+            alts r;
             render_pixel_subcubes(vol, &cams[view], w, h, px, py, mode, step, tf, lutc,
-                                  bands, cell_lo, n_sub, &out[4 * i], &fl, segC, segA, segV,
-                                  done, order);
-            flags[i] = fl;
+                                  bands, cell_lo, n_sub, &r, &wk);
+            memset(&out[i * VRO_MAXALT * 4], 0, sizeof(double) * VRO_MAXALT * 4);
+            for (int a = 0; a < r.n; ++a)
+                memcpy(&out[(i * VRO_MAXALT + a) * 4], r.v[a], 4 * sizeof(double));
+            nalt[i] = r.n;
+            flags[i] = r.flags;
         }
-        free(segC);
-        free(segA);
-        free(segV);
-        free(done);
-        free(order);
+        free(wk.C);
+        free(wk.A);
+        free(wk.V);
+        free(wk.done);
+        free(wk.order);
     }
     (void)nthreads;
     free(lutc);

@@ -20,21 +20,41 @@ TOL_FP32 = 1e-4
 TOL_PREC = {"f16": 2e-3, "i8": 1e-2}
 
 
-def bands_for(dims, cams, step):
-    """Tie bands for single-precision arithmetic on this geometry.
+def bands_for(dims, cams, step, w=None, h=None):
+    """Tie bands for single-precision arithmetic on this geometry
+    (``oracle.fp32_bands``): per ray, the sample count K may differ where
+    (t_exit - t_entry)/step lies within the rounding of t_entry and t_exit
+    (6 units of 2^-24 of |t| divided by the deciding direction component,
+    plus the origin's error) of an integer; per sample, the clip decision
+    where the value lies within its own rounding plus the position's
+    rounding times the local gradient of the clip; the termination decision
+    where alpha lies within the image tolerance of the threshold."""
+    return oracle.fp32_bands(dims, cams, step, w, h, band_a=TOL_FP32)
 
-    The sample count K = floor((t_exit - t_entry)/step) + 1 moves when the
-    quotient is within the rounding error of t_entry/t_exit (a few ulps of the
-    largest distance involved) of an integer; positions of rays parallel to a
-    face carry a few ulps of the camera coordinates.
-    """
-    eye = np.abs(np.asarray(cams["eye"], dtype=np.float64)).max()
-    diag = math.sqrt(sum((d - 1.0) ** 2 for d in dims))
-    t_scale = eye + diag + max(dims)
-    ulp = 2.0 ** -23
-    return oracle.Bands(band_k=2e-3 + 64 * ulp * t_scale / step,
-                        band_pos=16 * ulp * max(1.0, t_scale),
-                        band_clip=1e-4, band_a=1e-4)
+
+def tie_counts(res: oracle.Result) -> dict:
+    """Pixels flagged per tie kind (K, clip, termination, truncated list,
+    sub-cube boundary) and their fraction of all pixels."""
+    f = np.asarray(res.flags)
+    n = max(1, f.size)
+    out = {name: int(np.count_nonzero(f & bit))
+           for name, bit in (("k", 1), ("clip", 2), ("term", 4), ("trunc", 8),
+                             ("boundary", 16))}
+    out["any"] = int(np.count_nonzero(f))
+    out["frac"] = out["any"] / n
+    return out
+
+
+def assert_ties(res: oracle.Result, what="", k=0.01, clip=0.0, term=0.02, trunc=0.0):
+    """Bound the fraction of pixels whose acceptance set holds alternatives,
+    per kind: the bands are derived from the arithmetic, so a test whose
+    pixels are mostly ties checks little."""
+    t = tie_counts(res)
+    n = max(1, len(res.flags))
+    for name, bound in (("k", k), ("clip", clip), ("term", term), ("trunc", trunc)):
+        assert t[name] <= bound * n, "%s: %d of %d pixels are %s ties (bound %g)" % (
+            what, t[name], n, name, bound)
+    return t
 
 
 def sum_scale(abs_volume: oracle.Volume, cams, w, h, step, image, pixels=None):

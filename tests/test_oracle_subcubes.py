@@ -31,7 +31,7 @@ def test_one_subcube_is_the_one_pass_result():
     tf = oracle.TF(synth.default_lut(64), 1.0, 8.0, 1.0, 0.9)
     for mode in MODES:
         ref = oracle.render(vol, cams, w, h, mode, 0.37, tf)
-        got, _ = oracle.render_subcubes(vol, cams, w, h, mode, 0.37, tf, [0])
+        got = oracle.render_subcubes(vol, cams, w, h, mode, 0.37, tf, [0]).primary
         ch = 4 if mode == oracle.COMPOSITE else 1
         assert np.array_equal(got[:, :ch], ref.primary[:, :ch]), mode
 
@@ -45,7 +45,7 @@ def test_without_termination_any_split_is_the_one_pass_result(cell_lo):
     tf = oracle.TF(synth.default_lut(64, alpha_max=0.9), 1.0, 8.0, 1.0, 2.0)
     for mode in MODES:
         ref = oracle.render(vol, cams, w, h, mode, 0.37, tf).primary
-        got, _ = oracle.render_subcubes(vol, cams, w, h, mode, 0.37, tf, cell_lo)
+        got = oracle.render_subcubes(vol, cams, w, h, mode, 0.37, tf, cell_lo).primary
         if mode == oracle.MIP:
             assert np.array_equal(got[:, 0], ref[:, 0])
         else:
@@ -84,7 +84,7 @@ def test_constant_cube_each_subcube_stops_at_its_own_opacity(sign):
         return 1.0 - (1.0 - a) ** n
     A0, A1 = partial(Ks[0]), partial(Ks[1])
     A = 1.0 - (1.0 - A0) * (1.0 - A1)
-    got, _ = oracle.render_subcubes(vol, cams, 4, 3, oracle.COMPOSITE, step, tf, [0, m])
+    got = oracle.render_subcubes(vol, cams, 4, 3, oracle.COMPOSITE, step, tf, [0, m]).primary
     for p in range(got.shape[0]):
         assert abs(got[p, 3] - A) < 1e-12
         assert np.allclose(got[p, :3], rgba[:3] * A, rtol=1e-12, atol=1e-12)
