@@ -103,6 +103,34 @@ typedef struct vr_volume_s* vr_volume;
  * 2^40.                                                                    */
 int vr_volume_bytes(const int64_t dims[3], int dtype, size_t* bytes_out);
 
+/* Device bytes the library itself would allocate for a volume of these
+ * dims and dtype, so a caller can budget memory before attaching anything
+ * (paper abstract: data sets larger than GPU memory; §3.1 item 3's
+ * trilinear fetch is what the texture storage serves):
+ *   vr_texture_bytes     texture storage (vr_volume_attach_texture, or with
+ *                        pair != 0 vr_volume_attach_pair_texture; FP16 /
+ *                        int8 only): every layer's texels on the current
+ *                        device's layered-texture layout, plus int8 decode
+ *                        records.  VR_ERR_UNSUPPORTED beyond the device's
+ *                        layered-texture limits or for FP32 pairs.
+ *   vr_mip_bounds_bytes  MIP bounds of an FP32 volume with texture storage
+ *                        (vr_volume_attach_mip_bounds): binary16 texels in
+ *                        the texture's layout plus one word.  Filling them
+ *                        also takes a stream-ordered scratch buffer of at
+ *                        most 256 MiB, released on the stream.
+ * The figures count the texels; the driver may round an allocation up to
+ * its page size (2 MiB) and tile boundaries.  An attach that cannot get its
+ * memory fails with VR_ERR_OOM and says how many bytes it asked for.      */
+int vr_texture_bytes(const int64_t dims[3], int dtype, int pair, size_t* bytes_out);
+int vr_mip_bounds_bytes(const int64_t dims[3], size_t* bytes_out);
+
+/* Device bytes a volume holds now: *library_bytes the library's own
+ * allocations (texture storage and MIP bounds, as the two calls above
+ * count them), *caller_bytes the caller's buffers bound to it (the brick
+ * buffer as passed to vr_volume_create -- 0 once dropped -- and the
+ * empty-space masks).  Either pointer may be NULL.                         */
+int vr_volume_device_bytes(vr_volume vol, size_t* library_bytes, size_t* caller_bytes);
+
 /* Bind a caller-owned device buffer as a volume and, when src is not NULL,
  * pack the whole cube into it.
  *   dims         nx, ny, nz as above.
@@ -412,15 +440,20 @@ int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_by
  * the workspace vr_render_batch asks for.  This call renders the same
  * requests the same way but keeps its work and tile counters in a fixed
  * array inside the library's device image (260 bytes on every GPU that
- * loads the library, held until the process exits), so it allocates
- * nothing itself and calls nothing that does.
+ * loads the library, held until the process exits).  It allocates no device
+ * memory and calls nothing that does; on the host, the first batch call on
+ * each thread (this one or vr_render_batch) makes that thread's launch
+ * parameter block once, and later calls allocate nothing.
  *   n <= VR_BATCH_MAX; larger batches are rejected with VR_ERR_ARG (use
- *   vr_render_batch).  The first call on a device looks up the array's
- *   device address (cudaGetSymbolAddress); make that first call before any
- *   stream capture.  All calls share the one array and each launch zeroes it
- *   on `stream` before use, so two of these calls whose work overlaps on the
- *   GPU (different streams, or devices sharing nothing but this array) race
- *   and must be ordered by the caller.                                       */
+ *   vr_render_batch).  The first call in each CUDA context looks up the
+ *   array's device address (cudaGetSymbolAddress) and keeps it for that
+ *   context; make that first call before any stream capture.  A device reset
+ *   ends the context, and the next call looks the address up again.  Each
+ *   device (each context) has its own copy of the array, so calls on
+ *   different devices are independent; calls on one device share it, and
+ *   each launch zeroes it on `stream` before use, so two of these calls on
+ *   the same device whose work overlaps on the GPU (different streams)
+ *   race and must be ordered by the caller.                                  */
 int vr_render_batch_noalloc(const vr_request* reqs, int n, void* stream);
 
 /* Tile and ray-packet shapes of the batched launch (the batch autotuner's

@@ -10,5 +10,6 @@ larger than the device (``stream``).
 """
 from .api import (CAMERA_DTYPE, DTYPES, MODES, Request, Volume, batch_autotune,  # noqa: F401
                   batch_shapes, batch_workspace, get_batch_config, integrate_partials,
-                  render_batch, render_init, set_batch_config, volume_bytes)
+                  mip_bounds_bytes, render_batch, render_init, set_batch_config,
+                  texture_bytes, volume_bytes)
 from ._lib import VRError, load  # noqa: F401

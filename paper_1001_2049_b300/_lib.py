@@ -22,6 +22,11 @@ SIGNATURES = {
     "vr_version": (c_int, []),
     "vr_last_error": (ctypes.c_char_p, []),
     "vr_volume_bytes": (c_int, [ctypes.POINTER(c_int64), c_int, ctypes.POINTER(c_size_t)]),
+    "vr_texture_bytes": (c_int, [ctypes.POINTER(c_int64), c_int, c_int,
+                                 ctypes.POINTER(c_size_t)]),
+    "vr_mip_bounds_bytes": (c_int, [ctypes.POINTER(c_int64), ctypes.POINTER(c_size_t)]),
+    "vr_volume_device_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t),
+                                       ctypes.POINTER(c_size_t)]),
     "vr_volume_create": (c_int, [ctypes.POINTER(c_int64), c_int, c_void_p, c_int, c_void_p,
                                  c_size_t, c_void_p, ctypes.POINTER(c_void_p)]),
     "vr_volume_upload": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_int, c_void_p]),

@@ -213,6 +213,23 @@ def volume_bytes(dims, dtype="f32") -> int:
     return out.value
 
 
+def texture_bytes(dims, dtype="f32", pair=False) -> int:
+    """Device bytes of the texture storage the library allocates on
+    attach_texture (pair=True: attach_pair_texture) for such a cube."""
+    out = ctypes.c_size_t(0)
+    check(load().vr_texture_bytes(_dims_arr(dims), DTYPES[dtype], int(bool(pair)),
+                                  ctypes.byref(out)))
+    return out.value
+
+
+def mip_bounds_bytes(dims) -> int:
+    """Device bytes of the MIP bounds the library allocates on
+    attach_mip_bounds for an FP32 cube of these dims."""
+    out = ctypes.c_size_t(0)
+    check(load().vr_mip_bounds_bytes(_dims_arr(dims), ctypes.byref(out)))
+    return out.value
+
+
 class Volume:
     """A spectral cube resident on the GPU in the library's brick layout.
 
@@ -305,6 +322,13 @@ class Volume:
         (stream or torch.cuda.current_stream(self.device)).synchronize()
         self.buffer = None
         self._keep = None
+
+    def device_bytes(self):
+        """(library-owned, caller-owned) device bytes this volume holds now:
+        texture storage and MIP bounds; the brick buffer and the masks."""
+        lib_b, caller_b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        check(load().vr_volume_device_bytes(self._h, ctypes.byref(lib_b), ctypes.byref(caller_b)))
+        return int(lib_b.value), int(caller_b.value)
 
     def mask_bytes(self) -> int:
         n = ctypes.c_size_t(0)

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 
@@ -423,8 +424,15 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s, int 
         const int rc = check_request(reqs[i], i);
         if (rc) return rc;
     }
-    vr::BatchParams* B = new (std::nothrow) vr::BatchParams;
-    if (!B) return fail(VR_ERR_OOM, "out of host memory");
+    // the launch parameter block (about 25 KB, copied into each launch):
+    // one per thread, made at the thread's first batch call, so later calls
+    // allocate no host memory either
+    static thread_local std::unique_ptr<vr::BatchParams> tls_params;
+    if (!tls_params) {
+        tls_params.reset(new (std::nothrow) vr::BatchParams);
+        if (!tls_params) return fail(VR_ERR_OOM, "out of host memory");
+    }
+    vr::BatchParams* B = tls_params.get();
     int rc = VR_OK;
     const int order[vr::kNumBatchClasses] = {vr::kBatchTexPair, vr::kBatchTex,
                                              vr::kBatchBricks};
@@ -456,7 +464,6 @@ int batch_impl(const vr_request* reqs, int n, unsigned* ws, cudaStream_t s, int 
             }
         }
     }
-    delete B;
     return rc;
 }
 
@@ -596,6 +603,67 @@ int copy_texture_planes(vr::Volume* v, int64_t z0, int64_t n, const float* src, 
     return VR_OK;
 }
 
+// Layered-texture layout of a cube on the current device: slices are planes
+// (plain formats, nz + 2 with the edge planes repeated) or cells (pair, nz +
+// 1), stacked 2^shift per layer (each with a copy of its edge rows) when they
+// outnumber the layers.  Returns VR_OK or VR_ERR_UNSUPPORTED (beyond the
+// device's layered-texture limits).
+struct TexLayout {
+    int slices, shift, pitch, layers;
+};
+
+int texture_layout(const vr::VolumeGeom& g, bool pair, TexLayout* L)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int maxw = 0, maxh = 0, maxl = 0;
+    cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, dev);
+    cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, dev);
+    cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, dev);
+    cudaGetLastError();
+    maxl = std::min(maxl, vr::kMaxLayers);
+    if (maxl < 1) maxl = vr::kMaxLayers;      // no device: the sm_103 limits
+    if (maxw < 1) maxw = 32768;
+    if (maxh < 1) maxh = 32768;
+    L->slices = pair ? g.nz + 1 : g.nz + 2;
+    L->shift = 0;
+    while (((L->slices + (1 << L->shift) - 1) >> L->shift) > maxl) ++L->shift;
+    L->pitch = L->shift > 0 ? g.ny + 2 : g.ny;
+    L->layers = (L->slices + (1 << L->shift) - 1) >> L->shift;
+    if (g.nx > maxw || (int64_t)L->pitch << L->shift > maxh)
+        return fail(VR_ERR_UNSUPPORTED, "cube %d x %d x %d exceeds the layered texture limits",
+                    g.nx, g.ny, g.nz);
+    return VR_OK;
+}
+
+size_t texel_bytes(int format)
+{
+    switch (format) {
+    case VR_F32: return 4;
+    case VR_F16: return 2;
+    case VR_I8: return 1;
+    case vr::kF16Pair: return 4;
+    default: return 2;            // kI8Pair
+    }
+}
+
+// Device bytes of the texture storage (texels of every layer, plus the int8
+// decode records) and of the MIP bounds (binary16 texels in the same layout,
+// plus the maximum word).
+size_t texture_bytes(const vr::VolumeGeom& g, int format, const TexLayout& L)
+{
+    const size_t texels = (size_t)g.nx * ((size_t)L.pitch << L.shift) * L.layers;
+    const bool pair = format == vr::kF16Pair || format == vr::kI8Pair;
+    size_t dec = 0;
+    if (format == VR_I8 || format == vr::kI8Pair) dec = (size_t)L.slices * (pair ? 16 : 8);
+    return texels * texel_bytes(format) + dec;
+}
+
+size_t bounds_bytes(const vr::VolumeGeom& g, const TexLayout& L)
+{
+    return (size_t)g.nx * ((size_t)L.pitch << L.shift) * L.layers * 2 + sizeof(float);
+}
+
 int attach_bounds(vr::Volume* v, cudaStream_t s)
 {
     if (v->dtype != VR_F32)
@@ -616,8 +684,10 @@ int attach_bounds(vr::Volume* v, cudaStream_t s)
     if (e != cudaSuccess) {
         cudaGetLastError();
         v->bound_array = nullptr;
+        const TexLayout L{slices, v->stack_shift, v->stack_pitch, layers};
         return fail(e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA,
-                    "MIP bound storage: %s", cudaGetErrorString(e));
+                    "MIP bound storage of %zu bytes: %s", bounds_bytes(v->g, L),
+                    cudaGetErrorString(e));
     }
     e = cudaMalloc(&v->bound_vmax, sizeof(float));
     if (e == cudaSuccess) e = cudaMemsetAsync(v->bound_vmax, 0, sizeof(float), s);
@@ -662,23 +732,10 @@ int attach_texture(vr_volume vol, bool pair, void* stream)
         if (v->tex_format == format) return VR_OK;
         release_texture(v);
     }
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int maxw = 0, maxh = 0, maxl = 0;
-    cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, dev);
-    cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, dev);
-    cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, dev);
-    maxl = std::min(maxl, vr::kMaxLayers);
-    // slices: planes (plain, nz + 2 with the edge planes repeated) or cells
-    // (pair, nz + 1), stacked 2^shift per layer (each with a copy of its edge
-    // rows) when they outnumber the layers
-    const int slices = pair ? v->g.nz + 1 : v->g.nz + 2;
-    int shift = 0;
-    while (((slices + (1 << shift) - 1) >> shift) > maxl) ++shift;
-    const int pitch = shift > 0 ? v->g.ny + 2 : v->g.ny;
-    if (v->g.nx > maxw || (int64_t)pitch << shift > maxh)
-        return fail(VR_ERR_UNSUPPORTED, "cube %d x %d x %d exceeds the layered texture limits",
-                    v->g.nx, v->g.ny, v->g.nz);
+    TexLayout L;
+    const int lrc = texture_layout(v->g, pair, &L);
+    if (lrc) return lrc;
+    const int slices = L.slices, shift = L.shift, pitch = L.pitch;
     cudaChannelFormatDesc desc = format == VR_F32    ? cudaCreateChannelDesc<float>()
                                  : format == VR_F16   ? cudaCreateChannelDescHalf()
                                  : format == VR_I8    ? cudaCreateChannelDesc<signed char>()
@@ -692,7 +749,8 @@ int attach_texture(vr_volume vol, bool pair, void* stream)
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA,
-                    "texture storage: %s", cudaGetErrorString(e));
+                    "texture storage of %zu bytes: %s", texture_bytes(v->g, format, L),
+                    cudaGetErrorString(e));
     }
     v->array = arr;
     v->has_tex = true;
@@ -769,6 +827,59 @@ int vr_volume_bytes(const int64_t dims[3], int dtype, size_t* bytes_out)
     size_t b = vr::brick_bytes(g, dtype);
     if (dtype == VR_I8) b = vr::table_offset(g, dtype) + 2 * align_up((size_t)g.nz * 4, 256);
     *bytes_out = b;
+    return VR_OK;
+}
+
+int vr_texture_bytes(const int64_t dims[3], int dtype, int pair, size_t* bytes_out)
+{
+    vr::VolumeGeom g;
+    int rc = check_dims(dims, dtype, &g);
+    if (rc) return rc;
+    if (!bytes_out) return fail(VR_ERR_ARG, "bytes_out is NULL");
+    if (pair && dtype == VR_F32)
+        return fail(VR_ERR_UNSUPPORTED, "pair textures hold FP16 or int8 storage only");
+    TexLayout L;
+    rc = texture_layout(g, pair != 0, &L);
+    if (rc) return rc;
+    const int format = pair ? (dtype == VR_F16 ? vr::kF16Pair : vr::kI8Pair) : dtype;
+    *bytes_out = texture_bytes(g, format, L);
+    return VR_OK;
+}
+
+int vr_mip_bounds_bytes(const int64_t dims[3], size_t* bytes_out)
+{
+    vr::VolumeGeom g;
+    int rc = check_dims(dims, VR_F32, &g);
+    if (rc) return rc;
+    if (!bytes_out) return fail(VR_ERR_ARG, "bytes_out is NULL");
+    TexLayout L;
+    rc = texture_layout(g, false, &L);
+    if (rc) return rc;
+    *bytes_out = bounds_bytes(g, L);
+    return VR_OK;
+}
+
+int vr_volume_device_bytes(vr_volume vol, size_t* library_bytes, size_t* caller_bytes)
+{
+    if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
+    const vr::Volume* v = reinterpret_cast<const vr::Volume*>(vol);
+    size_t lib = 0, caller = 0;
+    if (v->has_tex) {
+        const bool pair = v->tex_format == vr::kF16Pair || v->tex_format == vr::kI8Pair;
+        const int slices = pair ? v->g.nz + 1 : v->g.nz + 2;
+        const TexLayout L{slices, v->stack_shift, v->stack_pitch,
+                          (slices + (1 << v->stack_shift) - 1) >> v->stack_shift};
+        lib += texture_bytes(v->g, v->tex_format, L);
+        if (v->bound_array) {
+            const TexLayout B{v->g.nz + 2, v->stack_shift, v->stack_pitch,
+                              (v->g.nz + 2 + (1 << v->stack_shift) - 1) >> v->stack_shift};
+            lib += bounds_bytes(v->g, B);
+        }
+    }
+    if (v->bricks) caller += v->bytes;
+    if (v->mask) caller += mask_macrocells(v->g) * sizeof(unsigned long long);
+    if (library_bytes) *library_bytes = lib;
+    if (caller_bytes) *caller_bytes = caller;
     return VR_OK;
 }
 

@@ -29,9 +29,10 @@ __global__ void __launch_bounds__(256) integrate_kernel(const __grid_constant__ 
     const size_t n = per_view * P.n_views;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
+        // 64-bit until the coordinates: one view may hold more than 2^31 pixels
         const int view = (int)(i / per_view);
-        const int rem = (int)(i - (size_t)view * per_view);
-        const int py = rem / P.w, px = rem - py * P.w;
+        const size_t rem = i - (size_t)view * per_view;
+        const int py = (int)(rem / (size_t)P.w), px = (int)(rem - (size_t)py * P.w);
         const bool up = ray::ray_dz_raw(P.cams[view], P.w, P.h, px, py) >= 0.0f;
         if constexpr (MODE == VR_COMPOSITE) {
             const float4* src = reinterpret_cast<const float4*>(P.partials);

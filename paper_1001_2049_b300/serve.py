@@ -77,6 +77,9 @@ class Server:
     be on the device at once.  ``per_request`` renders each request with its
     own single-view render call (``Volume.render``) instead of batched
     launches: the plain path the batched one is compared with.
+    ``resident`` holds, per cube, the device bytes it keeps for the whole
+    run (library-owned texture storage and MIP bounds, caller-owned bricks
+    and masks), which the output budget comes on top of.
     """
 
     def __init__(self, volumes: dict, mem_budget: int = 1 << 30, max_batch: int = 64,
@@ -98,6 +101,11 @@ class Server:
         self.next_ticket = 0
         self.launches = 0
         self.rejected = 0
+        self.resident = {name: v.device_bytes() for name, v in volumes.items()}
+
+    def resident_bytes(self) -> int:
+        """Device bytes the resident cubes hold (all owners)."""
+        return sum(a + b for a, b in self.resident.values())
 
     # -- client side ---------------------------------------------------------
     def submit(self, job: RenderJob) -> int:

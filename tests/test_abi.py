@@ -98,3 +98,26 @@ def test_batch_shapes_and_config_host_only():
         assert lib.vr_set_batch_config(n) != 0 and lib.vr_get_batch_config() == n - 1
     finally:
         lib.vr_set_batch_config(saved)
+
+
+def test_library_storage_byte_queries_host_only():
+    # what the library would allocate for texture storage and MIP bounds:
+    # one texel per voxel of every slice (planes plus the two repeated edge
+    # planes; pair texels one per cell plane), int8 decode records, binary16
+    # bounds plus the maximum word
+    from paper_1001_2049_b300 import mip_bounds_bytes, texture_bytes
+    nx, ny, nz = 40, 36, 50
+    assert texture_bytes((nx, ny, nz), "f32") == nx * ny * (nz + 2) * 4
+    assert texture_bytes((nx, ny, nz), "f16") == nx * ny * (nz + 2) * 2
+    assert texture_bytes((nx, ny, nz), "i8") == nx * ny * (nz + 2) + (nz + 2) * 8
+    assert texture_bytes((nx, ny, nz), "f16", pair=True) == nx * ny * (nz + 1) * 4
+    assert texture_bytes((nx, ny, nz), "i8", pair=True) == nx * ny * (nz + 1) * 2 + (nz + 1) * 16
+    assert mip_bounds_bytes((nx, ny, nz)) == nx * ny * (nz + 2) * 2 + 4
+    # deep cubes stack slices into at most 2048 layers (a power of two per
+    # layer), each slice with a copy of its first and last rows: 4002 slices
+    # -> 2 per layer, 4098 -> 4 per layer
+    assert texture_bytes((64, 32, 4000), "f16") == 64 * (2 * (32 + 2)) * 2001 * 2
+    assert texture_bytes((64, 32, 4096), "f16") == 64 * (4 * (32 + 2)) * 1025 * 2
+    from paper_1001_2049_b300 import VRError
+    with pytest.raises(VRError):
+        texture_bytes((nx, ny, 50), "f32", pair=True)

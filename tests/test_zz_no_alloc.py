@@ -16,27 +16,30 @@ import torch
 from paper_1001_2049_b300 import Volume, _lib, synth
 from paper_1001_2049_b300.api import MODES, _Request, _Transfer, batch_workspace
 
-from _util import TOL_FP32
-
 pytestmark = pytest.mark.gpu
 
 
 def _requests(n, seed):
-    """n requests over three volumes (texture and brick storage, three
-    storage types), mixed sizes, modes and transfer functions, with their
-    C records and freshly allocated outputs."""
-    specs = [((40, 36, 50), "f32", True), ((33, 45, 70), "f16", False),
-             ((30, 30, 60), "i8", True)]
+    """n requests over four volumes (plain-texel, pair-texel and brick
+    storage, three storage types), mixed sizes, modes, steps and transfer
+    functions, with their C records and freshly allocated outputs."""
+    # one volume per launch class of the batched kernel: plain texels,
+    # brick gathers, plain texels again, pair texels
+    specs = [((40, 36, 50), "f32", "texture"), ((33, 45, 70), "f16", "bricks"),
+             ((30, 30, 60), "i8", "texture"), ((28, 34, 44), "f16", "pair")]
     vols = []
-    for i, (dims, dt, tex) in enumerate(specs):
+    for i, (dims, dt, store) in enumerate(specs):
         v = Volume(synth.make_cube(dims, 4, ("uniform", 3.0, 9.0), 90 + i).cuda(), dt)
-        if tex:
+        if store == "texture":
             v.attach_texture()
+        elif store == "pair":
+            v.attach_pair_texture()
         v.set_transfer(synth.default_lut(), 1.0, 9.0, 1.0, 0.97)
         vols.append((v, dims))
     rng = np.random.default_rng(seed)
     lut = np.ascontiguousarray(synth.default_lut())
-    tf = _Transfer(lut.ctypes.data, lut.shape[0], 2.0, 9.0, 2.0, 0.95)
+    tfs = [_Transfer(lut.ctypes.data, lut.shape[0], 2.0, 9.0, 2.0, 0.95),
+           _Transfer(lut.ctypes.data, lut.shape[0], 0.0, 9.0, 1.0, 0.99)]
     arr = (_Request * n)()
     outs = []
     for i in range(n):
@@ -48,17 +51,22 @@ def _requests(n, seed):
         r = arr[i]
         r.vol = v.handle.value
         ctypes.memmove(ctypes.addressof(r.cam), cam.ctypes.data, 64)
-        r.w, r.h, r.mode, r.step = w, h, MODES[mode], 0.5
+        # three steps: more distinct corrected tables than one launch holds
+        r.w, r.h, r.mode, r.step = w, h, MODES[mode], (0.5, 0.37, 0.61)[i % 3]
         r.out = out.data_ptr()
         if mode == "composite" and i % 4 == 0:
-            r.tf = ctypes.addressof(tf)
+            r.tf = ctypes.addressof(tfs[(i // 4) % 2])
         outs.append(out)
-    return arr, outs, (vols, lut, tf)
+    return arr, outs, (vols, lut, tfs)
 
 
-def test_no_alloc_batch_matches_the_workspace_batch_on_two_calls():
+@pytest.mark.parametrize("n", [24, 64])
+def test_no_alloc_batch_matches_the_workspace_batch_on_two_calls(n):
+    # both calls take the batched launch path of vr_render_batch, so the
+    # images are the same bit for bit; with 64 requests over four storage
+    # kinds and several tables one call makes several launches on the
+    # shared counters, each clearing them first
     lib = _lib.load()
-    n = 24
     arr, outs, keep = _requests(n, 7)
     stream = torch.cuda.current_stream().cuda_stream
     ws = batch_workspace()
@@ -71,7 +79,7 @@ def test_no_alloc_batch_matches_the_workspace_batch_on_two_calls():
         _lib.check(lib.vr_render_batch_noalloc(arr, n, stream))
         torch.cuda.synchronize()
         for i, (o, ref) in enumerate(zip(outs, refs)):
-            assert torch.allclose(o, ref, rtol=0, atol=TOL_FP32, equal_nan=False), (call, i)
+            assert torch.equal(o, ref), (call, i)
     del keep
 
 
