@@ -20,7 +20,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -245,11 +244,7 @@ def oracle_errors(host_cube, cams, wl, pixels, values, w=W, h=H):
     the cube's max - min), and how many pixels exceed the stated tolerance."""
     import oracle
     from oracle import quantize
-    eye = float(np.abs(np.asarray(cams["eye"], dtype=np.float64)).max())
-    t_scale = eye + math.sqrt(sum((d - 1.0) ** 2 for d in wl.dims)) + max(wl.dims)
-    ulp = 2.0 ** -23
-    bands = oracle.Bands(band_k=2e-3 + 64 * ulp * t_scale / wl.step,
-                         band_pos=16 * ulp * max(1.0, t_scale), band_clip=1e-4, band_a=1e-4)
+    bands = oracle.fp32_bands(wl.dims, cams, wl.step, w, h)
     tf = oracle.TF(synth.default_lut(), wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
     vols = {"f32": oracle.Volume(host_cube)}
     if any(dt == "f16" for dt, _ in values):

@@ -32,7 +32,7 @@ def _rank(rank, world, port, out):
 @pytest.mark.parametrize("world", [2, 3])
 def test_job_figures_sum_samples_and_take_the_slowest_rank(world):
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         got = dict(out)
