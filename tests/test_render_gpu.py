@@ -4,6 +4,7 @@ Every image is compared pixel by pixel with the oracle's acceptance set
 (primary double-precision result plus the alternatives at the three
 discontinuities), within the tolerances stated in tests/_util.py.
 """
+import functools
 import math
 
 import numpy as np
@@ -863,6 +864,11 @@ def _sample_pixels(n_views, w, h, n, seed):
                      rng.integers(0, h, n)], axis=1).astype(np.int32)
 
 
+@functools.lru_cache(maxsize=2)
+def _hard_pixels_cached(n_views, w, h, dims, step, n, seed):
+    return _hard_pixels(synth.large_cameras(n_views, w, h), w, h, dims, step, n, seed)
+
+
 def _hard_pixels(cams, w, h, dims, step, n, seed):
     """Pixels where a single-precision render is most likely to part from
     the definition: rays that graze the box (at most 8 samples, or missing
@@ -913,7 +919,7 @@ def test_large_workload_sampled_pixels(large, dtype, tex):
     # grazing rays and near-integer sample counts
     n_rand = 60000
     pix = np.concatenate([_sample_pixels(len(cams), w, h, n_rand, 99),
-                          _hard_pixels(cams, w, h, wl.dims, wl.step, 4000, 98)])
+                          _hard_pixels_cached(len(cams), w, h, wl.dims, wl.step, 4000, 98)])
     ovol = oracle_volume(host, dtype)
     src = oracle.Volume(host)
     tf = oracle.TF(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
