@@ -646,7 +646,7 @@ def main():
     ap.add_argument("--no-masks", action="store_true",
                     help="composite without the empty-space masks")
     ap.add_argument("--no-bounds", action="store_true",
-                    help="MIP without the binary16 MIP bounds")
+                    help="MIP without the MIP bounds")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and served legs")
     ap.add_argument("--storage", default="texture", choices=["texture", "bricks"],
@@ -892,7 +892,7 @@ def main():
             "roofline": {"bound": "hbm",
                          "kernel": ("tex_kernel" if args.storage == "texture"
                                     else "march kernel") + " %s f32" % dom
-                                   + (" (binary16 MIP bounds)" if dom == "mip" and bounds_on
+                                   + (" (bfloat16 MIP bounds)" if dom == "mip" and bounds_on
                                       else ""),
                          "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",

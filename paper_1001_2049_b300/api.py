@@ -305,8 +305,9 @@ class Volume:
         check(load().vr_volume_detach_texture(self._h))
 
     def attach_mip_bounds(self, stream=None):
-        """FP32 volumes with texture storage: binary16 upper bounds of the
-        voxels (library-owned, 2 bytes per voxel); MIP renders then read
+        """FP32 volumes with texture storage: bfloat16 upper bounds of the
+        voxels, two planes per texel (library-owned, about 4 bytes per
+        voxel); MIP renders then read
         the FP32 texels only where a sample could raise the maximum, with
         identical images."""
         check(load().vr_volume_attach_mip_bounds(self._h, _stream_ptr(stream)))

@@ -477,6 +477,10 @@ void release_bounds(vr::Volume* v)
     v->bound_vmax = nullptr;
 }
 
+// MIP-bound cell slices holding planes [z0, z1): slice s packs planes s - 1
+// and s (clamped), so plane z is in slices z and z + 1.
+int fill_bound_planes(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s);
+
 // Fill MIP-bound slices [s0, s1), raising the device word of the largest
 // |voxel| the fills have seen (the kernels derive the rounding margin from
 // it, bound_margin; it only grows, so after uploads it stays conservative).
@@ -489,10 +493,10 @@ int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
     if (s0 >= s1) return VR_OK;
     const int nx = v->g.nx, ny = v->g.ny;
     if (v->stack_shift == 0) {
-        const size_t slice = (size_t)nx * ny * sizeof(unsigned short);
+        const size_t slice = (size_t)nx * ny * sizeof(unsigned);
         const int64_t chunk =
             std::max<int64_t>(1, std::min<int64_t>(s1 - s0, (int64_t)((256u << 20) / slice)));
-        unsigned short* buf = nullptr;
+        unsigned* buf = nullptr;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), chunk * slice, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -504,7 +508,7 @@ int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
             if (e == cudaSuccess) {
                 cudaMemcpy3DParms p;
                 std::memset(&p, 0, sizeof p);
-                p.srcPtr = make_cudaPitchedPtr(buf, (size_t)nx * sizeof(unsigned short), nx, ny);
+                p.srcPtr = make_cudaPitchedPtr(buf, (size_t)nx * sizeof(unsigned), nx, ny);
                 p.dstArray = v->bound_array;
                 p.dstPos = make_cudaPos(0, 0, (size_t)c0);
                 p.extent = make_cudaExtent(nx, ny, (size_t)(c1 - c0));
@@ -530,6 +534,11 @@ int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
     if (e != cudaSuccess) return cuda_fail(e, "bound fill");
     if (e2 != cudaSuccess) return cuda_fail(e2, "bound fill");
     return VR_OK;
+}
+
+int fill_bound_planes(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
+{
+    return fill_bound_slices(v, z0, std::min<int64_t>(z1, v->g.nz) + 1, s);
 }
 
 void release_texture(vr::Volume* v)
@@ -570,7 +579,7 @@ int refresh_texture(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
     cudaDestroySurfaceObject(surf);
     if (e != cudaSuccess) return cuda_fail(e, "texture fill");
     if (e2 != cudaSuccess) return cuda_fail(e2, "texture fill");
-    if (v->bound_array) return fill_bound_slices(v, s0, s1, s);   // same slices
+    if (v->bound_array) return fill_bound_planes(v, z0, z1, s);
     return VR_OK;
 }
 
@@ -596,10 +605,7 @@ int copy_texture_planes(vr::Volume* v, int64_t z0, int64_t n, const float* src, 
     if (e == cudaSuccess && z0 == 0) e = copy(0, 0, 1);
     if (e == cudaSuccess && z0 + n == nz) e = copy(nz - 1, nz + 1, 1);
     if (e != cudaSuccess) return cuda_fail(e, "texture copy");
-    if (v->bound_array) {
-        const int64_t s0 = z0 == 0 ? 0 : z0 + 1, s1 = z0 + n == nz ? nz + 2 : z0 + n + 1;
-        return fill_bound_slices(v, s0, s1, s);
-    }
+    if (v->bound_array) return fill_bound_planes(v, z0, z0 + n, s);
     return VR_OK;
 }
 
@@ -648,7 +654,7 @@ size_t texel_bytes(int format)
 }
 
 // Device bytes of the texture storage (texels of every layer, plus the int8
-// decode records) and of the MIP bounds (binary16 texels in the same layout,
+// decode records) and of the MIP bounds (bfloat16 pairs in cell slices,
 // plus the maximum word).
 size_t texture_bytes(const vr::VolumeGeom& g, int format, const TexLayout& L)
 {
@@ -659,32 +665,39 @@ size_t texture_bytes(const vr::VolumeGeom& g, int format, const TexLayout& L)
     return texels * texel_bytes(format) + dec;
 }
 
+// L: the layout of the bound texture's nz + 1 cell slices (see attach_bounds).
 size_t bounds_bytes(const vr::VolumeGeom& g, const TexLayout& L)
 {
-    return (size_t)g.nx * ((size_t)L.pitch << L.shift) * L.layers * 2 + sizeof(float);
+    return (size_t)g.nx * ((size_t)L.pitch << L.shift) * L.layers * 4 + sizeof(float);
+}
+
+// The bound texture's layout: the texture's stacking over nz + 1 cell slices.
+TexLayout bound_layout(const vr::VolumeGeom& g, int shift, int pitch)
+{
+    const int slices = g.nz + 1;
+    return TexLayout{slices, shift, pitch, (slices + (1 << shift) - 1) >> shift};
 }
 
 int attach_bounds(vr::Volume* v, cudaStream_t s)
 {
     if (v->dtype != VR_F32)
-        return fail(VR_ERR_UNSUPPORTED, "MIP bounds are for FP32 storage (binary16 bounds)");
+        return fail(VR_ERR_UNSUPPORTED, "MIP bounds are for FP32 storage");
     if (!v->has_tex || v->tex_format != VR_F32)
         return fail(VR_ERR_UNSUPPORTED, "MIP bounds need texture storage (attach it first)");
     if (v->bound_array) return VR_OK;
     if (v->texture_only)
         return fail(VR_ERR_UNSUPPORTED, "the volume's bricks were dropped: no new bounds");
-    // the texture's slices and stacking (vr_ray.cuh), in binary16
-    const int slices = v->g.nz + 2;
-    const int layers = (slices + (1 << v->stack_shift) - 1) >> v->stack_shift;
-    cudaChannelFormatDesc desc = cudaCreateChannelDescHalf();
+    // cell slices (two planes per 32-bit texel, as the pair formats) with the
+    // texture's stacking (vr_ray.cuh), in bfloat16
+    const TexLayout L = bound_layout(v->g, v->stack_shift, v->stack_pitch);
+    cudaChannelFormatDesc desc = cudaCreateChannelDesc<unsigned int>();
     cudaError_t e = cudaMalloc3DArray(
         &v->bound_array, &desc,
-        make_cudaExtent(v->g.nx, (size_t)v->stack_pitch << v->stack_shift, layers),
+        make_cudaExtent(v->g.nx, (size_t)v->stack_pitch << v->stack_shift, L.layers),
         cudaArrayLayered | cudaArraySurfaceLoadStore);
     if (e != cudaSuccess) {
         cudaGetLastError();
         v->bound_array = nullptr;
-        const TexLayout L{slices, v->stack_shift, v->stack_pitch, layers};
         return fail(e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA,
                     "MIP bound storage of %zu bytes: %s", bounds_bytes(v->g, L),
                     cudaGetErrorString(e));
@@ -712,7 +725,7 @@ int attach_bounds(vr::Volume* v, cudaStream_t s)
         release_bounds(v);
         return cuda_fail(e, "MIP bound texture object");
     }
-    int rc = fill_bound_slices(v, 0, slices, s);
+    int rc = fill_bound_slices(v, 0, L.slices, s);
     if (rc) release_bounds(v);
     return rc;
 }
@@ -855,7 +868,7 @@ int vr_mip_bounds_bytes(const int64_t dims[3], size_t* bytes_out)
     TexLayout L;
     rc = texture_layout(g, false, &L);
     if (rc) return rc;
-    *bytes_out = bounds_bytes(g, L);
+    *bytes_out = bounds_bytes(g, bound_layout(g, L.shift, L.pitch));
     return VR_OK;
 }
 
@@ -870,11 +883,8 @@ int vr_volume_device_bytes(vr_volume vol, size_t* library_bytes, size_t* caller_
         const TexLayout L{slices, v->stack_shift, v->stack_pitch,
                           (slices + (1 << v->stack_shift) - 1) >> v->stack_shift};
         lib += texture_bytes(v->g, v->tex_format, L);
-        if (v->bound_array) {
-            const TexLayout B{v->g.nz + 2, v->stack_shift, v->stack_pitch,
-                              (v->g.nz + 2 + (1 << v->stack_shift) - 1) >> v->stack_shift};
-            lib += bounds_bytes(v->g, B);
-        }
+        if (v->bound_array)
+            lib += bounds_bytes(v->g, bound_layout(v->g, v->stack_shift, v->stack_pitch));
     }
     if (v->bricks) caller += v->bytes;
     if (v->mask) caller += mask_macrocells(v->g) * sizeof(unsigned long long);

@@ -64,8 +64,9 @@ struct Volume {
     int stack_shift;        // 0: a layer per slice
     int stack_pitch;        // rows per stacked slice (ny + 2) when stacked
     void* dec;              // VR_I8: per-slice decode records (library-owned)
-    // optional MIP bounds (VR_F32 with texture storage, library-owned): the
-    // same slices, every voxel rounded toward +infinity to binary16
+    // optional MIP bounds (VR_F32 with texture storage, library-owned): cell
+    // slices as the pair formats (slice s packs planes s - 1 and s), every
+    // voxel rounded toward +infinity to bfloat16, stacked as the texture
     cudaArray_t bound_array;
     cudaTextureObject_t bound_tex;
     float* bound_vmax;      // device word: largest |voxel| seen by the fills
@@ -87,8 +88,9 @@ struct TexParams {
     int stack_shift, stack_pitch;   // see Volume
     const void* dec;        // VR_I8 / kI8Pair: float2 / float4 per slice
     int k_max;
-    // MIP bounds (0: none): binary16 texels rounded up from the FP32 voxels,
-    // laid out as `tex`; a sample whose bound plus the rounding margin
+    // MIP bounds (0: none): bfloat16 values rounded up from the FP32 voxels,
+    // two planes per 32-bit texel in cell slices (as the pair formats), with
+    // `tex`'s stacking; a sample whose bound plus the rounding margin
     // (bound_margin: from the largest |voxel|, a device word) stays below
     // the ray's running maximum cannot raise it (see march_tex_bound)
     cudaTextureObject_t bound;
@@ -251,13 +253,14 @@ cudaError_t fill_decode_records(const Volume& v, cudaStream_t s);
 // Fill texture slices [s0, s1) from the bricks through surface `surf`.
 cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1,
                          cudaStream_t s);
-// Fill MIP-bound slices [s0, s1) (VR_F32 bricks, binary16 rounded up)
-// through `surf`, raising *vmax to the largest |voxel| of those planes.
+// Fill MIP-bound cell slices [s0, s1) (VR_F32 bricks: slice s packs planes
+// s - 1 and s, clamped, each rounded up to bfloat16) through `surf`, raising
+// *vmax to the largest |voxel| of those planes.
 cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1, float* vmax,
                         cudaStream_t s);
 // The same slices written linearly (x fastest, slice after slice) to `dst`,
 // for a copy into an unstacked bound texture.
-cudaError_t fill_bounds_linear(const Volume& v, unsigned short* dst, int s0, int s1, float* vmax,
+cudaError_t fill_bounds_linear(const Volume& v, unsigned* dst, int s0, int s1, float* vmax,
                                cudaStream_t s);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
                         cudaStream_t s);

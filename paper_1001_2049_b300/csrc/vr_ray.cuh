@@ -241,31 +241,18 @@ __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, c
     }
 }
 
-// next_cell for the lockstep march (march_tex_lock), where a lane gathers
-// only for the samples it needs: one plane when only z rose by one, both
-// planes otherwise (measured faster there than the shared-slot form).
-template <int DT, bool STACK, typename TT, typename G>
-__device__ __forceinline__ void next_cell_up(const TT& T, cudaTextureObject_t t0, const G& c,
-                                             const float4& c0, const float4& c1, const G& n,
-                                             float4& n0, float4& n1)
+// floor(v) as an integer for |v| < 2^22 with one full-rate add (no
+// float-to-int conversion): s = v + 1.5 * 2^23 rounded toward -infinity is
+// floor(v) + 1.5 * 2^23 exactly, the float spacing in [2^23, 2^24) being 1,
+// so s's low mantissa bits hold floor(v) (IEEE 754 binary32), and s - 1.5 *
+// 2^23 is floor(v) as a float, exactly.  Sample positions stay within a
+// voxel or so of the box, and cube edges are at most 2^20.
+constexpr float kFloorShift = 0x1.8p23f;
+constexpr int kFloorShiftBits = 0x4B400000;
+
+__device__ __forceinline__ int floor_small(float v)
 {
-    if (n.gx == c.gx && n.gy == c.gy) {
-        if (n.iz == c.iz) {
-            n0 = c0;
-            n1 = c1;
-            return;
-        }
-        if constexpr (DT != kF16Pair && DT != kI8Pair) {
-            if (n.iz == c.iz + 1) {
-                float yt;
-                const int l = plane_layer<STACK>(T, n.iz + 1, n.gy, yt);
-                n0 = c1;
-                n1 = gather<DT>(t0, l, n.gx, yt);
-                return;
-            }
-        }
-    }
-    cell<DT, STACK>(T, t0, n.iz, n.gx, n.gy, n0, n1);
+    return __float_as_int(__fadd_rd(v, kFloorShift)) - kFloorShiftBits;
 }
 
 // Per-sample geometry: the gather coordinates of the cell and the weights.
@@ -286,13 +273,17 @@ __device__ __forceinline__ Geo geo(const PP& P, const Ray& r, float kf)
     Geo g;
     const float t = fmaf(kf, P.step, r.te);
     const float px = fmaf(t, r.dx, r.ox), py = fmaf(t, r.dy, r.oy), pz = fmaf(t, r.dz, r.oz);
-    const float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
+    const float flx = floorf(px), fly = floorf(py);
+    // the height's floor both as a float and as the slice index, from one
+    // full-rate add (no float-to-int conversion; see floor_small)
+    const float sz = __fadd_rd(pz, kFloorShift);
+    const float flz = sz - kFloorShift;
     g.gx = flx + 1.0f;
     g.gy = fly + 1.0f;
     g.fx = px - flx;
     g.fy = py - fly;
     g.fz = pz - flz;
-    g.iz = (int)flz + 1;
+    g.iz = __float_as_int(sz) - (kFloorShiftBits - 1);
     return g;
 }
 
@@ -419,21 +410,6 @@ struct Acc {
 // rounding moves them by a voxel, may lie outside, and their bits are never
 // used.  (A function rather than a lambda, so that it is inlined in every
 // kernel that marches with masks, the batched one included.)
-// floor(v) as an integer for |v| < 2^22 with one full-rate add (no
-// float-to-int conversion): s = v + 1.5 * 2^23 rounded toward -infinity is
-// floor(v) + 1.5 * 2^23 exactly, the float spacing in [2^23, 2^24) being 1,
-// so s's low mantissa bits hold floor(v) (IEEE 754 binary32).  Sample
-// positions stay within a voxel or so of the box, and cube edges are at most
-// 2^20.  (The same floor in geo, as floats, measured slower: one more
-// register in the bounded MIP march.)
-constexpr float kFloorShift = 0x1.8p23f;
-constexpr int kFloorShiftBits = 0x4B400000;
-
-__device__ __forceinline__ int floor_small(float v)
-{
-    return __float_as_int(__fadd_rd(v, kFloorShift)) - kFloorShiftBits;
-}
-
 // z_base: the first plane of a part volume (its masks cover its own planes).
 template <typename PP>
 __device__ __forceinline__ int mask_cell(const PP& P, const Ray& r, float kf, int& bit,
@@ -454,8 +430,12 @@ __device__ __forceinline__ int mask_cell(const PP& P, const Ray& r, float kf, in
 // lane fetches and evaluates a sample only when its cell's mask bit says the
 // clip can leave it visible; when no lane of the warp needs its sample, the
 // step costs the sample's cell alone.  Masks are loaded one sample ahead of
-// the gathers, gathers one sample ahead of the interpolation.  The result and
-// the sample count are those of march_tex.
+// the gathers, gathers one sample ahead of the interpolation.  Every step
+// loads its mask word and every needed sample gathers its cell afresh:
+// keeping the last word or the last cell's texels when they repeat measured
+// slower (the comparisons and selects cost more issue slots than the
+// cached loads and gathers they save).  The result and the sample count are
+// those of march_tex.
 template <int DT, int MODE, bool STACK, typename PP, typename TT>
 __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
                                               const float4* __restrict__ lut, const Ray& r,
@@ -473,7 +453,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
     const int m0 = mask_cell(P, r, 0.0f, b0);
     int m1 = mask_cell(P, r, 1.0f, b1), m2;
     const Rec r0 = __ldg(P.mask + m0);
-    Rec r1 = (m1 == m0) ? r0 : __ldg(P.mask + m1), r2;
+    Rec r1 = __ldg(P.mask + m1), r2;
     bool n0 = acc.need(r0, b0), n1;
     Geo g0, g1;
     float4 a0, a1, c0, c1;
@@ -485,28 +465,22 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
     for (;;) {
         // sample k + 2: cell and mask word; sample k + 1: geometry, gathers
         m2 = mask_cell(P, r, kf + 2.0f, b2);
-        r2 = (m2 == m1) ? r1 : __ldg(P.mask + m2);
+        r2 = __ldg(P.mask + m2);
         n1 = acc.need(r1, b1);
         if (n1) {
             g1 = geo(P, r, kf + 1.0f);
-            if (n0)
-                next_cell_up<DT, STACK>(T, t0, g0, a0, a1, g1, c0, c1);
-            else
-                cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
+            cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
         }
         ++k;
         if ((n0 && acc.add(P, lut, interp_t<DT, false>(T, a0, a1, g0))) || k >= r.K) break;
         kf += 1.0f;
         // the same one sample further on, the register sets swapped
         m1 = mask_cell(P, r, kf + 2.0f, b1);
-        r1 = (m1 == m2) ? r2 : __ldg(P.mask + m1);
+        r1 = __ldg(P.mask + m1);
         n0 = acc.need(r2, b2);
         if (n0) {
             g0 = geo(P, r, kf + 1.0f);
-            if (n1)
-                next_cell_up<DT, STACK>(T, t0, g1, c0, c1, g0, a0, a1);
-            else
-                cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
+            cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
         }
         ++k;
         if ((n1 && acc.add(P, lut, interp_t<DT, false>(T, c0, c1, g1))) || k >= r.K) break;
@@ -556,16 +530,47 @@ __device__ __forceinline__ float bound_margin(const TT& T)
     return fmaxf(__ldg(T.bound_vmax) * 0x1p-19f, 0x1p-126f);
 }
 
+// The MIP-bound texels of the cell at slice z (cell slices: slice z packs
+// the bounds of planes z - 1 and z, low half the lower plane) whose x/y
+// corner is texel (x-1, y-1): one gather returns all eight corners.
+template <bool STACK, typename TT>
+__device__ __forceinline__ uint4 bound_cell(const TT& T, cudaTextureObject_t tb, int z, float x,
+                                            float y)
+{
+    float yt;
+    const int l = plane_layer<STACK>(T, z, y, yt);
+    return gather_u32(tb, l, x, yt);
+}
+
+// The trilinear value of a cell's bound texels.  A bfloat16 is the upper
+// half of a float: the lower plane's bound is the texel shifted up by 16
+// bits; the upper plane's is the whole texel read as a float, whose low 16
+// bits (the lower plane's bound) only move it away from zero by less than
+// one bfloat16 step -- upwards for a positive bound, and the fill stores a
+// negative upper bound one step higher, so the texel stays an upper bound.
+__device__ __forceinline__ float bound_interp(const uint4& b, const Geo& g)
+{
+    return interp(make_float4(__uint_as_float(b.x << 16), __uint_as_float(b.y << 16),
+                              __uint_as_float(b.z << 16), __uint_as_float(b.w << 16)),
+                  make_float4(__uint_as_float(b.x), __uint_as_float(b.y),
+                              __uint_as_float(b.z), __uint_as_float(b.w)),
+                  g);
+}
+
 // MIP over FP32 texture storage with MIP bounds attached: the march of
-// march_tex runs over the bound texels (binary16, each voxel rounded toward
-// +infinity), whose trilinear value u is never below the sample's value v
-// by more than the FP32 rounding of the two interpolations (at most
-// 9 * 2^-24 of the largest |corner| each; bound_margin covers both).  A
-// sample is evaluated from the FP32 texture only when u + margin is not
-// below the running maximum, i.e. when it could raise it; a NaN or infinite
-// bound is never below.  Every sample that can change the maximum is
-// evaluated with march_tex's arithmetic, so the result and the sample count
-// are march_tex's bit for bit, while the march moves half the texel bytes.
+// march_tex runs over the bound texels (bfloat16, each voxel rounded toward
+// +infinity, both planes of a cell in one gather), whose trilinear value u
+// is never below the sample's value v by more than the FP32 rounding of the
+// two interpolations (at most 9 * 2^-24 of the largest |corner| each;
+// bound_margin covers both).  A sample is evaluated from the FP32 texture
+// only when u + margin is not below the running maximum, i.e. when it could
+// raise it; a NaN or infinite bound is never below.  Every sample that can
+// change the maximum is evaluated with march_tex's arithmetic, so the result
+// and the sample count are march_tex's bit for bit, while the march takes
+// one gather per sample for the bounds (gathering every sample, even in the
+// same cell, measured faster than testing for a change of cell and keeping
+// the held texels: the test and the selects cost more issue slots than the
+// gather).
 template <bool STACK, typename PP, typename TT>
 __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const Ray& r,
                                                Acc<VR_MIP>& acc)
@@ -574,26 +579,25 @@ __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const R
     const cudaTextureObject_t tb = T.bound, tf = T.tex;
     const float Kf = (float)r.K;
     const float margin = bound_margin(T);
-    auto take = [&](const Geo& g, const float4& u0, const float4& u1) {
-        if (!(interp(u0, u1, g) + margin < acc.m)) {
+    auto take = [&](const Geo& g, const uint4& u) {
+        if (!(bound_interp(u, g) + margin < acc.m)) {
             float4 e0, e1;
             cell<VR_F32, STACK>(T, tf, g.iz, g.gx, g.gy, e0, e1);
             acc.m = fmaxf(acc.m, interp(e0, e1, g));
         }
     };
     Geo ga = geo(P, r, 0.0f), gb;
-    float4 a0, a1, b0, b1;
-    cell<VR_F16, STACK>(T, tb, ga.iz, ga.gx, ga.gy, a0, a1);
+    uint4 a = bound_cell<STACK>(T, tb, ga.iz, ga.gx, ga.gy), b;
     float kf = 1.0f;
     for (;;) {
         gb = geo(P, r, kf);
-        next_cell<VR_F16, STACK>(T, tb, ga, a0, a1, gb, b0, b1);
-        take(ga, a0, a1);
+        b = bound_cell<STACK>(T, tb, gb.iz, gb.gx, gb.gy);
+        take(ga, a);
         if (kf >= Kf) break;
         kf += 1.0f;
         ga = geo(P, r, kf);
-        next_cell<VR_F16, STACK>(T, tb, gb, b0, b1, ga, a0, a1);
-        take(gb, b0, b1);
+        a = bound_cell<STACK>(T, tb, ga.iz, ga.gx, ga.gy);
+        take(gb, b);
         if (kf >= Kf) break;
         kf += 1.0f;
     }
@@ -719,7 +723,7 @@ __device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
     const int m0 = mask_cell(P, r, kf, b0, P.slice_base);
     int m1 = mask_cell(P, r, kf + 1.0f, b1, P.slice_base), m2;
     const Rec r0 = __ldg(P.mask + m0);
-    Rec r1 = (m1 == m0) ? r0 : __ldg(P.mask + m1), r2;
+    Rec r1 = __ldg(P.mask + m1), r2;
     bool n0 = acc.need(r0, b0), n1;
     Geo g0, g1;
     float4 a0, a1, c0, c1;
@@ -729,27 +733,21 @@ __device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
     }
     for (;;) {
         m2 = mask_cell(P, r, kf + 2.0f, b2, P.slice_base);
-        r2 = (m2 == m1) ? r1 : __ldg(P.mask + m2);
+        r2 = __ldg(P.mask + m2);
         n1 = acc.need(r1, b1);
         if (n1) {
             g1 = part_geo(kf + 1.0f);
-            if (n0)
-                next_cell_up<DT, STACK>(T, t0, g0, a0, a1, g1, c0, c1);
-            else
-                cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
+            cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
         }
         ++k;
         if ((n0 && acc.add(P, lut, interp_t<DT, false>(T, a0, a1, g0))) || k >= k1) break;
         kf += 1.0f;
         m1 = mask_cell(P, r, kf + 2.0f, b1, P.slice_base);
-        r1 = (m1 == m2) ? r2 : __ldg(P.mask + m1);
+        r1 = __ldg(P.mask + m1);
         n0 = acc.need(r2, b2);
         if (n0) {
             g0 = part_geo(kf + 1.0f);
-            if (n1)
-                next_cell_up<DT, STACK>(T, t0, g1, c0, c1, g0, a0, a1);
-            else
-                cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
+            cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
         }
         ++k;
         if ((n1 && acc.add(P, lut, interp_t<DT, false>(T, c0, c1, g1))) || k >= k1) break;
@@ -768,8 +766,8 @@ __device__ __forceinline__ int march_part_bound(const PP& P, const TT& T, const 
     if (k0 >= k1) return 0;
     const cudaTextureObject_t tb = T.bound, tf = T.tex;
     const float margin = bound_margin(T);
-    auto take = [&](const Geo& g, const float4& u0, const float4& u1) {
-        if (!(interp(u0, u1, g) + margin < acc.m)) {
+    auto take = [&](const Geo& g, const uint4& u) {
+        if (!(bound_interp(u, g) + margin < acc.m)) {
             float4 e0, e1;
             cell<VR_F32, STACK>(T, tf, g.iz, g.gx, g.gy, e0, e1);
             acc.m = fmaxf(acc.m, interp(e0, e1, g));
@@ -779,20 +777,19 @@ __device__ __forceinline__ int march_part_bound(const PP& P, const TT& T, const 
     float kf = (float)k0;
     Geo ga = geo(P, r, kf), gb;
     ga.iz -= P.slice_base;
-    float4 a0, a1, b0, b1;
-    cell<VR_F16, STACK>(T, tb, ga.iz, ga.gx, ga.gy, a0, a1);
+    uint4 a = bound_cell<STACK>(T, tb, ga.iz, ga.gx, ga.gy), b;
     kf += 1.0f;
     for (;;) {
         gb = geo(P, r, kf);
         gb.iz -= P.slice_base;
-        next_cell<VR_F16, STACK>(T, tb, ga, a0, a1, gb, b0, b1);
-        take(ga, a0, a1);
+        b = bound_cell<STACK>(T, tb, gb.iz, gb.gx, gb.gy);
+        take(ga, a);
         if (++k >= k1) break;
         kf += 1.0f;
         ga = geo(P, r, kf);
         ga.iz -= P.slice_base;
-        next_cell<VR_F16, STACK>(T, tb, gb, b0, b1, ga, a0, a1);
-        take(gb, b0, b1);
+        a = bound_cell<STACK>(T, tb, ga.iz, ga.gx, ga.gy);
+        take(gb, b);
         if (++k >= k1) break;
         kf += 1.0f;
     }

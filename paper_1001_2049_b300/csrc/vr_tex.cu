@@ -71,10 +71,46 @@ __global__ void __launch_bounds__(256) fill_kernel(const T* __restrict__ bricks,
     }
 }
 
-// MIP bounds: slices [s0, s1) laid out as fill_kernel lays out the FP32
-// texture, each voxel rounded toward +infinity to binary16 (never below the
-// voxel; +inf above 65504).  Also raises *vmax to the largest |voxel| read
-// (NaN ignored): |voxel| >= 0, so its bit pattern orders as an integer.
+// A float rounded toward +infinity to bfloat16 (its upper 16 bits): never
+// below the value; truncating the low bits raises a negative value, so only
+// positive values with low bits set move up one bfloat16 step (the largest
+// finite value to +inf).  NaN stays NaN (a NaN bound is never below a
+// running maximum, so its samples are always evaluated).
+__device__ __forceinline__ unsigned bf16_up(float v)
+{
+    const unsigned b = __float_as_uint(v);
+    if (v != v) return 0x7fc0u;
+    const unsigned hi = b >> 16;
+    return ((b & 0xffffu) != 0u && !(b >> 31)) ? hi + 1u : hi;
+}
+
+// The MIP-bound texel of cell slice sl at (x, y): the voxels of planes sl - 1
+// and sl (clamped to the cube), each rounded up to bfloat16, packed low =
+// plane sl - 1 (the pair layout of vr_ray.cuh); m is raised to their
+// largest |value| (NaN ignored).  The march reads the whole texel as the
+// upper plane's bound, the low half adding less than one bfloat16 step of
+// magnitude: so a negative upper bound is stored one step further up (a
+// bound of magnitude at most one step becomes +0).
+__device__ __forceinline__ unsigned bound_texel(const float* __restrict__ bricks,
+                                                const VolumeGeom& g, int x, int y, int sl,
+                                                float& m)
+{
+    const size_t row = ((size_t)(y >> kBrickShift) * g.nbx + (x >> kBrickShift)) * kBrickVoxels +
+                       ((y & 31) << 5) + (x & 31);
+    const size_t slab = (size_t)g.nbx * g.nby * kBrickVoxels;
+    const int za = min(max(sl - 1, 0), g.nz - 1), zb = min(sl, g.nz - 1);
+    const float lo = bricks[(size_t)(za >> kBrickShift) * slab + row + ((za & 31) << 10)];
+    const float hi = bricks[(size_t)(zb >> kBrickShift) * slab + row + ((zb & 31) << 10)];
+    m = fmaxf(m, fmaxf(fabsf(lo), fabsf(hi)));
+    unsigned h = bf16_up(hi);
+    if (h & 0x8000u) h = (h & 0x7fffu) <= 1u ? 0u : h - 1u;
+    return bf16_up(lo) | (h << 16);
+}
+
+// MIP bounds: cell slices [s0, s1) (slice s holds planes s - 1 and s, s in
+// [0, nz]) through a surface, stacked as the FP32 texture's slices.  Also
+// raises *vmax to the largest |voxel| read: |voxel| >= 0, so its bit pattern
+// orders as an integer.
 __global__ void __launch_bounds__(256) fill_bound_kernel(const float* __restrict__ bricks,
                                                          VolumeGeom g, cudaSurfaceObject_t surf,
                                                          int s0, int s1, int shift, int pitch,
@@ -84,16 +120,9 @@ __global__ void __launch_bounds__(256) fill_bound_kernel(const float* __restrict
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     float m = 0.0f;
     if (x < g.nx && y < g.ny) {
-        for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z) {
-            const int z = min(max(sl - 1, 0), g.nz - 1);
-            const size_t brick = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) *
-                                     g.nbx + (x >> kBrickShift);
-            const float v =
-                bricks[brick * kBrickVoxels + ((z & 31) << 10) + ((y & 31) << 5) + (x & 31)];
-            m = fmaxf(m, fabsf(v));
-            write_slice_row(surf, __half_as_ushort(__float2half_ru(v)), x, y, sl, g.ny, shift,
+        for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z)
+            write_slice_row(surf, bound_texel(bricks, g, x, y, sl, m), x, y, sl, g.ny, shift,
                             pitch);
-        }
     }
     raise_max(m, vmax);
 }
@@ -101,22 +130,15 @@ __global__ void __launch_bounds__(256) fill_bound_kernel(const float* __restrict
 // fill_bound_kernel's slices written linearly: slice s0 + j at dst + j nx ny,
 // x fastest (for a copy into an unstacked bound texture).
 __global__ void __launch_bounds__(256) fill_bound_linear_kernel(
-    const float* __restrict__ bricks, VolumeGeom g, unsigned short* __restrict__ dst, int s0,
-    int s1, float* __restrict__ vmax)
+    const float* __restrict__ bricks, VolumeGeom g, unsigned* __restrict__ dst, int s0, int s1,
+    float* __restrict__ vmax)
 {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     float m = 0.0f;
     if (x < g.nx && y < g.ny) {
-        for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z) {
-            const int z = min(max(sl - 1, 0), g.nz - 1);
-            const size_t brick = ((size_t)(z >> kBrickShift) * g.nby + (y >> kBrickShift)) *
-                                     g.nbx + (x >> kBrickShift);
-            const float v =
-                bricks[brick * kBrickVoxels + ((z & 31) << 10) + ((y & 31) << 5) + (x & 31)];
-            m = fmaxf(m, fabsf(v));
-            dst[((size_t)(sl - s0) * g.ny + y) * g.nx + x] = __half_as_ushort(__float2half_ru(v));
-        }
+        for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z)
+            dst[((size_t)(sl - s0) * g.ny + y) * g.nx + x] = bound_texel(bricks, g, x, y, sl, m);
     }
     raise_max(m, vmax);
 }
@@ -241,7 +263,7 @@ cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int z0, int z
     return cudaGetLastError();
 }
 
-cudaError_t fill_bounds_linear(const Volume& v, unsigned short* dst, int z0, int z1, float* vmax,
+cudaError_t fill_bounds_linear(const Volume& v, unsigned* dst, int z0, int z1, float* vmax,
                                cudaStream_t s)
 {
     if (z1 <= z0) return cudaSuccess;

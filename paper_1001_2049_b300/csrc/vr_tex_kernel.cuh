@@ -17,7 +17,7 @@
 // interpolated, which hides the texture latency behind the arithmetic.
 // With empty-space masks attached (SKIP, COMPOSITE), samples whose cell the
 // clip makes transparent are not fetched (vr_ray.cuh, march_tex_lock); with
-// MIP bounds attached (SKIP, MIP, FP32) the march reads binary16 upper
+// MIP bounds attached (SKIP, MIP, FP32) the march reads bfloat16 upper
 // bounds and fetches the FP32 corners only where a sample could raise the
 // maximum (march_tex_bound).
 #pragma once
@@ -86,7 +86,7 @@ cudaError_t launch_c(const MarchParams& p, const TexParams& t, cudaStream_t s)
 {
     // SKIP: COMPOSITE with empty-space masks (cells the clip makes
     // transparent are not fetched); MIP on FP32 storage with MIP bounds (the
-    // march reads the binary16 bounds and fetches the FP32 corners only of
+    // march reads the bfloat16 bounds and fetches the FP32 corners only of
     // samples that could raise the maximum).  Passing over MIP samples by
     // their cells' corner maxima would not pay: on noise about a quarter of
     // the cells have a corner above a ray's running maximum, so nearly every
