@@ -112,20 +112,38 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # algorithmic bytes: storage bytes of every voxel some sample's corners touch
 # ---------------------------------------------------------------------------
-# DRAM bytes (read + write) of one launch of the two render launches of the
-# 1024^3 / 32-view workload, from one ncu capture of the full-size launches
-# (one pass: dram__bytes_read.sum + dram__bytes_write.sum;
-# profiles/tex_kernel_f32_cube1024_orbit32.md): MIP at launch shape 2 150.31
-# GB read + 0.42 GB written; MIP with the binary16 MIP bounds at shape 6
-# 88.62 + 0.27 GB; composite with the empty-space masks at shape 7 32.01 +
-# 1.29 GB.
-# Other workloads (the --cube-edge/--views cases) report them scaled by their
-# algorithmic bytes.
-MEASURED_TRAFFIC = {"mip": 150.305302e9 + 0.415848e9,
-                    "mip_bounds": 88.621030e9 + 0.267783e9,
-                    "composite_masks": 32.006811e9 + 1.289451e9}
-MEASURED_ALGORITHMIC = {"mip": 136229959936.0, "mip_bounds": 136229959936.0,
-                        "composite_masks": 136433374037.6}
+# DRAM traffic of the two headline launches, per algorithmic byte, from one
+# ncu capture of the small case of the same kernels (512^3 FP32 cube, 4
+# orbit views at 960x540: inputs 4x the L2, a few GB on the device;
+# dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic bytes of
+# that launch), scaled here to the full-size launch by its algorithmic bytes.
+# At 512^3 the cube is 4x the L2 against 34x at 1024^3, so a kernel that
+# re-reads voxels across a view re-reads a little more at full size (the
+# MIP march without bounds: 0.95 at 512^3, 1.11 at 1024^3).  The ratios
+# hold for the kernel sources they were taken on: KERNEL_SHA is the digest
+# of every CUDA/C++ source of the library (kernel_sources_sha); when the
+# sources differ the bench reports no traffic rather than a stale one.
+TRAFFIC_CAPTURE = {
+    "capture": "prof_r2a: bench.py --cube-edge 512 --views 4 --shapes 6,3 (ncu --set full)",
+    "kernel_sha": None,
+    "mip_bounds": None,
+    "composite_masks": None,
+}
+
+
+def kernel_sources_sha() -> str:
+    """Digest of the library's CUDA/C++ sources and public header."""
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    csrc = os.path.join(root, "paper_1001_2049_b300", "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
+                   if f.endswith((".cu", ".cuh", ".cpp", ".h")))
+    h = hashlib.sha256()
+    for f in files + [os.path.join(root, "include", "vr.h")]:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def touched_voxels(cam, dims, step, w, h, device):
@@ -563,7 +581,14 @@ def _served_volume(i, dt, dev):
     return v
 
 
-def _serve(vols, names, rate, duration, batched, seed):
+#: Continuous batching splits images into row bands of about BAND_RAYS rays
+#: and gives a launch at most LAUNCH_RAYS rays, so no launch -- and none of
+#: the requests that arrive while it runs -- waits on one large view.
+BAND_RAYS = 1 << 19
+LAUNCH_RAYS = 1 << 22
+
+
+def _serve(vols, names, rate, duration, batched, seed, split=True):
     from paper_1001_2049_b300.serve import RenderJob, Server, latency_stats, run_poisson
     rng = np.random.default_rng(seed)
     dims = {n: vols[n].dims for n in names}
@@ -572,8 +597,12 @@ def _serve(vols, names, rate, duration, batched, seed):
         name = names[int(rng.integers(0, len(names)))]
         cam, w, h, mode, tf = synth.serve_request(dims[name], rng)
         return RenderJob(name, cam, w, h, mode, 0.5, tf)
-    server = (Server(vols, mem_budget=8 << 30, max_batch=64, streams=2) if batched else
-              Server(vols, mem_budget=8 << 30, max_batch=1, streams=1, per_request=True))
+    if batched:
+        server = Server(vols, mem_budget=8 << 30, max_batch=64, streams=2,
+                        band_rays=BAND_RAYS if split else 0,
+                        launch_rays=LAUNCH_RAYS if split else 0)
+    else:
+        server = Server(vols, mem_budget=8 << 30, max_batch=1, streams=1, per_request=True)
     done, wall, n = run_poisson(server, make, rate, duration, seed=seed)
     st = latency_stats(done)
     st["throughput_req_s"] = n / wall
@@ -581,15 +610,17 @@ def _serve(vols, names, rate, duration, batched, seed):
     return st
 
 
-def serving_leg(dev, rates=(50.0, 100.0, 200.0, 500.0), duration=3.0):
+def serving_leg(dev, rates=(50.0, 100.0, 200.0, 500.0), duration=20.0):
     """The served workload: Poisson arrivals of random requests (a random
     direction, a resolution from 512^2 to 1920x1080, 80 % composite, clip
     U[2,5] sigma) over six resident cubes (four 2048x2048x4096 and two
     1024^3, FP16, texture storage only: 146 GB of cube data), served with
-    continuous batching.  Head to head with the plain FP32 path (one
-    single-view render per request) on the cubes whose FP32 copies fit
-    together in memory (two large, two small): the same request streams on
-    those four cubes, served both ways."""
+    continuous batching (images split into row bands, launches capped in
+    rays; at 200 req/s also without splitting, for comparison).  Head to
+    head with the plain FP32 path (one single-view render per request) on
+    the cubes whose FP32 copies fit together in memory (two large, two
+    small): the same request streams on those four cubes, served both
+    ways."""
     t0 = time.perf_counter()
     names = [n for n, _ in synth.SERVE_CUBES]
     sub = [names[0], names[1], names[4], names[5]]
@@ -598,11 +629,17 @@ def serving_leg(dev, rates=(50.0, 100.0, 200.0, 500.0), duration=3.0):
     build_f16 = time.perf_counter() - t0
     out = {"cubes": names, "storage": "f16 layered textures, bricks dropped",
            "resident_cube_bytes": sum(2 * d[0] * d[1] * d[2] for _, d in synth.SERVE_CUBES),
+           "resident_device_bytes": {n: dict(zip(("library", "caller"), vols[n].device_bytes()))
+                                     for n in names},
+           "band_rays": BAND_RAYS, "launch_rays": LAUNCH_RAYS,
            "duration_s_per_rate": duration, "build_s": build_f16, "rates": {},
            "head_to_head": {"cubes": sub, "rates": {}}}
     for rate in rates:
         out["rates"][str(int(rate))] = _serve(vols, names, rate, duration, True,
                                              synth.SERVE_SEED + int(rate))
+        if rate == 200.0:
+            out["rates"]["200_without_splitting"] = _serve(
+                vols, names, rate, duration, True, synth.SERVE_SEED + int(rate), split=False)
         out["head_to_head"]["rates"][str(int(rate))] = {
             "continuous_batching_f16": _serve(vols, sub, rate, duration, True,
                                               synth.SERVE_SEED + 1000 + int(rate))}
@@ -810,11 +847,15 @@ def main():
             (mip_ms, mip_bytes, "mip")
         achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
 
+        sha = kernel_sources_sha()
+        fresh = TRAFFIC_CAPTURE["kernel_sha"] == sha
+
         def measured(kind, alg):
-            if args.storage != "texture" or kind is None or MEASURED_TRAFFIC.get(kind) is None:
+            if args.storage != "texture" or kind is None or not fresh or \
+                    TRAFFIC_CAPTURE.get(kind) is None:
                 return None
-            return MEASURED_TRAFFIC[kind] * alg / MEASURED_ALGORITHMIC[kind]
-        kinds = {"mip": "mip_bounds" if bounds_on else "mip",
+            return TRAFFIC_CAPTURE[kind] * alg
+        kinds = {"mip": "mip_bounds" if bounds_on else None,
                  "composite": "composite_masks" if masks_on else None}
         traffic = measured(kinds[dom], dom_bytes)
         comp_traffic = measured(kinds["composite"], comp_bytes)
@@ -897,9 +938,13 @@ def main():
                          "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum "
-                                           "of the full-size launch (one pass)"
-                                           if traffic else None,
+                         "traffic_source": (
+                             "ncu dram__bytes_read.sum + dram__bytes_write.sum per algorithmic "
+                             "byte of the small case (%s), times this launch's algorithmic "
+                             "bytes" % TRAFFIC_CAPTURE["capture"]) if traffic else (
+                             "null: the kernel sources (%s) differ from those of the capture "
+                             "(%s)" % (sha, TRAFFIC_CAPTURE["kernel_sha"])),
+                         "kernel_sources_sha": sha,
                          "algorithmic_bytes_per_launch": dom_bytes, "dominant": dom,
                          "touched_voxels_per_view": touched,
                          "composite": {"achieved": comp_bytes / (comp_ms / 1000.0) / 1e9,

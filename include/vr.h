@@ -411,6 +411,12 @@ typedef struct {
                                     done_value once this request's image is
                                     complete (written after a system fence)    */
     unsigned int done_value;
+    int32_t row0, rows;          /* rows > 0: render only rows [row0, row0 +
+                                    rows) of the w x h image (the same rays,
+                                    bit for bit), `out` holding just those rows
+                                    (rows x w pixels); rows = 0 (and row0 = 0):
+                                    the whole image.  Lets a caller split a
+                                    large view over several launches.          */
 } vr_request;
 
 /* Bytes of device workspace vr_render_batch needs (work and tile counters). */
@@ -514,7 +520,8 @@ int vr_volume_info(vr_volume vol, int64_t dims[3], int* dtype, void** brick_buf)
 /* Message for the last failing call on this thread ("" if none).           */
 const char* vr_last_error(void);
 
-/* ABI version of this header: 1.                                            */
+/* ABI version of this header: 2 (2 added vr_request's row band, making the
+ * record 136 bytes).                                                        */
 int vr_version(void);
 
 #ifdef __cplusplus

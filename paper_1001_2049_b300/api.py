@@ -48,10 +48,11 @@ class _Request(ctypes.Structure):
                 ("h", ctypes.c_int32), ("mode", ctypes.c_int32), ("step", ctypes.c_float),
                 ("out", ctypes.c_void_p), ("tf", ctypes.c_void_p),
                 ("samples", ctypes.c_void_p), ("done", ctypes.c_void_p),
-                ("done_value", ctypes.c_uint32)]
+                ("done_value", ctypes.c_uint32), ("row0", ctypes.c_int32),
+                ("rows", ctypes.c_int32)]
 
 
-assert ctypes.sizeof(_Camera) == 64 and ctypes.sizeof(_Request) == 128
+assert ctypes.sizeof(_Camera) == 64 and ctypes.sizeof(_Request) == 136
 
 
 @dataclass
@@ -59,7 +60,9 @@ class Request:
     """One view of one volume for ``render_batch``.  ``tf`` = (lut, v_lo,
     v_hi, clip, term_alpha) overrides the volume's transfer function;
     ``done`` = (int32 tensor, index) gets ``done_value`` when the image is
-    complete (a pinned host tensor lets the host watch it)."""
+    complete (a pinned host tensor lets the host watch it).  ``band`` =
+    (row0, rows) renders only those rows of the w x h image, into an ``out``
+    of rows x w pixels (the same rays as the whole image's)."""
     volume: "Volume"
     cam: np.void
     w: int
@@ -71,6 +74,7 @@ class Request:
     samples: torch.Tensor | None = None
     done: tuple | None = None
     done_value: int = 1
+    band: tuple | None = None
 
 
 def render_init(out: torch.Tensor, mode: str, stream=None) -> torch.Tensor:
@@ -121,7 +125,8 @@ def _batch_args(requests):
     keep, outs = [], []
     for i, rq in enumerate(requests):
         m = MODES[rq.mode]
-        shape = (rq.h, rq.w, 4) if m == VR_COMPOSITE else (rq.h, rq.w)
+        rows = rq.band[1] if rq.band is not None else rq.h
+        shape = (rows, rq.w, 4) if m == VR_COMPOSITE else (rows, rq.w)
         out = rq.out
         if out is None:
             out = torch.empty(shape, dtype=torch.float32, device=rq.volume.device)
@@ -146,6 +151,8 @@ def _batch_args(requests):
             flags, idx = rq.done
             r.done = flags.data_ptr() + 4 * int(idx)
             r.done_value = int(rq.done_value)
+        if rq.band is not None:
+            r.row0, r.rows = int(rq.band[0]), int(rq.band[1])
     return arr, keep, outs
 
 

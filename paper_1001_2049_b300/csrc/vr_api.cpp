@@ -269,6 +269,10 @@ int check_request(const vr_request& rq, int index)
     if (rc) return rc;
     if (rq.done && reinterpret_cast<uintptr_t>(rq.done) % 4 != 0)
         return fail(VR_ERR_ARG, "request %d: done must be 4-byte aligned", index);
+    if (rq.rows < 0 || rq.row0 < 0 || (rq.rows == 0 && rq.row0 != 0) ||
+        (int64_t)rq.row0 + rq.rows > rq.h)
+        return fail(VR_ERR_ARG, "request %d: row band [%d, %d + %d) outside the %d rows", index,
+                    rq.row0, rq.row0, rq.rows, rq.h);
     if (rq.tf) {
         const vr_transfer& t = *rq.tf;
         if (!t.rgba_lut || t.n < 2 || t.n > VR_MAX_LUT)
@@ -374,9 +378,12 @@ int batch_request(const vr_request& rq, vr::BatchParams* B, int* n_tex, vr::Volu
     q.dtype = v->dtype;
     q.tex_slot = tex_slot;
     q.lut_slot = lut_slot;
+    // the rows this request renders: a band of the image, or all of it
+    q.row0 = rq.rows > 0 ? rq.row0 : 0;
+    q.row_end = rq.rows > 0 ? rq.row0 + rq.rows : rq.h;
     const vr::BatchShape& S = vr::kBatchShapes[cfg];
     q.tiles_x = (rq.w + S.tx - 1) / S.tx;
-    q.n_tiles = q.tiles_x * ((rq.h + S.ty - 1) / S.ty);
+    q.n_tiles = q.tiles_x * ((q.row_end - q.row0 + S.ty - 1) / S.ty);
     q.first_item = B->total_items;
     B->total_items += q.n_tiles;
     B->n++;
@@ -827,7 +834,9 @@ size_t table_offset(const VolumeGeom& g, int dtype)
 
 extern "C" {
 
-int vr_version(void) { return 1; }
+static_assert(sizeof(vr_request) == 136, "vr_request is 136 bytes in ABI version 2");
+
+int vr_version(void) { return 2; }
 
 const char* vr_last_error(void) { return g_err.c_str(); }
 

@@ -115,7 +115,7 @@ __device__ __forceinline__ unsigned tex_pixel(const BatchReq& q, const BatchTex&
     const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
     ray::Acc<MODE> acc;
     const int k = ray::march_tex<DT, MODE, STACK>(q, T, lut, r, acc);
-    const size_t pix = (size_t)py * q.w + px;
+    const size_t pix = (size_t)(py - q.row0) * q.w + px;
     if (MODE == VR_COMPOSITE)
         reinterpret_cast<float4*>(q.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);
     else
@@ -198,16 +198,16 @@ __global__ void __launch_bounds__(kThreads, CLS == kBatchTexPair ? VR_BATCH_PAIR
         const int t = item - q.first_item;
         const int tx = t % q.tiles_x, ty = t / q.tiles_x;
         const int px = tx * S.tx + (warp % wpr) * S.px + (lane % S.px);
-        const int py = ty * S.ty + (warp / wpr) * S.py + (lane / S.px);
+        const int py = q.row0 + ty * S.ty + (warp / wpr) * S.py + (lane / S.px);
         unsigned count = 0;
-        if (px < q.w && py < q.h) {
+        if (px < q.w && py < q.row_end) {
             if constexpr (CLS == kBatchTex || CLS == kBatchTexPair) {
                 count = tex_pixel_any<CLS == kBatchTexPair>(q, B.tex[q.tex_slot], s_lut, px, py);
             } else {
                 const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
                 AccRT acc(q.mode);
                 count = (unsigned)march_bricks_rt(q, s_lut, r, acc);
-                const size_t pix = (size_t)py * q.w + px;
+                const size_t pix = (size_t)(py - q.row0) * q.w + px;
                 if (q.mode == VR_COMPOSITE)
                     reinterpret_cast<float4*>(q.out)[pix] =
                         make_float4(acc.r, acc.g, acc.b, acc.A);

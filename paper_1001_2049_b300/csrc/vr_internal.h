@@ -158,6 +158,7 @@ struct BatchReq {
     int tex_slot;          // -1: gather from the bricks
     int lut_slot;
     int tiles_x, n_tiles, first_item;
+    int row0, row_end;     // the image rows rendered; `out` starts at row0
     unsigned done_value;
 };
 

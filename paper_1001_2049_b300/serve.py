@@ -9,14 +9,20 @@ function for one of the resident cubes) arrive at any time; the server
   * admits a request when a launch slot is free and its output image fits in
     the memory budget still unused by requests in flight (admission by
     memory, first come first served);
-  * batches everything admitted since the last launch into one persistent
-    launch (``vr_render_batch``) on the next free stream, so requests that
-    arrive while others are on the GPU run in the next launch, overlapping
-    the running one on the device (continuous batching);
+  * batches admitted work into one persistent launch (``vr_render_batch``)
+    on the next free stream, so requests that arrive while others are on the
+    GPU run in the next launch, overlapping the running one on the device
+    (continuous batching).  A launch takes at most ``launch_rays`` rays, and
+    an image larger than ``band_rays`` is split into row bands (the same rays
+    bit for bit, each band a request of its own), so one large view cannot
+    hold a launch -- and the requests arriving behind it -- for long;
   * sees each request finish individually through its completion word in
     page-locked host memory, written by the kernel once the request's image
     is complete, and records its latency (completion - arrival, host
-    monotonic clock) for p50 / p99.
+    monotonic clock) for p50 / p99;
+  * can cancel a request: not yet admitted, it is dropped; admitted, its
+    bands not yet launched are dropped and the rest run out (a launched
+    kernel is not interrupted), and it is reported as cancelled.
 
 All rendering is done by the library's kernels; this is host-side control.
 """
@@ -34,6 +40,30 @@ from .api import MODES, Request, Volume, batch_workspace, render_batch
 from ._lib import VR_COMPOSITE
 
 
+def plan_bands(h: int, w: int, band_rays: int):
+    """Row bands (row0, rows) covering an h x w image, each of about
+    ``band_rays`` rays (whole rows; 0 or an image within the limit: one band
+    of every row)."""
+    if band_rays <= 0 or h * w <= band_rays:
+        return [(0, h)]
+    rows = max(1, band_rays // max(1, w))
+    return [(r, min(rows, h - r)) for r in range(0, h, rows)]
+
+
+def take_units(queue, max_units: int, launch_rays: int):
+    """Pop the units of the next launch from the front of ``queue`` (first
+    come, first served): at most ``max_units`` and, beyond the first, no
+    more than ``launch_rays`` rays in all (0: no ray limit)."""
+    out, rays = [], 0
+    while queue and len(out) < max_units:
+        u = queue[0]
+        if out and launch_rays > 0 and rays + u.rays > launch_rays:
+            break
+        out.append(queue.popleft())
+        rays += u.rays
+    return out
+
+
 @dataclass
 class RenderJob:
     """One render request as submitted to the server."""
@@ -48,8 +78,12 @@ class RenderJob:
     admitted: float = 0.0
     finished: float = 0.0
     out: torch.Tensor | None = None
-    slot: int = -1
     ticket: int = -1
+    cancelled: bool = False
+    units: int = 0                       # bands to render (planned, less any cancelled)
+    launched: int = 0                    # bands handed to a launch
+    seen: int = 0                        # bands seen complete (done word or launch)
+    retired: int = 0                     # bands whose launch has completed
 
     @property
     def out_bytes(self):
@@ -61,11 +95,24 @@ class RenderJob:
 
 
 @dataclass
+class _Unit:
+    """One row band of a job: one request of a batched launch."""
+    job: RenderJob
+    row0: int
+    rows: int
+    seen: bool = False
+
+    @property
+    def rays(self):
+        return self.rows * self.job.w
+
+
+@dataclass
 class _Launch:
-    jobs: list
+    units: list
     stream: torch.cuda.Stream
     event: torch.cuda.Event
-    flags: torch.Tensor | None          # pinned int32, one per job (batched launches)
+    flags: torch.Tensor | None          # pinned int32, one per unit (batched launches)
     issued: float = 0.0
 
 
@@ -73,29 +120,35 @@ class Server:
     """Render server over ``volumes`` (name -> Volume, resident on the GPU).
 
     ``mem_budget`` bounds the bytes of output images of requests in flight;
-    ``max_batch`` the requests per launch; ``streams`` the launches that can
-    be on the device at once.  ``per_request`` renders each request with its
-    own single-view render call (``Volume.render``) instead of batched
-    launches: the plain path the batched one is compared with.
+    ``max_batch`` the requests (bands) per launch; ``streams`` the launches
+    that can be on the device at once; ``band_rays`` the rays of a row band
+    (0: images are not split) and ``launch_rays`` the rays of a launch (0: no
+    limit).  ``per_request`` renders each request with its own single-view
+    render call (``Volume.render``) instead of batched launches: the plain
+    path the batched one is compared with.
     ``resident`` holds, per cube, the device bytes it keeps for the whole
     run (library-owned texture storage and MIP bounds, caller-owned bricks
     and masks), which the output budget comes on top of.
     """
 
     def __init__(self, volumes: dict, mem_budget: int = 1 << 30, max_batch: int = 64,
-                 streams: int = 2, keep_outputs: bool = False, per_request: bool = False):
+                 streams: int = 2, keep_outputs: bool = False, per_request: bool = False,
+                 band_rays: int = 0, launch_rays: int = 0):
         self.volumes = volumes
         self.per_request = per_request
         self.mem_budget = int(mem_budget)
         self.max_batch = int(max_batch)
         self.keep_outputs = keep_outputs
+        self.band_rays = 0 if per_request else int(band_rays)
+        self.launch_rays = 0 if per_request else int(launch_rays)
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.workspaces = [batch_workspace() for _ in range(streams)]
         self.free_streams = collections.deque(range(streams))
         self.pending = collections.deque()       # submitted, not admitted
-        self.admitted = []                       # admitted, not launched
+        self.queue = collections.deque()         # bands of admitted jobs, not launched
         self.in_flight = []                      # launches on the device
         self.done = []                           # finished jobs
+        self.cancelled = []                      # cancelled jobs, once nothing of theirs runs
         self.mem_in_use = 0
         self.lock = threading.Lock()
         self.next_ticket = 0
@@ -121,72 +174,121 @@ class Server:
             self.pending.append(job)
         return job.ticket
 
+    def cancel(self, ticket: int) -> bool:
+        """Cancel a submitted request; False if it is unknown or finished.
+        Bands already launched run out; the request is then listed in
+        ``cancelled`` instead of ``done``."""
+        with self.lock:
+            for job in self.pending:
+                if job.ticket == ticket:
+                    self.pending.remove(job)
+                    job.cancelled = True
+                    self.cancelled.append(job)
+                    return True
+            jobs = {u.job.ticket: u.job for u in self.queue}
+            for ln in self.in_flight:
+                for u in ln.units:
+                    jobs.setdefault(u.job.ticket, u.job)
+            job = jobs.get(ticket)
+            if job is None or job.cancelled:
+                return False
+            job.cancelled = True
+            dropped = [u for u in self.queue if u.job is job]
+            for u in dropped:
+                self.queue.remove(u)
+            job.units -= len(dropped)
+            self._retire_if_complete(job)
+            return True
+
     # -- server side ---------------------------------------------------------
     def _admit(self):
         with self.lock:
-            while self.pending and len(self.admitted) < self.max_batch:
+            while self.pending and len(self.queue) < self.max_batch:
                 job = self.pending[0]
                 if self.mem_in_use + job.out_bytes > self.mem_budget:
                     break                          # first come, first served
                 self.pending.popleft()
                 self.mem_in_use += job.out_bytes
                 job.admitted = time.monotonic()
-                self.admitted.append(job)
+                bands = plan_bands(job.h, job.w, self.band_rays)
+                job.units = len(bands)
+                for row0, rows in bands:
+                    self.queue.append(_Unit(job, row0, rows))
 
     def _launch(self):
-        if not self.admitted or not self.free_streams:
+        if not self.queue or not self.free_streams:
             return False
         si = self.free_streams.popleft()
         stream = self.streams[si]
-        jobs, self.admitted = self.admitted, []
+        with self.lock:
+            units = take_units(self.queue, self.max_batch, self.launch_rays)
         if self.per_request:
             with torch.cuda.stream(stream):
-                for job in jobs:
+                for u in units:
+                    job = u.job
                     vol = self.volumes[job.cube]
                     if job.tf is not None:
                         vol.set_transfer(*job.tf)
                     job.out = vol.render(np.asarray([job.cam]), job.w, job.h, job.mode,
                                          job.step, stream=stream)
+                    job.launched += 1
                 ev = torch.cuda.Event()
                 ev.record(stream)
-            self.in_flight.append(_Launch(jobs, stream, ev, None, time.monotonic()))
+            self.in_flight.append(_Launch(units, stream, ev, None, time.monotonic()))
             self.launches += 1
             return True
-        flags = torch.zeros(len(jobs), dtype=torch.int32).pin_memory()
+        flags = torch.zeros(len(units), dtype=torch.int32).pin_memory()
         reqs = []
         with torch.cuda.stream(stream):
-            for i, job in enumerate(jobs):
-                shape = (job.h, job.w, 4) if MODES[job.mode] == VR_COMPOSITE else (job.h, job.w)
-                job.out = torch.empty(shape, dtype=torch.float32, device="cuda")
-                job.slot = i
+            for i, u in enumerate(units):
+                job = u.job
+                if job.out is None:
+                    shape = ((job.h, job.w, 4) if MODES[job.mode] == VR_COMPOSITE
+                             else (job.h, job.w))
+                    job.out = torch.empty(shape, dtype=torch.float32, device="cuda")
+                band = None if u.rows == job.h else (u.row0, u.rows)
                 reqs.append(Request(self.volumes[job.cube], job.cam, job.w, job.h, job.mode,
-                                    job.step, out=job.out, tf=job.tf, done=(flags, i),
-                                    done_value=1))
+                                    job.step, out=job.out[u.row0:u.row0 + u.rows], tf=job.tf,
+                                    done=(flags, i), done_value=1, band=band))
+                job.launched += 1
             render_batch(reqs, self.workspaces[si], stream=stream)
             ev = torch.cuda.Event()
             ev.record(stream)
-        self.in_flight.append(_Launch(jobs, stream, ev, flags, time.monotonic()))
+        self.in_flight.append(_Launch(units, stream, ev, flags, time.monotonic()))
         self.launches += 1
         return True
 
+    def _retire_if_complete(self, job: RenderJob):
+        """A job leaves the server once every band handed to a launch has
+        retired and no band waits in the queue (units counts what remains)."""
+        if job.retired < job.launched or job.units > job.launched:
+            return
+        if job.finished == 0.0:
+            job.finished = time.monotonic()
+        self.mem_in_use -= job.out_bytes
+        if not self.keep_outputs:
+            job.out = None
+        (self.cancelled if job.cancelled else self.done).append(job)
+
     def _reap(self):
-        """Record jobs whose completion word is set; free finished launches."""
+        """Record bands whose completion word is set (a job finishes with its
+        last band); free finished launches."""
         now = time.monotonic()
         still = []
         for ln in self.in_flight:
-            if ln.flags is not None:
-                f = ln.flags.numpy()
-                for job in ln.jobs:
-                    if job.finished == 0.0 and f[job.slot] != 0:
-                        job.finished = now
-            if ln.event.query():
-                for job in ln.jobs:
-                    if job.finished == 0.0:
-                        job.finished = now
-                    self.mem_in_use -= job.out_bytes
-                    if not self.keep_outputs:
-                        job.out = None
-                    self.done.append(job)
+            finished = ln.event.query()
+            f = ln.flags.numpy() if ln.flags is not None else None
+            for i, u in enumerate(ln.units):
+                if not u.seen and (finished or (f is not None and f[i] != 0)):
+                    u.seen = True
+                    u.job.seen += 1
+                    if u.job.seen == u.job.units and u.job.finished == 0.0:
+                        u.job.finished = now
+            if finished:
+                for u in ln.units:
+                    u.job.retired += 1
+                    with self.lock:
+                        self._retire_if_complete(u.job)
                 self.free_streams.append(self.streams.index(ln.stream))
             else:
                 still.append(ln)
@@ -200,7 +302,7 @@ class Server:
 
     def idle(self):
         with self.lock:
-            return not self.pending and not self.admitted and not self.in_flight
+            return not self.pending and not self.queue and not self.in_flight
 
     def drain(self, timeout: float = 120.0):
         t0 = time.monotonic()

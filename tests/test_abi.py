@@ -41,7 +41,7 @@ def test_library_is_built_for_sm_103a():
 
 def test_version_and_volume_bytes_host_only():
     lib = _lib.load()
-    assert lib.vr_version() == 1
+    assert lib.vr_version() == 2
     out = ctypes.c_size_t(0)
     dims = (ctypes.c_int64 * 3)(64, 64, 128)
     assert lib.vr_volume_bytes(dims, _lib.VR_F32, ctypes.byref(out)) == 0

@@ -240,3 +240,52 @@ def test_batch_on_masked_volumes_equals_renders_without():
         assert torch.equal(a, b), (k, reqs[k].mode, reqs[k].tf[1])
     for rq, img in zip(twin_reqs[:8], ref[:8]):
         assert torch.equal(single(rq), img)
+
+
+def test_row_bands_give_the_whole_images_rows(scene):
+    # a request limited to a band of rows renders exactly those rows of the
+    # whole image (the same rays), whatever the band and the tile shape;
+    # bands of one image can go to different launches
+    reqs = requests_for(scene, 18, 9)
+    whole = render_batch(reqs)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    band_reqs = []
+    for rq in reqs:
+        cuts = sorted({0, rq.h} | {int(x) for x in rng.integers(1, max(2, rq.h), 2)})
+        for r0, r1 in zip(cuts[:-1], cuts[1:]):
+            band_reqs.append(Request(rq.volume, rq.cam, rq.w, rq.h, rq.mode, rq.step, tf=rq.tf,
+                                     band=(r0, r1 - r0)))
+    outs = []
+    for k in range(0, len(band_reqs), 7):                 # several launches
+        outs += render_batch(band_reqs[k:k + 7])
+    torch.cuda.synchronize()
+    i = 0
+    for rq, ref in zip(reqs, whole):
+        got = []
+        while i < len(band_reqs) and band_reqs[i].cam is rq.cam:
+            got.append(outs[i])
+            i += 1
+        assert torch.equal(torch.cat(got), ref), rq.mode
+    assert i == len(band_reqs)
+
+
+def test_row_band_arguments_are_checked(scene):
+    # through the C ABI: a band must lie inside the image, rows = 0 means the
+    # whole image (with row0 = 0)
+    from paper_1001_2049_b300 import _lib
+    from paper_1001_2049_b300.api import _batch_args
+    v = scene[0][0]
+    cam = synth.random_sphere_cameras(scene[0][2], 1, 16, 12, 1)[0]
+    arr, keep, outs = _batch_args([Request(v, cam, 16, 12, "mip", 0.5)])
+    ws = batch_workspace()
+    lib = _lib.load()
+    for row0, rows in ((0, 13), (5, 8), (-1, 3), (2, -1), (3, 0)):
+        arr[0].row0, arr[0].rows = row0, rows
+        rc = lib.vr_render_batch(arr, 1, ws.data_ptr(), ws.numel(), None)
+        assert rc == _lib.VR_ERR_ARG, (row0, rows)
+        assert b"row band" in lib.vr_last_error()
+    arr[0].row0, arr[0].rows = 4, 8
+    assert lib.vr_render_batch(arr, 1, ws.data_ptr(), ws.numel(), None) == 0
+    torch.cuda.synchronize()
+    del keep

@@ -110,3 +110,41 @@ def test_per_request_server_gives_the_same_images(cubes):
         assert job.out.shape[0] == 1
         ref = alone(cubes, job)
         assert torch.allclose(job.out[0], ref, rtol=0, atol=1e-6), (job.cube, job.mode)
+
+
+def test_split_requests_are_the_same_alone_and_in_the_mix(cubes):
+    # images split into row bands of about 300 rays, launches of at most
+    # 2000 rays: every band of a request may run in a different launch, and
+    # the assembled image is the single-view render's
+    server = Server({k: v[0] for k, v in cubes.items()}, mem_budget=1 << 22, max_batch=16,
+                    streams=2, keep_outputs=True, band_rays=300, launch_rays=2000)
+    jobs = make_jobs(cubes, 40, 5)
+    for k in range(0, len(jobs), 6):
+        for job in jobs[k:k + 6]:
+            server.submit(job)
+        server.step()
+    server.drain()
+    assert len(server.done) == len(jobs)
+    assert server.launches > len(jobs) // 4
+    assert server.mem_in_use == 0
+    for job in jobs:
+        ref = alone(cubes, job)
+        assert torch.allclose(job.out, ref, rtol=0, atol=1e-6), (job.cube, job.mode)
+        assert job.finished >= job.admitted >= job.arrival
+
+
+def test_cancelled_requests_leave_the_server(cubes):
+    server = Server({k: v[0] for k, v in cubes.items()}, mem_budget=1 << 20, max_batch=4,
+                    streams=1, keep_outputs=True, band_rays=256, launch_rays=1024)
+    jobs = make_jobs(cubes, 24, 6)
+    tickets = [server.submit(j) for j in jobs]
+    server.step()                                  # some admitted and one launch out
+    cancel = tickets[1::3]
+    assert all(server.cancel(t) for t in cancel)
+    assert not server.cancel(10 ** 6)
+    server.drain()
+    assert sorted(j.ticket for j in server.cancelled) == sorted(cancel)
+    assert sorted(j.ticket for j in server.done) == sorted(set(tickets) - set(cancel))
+    assert server.mem_in_use == 0 and server.idle()
+    for job in server.done:
+        assert torch.allclose(job.out, alone(cubes, job), rtol=0, atol=1e-6)
