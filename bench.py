@@ -124,10 +124,13 @@ class Clocks:
 # of every CUDA/C++ source of the library (kernel_sources_sha); when the
 # sources differ the bench reports no traffic rather than a stale one.
 TRAFFIC_CAPTURE = {
-    "capture": "prof_r2a: bench.py --cube-edge 512 --views 4 --shapes 6,3 (ncu --set full)",
-    "kernel_sha": None,
-    "mip_bounds": None,
-    "composite_masks": None,
+    "capture": "prof_r2a: bench.py --cube-edge 512 --views 4 --steps 1 --warmup 1 --shapes 6,3 "
+               "(ncu --set full; profiles/tex_kernel_f32_cube1024_orbit32.md)",
+    "kernel_sha": "f9ba8ca55c84db7b",
+    # MIP with bfloat16 bounds, shape 3: (2.407082 + 0.011679) GB over 2.130716 GB
+    "mip_bounds": (2.407082e9 + 0.011679e9) / 2.130716e9,
+    # composite with masks, shape 6: (0.352616 + 0.033497) GB over 2.153293 GB
+    "composite_masks": (0.352616e9 + 0.033497e9) / 2.153293e9,
 }
 
 
@@ -195,9 +198,23 @@ def touched_voxels(cam, dims, step, w, h, device):
 # ---------------------------------------------------------------------------
 # the reference arm and the CPU baseline: the FP64 oracle on host cores
 # ---------------------------------------------------------------------------
-def oracle_throughput(host_cube, cams, wl, budget_s, seed=5, w=W, h=H):
+def cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo), or the platform's."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
+def oracle_throughput(host_cube, cams, wl, budget_s, seed=5, w=W, h=H, nthreads=0):
     """Run the oracle on random pixels of the views (composite then MIP) for
-    about budget_s seconds; returns (samples/s, frames/s, threads, sample)."""
+    about budget_s seconds (nthreads: OpenMP threads, 0 = all); returns
+    (samples/s, frames/s, threads, sample)."""
     import oracle
     vol = oracle.Volume(host_cube)
     tf = oracle.TF(synth.default_lut(), wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
@@ -209,25 +226,28 @@ def oracle_throughput(host_cube, cams, wl, budget_s, seed=5, w=W, h=H):
                         rng.integers(0, h, n)], axis=1).astype(np.int32)
         for mode in (oracle.COMPOSITE, oracle.MIP):
             t0 = time.perf_counter()
-            r = oracle.render(vol, cams, w, h, mode, wl.step, tf, pixels=pix, bands=nb)
+            r = oracle.render(vol, cams, w, h, mode, wl.step, tf, pixels=pix, bands=nb,
+                              nthreads=nthreads)
             secs += time.perf_counter() - t0
             samples += int(r.nsamples.sum())
             pixels_done += n
         n = min(n * 2, 1 << 18)
     # a frame = W*H pixels; the two modes each count as frames
     fps = pixels_done / (w * h) / secs
-    sample = "%d random pixels of the 32 views (composite and MIP), %.1f s" % (pixels_done, secs)
-    return samples / secs, fps, oracle.num_threads(), sample
+    sample = "%d random pixels of the %d views (composite and MIP), %.1f s" % (
+        pixels_done, len(cams), secs)
+    return samples / secs, fps, nthreads if nthreads > 0 else oracle.num_threads(), sample
 
 
-def precision_leg(cube, cams, W, H, wl, lut, pixels, reps=3):
+def precision_leg(cube, cams, W, H, wl, lut, pixels, reps=3, touched=None, peak=None):
     """The same cube and views stored as FP16 and as int8 with per-plane
     scale and offset, in both texture formats (one texel per voxel, and
     pair texels: a voxel with its neighbour in the next plane; the same
     images bit for bit), empty-space masks for the composite launch: launch
-    times of each format, the faster format's as the row's, and the images'
-    values at ``pixels`` for the error against the oracle (evaluated in the
-    CPU leg)."""
+    times of each format, the faster format's as the row's, its roofline at
+    the storage's own bytes (``touched`` voxels a view at 2 or 1 bytes, plus
+    the images; int8 adds its two per-plane tables), and the images' values at
+    ``pixels`` for the error against the oracle (evaluated in the CPU leg)."""
     out, values = {}, {}
     stream = torch.cuda.current_stream()
     comp = torch.empty((len(cams), H, W, 4), dtype=torch.float32, device=cube.device)
@@ -252,6 +272,16 @@ def precision_leg(cube, cams, W, H, wl, lut, pixels, reps=3):
         best = min(formats.values(),
                    key=lambda r: r["composite_ms_per_launch"] + r["mip_ms_per_launch"])
         out[dt] = dict(best, formats=formats)
+        if touched and peak:
+            vb = {"f16": 2, "i8": 1}[dt]
+            tables = 2 * 4 * wl.dims[2] if dt == "i8" else 0
+            roof = {}
+            for mode, px_bytes in (("composite", 16), ("mip", 4)):
+                alg = (touched * vb + W * H * px_bytes + tables) * len(cams)
+                gbs = alg / (best[mode + "_ms_per_launch"] / 1000.0) / 1e9
+                roof[mode] = {"algorithmic_bytes_per_launch": alg, "achieved_gbs": gbs,
+                              "frac": gbs / peak}
+            out[dt]["roofline_at_storage_bytes"] = roof
     return out, values
 
 
@@ -319,7 +349,7 @@ def run_reference(args):
                    "fps": fps,
                    "projected_ms_per_full_step": 1000.0 * 64 / fps if fps else None},
         "cpu_baseline": {"value": sps, "unit": "samples/s", "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": sps, "unit": "samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -443,6 +473,71 @@ def batched_leg(dev, reps=3):
     for v in vols + f32:
         v.close()
     return res
+
+
+def small_workload_leg(dev, reps=50, check=True):
+    """The 64x64x128 workload: its 256^2 orthographic view along the
+    frequency axis and the 32 orbit views at 256^2 (the precision variants'
+    views), stored as FP32, FP16 and int8 (texture storage; empty-space
+    masks for compositing; MIP bounds for FP32), MIP and composite: ms per
+    launch, frames/s and samples/s (launch-bound at this size: no roofline
+    figure).  With ``check``, each image's largest error at every pixel
+    against the FP64 oracle on the decoded storage and on the float32
+    source, acceptance sets as in the tests."""
+    wl = synth.SMALL
+    lut = synth.default_lut()
+    cube = wl.cube(dev)
+    host = cube.cpu().numpy()
+    views = {"ortho_256": (synth.small_camera(), 256, 256),
+             "orbit32_256": (synth.orbit_cameras(wl.dims, 32, 256, 256), 256, 256)}
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": wl.name, "cube": "64x64x128 float32, 5 sources SNR 3-10", "step": wl.step,
+           "clip_sigma": wl.clip, "rows": {}}
+    if check:
+        import oracle
+        from oracle import quantize
+        ovols = {"f32": oracle.Volume(host), "f16": oracle.Volume(quantize.to_f16(host)),
+                 "i8": oracle.Volume(*quantize.quantize_i8(host))}
+        tf = oracle.TF(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
+        tol = {"f32": 1e-4, "f16": 2e-3, "i8": 1e-2}
+        mip_scale = float(host.max() - host.min())
+    for dt in ("f32", "f16", "i8"):
+        v = Volume(cube, dt)
+        v.attach_texture()
+        v.attach_masks()
+        if dt == "f32":
+            v.attach_mip_bounds()
+        v.set_transfer(lut, wl.clip, wl.v_hi, wl.clip, wl.term_alpha)
+        for vname, (cams, w, h) in views.items():
+            row = {}
+            for mode in ("composite", "mip"):
+                img = torch.empty((len(cams), h, w, 4) if mode == "composite" else
+                                  (len(cams), h, w), device=dev)
+                cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+                v.render(cams, w, h, mode, wl.step, out=img, count=cnt)
+                torch.cuda.synchronize()
+                ms = event_ms(lambda: v.render(cams, w, h, mode, wl.step, out=img), reps,
+                              stream)
+                r = {"ms_per_launch": ms, "fps": len(cams) / (ms / 1000.0),
+                     "samples_per_s": int(cnt.item()) / (ms / 1000.0)}
+                if check:
+                    got = img.cpu().numpy().reshape(-1, 4 if mode == "composite" else 1)
+                    om = oracle.COMPOSITE if mode == "composite" else oracle.MIP
+                    bands = oracle.fp32_bands(wl.dims, cams, wl.step, w, h)
+                    sc = mip_scale if mode == "mip" else 1.0
+                    for ref, key in ((dt, "vs_decoded"), ("f32", "vs_source")):
+                        if dt == "f32" and key == "vs_source":
+                            continue
+                        res = oracle.render(ovols[ref], cams, w, h, om, wl.step, tf, bands=bands)
+                        ok, err = oracle.match(res, got, 1e-4 if key == "vs_decoded" else tol[dt],
+                                               got.shape[1], sc)
+                        fin = err[np.isfinite(err)]
+                        r["max_err_" + key] = float(fin.max()) if fin.size else 0.0
+                        r["pixels_over_tol_" + key] = int((~ok).sum())
+                row[mode] = r
+            out["rows"]["%s %s" % (dt, vname)] = row
+        v.close()
+    return out
 
 
 def tf_edit_leg(vol, cams, W, H, wl, lut):
@@ -871,7 +966,8 @@ def main():
             idx = torch.from_numpy(pixels.astype(np.int64)).to(dev)
             values[("f32", "composite")] = comp[idx[:, 0], idx[:, 2], idx[:, 1]].cpu().numpy()
             values[("f32", "mip")] = mip[idx[:, 0], idx[:, 2], idx[:, 1]].cpu().numpy()
-            prec, pv = precision_leg(cube, cams, W, H, wl, lut, pixels)
+            prec, pv = precision_leg(cube, cams, W, H, wl, lut, pixels, touched=touched,
+                                     peak=peak)
             values.update(pv)
             for dt, row in prec.items():
                 ms = row["composite_ms_per_launch"] + row["mip_ms_per_launch"]
@@ -883,7 +979,13 @@ def main():
             sps, cfps, threads, sample = oracle_throughput(host_cube, cams, wl,
                                                            args.cpu_budget, w=W, h=H)
             cpu = {"value": sps, "unit": "samples/s", "cores": threads, "kind": "oracle",
-                   "sample": sample, "fps": cfps}
+                   "sample": sample, "fps": cfps, "cpu_model": cpu_model(),
+                   "nproc": os.cpu_count()}
+            # the same oracle on one thread, on a smaller sample
+            sps1, _, _, sample1 = oracle_throughput(host_cube, cams, wl,
+                                                    max(2.0, args.cpu_budget / 5), seed=11,
+                                                    w=W, h=H, nthreads=1)
+            cpu["one_thread"] = {"value": sps1, "unit": "samples/s", "sample": sample1}
             if values:
                 # the oracle's results at the checked pixels also give the
                 # error of every storage's images against FP64
@@ -904,6 +1006,8 @@ def main():
             vol.close()
             del vol, cube
             torch.cuda.empty_cache()
+            extra["small_workload"] = run_leg(
+                lambda: small_workload_leg(dev, check=args.cpu_budget > 0))
             extra["batched"] = run_leg(lambda: batched_leg(dev))
             torch.cuda.empty_cache()
             extra["serving"] = run_leg(lambda: serving_leg(dev))

@@ -82,6 +82,12 @@ def lib():
             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_TF),
             ctypes.POINTER(_Bands), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        _lib.vro_render_partial.restype = ctypes.c_int
+        _lib.vro_render_partial.argtypes = [
+            ctypes.POINTER(_Volume), ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+            ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_TF),
+            ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_int]
         _lib.vro_maxalt.restype = ctypes.c_int
         _lib.vro_num_threads.restype = ctypes.c_int
         _lib.vro_sample_at.restype = ctypes.c_double
@@ -299,6 +305,37 @@ def render_subcubes(volume: Volume, cams: np.ndarray, w: int, h: int, mode: int,
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     return Result(out, nalt, flags, np.zeros(npix, dtype=np.int64))
+
+
+def render_partial(volume: Volume, cams: np.ndarray, w: int, h: int, mode: int,
+                   step: float, tf: TF, cell_lo, part: int,
+                   pixels: np.ndarray | None = None, nthreads: int = 0) -> np.ndarray:
+    """Sub-cube ``part`` of the split ``cell_lo`` rendered alone into its
+    partial result (the primary FP64 values, (npix, 4): composite (C, A);
+    MIP / SUM in channel 0), from an empty start, stopping at its own
+    opacity -- what one node renders before scene integration (§3.1 item
+    4)."""
+    cams = np.ascontiguousarray(cams)
+    assert cams.dtype.itemsize == 64
+    n_views = cams.shape[0]
+    if pixels is None:
+        v, py, px = np.meshgrid(np.arange(n_views), np.arange(h), np.arange(w),
+                                indexing="ij")
+        pixels = np.stack([v.ravel(), px.ravel(), py.ravel()], axis=1)
+    pixels = np.ascontiguousarray(pixels, dtype=np.int32)
+    npix = pixels.shape[0]
+    lo = np.ascontiguousarray(cell_lo, dtype=np.int64)
+    out = np.zeros((npix, 4), dtype=np.float64)
+    cv, keep_v = volume._c()
+    ct, keep_t = tf._c()
+    rc = lib().vro_render_partial(ctypes.byref(cv), cams.ctypes.data, n_views, w, h, mode,
+                                  float(step), ctypes.byref(ct), lo.ctypes.data, int(lo.size),
+                                  int(part), pixels.ctypes.data, npix, out.ctypes.data,
+                                  int(nthreads))
+    del keep_v, keep_t
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    return out
 
 
 def sample_at(volume: Volume, x: float, y: float, z: float) -> float:

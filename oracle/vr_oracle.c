@@ -889,6 +889,90 @@ int vro_render_subcubes(const vro_volume* vol, const vro_camera* cams, int n_vie
     return bad ? -1 : 0;
 }
 
+/*
+ * One sub-cube's partial result alone (the image a node of the paper's
+ * pipeline renders for its sub-cube before scene integration, §3.1 item 4):
+ * the primary FP64 result of sub-cube `part` of the split cell_lo[0..n_sub)
+ * (as vro_render_subcubes), from an empty start, stopping at its own
+ * opacity.  out[i*4 + c]: composite (C, A), MIP the maximum (-inf when no
+ * sample falls in the sub-cube), SUM the sum, in channel 0.
+ */
+int vro_render_partial(const vro_volume* vol, const vro_camera* cams, int n_views, int w,
+                       int h, int mode, double step, const vro_tf* tf, const int64_t* cell_lo,
+                       int n_sub, int part, const int32_t* pix, int64_t npix, double* out,
+                       int nthreads)
+{
+    if (!vol || !cams || !tf || !cell_lo || !pix || !out) return -1;
+    if (vol->n[0] < 2 || vol->n[1] < 2 || vol->n[2] < 2 || !(step > 0.0) ||
+        tf->n_lut < 2 || w <= 0 || h <= 0 || n_views <= 0 || n_sub < 1 || part < 0 ||
+        part >= n_sub)
+        return -1;
+    if (mode != VRO_MIP && mode != VRO_COMPOSITE && mode != VRO_SUM) return -1;
+    if (cell_lo[0] != 0) return -1;
+    for (int i = 1; i < n_sub; ++i)
+        if (!(cell_lo[i] > cell_lo[i - 1]) || cell_lo[i] >= vol->n[2] - 1) return -1;
+    double* lutc = (double*)malloc(sizeof(double) * 4 * (size_t)tf->n_lut);
+    if (!lutc) return -1;
+    correct_table(tf, step, lutc);
+    double clip_rgba[4];
+    classify(tf, lutc, tf->clip, clip_rgba);
+    const vro_bands none_b = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int bad = 0;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel num_threads(nt) reduction(| : bad)
+#endif
+    {
+        sub_work wk;
+        wk.C = (double*)malloc(sizeof(double) * 3 * (size_t)n_sub);
+        wk.A = (double*)malloc(sizeof(double) * (size_t)n_sub);
+        wk.V = (double*)malloc(sizeof(double) * (size_t)n_sub);
+        wk.done = (int*)malloc(sizeof(int) * (size_t)n_sub);
+        wk.order = (int*)malloc(sizeof(int) * 2 * (size_t)n_sub + 2 * sizeof(int));
+        if (!wk.C || !wk.A || !wk.V || !wk.done || !wk.order) bad = 1;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t i = 0; i < npix; ++i) {
+            int view = pix[3 * i], px = pix[3 * i + 1], py = pix[3 * i + 2];
+            if (bad || view < 0 || view >= n_views || px < 0 || px >= w || py < 0 || py >= h) {
+                bad = 1;
+                continue;
+            }
+            double o[3], d[3];
+            make_ray(&cams[view], w, h, px, py, o, d);
+            double tn, tf_, miss_dist, face_dist, dn, df;
+            slab(o, d, vol->n, &tn, &tf_, &miss_dist, &face_dist, &dn, &df);
+            double t_entry = tn > 0.0 ? tn : 0.0;
+            int64_t K = (miss_dist == 0.0 && tf_ >= t_entry)
+                            ? (int64_t)floor((tf_ - t_entry) / step) + 1 : 0;
+            ray_err e = make_ray_err(&none_b, o, tn, dn);
+            sub_variant nv = {-1, -1, 0, -1, -1};
+            double res[4];
+            subcube_march(vol, o, d, t_entry, K, step, mode, tf, lutc, clip_rgba[3], &none_b,
+                          &e, cell_lo, n_sub, &nv, NULL, &wk, res);
+            double* r = &out[4 * i];
+            if (mode == VRO_COMPOSITE) {
+                r[0] = wk.C[3 * part];
+                r[1] = wk.C[3 * part + 1];
+                r[2] = wk.C[3 * part + 2];
+                r[3] = wk.A[part];
+            } else {
+                r[0] = wk.V[part];
+                r[1] = r[2] = r[3] = 0.0;
+            }
+        }
+        free(wk.C);
+        free(wk.A);
+        free(wk.V);
+        free(wk.done);
+        free(wk.order);
+    }
+    (void)nthreads;
+    free(lutc);
+    return bad ? -1 : 0;
+}
+
 /* Exposed pieces for the oracle's own tests: one trilinear sample at a point
  * and the corrected table entry for a value.                             */
 double vro_sample_at(const vro_volume* vol, double x, double y, double z)

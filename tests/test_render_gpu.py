@@ -140,6 +140,24 @@ def test_small_workload_reduced_precision(small, dtype, mode):
                ties=SMALL_TIES)
 
 
+@pytest.mark.parametrize("dtype", ["f16", "i8"])
+@pytest.mark.parametrize("mode", ["mip", "composite"])
+def test_small_workload_orbit_views_reduced_precision(small, dtype, mode):
+    # the precision variants' 32 orbit views of the 64x64x128 cube at 256^2
+    # (texture storage, as the benchmark renders them): kernel parity
+    # against the oracle on the decoded storage, and the stated precision
+    # cost against the oracle on the float32 source
+    wl, cube, lut, _ = small
+    cams = synth.orbit_cameras(wl.dims, 32, 256, 256)
+    run_parity(cube, dtype, cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+               wl.term_alpha, what="small orbit %s %s decoded" % (dtype, mode), tex=True,
+               ties={"term": 0.05, "trunc": 0.05})
+    run_parity(cube, dtype, cams, 256, 256, mode, wl.step, lut, wl.clip, wl.v_hi, wl.clip,
+               wl.term_alpha, tol=TOL_PREC[dtype], reference="source", tex=True,
+               what="small orbit %s %s vs fp32 source" % (dtype, mode),
+               ties={"term": 0.05, "trunc": 0.05})
+
+
 def test_small_workload_sample_count(small):
     wl, cube, lut, cams = small
     for mode in ("mip", "composite"):
