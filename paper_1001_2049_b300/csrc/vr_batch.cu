@@ -114,7 +114,7 @@ __device__ __forceinline__ unsigned tex_pixel(const BatchReq& q, const BatchTex&
 {
     const ray::Ray r = ray::setup_ray(q, q.cam, px, py, q.k_max);
     ray::Acc<MODE> acc;
-    const int k = ray::march_tex<DT, MODE, STACK>(q, T, lut, r, acc);
+    const int k = ray::march_tex<DT, MODE, STACK, true>(q, T, lut, r, acc);
     const size_t pix = (size_t)(py - q.row0) * q.w + px;
     if (MODE == VR_COMPOSITE)
         reinterpret_cast<float4*>(q.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);

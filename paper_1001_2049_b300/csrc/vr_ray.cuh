@@ -206,19 +206,26 @@ __device__ __forceinline__ void cell(const TT& T, cudaTextureObject_t t0, int z,
 // skipped by the lanes that hold that plane already (the lower one when z
 // rose by one, the upper one when z fell by one): whatever mix of moves the
 // lanes make, a warp issues at most two gathers per sample.
-template <int DT, bool STACK, typename TT, typename G>
+template <int DT, bool STACK, bool KEEP_PAIR, typename TT, typename G>
 __device__ __forceinline__ void next_cell(const TT& T, cudaTextureObject_t t0, const G& c,
                                           const float4& c0, const float4& c1, const G& n,
                                           float4& n0, float4& n1)
 {
     if constexpr (DT == kF16Pair || DT == kI8Pair) {
-        // one gather per sample, even in the same cell: measured faster than
-        // testing for a change of cell and keeping the held texels (1024^3
-        // FP16, 32 views at 1080p: MIP 57.6 -> 44.5 ms, composite 59.4 ->
-        // 48.9 ms), the test and selects costing more issue slots than the
-        // gather; plain formats keep their planes (two gathers a sample
-        // measured slower than the slot test)
-        cell<DT, STACK>(T, t0, n.iz, n.gx, n.gy, n0, n1);
+        // the single-view kernels gather every sample, even in the same cell:
+        // measured faster than testing for a change of cell and keeping the
+        // held texels (1024^3 FP16, 32 views at 1080p: MIP 57.6 -> 44.5 ms,
+        // composite 59.4 -> 48.9 ms), the test and selects costing more issue
+        // slots than the gather.  The batched kernel, short of registers at
+        // six blocks per SM, keeps them (KEEP_PAIR: 53.8 -> 49.1 ms on the
+        // batched workload).  Plain formats keep their planes either way
+        // (two gathers a sample measured slower than the slot test).
+        if (KEEP_PAIR && n.gx == c.gx && n.gy == c.gy && n.iz == c.iz) {
+            n0 = c0;
+            n1 = c1;
+        } else {
+            cell<DT, STACK>(T, t0, n.iz, n.gx, n.gy, n0, n1);
+        }
     } else {
         const bool xy = n.gx == c.gx && n.gy == c.gy;
         const int dz = n.iz - c.iz;
@@ -395,7 +402,7 @@ struct Acc {
         return A >= P.term_alpha;
     }
 
-    // Lockstep skipping (march_tex_lock, COMPOSITE): may the sample whose
+    // Skipping (march_win, COMPOSITE): may the sample whose
     // macrocell mask is `rec` and whose cell is bit `bit` of it be visible?
     __device__ __forceinline__ bool need(unsigned long long rec, int bit) const
     {
@@ -425,69 +432,91 @@ __device__ __forceinline__ int mask_cell(const PP& P, const Ray& r, float kf, in
     return (int)min((unsigned)i, (unsigned)P.mlast);
 }
 
-// march_tex with empty-space skipping in lockstep (COMPOSITE): every lane
-// steps through its samples at the same pace as without skipping (the
-// warp's rays stay side by side, so their gathers share cache lines), but a
-// lane fetches and evaluates a sample only when its cell's mask bit says the
-// clip can leave it visible; when no lane of the warp needs its sample, the
-// step costs the sample's cell alone.  Masks are loaded one sample ahead of
-// the gathers, gathers one sample ahead of the interpolation.  Every step
-// loads its mask word and every needed sample gathers its cell afresh:
-// keeping the last word or the last cell's texels when they repeat measured
-// slower (the comparisons and selects cost more issue slots than the
-// cached loads and gathers they save).  The result and the sample count are
-// those of march_tex.
-template <int DT, int MODE, bool STACK, typename PP, typename TT>
-__device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
-                                              const float4* __restrict__ lut, const Ray& r,
-                                              Acc<MODE>& acc)
+// march_tex with empty-space skipping in windows (COMPOSITE): the warp's
+// lanes scan kWin samples in lockstep -- each step only the sample's cell,
+// its mask word and bit, setting the step's bit in the lane's window mask
+// when the clip can leave the sample visible -- and then evaluate the
+// window's marked samples in order, lowest first, every lane taking its
+// next one in the same round: the rare visible samples of a noise ray are
+// evaluated together with the other lanes' instead of each in a lockstep
+// step of its own (1024^3, 32 views at 1080p: 44.5 -> 37.3 ms against the
+// lockstep march that tested and evaluated sample by sample).  Within a
+// round the gathers of a lane's next sample are issued before its current
+// one is interpolated.  Samples [k0, k1) are composited in increasing order
+// with march_tex's arithmetic, so the result and the sample count (the
+// samples stepped until the ray stops) are march_tex's.  PART: the volume
+// holds a part of the cube starting at plane P.slice_base (texture slices
+// and mask macrocells are the part's own).  All lanes of the calling warp
+// that have samples must call it together (warp votes).
+constexpr int kWin = 32;
+
+template <int DT, int MODE, bool STACK, bool PART, typename PP, typename TT>
+__device__ __forceinline__ int march_win(const PP& P, const TT& T, const float4* __restrict__ lut,
+                                         const Ray& r, Acc<MODE>& acc, int k0, int k1)
 {
     static_assert(MODE == VR_COMPOSITE, "skipping is for compositing");
-    using Rec = unsigned long long;
-    if (r.K <= 0) return 0;
+    const unsigned lanes = __activemask();
     const cudaTextureObject_t t0 = T.tex;
-    // the mask test needs only a sample's cell (integer floors of its
-    // position); the full geometry (weights, gather coordinates) is computed
-    // for the samples a lane needs, one sample ahead of their interpolation.
-    int k = 0;
-    int b0, b1, b2;
-    const int m0 = mask_cell(P, r, 0.0f, b0);
-    int m1 = mask_cell(P, r, 1.0f, b1), m2;
-    const Rec r0 = __ldg(P.mask + m0);
-    Rec r1 = __ldg(P.mask + m1), r2;
-    bool n0 = acc.need(r0, b0), n1;
-    Geo g0, g1;
-    float4 a0, a1, c0, c1;
-    if (n0) {
-        g0 = geo(P, r, 0.0f);
-        cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
-    }
-    float kf = 0.0f;
-    for (;;) {
-        // sample k + 2: cell and mask word; sample k + 1: geometry, gathers
-        m2 = mask_cell(P, r, kf + 2.0f, b2);
-        r2 = __ldg(P.mask + m2);
-        n1 = acc.need(r1, b1);
-        if (n1) {
-            g1 = geo(P, r, kf + 1.0f);
-            cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
+    const int z_base = PART ? P.slice_base : 0;
+    int stop = k1;                     // the samples stepped end here (k1 unless the ray stops)
+    bool live = k0 < k1;
+    for (int ws = k0; __any_sync(lanes, live); ws += kWin) {
+        // scan: one bit per sample of the window that the clip can leave visible
+        unsigned bits = 0;
+        if (live) {
+            const int n = min(kWin, k1 - ws);
+#pragma unroll 4
+            for (int j = 0; j < kWin; ++j) {
+                int bit;
+                const int m = mask_cell(P, r, (float)(ws + j), bit, z_base);
+                const unsigned long long rec = __ldg(P.mask + m);
+                if (j < n && ((rec >> bit) & 1ull)) bits |= 1u << j;
+            }
         }
-        ++k;
-        if ((n0 && acc.add(P, lut, interp_t<DT, false>(T, a0, a1, g0))) || k >= r.K) break;
-        kf += 1.0f;
-        // the same one sample further on, the register sets swapped
-        m1 = mask_cell(P, r, kf + 2.0f, b1);
-        r1 = __ldg(P.mask + m1);
-        n0 = acc.need(r2, b2);
-        if (n0) {
-            g0 = geo(P, r, kf + 1.0f);
-            cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
+        // evaluate the marked samples in order, a round per sample of a lane
+        Geo ga, gb;
+        float4 a0, a1, b0, b1;
+        int ka = 0, kb = 0;
+        bool ha = bits != 0, hb;
+        if (ha) {
+            ka = ws + __ffs(bits) - 1;
+            bits &= bits - 1;
+            ga = geo(P, r, (float)ka);
+            ga.iz -= z_base;
+            cell<DT, STACK>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
         }
-        ++k;
-        if ((n1 && acc.add(P, lut, interp_t<DT, false>(T, c0, c1, g1))) || k >= r.K) break;
-        kf += 1.0f;
+        while (__any_sync(lanes, ha)) {
+            hb = bits != 0;
+            if (hb) {
+                kb = ws + __ffs(bits) - 1;
+                bits &= bits - 1;
+                gb = geo(P, r, (float)kb);
+                gb.iz -= z_base;
+                cell<DT, STACK>(T, t0, gb.iz, gb.gx, gb.gy, b0, b1);
+            }
+            if (ha && acc.add(P, lut, interp_t<DT, false>(T, a0, a1, ga))) {
+                stop = ka + 1;                 // the ray stops after this sample
+                live = false;
+                bits = 0;
+                hb = false;
+            }
+            ha = hb;
+            ka = kb;
+            ga = gb;
+            a0 = b0;
+            a1 = b1;
+        }
+        if (ws + kWin >= k1) live = false;
     }
-    return k;
+    return k0 < k1 ? stop - k0 : 0;
+}
+
+template <int DT, int MODE, bool STACK, typename PP, typename TT>
+__device__ __forceinline__ int march_tex_win(const PP& P, const TT& T,
+                                             const float4* __restrict__ lut, const Ray& r,
+                                             Acc<MODE>& acc)
+{
+    return march_win<DT, MODE, STACK, false>(P, T, lut, r, acc, 0, r.K);
 }
 
 // The gathers of sample k + 1 are issued before sample k is interpolated, so
@@ -495,7 +524,7 @@ __device__ __forceinline__ int march_tex_lock(const PP& P, const TT& T,
 // loop is unrolled twice with two register sets that swap roles, so a
 // pending gather result is only copied when the next sample reuses it.
 // Returns the number of samples evaluated.
-template <int DT, int MODE, bool STACK, typename PP, typename TT>
+template <int DT, int MODE, bool STACK, bool KEEP_PAIR = false, typename PP, typename TT>
 __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4* __restrict__ lut,
                                          const Ray& r, Acc<MODE>& acc)
 {
@@ -510,12 +539,12 @@ __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4*
     for (;;) {
         gb = geo(P, r, kf);
         fetch_dec<DT>(T, gb);
-        next_cell<DT, STACK>(T, t0, ga, a0, a1, gb, b0, b1);
+        next_cell<DT, STACK, KEEP_PAIR>(T, t0, ga, a0, a1, gb, b0, b1);
         if (acc.add(P, lut, interp_t<DT, true>(T, a0, a1, ga)) || kf >= Kf) break;
         kf += 1.0f;
         ga = geo(P, r, kf);
         fetch_dec<DT>(T, ga);
-        next_cell<DT, STACK>(T, t0, gb, b0, b1, ga, a0, a1);
+        next_cell<DT, STACK, KEEP_PAIR>(T, t0, gb, b0, b1, ga, a0, a1);
         if (acc.add(P, lut, interp_t<DT, true>(T, b0, b1, gb)) || kf >= Kf) break;
         kf += 1.0f;
     }
@@ -684,74 +713,16 @@ __device__ __forceinline__ int march_part(const PP& P, const TT& T,
         gb = geo(P, r, kf);
         gb.iz -= P.slice_base;
         fetch_dec<DT>(T, gb);
-        next_cell<DT, STACK>(T, t0, ga, a0, a1, gb, b0, b1);
+        next_cell<DT, STACK, false>(T, t0, ga, a0, a1, gb, b0, b1);
         ++k;
         if (acc.add(P, lut, interp_t<DT, true>(T, a0, a1, ga)) || k >= k1) break;
         kf += 1.0f;
         ga = geo(P, r, kf);
         ga.iz -= P.slice_base;
         fetch_dec<DT>(T, ga);
-        next_cell<DT, STACK>(T, t0, gb, b0, b1, ga, a0, a1);
+        next_cell<DT, STACK, false>(T, t0, gb, b0, b1, ga, a0, a1);
         ++k;
         if (acc.add(P, lut, interp_t<DT, true>(T, b0, b1, gb)) || k >= k1) break;
-        kf += 1.0f;
-    }
-    return k - k0;
-}
-
-// march_tex_lock over samples [k0, k1) of a part (COMPOSITE with the part
-// volume's empty-space masks), continuing `acc`: texture slices and mask
-// macrocells are the part's own (height coordinates shifted by the part's
-// first plane).  The result and the sample count are march_part's.
-template <int DT, bool STACK, typename PP, typename TT>
-__device__ __forceinline__ int march_part_lock(const PP& P, const TT& T,
-                                               const float4* __restrict__ lut, const Ray& r,
-                                               Acc<VR_COMPOSITE>& acc, int k0, int k1)
-{
-    using Rec = unsigned long long;
-    if (k0 >= k1) return 0;
-    const cudaTextureObject_t t0 = T.tex;
-    // mask_cell in the part's gather coordinates (clamped to the mask array:
-    // look-ahead samples past the range lie outside the part)
-    auto part_geo = [&](float kf) {
-        Geo g = geo(P, r, kf);
-        g.iz -= P.slice_base;
-        return g;
-    };
-    int k = k0;
-    float kf = (float)k0;
-    int b0, b1, b2;
-    const int m0 = mask_cell(P, r, kf, b0, P.slice_base);
-    int m1 = mask_cell(P, r, kf + 1.0f, b1, P.slice_base), m2;
-    const Rec r0 = __ldg(P.mask + m0);
-    Rec r1 = __ldg(P.mask + m1), r2;
-    bool n0 = acc.need(r0, b0), n1;
-    Geo g0, g1;
-    float4 a0, a1, c0, c1;
-    if (n0) {
-        g0 = part_geo(kf);
-        cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
-    }
-    for (;;) {
-        m2 = mask_cell(P, r, kf + 2.0f, b2, P.slice_base);
-        r2 = __ldg(P.mask + m2);
-        n1 = acc.need(r1, b1);
-        if (n1) {
-            g1 = part_geo(kf + 1.0f);
-            cell<DT, STACK>(T, t0, g1.iz, g1.gx, g1.gy, c0, c1);
-        }
-        ++k;
-        if ((n0 && acc.add(P, lut, interp_t<DT, false>(T, a0, a1, g0))) || k >= k1) break;
-        kf += 1.0f;
-        m1 = mask_cell(P, r, kf + 2.0f, b1, P.slice_base);
-        r1 = __ldg(P.mask + m1);
-        n0 = acc.need(r2, b2);
-        if (n0) {
-            g0 = part_geo(kf + 1.0f);
-            cell<DT, STACK>(T, t0, g0.iz, g0.gx, g0.gy, a0, a1);
-        }
-        ++k;
-        if ((n1 && acc.add(P, lut, interp_t<DT, false>(T, c0, c1, g1))) || k >= k1) break;
         kf += 1.0f;
     }
     return k - k0;

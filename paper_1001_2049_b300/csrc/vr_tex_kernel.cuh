@@ -16,7 +16,7 @@
 // The gathers of the next sample are issued before the current sample is
 // interpolated, which hides the texture latency behind the arithmetic.
 // With empty-space masks attached (SKIP, COMPOSITE), samples whose cell the
-// clip makes transparent are not fetched (vr_ray.cuh, march_tex_lock); with
+// clip makes transparent are not fetched (vr_ray.cuh, march_tex_win); with
 // MIP bounds attached (SKIP, MIP, FP32) the march reads bfloat16 upper
 // bounds and fetches the FP32 corners only where a sample could raise the
 // maximum (march_tex_bound).
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG
         if constexpr (SKIP && MODE == VR_MIP)
             count = (unsigned)ray::march_tex_bound<STACK>(P, T, r, acc);
         else if constexpr (SKIP)
-            count = (unsigned)ray::march_tex_lock<DT, MODE, STACK>(P, T, s_lut, r, acc);
+            count = (unsigned)ray::march_tex_win<DT, MODE, STACK>(P, T, s_lut, r, acc);
         else
             count = (unsigned)ray::march_tex<DT, MODE, STACK>(P, T, s_lut, r, acc);
         const size_t pix = ((size_t)view * P.h + py) * P.w + px;
@@ -143,7 +143,7 @@ cudaError_t launch_dt(const MarchParams& p, const TexParams& t, int mode, int cf
 // the samples of the part's cells (the same samples, in the same order, as
 // the one-pass render takes there), then writes the state back.
 // MASKED (COMPOSITE with the part's empty-space masks): 16 x 8 blocks at 64
-// registers, the shape at which the lockstep march runs fastest; otherwise
+// registers, the shape at which the masked march ran fastest; otherwise
 // 16 x 16 blocks at up to 51 registers (five blocks per SM).  Warps hold
 // 8 x 4 packets either way.
 template <int DT, int MODE, bool STACK, bool MASKED>
@@ -200,8 +200,8 @@ __global__ void __launch_bounds__(MASKED ? 128 : 256, MASKED ? 8 : 5)
                                                                          acc, k0, k1);
         } else if constexpr (MODE == VR_COMPOSITE && MASKED) {
             // with empty-space masks, as the one-pass render
-            count = (unsigned)ray::march_part_lock<DT, STACK>(P, T, s_lut, r, acc, k0,
-                                                              k1);
+            count = (unsigned)ray::march_win<DT, VR_COMPOSITE, STACK, true>(P, T, s_lut, r,
+                                                                             acc, k0, k1);
         } else {
             count = (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r, acc, k0,
                                                               k1);
