@@ -517,6 +517,20 @@ int vr_volume_destroy(vr_volume vol);
  * NULL).                                                                     */
 int vr_volume_info(vr_volume vol, int64_t dims[3], int* dtype, void** brick_buf);
 
+/* The checked build (the library compiled with VR_DEBUG: libvr_debug.so,
+ * no counterpart in the paper; it stands in for a memory checker, which
+ * this pool does not run): the texture-gather, part, batched and
+ * integration kernels test every output index, brick address, partial-image
+ * index and batched tile they compute against the buffer it addresses; a
+ * failed test sets a bit and skips the access, never trapping.  This call
+ * waits for the device, stores the bits recorded since the last clear in
+ * *flags (1 output pixel outside the image set, 2 brick address outside the
+ * brick buffer, 4 partial-image index outside the integration's input, 8 a
+ * batched tile outside its request, 0x80000000 the words could not be read)
+ * and clears them when `clear` is non-zero.  VR_ERR_UNSUPPORTED (with *flags
+ * = 0) in the regular build.                                                */
+int vr_debug_status(unsigned* flags, int clear);
+
 /* Message for the last failing call on this thread ("" if none).           */
 const char* vr_last_error(void);
 

@@ -67,6 +67,7 @@ SIGNATURES = {
     "vr_autotune": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_void_p,
                             c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_float)]),
     "vr_set_launch_config": (c_int, [c_void_p, c_int, c_int]),
+    "vr_debug_status": (c_int, [ctypes.POINTER(ctypes.c_uint), c_int]),
 }
 
 
@@ -81,12 +82,14 @@ _lib = None
 
 def load() -> ctypes.CDLL:
     """Load libvr.so (building it first when it is missing or older than its
-    sources).  Raises if it cannot be built or loaded: there is no fallback."""
+    sources; with VR_DEBUG=1 in the environment, the checked libvr_debug.so).
+    Raises if it cannot be built or loaded: there is no fallback."""
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if _build.stale():
-            path = _build.build()
+        debug = os.environ.get("VR_DEBUG") == "1"
+        path = _build.DEBUG_LIB if debug else _build.LIB
+        if _build.stale(path):
+            path = _build.build(debug=debug)
         if not os.path.exists(path):
             raise ImportError("libvr.so is missing and could not be built")
         lib = ctypes.CDLL(path)

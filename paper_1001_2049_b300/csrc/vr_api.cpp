@@ -12,7 +12,23 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "vr_internal.h"
+
+namespace {
+
+// An NVTX range around an entry point (named "vr_render" etc.), so a
+// profiler's timeline shows the library's calls around their kernels; the
+// header-only NVTX calls do nothing unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -836,6 +852,24 @@ extern "C" {
 
 static_assert(sizeof(vr_request) == 136, "vr_request is 136 bytes in ABI version 2");
 
+int vr_debug_status(unsigned* flags, int clear)
+{
+#ifdef VR_DEBUG
+    if (!flags) return fail(VR_ERR_ARG, "flags is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronising for the check words");
+    const bool c = clear != 0;
+    *flags = vr::debug_flags_tex_f32(c) | vr::debug_flags_tex_f16(c) | vr::debug_flags_tex_i8(c) |
+             vr::debug_flags_tex_f16pair(c) | vr::debug_flags_tex_i8pair(c) |
+             vr::debug_flags_batch(c) | vr::debug_flags_integrate(c);
+    return VR_OK;
+#else
+    (void)clear;
+    if (flags) *flags = 0;
+    return fail(VR_ERR_UNSUPPORTED, "not a checked build (compile with VR_DEBUG)");
+#endif
+}
+
 int vr_version(void) { return 2; }
 
 const char* vr_last_error(void) { return g_err.c_str(); }
@@ -905,6 +939,7 @@ int vr_volume_device_bytes(vr_volume vol, size_t* library_bytes, size_t* caller_
 int vr_volume_create(const int64_t dims[3], int dtype, const float* src, int src_on_device,
                      void* brick_buf, size_t brick_bytes, void* stream, vr_volume* out)
 {
+    const NvtxRange nvtx_range("vr_volume_create");
     if (!out) return fail(VR_ERR_ARG, "out is NULL");
     *out = nullptr;
     vr::VolumeGeom g;
@@ -945,6 +980,7 @@ int vr_volume_create(const int64_t dims[3], int dtype, const float* src, int src
 int vr_volume_upload(vr_volume vol, int64_t z0, int64_t nplanes, const float* src,
                      int src_on_device, void* stream)
 {
+    const NvtxRange nvtx_range("vr_volume_upload");
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
     vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
     if (!src) return fail(VR_ERR_ARG, "src is NULL");
@@ -1000,28 +1036,33 @@ int vr_set_transfer(vr_volume vol, const float* rgba_lut, int n, float v_lo, flo
 int vr_render(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
               float step, float* out, void* stream)
 {
+    const NvtxRange nvtx_range("vr_render");
     return render_impl(vol, cams, n_views, w, h, mode, step, out, nullptr, stream);
 }
 
 int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
                       float step, float* out, unsigned long long* d_samples, void* stream)
 {
+    const NvtxRange nvtx_range("vr_render_counted");
     if (!d_samples) return fail(VR_ERR_ARG, "d_samples is NULL");
     return render_impl(vol, cams, n_views, w, h, mode, step, out, d_samples, stream);
 }
 
 int vr_volume_attach_texture(vr_volume vol, void* stream)
 {
+    const NvtxRange nvtx_range("vr_volume_attach_texture");
     return attach_texture(vol, false, stream);
 }
 
 int vr_volume_attach_pair_texture(vr_volume vol, void* stream)
 {
+    const NvtxRange nvtx_range("vr_volume_attach_pair_texture");
     return attach_texture(vol, true, stream);
 }
 
 int vr_volume_attach_mip_bounds(vr_volume vol, void* stream)
 {
+    const NvtxRange nvtx_range("vr_volume_attach_mip_bounds");
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
     return attach_bounds(reinterpret_cast<vr::Volume*>(vol), static_cast<cudaStream_t>(stream));
 }
@@ -1072,6 +1113,7 @@ int vr_render_init(float* out, int n_views, int w, int h, int mode, void* stream
 int vr_integrate_partials(const float* partials, int n_parts, const vr_camera* cams,
                           int n_views, int w, int h, int mode, float* out, void* stream)
 {
+    const NvtxRange nvtx_range("vr_integrate_partials");
     if (!partials || !out) return fail(VR_ERR_ARG, "partials or out is NULL");
     if (!cams) return fail(VR_ERR_ARG, "cams is NULL");
     if (n_parts < 1) return fail(VR_ERR_ARG, "n_parts = %d < 1", n_parts);
@@ -1120,6 +1162,7 @@ int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
                    int w, int h, int mode, float step, int sweep, float* out,
                    unsigned long long* d_samples, void* stream)
 {
+    const NvtxRange nvtx_range("vr_render_part");
     if (!part) return fail(VR_ERR_ARG, "volume is NULL");
     vr::Volume* v = reinterpret_cast<vr::Volume*>(part);
     if (!full_dims) return fail(VR_ERR_ARG, "full_dims is NULL");
@@ -1171,6 +1214,7 @@ int vr_render_part(vr_volume part, const int64_t full_dims[3], int64_t z_first,
 
 int vr_volume_build_masks(vr_volume vol, void* stream)
 {
+    const NvtxRange nvtx_range("vr_volume_build_masks");
     if (!vol) return fail(VR_ERR_ARG, "volume is NULL");
     vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
     if (!v->mask) return fail(VR_ERR_UNSUPPORTED, "no masks are attached");
@@ -1245,6 +1289,7 @@ int check_batch_args(const vr_request* reqs, int n, void* workspace, size_t ws_b
 int vr_render_batch(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,
                     void* stream)
 {
+    const NvtxRange nvtx_range("vr_render_batch");
     const int rc = check_batch_args(reqs, n, workspace, ws_bytes);
     if (rc || n == 0) return rc;
     return batch_impl(reqs, n, static_cast<unsigned*>(workspace),
@@ -1278,6 +1323,7 @@ int vr_get_batch_config(void) { return g_batch_cfg.load(); }
 int vr_batch_autotune(const vr_request* reqs, int n, void* workspace, size_t ws_bytes,
                       void* stream, int* best_cfg, float* best_ms)
 {
+    const NvtxRange nvtx_range("vr_batch_autotune");
     int rc = check_batch_args(reqs, n, workspace, ws_bytes);
     if (rc) return rc;
     if (n == 0) {
@@ -1352,6 +1398,7 @@ int vr_set_launch_config(vr_volume vol, int mode, int cfg)
 int vr_autotune(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int mode,
                 float step, float* out, void* stream, int* best_cfg, float* best_ms)
 {
+    const NvtxRange nvtx_range("vr_autotune");
     vr::MarchParams p;
     vr::TexParams tp;
     int rc = prepare(vol, cams, n_views, w, h, mode, step, out, nullptr, &p, &tp);

@@ -116,7 +116,8 @@ __device__ __forceinline__ unsigned tex_pixel(const BatchReq& q, const BatchTex&
     ray::Acc<MODE> acc;
     const int k = ray::march_tex<DT, MODE, STACK, true>(q, T, lut, r, acc);
     const size_t pix = (size_t)(py - q.row0) * q.w + px;
-    if (MODE == VR_COMPOSITE)
+    if (!ray::debug_ok(py >= q.row0 && pix < (size_t)(q.row_end - q.row0) * q.w, 1)) {
+    } else if (MODE == VR_COMPOSITE)
         reinterpret_cast<float4*>(q.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);
     else
         q.out[pix] = acc.m;
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(kThreads, CLS == kBatchTexPair ? VR_BATCH_PAIR
             __syncthreads();
         }
         const int t = item - q.first_item;
+        if (!ray::debug_ok(t >= 0 && t < q.n_tiles, 8)) continue;
         const int tx = t % q.tiles_x, ty = t / q.tiles_x;
         const int px = tx * S.tx + (warp % wpr) * S.px + (lane % S.px);
         const int py = q.row0 + ty * S.ty + (warp / wpr) * S.py + (lane / S.px);
@@ -208,7 +210,8 @@ __global__ void __launch_bounds__(kThreads, CLS == kBatchTexPair ? VR_BATCH_PAIR
                 AccRT acc(q.mode);
                 count = (unsigned)march_bricks_rt(q, s_lut, r, acc);
                 const size_t pix = (size_t)(py - q.row0) * q.w + px;
-                if (q.mode == VR_COMPOSITE)
+                if (!ray::debug_ok(pix < (size_t)(q.row_end - q.row0) * q.w, 1)) {
+                } else if (q.mode == VR_COMPOSITE)
                     reinterpret_cast<float4*>(q.out)[pix] =
                         make_float4(acc.r, acc.g, acc.b, acc.A);
                 else
@@ -282,5 +285,8 @@ int batch_blocks_per_sm(int cls, int cfg)
     }
     return n > 0 ? n : 1;
 }
+
+// the checked build's device word of this translation unit
+VR_DEBUG_ACCESSOR(debug_flags_batch)
 
 }  // namespace vr

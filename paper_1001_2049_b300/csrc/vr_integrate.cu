@@ -39,7 +39,9 @@ __global__ void __launch_bounds__(256) integrate_kernel(const __grid_constant__ 
             float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             for (int j = 0; j < P.n_parts; ++j) {
                 const int part = up ? j : P.n_parts - 1 - j;
-                const float4 c = src[(size_t)part * P.part_stride + i];
+                const size_t at = (size_t)part * P.part_stride + i;
+                if (!ray::debug_ok(at < (size_t)P.n_parts * P.part_stride, 4)) continue;
+                const float4 c = src[at];
                 const float T = 1.0f - acc.w;
                 acc.x = fmaf(T, c.x, acc.x);
                 acc.y = fmaf(T, c.y, acc.y);
@@ -76,5 +78,8 @@ cudaError_t launch_integrate(const IntegrateParams& p, int mode, cudaStream_t s)
     }
     return cudaGetLastError();
 }
+
+// the checked build's device word of this translation unit
+VR_DEBUG_ACCESSOR(debug_flags_integrate)
 
 }  // namespace vr

@@ -265,5 +265,15 @@ cudaError_t fill_bounds_linear(const Volume& v, unsigned* dst, int s0, int s1, f
                                cudaStream_t s);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
                         cudaStream_t s);
+// The checked build (VR_DEBUG): the failed-check bits each translation unit
+// with checked kernels recorded (read, and cleared when `clear`); 0 in other
+// builds.
+unsigned debug_flags_tex_f32(bool clear);
+unsigned debug_flags_tex_f16(bool clear);
+unsigned debug_flags_tex_i8(bool clear);
+unsigned debug_flags_tex_f16pair(bool clear);
+unsigned debug_flags_tex_i8pair(bool clear);
+unsigned debug_flags_batch(bool clear);
+unsigned debug_flags_integrate(bool clear);
 
 }  // namespace vr

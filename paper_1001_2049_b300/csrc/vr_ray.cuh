@@ -19,6 +19,39 @@
 namespace vr {
 namespace ray {
 
+// ---- the checked build (compiled with VR_DEBUG) ----
+// Kernels test the indices they compute against the buffers they address;
+// a failed test records its bit in a device word of the translation unit and
+// the access is skipped (no trap, no fault): vr_debug_status reads and
+// clears the words.  Bits: 1 an output pixel outside the image set, 2 a
+// brick address outside the brick buffer, 4 a partial image index outside
+// the integration's input, 8 a batched tile outside its request.  Without
+// VR_DEBUG the tests compile to nothing.
+#ifdef VR_DEBUG
+static __device__ unsigned g_debug_flags;
+__device__ __forceinline__ bool debug_ok(bool cond, unsigned bit)
+{
+    if (!cond) atomicOr(&g_debug_flags, bit);
+    return cond;
+}
+#define VR_DEBUG_ACCESSOR(name)                                                   \
+    unsigned name(bool clear)                                                     \
+    {                                                                             \
+        unsigned v = 0;                                                           \
+        if (cudaMemcpyFromSymbol(&v, ray::g_debug_flags, sizeof v) != cudaSuccess) \
+            v = 0x80000000u;                                                      \
+        if (clear) {                                                              \
+            const unsigned zero = 0;                                              \
+            cudaMemcpyToSymbol(ray::g_debug_flags, &zero, sizeof zero);           \
+        }                                                                         \
+        return v;                                                                 \
+    }
+#else
+__device__ __forceinline__ constexpr bool debug_ok(bool, unsigned) { return true; }
+#define VR_DEBUG_ACCESSOR(name) \
+    unsigned name(bool) { return 0; }
+#endif
+
 __device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(f, b - a, a); }
 
 // Four texels around (x, y) of a layer: with x = i + 1, y = j + 1 (texel
@@ -792,6 +825,8 @@ __device__ __forceinline__ float sample_bricks(const PP& P, float px, float py, 
     const size_t sx = ((ix & 31) == 31) ? (size_t)(kBrickVoxels - 31) : 1;
     const size_t sy = ((iy & 31) == 31) ? (size_t)g.nbx * kBrickVoxels - 31 * 32 : 32;
     const size_t sz = ((iz & 31) == 31) ? (size_t)g.nbx * g.nby * kBrickVoxels - 31 * 1024 : 1024;
+    if (!debug_ok(base + sx + sy + sz < (size_t)g.nbx * g.nby * g.nbz * kBrickVoxels, 2))
+        return 0.0f;
     float c000 = load_voxel<DT>(P.bricks, base);
     float c100 = load_voxel<DT>(P.bricks, base + sx);
     float c010 = load_voxel<DT>(P.bricks, base + sy);

@@ -16,4 +16,7 @@ cudaError_t launch_part_f16pair(const MarchParams& p, const TexParams& t, int mo
     return tex::launch_part_dt<kF16Pair>(p, t, mode, s);
 }
 
+// the checked build's device word of this translation unit
+VR_DEBUG_ACCESSOR(debug_flags_tex_f16pair)
+
 }  // namespace vr

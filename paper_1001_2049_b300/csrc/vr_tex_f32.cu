@@ -16,4 +16,7 @@ cudaError_t launch_part_f32(const MarchParams& p, const TexParams& t, int mode,
     return tex::launch_part_dt<VR_F32>(p, t, mode, s);
 }
 
+// the checked build's device word of this translation unit
+VR_DEBUG_ACCESSOR(debug_flags_tex_f32)
+
 }  // namespace vr

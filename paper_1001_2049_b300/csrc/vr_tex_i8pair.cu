@@ -16,4 +16,7 @@ cudaError_t launch_part_i8pair(const MarchParams& p, const TexParams& t, int mod
     return tex::launch_part_dt<kI8Pair>(p, t, mode, s);
 }
 
+// the checked build's device word of this translation unit
+VR_DEBUG_ACCESSOR(debug_flags_tex_i8pair)
+
 }  // namespace vr

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(kShapes[CFG].bx * kShapes[CFG].by, kShapes[CFG
         else
             count = (unsigned)ray::march_tex<DT, MODE, STACK>(P, T, s_lut, r, acc);
         const size_t pix = ((size_t)view * P.h + py) * P.w + px;
-        if (MODE == VR_COMPOSITE)
+        if (!ray::debug_ok(pix < (size_t)P.n_views * P.h * P.w, 1)) {
+        } else if (MODE == VR_COMPOSITE)
             reinterpret_cast<float4*>(P.out)[pix] = make_float4(acc.r, acc.g, acc.b, acc.A);
         else
             P.out[pix] = acc.m;
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(MASKED ? 128 : 256, MASKED ? 8 : 5)
             count = (unsigned)ray::march_part<DT, MODE, STACK>(P, T, s_lut, r, acc, k0,
                                                               k1);
         }
-        if (MODE == VR_COMPOSITE)
+        if (!ray::debug_ok(pix < (size_t)P.n_views * P.h * P.w, 1)) {
+        } else if (MODE == VR_COMPOSITE)
             reinterpret_cast<float4*>(P.out)[pix] =
                 make_float4(acc.r, acc.g, acc.b, acc.A);
         else

@@ -121,3 +121,19 @@ def test_library_storage_byte_queries_host_only():
     from paper_1001_2049_b300 import VRError
     with pytest.raises(VRError):
         texture_bytes((nx, ny, 50), "f32", pair=True)
+
+
+def test_checked_build_exports_its_status_and_the_regular_one_refuses():
+    import subprocess
+    lib = _lib.load()
+    flags = ctypes.c_uint(7)
+    assert lib.vr_debug_status(ctypes.byref(flags), 0) == _lib.VR_ERR_UNSUPPORTED
+    assert flags.value == 0
+    path = build.build(debug=True)
+    dbg = ctypes.CDLL(path)
+    names = declared_functions()
+    for n in names:
+        assert hasattr(dbg, n), n
+    # the regular library's kernels carry no checks: its objects were built
+    # without VR_DEBUG (the checked library is a separate file)
+    assert os.path.basename(path) == "libvr_debug.so" and path != build.LIB
