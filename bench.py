@@ -124,13 +124,13 @@ class Clocks:
 # of every CUDA/C++ source of the library (kernel_sources_sha); when the
 # sources differ the bench reports no traffic rather than a stale one.
 TRAFFIC_CAPTURE = {
-    "capture": "prof_r2a: bench.py --cube-edge 512 --views 4 --steps 1 --warmup 1 --shapes 6,3 "
+    "capture": "prof_r2b: bench.py --cube-edge 512 --views 4 --steps 1 --warmup 1 --shapes 7,3 "
                "(ncu --set full; profiles/tex_kernel_f32_cube1024_orbit32.md)",
-    "kernel_sha": "f9ba8ca55c84db7b",
-    # MIP with bfloat16 bounds, shape 3: (2.407082 + 0.011679) GB over 2.130716 GB
-    "mip_bounds": (2.407082e9 + 0.011679e9) / 2.130716e9,
-    # composite with masks, shape 6: (0.352616 + 0.033497) GB over 2.153293 GB
-    "composite_masks": (0.352616e9 + 0.033497e9) / 2.153293e9,
+    "kernel_sha": "12a50f97d3e8196b",
+    # MIP with bfloat16 bounds, shape 3: (2.407831 + 0.011652) GB over 2.130716 GB
+    "mip_bounds": (2.407831e9 + 0.011652e9) / 2.130716e9,
+    # composite with masks, windowed march, shape 7: (0.373391 + 0.033577) GB over 2.153293 GB
+    "composite_masks": (0.373391e9 + 0.033577e9) / 2.153293e9,
 }
 
 
@@ -705,13 +705,16 @@ def _serve(vols, names, rate, duration, batched, seed, split=True):
     return st
 
 
-def serving_leg(dev, rates=(50.0, 100.0, 200.0, 500.0), duration=20.0):
+def serving_leg(dev, rates=(50.0, 100.0, 200.0, 500.0), duration=20.0, saturated=5.0):
     """The served workload: Poisson arrivals of random requests (a random
     direction, a resolution from 512^2 to 1920x1080, 80 % composite, clip
     U[2,5] sigma) over six resident cubes (four 2048x2048x4096 and two
     1024^3, FP16, texture storage only: 146 GB of cube data), served with
     continuous batching (images split into row bands, launches capped in
-    rays; at 200 req/s also without splitting, for comparison).  Head to
+    rays; at 200 req/s also without splitting, for comparison).  Each rate
+    runs ``duration`` seconds, except 500 req/s, above what one GPU serves,
+    which runs ``saturated`` seconds: there the queue only grows, and the
+    figure of interest is the throughput, not the latency of a backlog.  Head to
     head with the plain FP32 path (one single-view render per request) on
     the cubes whose FP32 copies fit together in memory (two large, two
     small): the same request streams on those four cubes, served both
@@ -727,16 +730,18 @@ def serving_leg(dev, rates=(50.0, 100.0, 200.0, 500.0), duration=20.0):
            "resident_device_bytes": {n: dict(zip(("library", "caller"), vols[n].device_bytes()))
                                      for n in names},
            "band_rays": BAND_RAYS, "launch_rays": LAUNCH_RAYS,
-           "duration_s_per_rate": duration, "build_s": build_f16, "rates": {},
+           "duration_s_per_rate": duration, "duration_s_at_500": saturated,
+           "build_s": build_f16, "rates": {},
            "head_to_head": {"cubes": sub, "rates": {}}}
     for rate in rates:
-        out["rates"][str(int(rate))] = _serve(vols, names, rate, duration, True,
+        secs = saturated if rate >= 500.0 else duration
+        out["rates"][str(int(rate))] = _serve(vols, names, rate, secs, True,
                                              synth.SERVE_SEED + int(rate))
         if rate == 200.0:
             out["rates"]["200_without_splitting"] = _serve(
                 vols, names, rate, duration, True, synth.SERVE_SEED + int(rate), split=False)
         out["head_to_head"]["rates"][str(int(rate))] = {
-            "continuous_batching_f16": _serve(vols, sub, rate, duration, True,
+            "continuous_batching_f16": _serve(vols, sub, rate, secs, True,
                                               synth.SERVE_SEED + 1000 + int(rate))}
     for v in vols.values():
         v.close()
@@ -744,8 +749,9 @@ def serving_leg(dev, rates=(50.0, 100.0, 200.0, 500.0), duration=20.0):
     torch.cuda.empty_cache()
     f32 = {n: _served_volume(names.index(n), "f32", dev) for n in sub}
     for rate in rates:
+        secs = saturated if rate >= 500.0 else duration
         out["head_to_head"]["rates"][str(int(rate))]["plain_f32_per_request"] = _serve(
-            f32, sub, rate, duration, False, synth.SERVE_SEED + 1000 + int(rate))
+            f32, sub, rate, secs, False, synth.SERVE_SEED + 1000 + int(rate))
     for v in f32.values():
         v.close()
     del f32
