@@ -756,7 +756,7 @@ def test_masks_ragged_cubes(dims, step, dtype):
 
 
 # ---------------------------------------------------------------------------
-# MIP bounds: binary16 upper bounds decide which samples read the FP32 texels
+# MIP bounds: bfloat16 upper bounds decide which samples read the FP32 texels
 # ---------------------------------------------------------------------------
 def _mip_with_and_without_bounds(vol, cams, w, h, step):
     outs = []
@@ -781,9 +781,9 @@ def test_mip_bounds_leave_images_and_counts_unchanged(dims):
     assert na == nb
 
 
-def test_mip_bounds_with_values_binary16_cannot_hold():
-    # voxels above 65504 (bound +inf), hugely negative (bound -65504), NaN
-    # and infinite voxels, tiny and subnormal values: identical images
+def test_mip_bounds_with_extreme_values():
+    # voxels beyond binary16's range, hugely negative, NaN and infinite
+    # voxels, tiny and subnormal values: identical images
     dims = (23, 19, 31)
     cube, cams = _skip_cases(dims, 77)
     rng = np.random.default_rng(5)
@@ -807,6 +807,34 @@ def test_mip_bounds_with_values_binary16_cannot_hold():
     vol.attach_texture()
     (a, _), (b, _) = _mip_with_and_without_bounds(vol, cams, 29, 19, 0.5)
     assert torch.equal(a, b)
+    # the largest finite floats (their bfloat16 bound rounds up to +inf, or
+    # stays finite for -FLT_MAX) beside ordinary noise
+    big, _ = _skip_cases(dims, 78)
+    fb = big.reshape(-1)
+    fmax = np.finfo(np.float32).max
+    fb[idx[:5]] = fmax
+    fb[idx[5:10]] = -fmax
+    vol = Volume(torch.from_numpy(big).cuda(), "f32")
+    vol.attach_texture()
+    (a, na), (b, nb) = _mip_with_and_without_bounds(vol, cams, 29, 19, 0.5)
+    assert torch.equal(a, b) and na == nb
+
+
+def test_mip_bounds_on_negative_cubes():
+    # every voxel negative, so every ray's maximum is negative and the bounds
+    # of the upper planes are the ones stored one bfloat16 step higher (read
+    # back as a whole texel); values with low bits set in every magnitude
+    dims = (29, 23, 37)
+    cube, cams = _skip_cases(dims, 79)
+    for shift, scale in ((-40.0, 1.0), (-1.0e-3, 1.0e-4), (-3.0e5, 7.0e3)):
+        neg = (cube * np.float32(scale) + np.float32(shift)).astype(np.float32)
+        neg = np.minimum(neg, np.float32(-1e-38))
+        vol = Volume(torch.from_numpy(neg).cuda(), "f32")
+        vol.attach_texture()
+        (a, na), (b, nb) = _mip_with_and_without_bounds(vol, cams, 29, 19, 0.37)
+        assert torch.equal(a, b), shift
+        assert na == nb
+        assert float(a.max()) < 0.0
 
 
 def test_mip_bounds_small_workload_against_the_oracle(small):
