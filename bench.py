@@ -540,6 +540,29 @@ def small_workload_leg(dev, reps=50, check=True):
     return out
 
 
+def object_order_leg(vol, cams, W, H, wl, mip, mip_ms, reps=3):
+    """MIP of the same views in object order (sub-cubes of 32^3 cells staged
+    in shared memory once for all views, read from the bricks): its launch
+    time against the texture march's, and whether its images and sample
+    count are the texture march's bit for bit."""
+    dev = mip.device
+    out = torch.empty_like(mip)
+    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    vol.render_object_order(cams, W, H, "mip", wl.step, out=out, count=n)
+    torch.cuda.synchronize()
+    n_tex = torch.zeros(1, dtype=torch.int64, device=dev)
+    vol.render(cams, W, H, "mip", wl.step, out=torch.empty_like(mip), count=n_tex)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ms = event_ms(lambda: vol.render_object_order(cams, W, H, "mip", wl.step, out=out), reps, s)
+    return {"ms_per_launch": ms, "texture_mip_ms_per_launch": mip_ms,
+            "vs_texture": mip_ms / ms,
+            "images_identical_to_texture_mip": bool(torch.equal(out, mip)),
+            "samples": int(n.item()), "samples_identical": int(n.item()) == int(n_tex.item()),
+            "sub_cubes": int(np.prod([(d - 2) // 32 + 1 for d in wl.dims])),
+            "reads": "bricks (no texture storage)"}
+
+
 def tf_edit_leg(vol, cams, W, H, wl, lut):
     """Interactive transfer-function editing: a sequence of clip levels, each
     set and followed by one 1080p composite view; latency from the
@@ -1000,6 +1023,8 @@ def main():
             del host_cube
         extra = {}
         if not args.no_extra and W == 1920:
+            extra["object_order"] = run_leg(
+                lambda: object_order_leg(vol, cams, W, H, wl, mip, mip_ms))
             if args.storage == "texture" and not args.no_masks:
                 extra["tf_edit"] = run_leg(lambda: tf_edit_leg(vol, cams, W, H, wl, lut))
             if args.storage == "texture":

@@ -207,6 +207,23 @@ int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w,
                       int h, int mode, float step, float* out,
                       unsigned long long* d_samples, void* stream);
 
+/* MIP in object order (paper §3.1 process items 1-5: the cube partitioned
+ * into sub-cubes, each ray cast into an image, the images combined): the
+ * cube is cut into sub-cubes of 32^3 cells; one thread block stages a
+ * sub-cube's voxels from the bricks into shared memory once and renders,
+ * for every view of the call (in launches of up to 64 views), the samples
+ * of every ray that fall in it, combining the rays' partial maxima in `out`
+ * with atomic maxima.  The same images and sample counts as vr_render's
+ * MIP, bit for bit: each sample is taken by exactly one sub-cube and
+ * computed with vr_render's arithmetic.  Reads the bricks (not the texture
+ * storage; VR_ERR_UNSUPPORTED once they were dropped); `out` is first
+ * filled with -inf.  mode must be VR_MIP (VR_ERR_ARG otherwise: the
+ * composite needs each ray's samples in order).  d_samples may be NULL.
+ * Other arguments as in vr_render.                                         */
+int vr_render_object_order(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
+                           int mode, float step, float* out, unsigned long long* d_samples,
+                           void* stream);
+
 /* Bytes of the volume's empty-space masks: 8 bytes per macrocell of
  * 4 x 4 x 4 cells, (nx/4 + 1) * (ny/4 + 1) * (nz/4 + 1) macrocells (integer
  * division; the gather coordinates 0 .. n of every axis, four per macrocell).
@@ -518,15 +535,17 @@ int vr_volume_destroy(vr_volume vol);
 int vr_volume_info(vr_volume vol, int64_t dims[3], int* dtype, void** brick_buf);
 
 /* The checked build (the library compiled with VR_DEBUG: libvr_debug.so,
- * no counterpart in the paper; it stands in for a memory checker, which
- * this pool does not run): the texture-gather, part, batched and
- * integration kernels test every output index, brick address, partial-image
- * index and batched tile they compute against the buffer it addresses; a
+ * no counterpart in the paper; a bounds checker built into the kernels,
+ * standing in for an external memory checker): the texture-gather, part, batched, integration
+ * and object-order kernels test every output index, brick address,
+ * partial-image index, batched tile and staged sample they compute against
+ * the buffer it addresses; a
  * failed test sets a bit and skips the access, never trapping.  This call
  * waits for the device, stores the bits recorded since the last clear in
  * *flags (1 output pixel outside the image set, 2 brick address outside the
  * brick buffer, 4 partial-image index outside the integration's input, 8 a
- * batched tile outside its request, 0x80000000 the words could not be read)
+ * batched tile outside its request, 16 an object-order sample outside its
+ * staged sub-cube, 0x80000000 the words could not be read)
  * and clears them when `clear` is non-zero.  VR_ERR_UNSUPPORTED (with *flags
  * = 0) in the regular build.                                                */
 int vr_debug_status(unsigned* flags, int clear);

@@ -35,6 +35,8 @@ SIGNATURES = {
                           c_void_p]),
     "vr_render_counted": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float,
                                   c_void_p, c_void_p, c_void_p]),
+    "vr_render_object_order": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int,
+                                       c_float, c_void_p, c_void_p, c_void_p]),
     "vr_volume_destroy": (c_int, [c_void_p]),
     "vr_volume_attach_texture": (c_int, [c_void_p, c_void_p]),
     "vr_volume_mask_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),

@@ -399,6 +399,30 @@ class Volume:
                                         _stream_ptr(stream)))
         return out
 
+    def render_object_order(self, cams: np.ndarray, w: int, h: int, mode: str = "mip",
+                            step: float = 0.5, out: torch.Tensor | None = None, stream=None,
+                            count: torch.Tensor | None = None) -> torch.Tensor:
+        """MIP of len(cams) views in object order (vr_render_object_order):
+        sub-cubes of 32^3 cells staged in shared memory once for all views,
+        the same images and counts as ``render(..., "mip")``.  Returns
+        (views, h, w); ``count`` as in render."""
+        cams = np.ascontiguousarray(cams)
+        if cams.dtype.itemsize != 64:
+            raise ValueError("cams must be an array of 64-byte camera records")
+        m = MODES[mode]
+        shape = (len(cams), h, w)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=self.device)
+        elif tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 tensor of shape %s" % (shape,))
+        if count is not None and (count.dtype != torch.int64 or not count.is_cuda):
+            raise ValueError("count must be an int64 CUDA tensor")
+        check(load().vr_render_object_order(self._h, cams.ctypes.data, len(cams), w, h, m,
+                                            float(step), out.data_ptr(),
+                                            count.data_ptr() if count is not None else None,
+                                            _stream_ptr(stream)))
+        return out
+
     def render_part(self, full_dims, z_first: int, cell_lo: int, cell_hi: int, cams: np.ndarray,
                     w: int, h: int, mode: str, step: float, sweep: int, out: torch.Tensor,
                     count: torch.Tensor | None = None, stream=None):

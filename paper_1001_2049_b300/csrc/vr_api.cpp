@@ -861,7 +861,8 @@ int vr_debug_status(unsigned* flags, int clear)
     const bool c = clear != 0;
     *flags = vr::debug_flags_tex_f32(c) | vr::debug_flags_tex_f16(c) | vr::debug_flags_tex_i8(c) |
              vr::debug_flags_tex_f16pair(c) | vr::debug_flags_tex_i8pair(c) |
-             vr::debug_flags_batch(c) | vr::debug_flags_integrate(c);
+             vr::debug_flags_batch(c) | vr::debug_flags_integrate(c) |
+             vr::debug_flags_object(c);
     return VR_OK;
 #else
     (void)clear;
@@ -1046,6 +1047,35 @@ int vr_render_counted(vr_volume vol, const vr_camera* cams, int n_views, int w, 
     const NvtxRange nvtx_range("vr_render_counted");
     if (!d_samples) return fail(VR_ERR_ARG, "d_samples is NULL");
     return render_impl(vol, cams, n_views, w, h, mode, step, out, d_samples, stream);
+}
+
+int vr_render_object_order(vr_volume vol, const vr_camera* cams, int n_views, int w, int h,
+                           int mode, float step, float* out, unsigned long long* d_samples,
+                           void* stream)
+{
+    const NvtxRange nvtx_range("vr_render_object_order");
+    if (mode == VR_COMPOSITE || mode == VR_SUM)
+        return fail(VR_ERR_ARG, "object-order rendering takes MIP only (mode %d)", mode);
+    vr::MarchParams p;
+    vr::TexParams tp;
+    int rc = prepare(vol, cams, n_views, w, h, mode, step, out, d_samples, &p, &tp);
+    if (rc) return rc;
+    vr::Volume* v = reinterpret_cast<vr::Volume*>(vol);
+    if (v->texture_only)
+        return fail(VR_ERR_UNSUPPORTED, "object-order rendering reads the bricks, which were dropped");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = vr::launch_render_init(out, (size_t)n_views * w * h, VR_MIP, s);
+    if (e != cudaSuccess) return cuda_fail(e, "init launch");
+    const size_t per_view = (size_t)w * h;
+    for (int v0 = 0; v0 < n_views; v0 += vr::kMaxViewsPerLaunch) {
+        const int nv = std::min(vr::kMaxViewsPerLaunch, n_views - v0);
+        p.n_views = nv;
+        std::memcpy(p.cams, cams + v0, sizeof(vr_camera) * nv);
+        p.out = out + per_view * v0;
+        e = vr::launch_object(p, tp.k_max, v->dtype, s);
+        if (e != cudaSuccess) return cuda_fail(e, "object-order launch");
+    }
+    return VR_OK;
 }
 
 int vr_volume_attach_texture(vr_volume vol, void* stream)

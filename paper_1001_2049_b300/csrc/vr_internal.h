@@ -222,6 +222,9 @@ struct IntegrateParams {
     vr_camera cams[kMaxViewsPerLaunch];
 };
 cudaError_t launch_integrate(const IntegrateParams& p, int mode, cudaStream_t s);
+// Object-order MIP (vr_object.cu): one block per sub-cube of 32^3 cells,
+// adding each ray's partial maxima to `p.out` (filled with -inf first).
+cudaError_t launch_object(const MarchParams& p, int k_max, int dtype, cudaStream_t s);
 
 cudaError_t launch_part(const MarchParams& p, const TexParams& t, int format, int mode,
                         cudaStream_t s);
@@ -275,5 +278,6 @@ unsigned debug_flags_tex_f16pair(bool clear);
 unsigned debug_flags_tex_i8pair(bool clear);
 unsigned debug_flags_batch(bool clear);
 unsigned debug_flags_integrate(bool clear);
+unsigned debug_flags_object(bool clear);
 
 }  // namespace vr

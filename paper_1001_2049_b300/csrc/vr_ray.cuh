@@ -25,7 +25,8 @@ namespace ray {
 // the access is skipped (no trap, no fault): vr_debug_status reads and
 // clears the words.  Bits: 1 an output pixel outside the image set, 2 a
 // brick address outside the brick buffer, 4 a partial image index outside
-// the integration's input, 8 a batched tile outside its request.  Without
+// the integration's input, 8 a batched tile outside its request, 16 an
+// object-order sample outside its staged sub-cube.  Without
 // VR_DEBUG the tests compile to nothing.
 #ifdef VR_DEBUG
 static __device__ unsigned g_debug_flags;

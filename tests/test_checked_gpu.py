@@ -1,10 +1,11 @@
 """The checked build (VR_DEBUG: kernels test every output index, brick
-address, partial-image index and batched tile they compute, record failures
-and skip the access, never trapping) on the GPU: renders through every
-checked kernel -- texture, pair-texture and brick storage, masks, MIP bounds,
-the batched launch with row bands, parts and scene integration -- record no
-failed check, and give the regular library's images bit for bit.  Runs in a
-child process, since a process loads one of the two libraries."""
+address, partial-image index, batched tile and staged sample they compute,
+record failures and skip the access, never trapping) on the GPU: renders
+through every checked kernel -- texture, pair-texture and brick storage,
+masks, MIP bounds, object order, the batched launch with row bands, parts
+and scene integration -- record no failed check, and give the regular
+library's images bit for bit.  Runs in a child process, since a process
+loads one of the two libraries."""
 import json
 import os
 import subprocess
@@ -37,6 +38,7 @@ for dt, store in (("f32", "texture"), ("f16", "pair"), ("i8", "bricks")):
     v.set_transfer(synth.default_lut(), 0.0, 8.0, 1.0, 0.95)
     for mode in ("composite", "mip"):
         add(v.render(cams, 23, 17, mode, 0.5))
+    add(v.render_object_order(cams, 23, 17, "mip", 0.5))
     reqs = [Request(v, c, 23, 17, m, 0.5, band=b) for c in cams for m in ("mip", "composite")
             for b in (None, (3, 9))]
     for o in render_batch(reqs):
