@@ -114,9 +114,10 @@ int vr_volume_bytes(const int64_t dims[3], int dtype, size_t* bytes_out);
  *                        records.  VR_ERR_UNSUPPORTED beyond the device's
  *                        layered-texture limits or for FP32 pairs.
  *   vr_mip_bounds_bytes  MIP bounds of an FP32 volume with texture storage
- *                        (vr_volume_attach_mip_bounds): bfloat16 bounds of
- *                        two planes per 4-byte texel, nz + 1 cell slices
- *                        stacked as the texture, plus one word.  Filling them
+ *                        (vr_volume_attach_mip_bounds): 8-bit codes of two
+ *                        planes per 2-byte texel, nz + 1 cell slices
+ *                        stacked as the texture, plus a 32-byte scale
+ *                        record.  Filling them
  *                        also takes a stream-ordered scratch buffer of at
  *                        most 256 MiB, released on the stream.
  * The figures count the texels; the driver may round an allocation up to
@@ -287,19 +288,22 @@ int vr_volume_attach_pair_texture(vr_volume vol, void* stream);
 int vr_volume_detach_texture(vr_volume vol);
 
 /* MIP bounds for a VR_F32 volume with (plain) texture storage: a second
- * layered texture holding every voxel rounded toward +infinity to bfloat16,
- * the two planes of a cell in one 4-byte texel (cell slices, as the pair
- * formats; about 4 bytes per voxel, library-owned), so one four-texel
- * gather returns the bounds of all eight corners of a sample's cell.  A MIP
- * render (the maximum of the samples, §3.1 process item 3) then marches the
- * bounds:
- * their trilinear value is an upper bound of the sample's value up to the
- * FP32 rounding of the two interpolations, which a margin of 2^-19 times the
- * largest |voxel| covers, so a sample is read from the FP32 texture only when
- * it could raise the ray's running maximum (the largest |voxel| is kept in
- * device memory, raised by every fill, and the kernels read it there).  MIP
- * images and sample counts are those without bounds bit for bit (infinite
- * or NaN voxels give bounds that never exclude a sample).
+ * layered texture holding every voxel v as an 8-bit code c with L + c delta
+ * >= v, on one scale for the whole cube (L its smallest finite voxel, 255
+ * delta a little above its range), the two planes of a cell in one 2-byte
+ * texel (cell slices, as the pair formats; about 2 bytes per voxel,
+ * library-owned), so one four-texel gather returns the codes of all eight
+ * corners of a sample's cell.  A MIP render (the maximum of the samples,
+ * §3.1 process item 3) then marches the codes: their trilinear value bounds
+ * the sample's value from above, and after allowing for the FP32 rounding
+ * of both interpolations (2^-19 times the largest |voxel|, and the codes'
+ * own rounding) a sample is read from the FP32 texture only when it could
+ * raise the ray's running maximum.  The scale lives in device memory,
+ * derived on the device when the bounds are attached and again when every
+ * plane is uploaded.  MIP images and sample counts are those without bounds
+ * bit for bit.  A cube the scale cannot cover (a +inf voxel, a range that
+ * overflows, or a partial upload beyond the range) keeps its images but
+ * evaluates every sample until the bounds are attached again.
  * MIP renders through vr_render_part use a part's bounds too; no effect on
  * COMPOSITE and SUM renders or on the batched launch.  Uploads refresh the
  * bounds with the texture.  VR_ERR_UNSUPPORTED for other storage types,

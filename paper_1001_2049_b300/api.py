@@ -312,11 +312,14 @@ class Volume:
         check(load().vr_volume_detach_texture(self._h))
 
     def attach_mip_bounds(self, stream=None):
-        """FP32 volumes with texture storage: bfloat16 upper bounds of the
-        voxels, two planes per texel (library-owned, about 4 bytes per
-        voxel); MIP renders then read
-        the FP32 texels only where a sample could raise the maximum, with
-        identical images."""
+        """FP32 volumes with texture storage: 8-bit upper-bound codes of the
+        voxels on one scale for the whole cube, two planes per texel
+        (library-owned, about 2 bytes per voxel); MIP renders then read the
+        FP32 texels only where a sample could raise the maximum, with
+        identical images.  An upload of every plane derives the scale again;
+        a partial upload with values outside the cube's range turns the
+        skipping off (still identical images) until the bounds are attached
+        again."""
         check(load().vr_volume_attach_mip_bounds(self._h, _stream_ptr(stream)))
 
     def detach_mip_bounds(self):

@@ -213,7 +213,7 @@ int prepare(vr_volume vol, const vr_camera* cams, int n_views, int w, int h, int
     tp->dec = v->dec;
     tp->k_max = (int)(diag / step) + 2;
     tp->bound = v->bound_tex;
-    tp->bound_vmax = v->bound_vmax;
+    tp->bound_scale = v->bound_scale;
     p->mask = v->mask;
     p->mnx = v->mnx;
     p->mny = v->mny;
@@ -494,19 +494,18 @@ void release_bounds(vr::Volume* v)
 {
     if (v->bound_tex) cudaDestroyTextureObject(v->bound_tex);
     if (v->bound_array) cudaFreeArray(v->bound_array);
-    if (v->bound_vmax) cudaFree(v->bound_vmax);
+    if (v->bound_scale) cudaFree(v->bound_scale);
     v->bound_tex = 0;
     v->bound_array = nullptr;
-    v->bound_vmax = nullptr;
+    v->bound_scale = nullptr;
 }
 
 // MIP-bound cell slices holding planes [z0, z1): slice s packs planes s - 1
 // and s (clamped), so plane z is in slices z and z + 1.
 int fill_bound_planes(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s);
 
-// Fill MIP-bound slices [s0, s1), raising the device word of the largest
-// |voxel| the fills have seen (the kernels derive the rounding margin from
-// it, bound_margin; it only grows, so after uploads it stays conservative).
+// Fill MIP-bound slices [s0, s1) with the codes of the volume's bound scale
+// (a voxel the scale does not cover turns skipping off, see BoundScale).
 // An unstacked bound texture is written linearly to a stream-ordered scratch
 // buffer and copied into the array, chunk by chunk, with no wait; a stacked
 // one through a surface, the stream waited for before the surface object is
@@ -516,10 +515,10 @@ int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
     if (s0 >= s1) return VR_OK;
     const int nx = v->g.nx, ny = v->g.ny;
     if (v->stack_shift == 0) {
-        const size_t slice = (size_t)nx * ny * sizeof(unsigned);
+        const size_t slice = (size_t)nx * ny * sizeof(unsigned short);
         const int64_t chunk =
             std::max<int64_t>(1, std::min<int64_t>(s1 - s0, (int64_t)((256u << 20) / slice)));
-        unsigned* buf = nullptr;
+        unsigned short* buf = nullptr;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), chunk * slice, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -527,11 +526,11 @@ int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
         }
         for (int64_t c0 = s0; c0 < s1 && e == cudaSuccess; c0 += chunk) {
             const int64_t c1 = std::min(s1, c0 + chunk);
-            e = vr::fill_bounds_linear(*v, buf, (int)c0, (int)c1, v->bound_vmax, s);
+            e = vr::fill_bounds_linear(*v, buf, (int)c0, (int)c1, s);
             if (e == cudaSuccess) {
                 cudaMemcpy3DParms p;
                 std::memset(&p, 0, sizeof p);
-                p.srcPtr = make_cudaPitchedPtr(buf, (size_t)nx * sizeof(unsigned), nx, ny);
+                p.srcPtr = make_cudaPitchedPtr(buf, (size_t)nx * sizeof(unsigned short), nx, ny);
                 p.dstArray = v->bound_array;
                 p.dstPos = make_cudaPos(0, 0, (size_t)c0);
                 p.extent = make_cudaExtent(nx, ny, (size_t)(c1 - c0));
@@ -551,7 +550,7 @@ int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
     cudaSurfaceObject_t surf = 0;
     cudaError_t e = cudaCreateSurfaceObject(&surf, &rd);
     if (e != cudaSuccess) return cuda_fail(e, "surface object");
-    e = vr::fill_bounds(*v, surf, (int)s0, (int)s1, v->bound_vmax, s);
+    e = vr::fill_bounds(*v, surf, (int)s0, (int)s1, s);
     const cudaError_t e2 = cudaStreamSynchronize(s);   // before the surface object goes
     cudaDestroySurfaceObject(surf);
     if (e != cudaSuccess) return cuda_fail(e, "bound fill");
@@ -561,6 +560,12 @@ int fill_bound_slices(vr::Volume* v, int64_t s0, int64_t s1, cudaStream_t s)
 
 int fill_bound_planes(vr::Volume* v, int64_t z0, int64_t z1, cudaStream_t s)
 {
+    // new contents for every plane (a part volume taking its next part): the
+    // scale is derived again from them
+    if (z0 == 0 && z1 >= v->g.nz) {
+        const cudaError_t e = vr::bound_scale(*v, s);
+        if (e != cudaSuccess) return cuda_fail(e, "MIP bound scale");
+    }
     return fill_bound_slices(v, z0, std::min<int64_t>(z1, v->g.nz) + 1, s);
 }
 
@@ -677,8 +682,8 @@ size_t texel_bytes(int format)
 }
 
 // Device bytes of the texture storage (texels of every layer, plus the int8
-// decode records) and of the MIP bounds (bfloat16 pairs in cell slices,
-// plus the maximum word).
+// decode records) and of the MIP bounds (8-bit code pairs in cell slices,
+// plus the scale record).
 size_t texture_bytes(const vr::VolumeGeom& g, int format, const TexLayout& L)
 {
     const size_t texels = (size_t)g.nx * ((size_t)L.pitch << L.shift) * L.layers;
@@ -691,7 +696,7 @@ size_t texture_bytes(const vr::VolumeGeom& g, int format, const TexLayout& L)
 // L: the layout of the bound texture's nz + 1 cell slices (see attach_bounds).
 size_t bounds_bytes(const vr::VolumeGeom& g, const TexLayout& L)
 {
-    return (size_t)g.nx * ((size_t)L.pitch << L.shift) * L.layers * 4 + sizeof(float);
+    return (size_t)g.nx * ((size_t)L.pitch << L.shift) * L.layers * 2 + sizeof(vr::BoundScale);
 }
 
 // The bound texture's layout: the texture's stacking over nz + 1 cell slices.
@@ -710,10 +715,10 @@ int attach_bounds(vr::Volume* v, cudaStream_t s)
     if (v->bound_array) return VR_OK;
     if (v->texture_only)
         return fail(VR_ERR_UNSUPPORTED, "the volume's bricks were dropped: no new bounds");
-    // cell slices (two planes per 32-bit texel, as the pair formats) with the
-    // texture's stacking (vr_ray.cuh), in bfloat16
+    // cell slices (the 8-bit codes of two planes per 16-bit texel, as the pair
+    // formats) with the texture's stacking (vr_ray.cuh)
     const TexLayout L = bound_layout(v->g, v->stack_shift, v->stack_pitch);
-    cudaChannelFormatDesc desc = cudaCreateChannelDesc<unsigned int>();
+    cudaChannelFormatDesc desc = cudaCreateChannelDesc<unsigned short>();
     cudaError_t e = cudaMalloc3DArray(
         &v->bound_array, &desc,
         make_cudaExtent(v->g.nx, (size_t)v->stack_pitch << v->stack_shift, L.layers),
@@ -725,12 +730,12 @@ int attach_bounds(vr::Volume* v, cudaStream_t s)
                     "MIP bound storage of %zu bytes: %s", bounds_bytes(v->g, L),
                     cudaGetErrorString(e));
     }
-    e = cudaMalloc(&v->bound_vmax, sizeof(float));
-    if (e == cudaSuccess) e = cudaMemsetAsync(v->bound_vmax, 0, sizeof(float), s);
+    e = cudaMalloc(reinterpret_cast<void**>(&v->bound_scale), sizeof(vr::BoundScale));
     if (e != cudaSuccess) {
         cudaGetLastError();
+        v->bound_scale = nullptr;
         release_bounds(v);
-        return fail(VR_ERR_OOM, "MIP bound maximum: %s", cudaGetErrorString(e));
+        return fail(VR_ERR_OOM, "MIP bound scale: %s", cudaGetErrorString(e));
     }
     cudaResourceDesc rd;
     std::memset(&rd, 0, sizeof rd);
@@ -747,6 +752,11 @@ int attach_bounds(vr::Volume* v, cudaStream_t s)
         v->bound_tex = 0;
         release_bounds(v);
         return cuda_fail(e, "MIP bound texture object");
+    }
+    e = vr::bound_scale(*v, s);
+    if (e != cudaSuccess) {
+        release_bounds(v);
+        return cuda_fail(e, "MIP bound scale");
     }
     int rc = fill_bound_slices(v, 0, L.slices, s);
     if (rc) release_bounds(v);

@@ -31,6 +31,25 @@ constexpr int kI8Pair = 4;
 constexpr int kMacroShift = 2;
 constexpr int kMacro = 1 << kMacroShift;
 
+// MIP bounds: every voxel v is stored as an 8-bit code c with L + c delta >=
+// v (exact arithmetic), two planes per 16-bit texel (cell slices, as the pair
+// formats), one code scale for the whole cube.  The march tests a sample by
+// the trilinear value of its cell's codes, each read as the float
+// 1 + c 2^-15, against a limit derived from the ray's running maximum
+// (vr_ray.cuh, bound_limit).  This device record holds the scale and the
+// limit's constants; vr_tex.cu derives them from the cube's smallest and
+// largest finite voxels (reduced into lo / hi as ordered bit patterns) and
+// sets le = +inf, which makes every sample a candidate, when the cube holds
+// +inf, its range is not finite, or a later fill meets a voxel the scale
+// does not cover.
+struct BoundScale {
+    float L, delta;         // code c stands for L + c delta, c in [0, 255]
+    float le, inv_q;        // bound_limit: (m - le) inv_q + 1 - 2^-19, rounded down
+    float vlim;             // largest |voxel| le's rounding term covers
+    unsigned lo, hi;        // ordered bit patterns of the smallest / largest finite voxel
+    unsigned inf;           // nonzero: a +inf voxel was seen
+};
+
 // Geometry of a bricked volume, as the kernels see it.
 struct VolumeGeom {
     int nx, ny, nz;         // voxel dims
@@ -66,10 +85,10 @@ struct Volume {
     void* dec;              // VR_I8: per-slice decode records (library-owned)
     // optional MIP bounds (VR_F32 with texture storage, library-owned): cell
     // slices as the pair formats (slice s packs planes s - 1 and s), every
-    // voxel rounded toward +infinity to bfloat16, stacked as the texture
+    // voxel as an 8-bit upper-bound code (BoundScale), stacked as the texture
     cudaArray_t bound_array;
     cudaTextureObject_t bound_tex;
-    float* bound_vmax;      // device word: largest |voxel| seen by the fills
+    BoundScale* bound_scale;    // device record of the code scale
     int cfg[3];             // texture-kernel launch shape per mode (autotuned)
     // optional empty-space masks (caller-owned device buffer)
     unsigned long long* mask;   // valid for clip level mask_clip
@@ -88,13 +107,13 @@ struct TexParams {
     int stack_shift, stack_pitch;   // see Volume
     const void* dec;        // VR_I8 / kI8Pair: float2 / float4 per slice
     int k_max;
-    // MIP bounds (0: none): bfloat16 values rounded up from the FP32 voxels,
-    // two planes per 32-bit texel in cell slices (as the pair formats), with
-    // `tex`'s stacking; a sample whose bound plus the rounding margin
-    // (bound_margin: from the largest |voxel|, a device word) stays below
-    // the ray's running maximum cannot raise it (see march_tex_bound)
+    // MIP bounds (0: none): 8-bit upper-bound codes of the FP32 voxels, two
+    // planes per 16-bit texel in cell slices (as the pair formats), with
+    // `tex`'s stacking, and their scale (BoundScale); a sample whose bound
+    // stays below the limit derived from the ray's running maximum cannot
+    // raise it (see march_tex_bound)
     cudaTextureObject_t bound;
-    const float* bound_vmax;
+    const BoundScale* bound_scale;
 };
 
 size_t brick_bytes(const VolumeGeom& g, int dtype);   // voxel part only
@@ -257,14 +276,18 @@ cudaError_t fill_decode_records(const Volume& v, cudaStream_t s);
 // Fill texture slices [s0, s1) from the bricks through surface `surf`.
 cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1,
                          cudaStream_t s);
-// Fill MIP-bound cell slices [s0, s1) (VR_F32 bricks: slice s packs planes
-// s - 1 and s, clamped, each rounded up to bfloat16) through `surf`, raising
-// *vmax to the largest |voxel| of those planes.
-cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1, float* vmax,
+// The MIP bounds' code scale of the whole cube (VR_F32 bricks): reset
+// v.bound_scale, reduce the smallest and largest finite voxel into it and
+// derive the scale and the march's constants.
+cudaError_t bound_scale(const Volume& v, cudaStream_t s);
+// Fill MIP-bound cell slices [s0, s1) (VR_F32 bricks: slice s packs the codes
+// of planes s - 1 and s, clamped) through `surf`; a voxel above the scale's
+// cap turns skipping off (BoundScale).
+cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int s0, int s1,
                         cudaStream_t s);
 // The same slices written linearly (x fastest, slice after slice) to `dst`,
 // for a copy into an unstacked bound texture.
-cudaError_t fill_bounds_linear(const Volume& v, unsigned* dst, int s0, int s1, float* vmax,
+cudaError_t fill_bounds_linear(const Volume& v, unsigned short* dst, int s0, int s1,
                                cudaStream_t s);
 cudaError_t launch_pack(const Volume& v, int64_t z0, int64_t nplanes, const float* src,
                         cudaStream_t s);

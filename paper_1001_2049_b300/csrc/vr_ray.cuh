@@ -585,17 +585,36 @@ __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4*
     return (int)kf;
 }
 
-// The rounding margin of MIP bounds: 2^-19 of the largest |voxel| the bound
-// fills have seen (a device word, read once per ray), at least the smallest
-// normal float so that subnormal rounding is covered; +inf when a voxel is.
-template <typename TT>
-__device__ __forceinline__ float bound_margin(const TT& T)
+// ---- MIP bounds (8-bit upper-bound codes, BoundScale) ----
+// A cell's corners carry codes c_i with L + c_i delta >= v_i; each is read
+// as the float y_i = 1 + c_i 2^-15 (exact), and the sample's test value is
+// the float trilinear value y of the y_i with the sample's fractions.  With
+// Y the exact trilinear value of the y_i, the exact one of the decoded
+// corners is U = L + Q (Y - 1), Q = delta 2^15, and U is at least the exact
+// trilinear value of the voxels.  The float y is within 18 * 2^-24 of Y
+// (three levels of lerps of values below 2, each adding at most 3 * 2^-24 of
+// the largest), and the sample's float value v within e of the exact
+// trilinear value of the voxels (le = L + e rounded up).  So y < (m - le) /
+// Q + 1 - 2^-19 implies v < m: such a sample cannot raise the running
+// maximum m.  bound_limit evaluates the right-hand side rounded toward -inf
+// at each step (inv_q = 1/Q rounded down, and m - le >= 0 whenever the limit
+// is 1 or more, which every y is), so it never exceeds the exact value; for
+// m = -inf it is -inf, and with le = +inf (skipping off) it is -inf or NaN:
+// every sample is then evaluated.
+__device__ __forceinline__ float bound_limit(float m, float2 q)
 {
-    return fmaxf(__ldg(T.bound_vmax) * 0x1p-19f, 0x1p-126f);
+    return __fmaf_rd(__fsub_rd(m, q.x), q.y, 1.0f - 0x1p-19f);
+}
+
+// {le, inv_q} of the volume's bound scale (read once per ray).
+template <typename TT>
+__device__ __forceinline__ float2 bound_consts(const TT& T)
+{
+    return __ldg(reinterpret_cast<const float2*>(&T.bound_scale->le));
 }
 
 // The MIP-bound texels of the cell at slice z (cell slices: slice z packs
-// the bounds of planes z - 1 and z, low half the lower plane) whose x/y
+// the codes of planes z - 1 and z, low byte the lower plane) whose x/y
 // corner is texel (x-1, y-1): one gather returns all eight corners.
 template <bool STACK, typename TT>
 __device__ __forceinline__ uint4 bound_cell(const TT& T, cudaTextureObject_t tb, int z, float x,
@@ -606,35 +625,27 @@ __device__ __forceinline__ uint4 bound_cell(const TT& T, cudaTextureObject_t tb,
     return gather_u32(tb, l, x, yt);
 }
 
-// The trilinear value of a cell's bound texels.  A bfloat16 is the upper
-// half of a float: the lower plane's bound is the texel shifted up by 16
-// bits; the upper plane's is the whole texel read as a float, whose low 16
-// bits (the lower plane's bound) only move it away from zero by less than
-// one bfloat16 step -- upwards for a positive bound, and the fill stores a
-// negative upper bound one step higher, so the texel stays an upper bound.
+// The test value y of a cell's bound texels: each code byte moved into the
+// mantissa of 1.0f (bits 8-15: 1 + c 2^-15) by one byte permute, then the
+// trilinear interpolation of the eight values.
 __device__ __forceinline__ float bound_interp(const uint4& b, const Geo& g)
 {
-    return interp(make_float4(__uint_as_float(b.x << 16), __uint_as_float(b.y << 16),
-                              __uint_as_float(b.z << 16), __uint_as_float(b.w << 16)),
-                  make_float4(__uint_as_float(b.x), __uint_as_float(b.y),
-                              __uint_as_float(b.z), __uint_as_float(b.w)),
-                  g);
+    auto lo = [](unsigned w) { return __uint_as_float(__byte_perm(w, 0x3f800000u, 0x7604)); };
+    auto hi = [](unsigned w) { return __uint_as_float(__byte_perm(w, 0x3f800000u, 0x7614)); };
+    return interp(make_float4(lo(b.x), lo(b.y), lo(b.z), lo(b.w)),
+                  make_float4(hi(b.x), hi(b.y), hi(b.z), hi(b.w)), g);
 }
 
 // MIP over FP32 texture storage with MIP bounds attached: the march of
-// march_tex runs over the bound texels (bfloat16, each voxel rounded toward
-// +infinity, both planes of a cell in one gather), whose trilinear value u
-// is never below the sample's value v by more than the FP32 rounding of the
-// two interpolations (at most 9 * 2^-24 of the largest |corner| each;
-// bound_margin covers both).  A sample is evaluated from the FP32 texture
-// only when u + margin is not below the running maximum, i.e. when it could
-// raise it; a NaN or infinite bound is never below.  Every sample that can
-// change the maximum is evaluated with march_tex's arithmetic, so the result
-// and the sample count are march_tex's bit for bit, while the march takes
-// one gather per sample for the bounds (gathering every sample, even in the
-// same cell, measured faster than testing for a change of cell and keeping
-// the held texels: the test and the selects cost more issue slots than the
-// gather).
+// march_tex runs over the bound texels (8-bit codes, both planes of a cell
+// in one 16-bit texel, one gather a sample), and a sample is evaluated from
+// the FP32 texture only when its test value is not below the limit of the
+// running maximum (bound_limit), i.e. when it could raise the maximum.  Every
+// sample that can change the maximum is evaluated with march_tex's
+// arithmetic, so the result and the sample count are march_tex's bit for
+// bit.  (Gathering every sample, even in the same cell, measured faster than
+// testing for a change of cell and keeping the held texels: the test and
+// the selects cost more issue slots than the gather.)
 template <bool STACK, typename PP, typename TT>
 __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const Ray& r,
                                                Acc<VR_MIP>& acc)
@@ -642,12 +653,14 @@ __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const R
     if (r.K <= 0) return 0;
     const cudaTextureObject_t tb = T.bound, tf = T.tex;
     const float Kf = (float)r.K;
-    const float margin = bound_margin(T);
+    const float2 q = bound_consts(T);
+    float lim = bound_limit(acc.m, q);
     auto take = [&](const Geo& g, const uint4& u) {
-        if (!(bound_interp(u, g) + margin < acc.m)) {
+        if (!(bound_interp(u, g) < lim)) {
             float4 e0, e1;
             cell<VR_F32, STACK>(T, tf, g.iz, g.gx, g.gy, e0, e1);
             acc.m = fmaxf(acc.m, interp(e0, e1, g));
+            lim = bound_limit(acc.m, q);
         }
     };
     Geo ga = geo(P, r, 0.0f), gb;
@@ -771,12 +784,14 @@ __device__ __forceinline__ int march_part_bound(const PP& P, const TT& T, const 
 {
     if (k0 >= k1) return 0;
     const cudaTextureObject_t tb = T.bound, tf = T.tex;
-    const float margin = bound_margin(T);
+    const float2 q = bound_consts(T);
+    float lim = bound_limit(acc.m, q);
     auto take = [&](const Geo& g, const uint4& u) {
-        if (!(bound_interp(u, g) + margin < acc.m)) {
+        if (!(bound_interp(u, g) < lim)) {
             float4 e0, e1;
             cell<VR_F32, STACK>(T, tf, g.iz, g.gx, g.gy, e0, e1);
             acc.m = fmaxf(acc.m, interp(e0, e1, g));
+            lim = bound_limit(acc.m, q);
         }
     };
     int k = k0;

@@ -36,22 +36,6 @@ __device__ __forceinline__ void write_slice_row(cudaSurfaceObject_t surf, W v, i
     if (y == ny - 1) surf2DLayeredwrite(v, surf, x * (int)sizeof(W), base + ny, layer);
 }
 
-// *vmax = max(*vmax, the largest m of the block's 256 threads); one atomic per
-// block (the bit patterns of values >= 0 order as integers).  Every thread of
-// the block calls it.
-__device__ __forceinline__ void raise_max(float m, float* vmax)
-{
-    __shared__ float warp_max[8];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < 8; ++w) m = fmaxf(m, warp_max[w]);
-        atomicMax(reinterpret_cast<int*>(vmax), __float_as_int(m));
-    }
-}
-
 // Plain formats: slices [s0, s1) of the texture; slice s holds plane s - 1,
 // slices 0 and nz + 1 repeat the edge planes.
 template <typename T>
@@ -71,76 +55,189 @@ __global__ void __launch_bounds__(256) fill_kernel(const T* __restrict__ bricks,
     }
 }
 
-// A float rounded toward +infinity to bfloat16 (its upper 16 bits): never
-// below the value; truncating the low bits raises a negative value, so only
-// positive values with low bits set move up one bfloat16 step (the largest
-// finite value to +inf).  NaN stays NaN (a NaN bound is never below a
-// running maximum, so its samples are always evaluated).
-__device__ __forceinline__ unsigned bf16_up(float v)
+// ---- MIP bounds: 8-bit upper-bound codes (BoundScale) ----
+
+// Order-preserving bit pattern of a float: unsigned comparison of the
+// patterns orders the values (negative values have every bit flipped,
+// non-negative ones the sign bit set).
+__device__ __forceinline__ unsigned ordered_bits(float v)
 {
     const unsigned b = __float_as_uint(v);
-    if (v != v) return 0x7fc0u;
-    const unsigned hi = b >> 16;
-    return ((b & 0xffffu) != 0u && !(b >> 31)) ? hi + 1u : hi;
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-// The MIP-bound texel of cell slice sl at (x, y): the voxels of planes sl - 1
-// and sl (clamped to the cube), each rounded up to bfloat16, packed low =
-// plane sl - 1 (the pair layout of vr_ray.cuh); m is raised to their
-// largest |value| (NaN ignored).  The march reads the whole texel as the
-// upper plane's bound, the low half adding less than one bfloat16 step of
-// magnitude: so a negative upper bound is stored one step further up (a
-// bound of magnitude at most one step becomes +0).
-__device__ __forceinline__ unsigned bound_texel(const float* __restrict__ bricks,
-                                                const VolumeGeom& g, int x, int y, int sl,
-                                                float& m)
+__device__ __forceinline__ float from_ordered(unsigned k)
 {
-    const size_t row = ((size_t)(y >> kBrickShift) * g.nbx + (x >> kBrickShift)) * kBrickVoxels +
-                       ((y & 31) << 5) + (x & 31);
-    const size_t slab = (size_t)g.nbx * g.nby * kBrickVoxels;
-    const int za = min(max(sl - 1, 0), g.nz - 1), zb = min(sl, g.nz - 1);
-    const float lo = bricks[(size_t)(za >> kBrickShift) * slab + row + ((za & 31) << 10)];
-    const float hi = bricks[(size_t)(zb >> kBrickShift) * slab + row + ((zb & 31) << 10)];
-    m = fmaxf(m, fmaxf(fabsf(lo), fabsf(hi)));
-    unsigned h = bf16_up(hi);
-    if (h & 0x8000u) h = (h & 0x7fffu) <= 1u ? 0u : h - 1u;
-    return bf16_up(lo) | (h << 16);
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// MIP bounds: cell slices [s0, s1) (slice s holds planes s - 1 and s, s in
-// [0, nz]) through a surface, stacked as the FP32 texture's slices.  Also
-// raises *vmax to the largest |voxel| read: |voxel| >= 0, so its bit pattern
-// orders as an integer.
-__global__ void __launch_bounds__(256) fill_bound_kernel(const float* __restrict__ bricks,
-                                                         VolumeGeom g, cudaSurfaceObject_t surf,
-                                                         int s0, int s1, int shift, int pitch,
-                                                         float* __restrict__ vmax)
+// Address of voxel (x, y, z) in the FP32 bricks.
+__device__ __forceinline__ size_t voxel_index(const VolumeGeom& g, int x, int y, int z)
+{
+    return ((size_t)((z >> kBrickShift) * g.nby + (y >> kBrickShift)) * g.nbx +
+            (x >> kBrickShift)) * kBrickVoxels +
+           ((z & 31) << 10) + ((y & 31) << 5) + (x & 31);
+}
+
+__global__ void bound_reset_kernel(BoundScale* __restrict__ b)
+{
+    b->lo = 0xffffffffu;
+    b->hi = 0u;
+    b->inf = 0u;
+}
+
+// The smallest and largest finite voxel of the cube (each thread a column of
+// voxels along z, one pair of atomics per block), and whether a voxel is +inf.
+__global__ void __launch_bounds__(256) bound_range_kernel(const float* __restrict__ bricks,
+                                                          VolumeGeom g,
+                                                          BoundScale* __restrict__ b)
 {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    float m = 0.0f;
+    unsigned lo = 0xffffffffu, hi = 0u, inf = 0u;
+    if (x < g.nx && y < g.ny) {
+        for (int z = blockIdx.z; z < g.nz; z += gridDim.z) {
+            const float v = bricks[voxel_index(g, x, y, z)];
+            if (isfinite(v)) {
+                const unsigned k = ordered_bits(v);
+                lo = min(lo, k);
+                hi = max(hi, k);
+            } else if (v > 0.0f) {
+                inf = 1u;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        inf |= __shfl_xor_sync(0xffffffffu, inf, o);
+    }
+    __shared__ unsigned s_lo[8], s_hi[8], s_inf[8];
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+        s_inf[threadIdx.x >> 5] = inf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) {
+            lo = min(lo, s_lo[w]);
+            hi = max(hi, s_hi[w]);
+            inf |= s_inf[w];
+        }
+        atomicMin(&b->lo, lo);
+        atomicMax(&b->hi, hi);
+        if (inf) atomicOr(&b->inf, 1u);
+    }
+}
+
+// The code scale from the cube's range [lo, hi]: L = lo, delta = (hi - lo) /
+// 254 rounded up (so 255 delta exceeds the range by more than the rounding
+// of the codes' test below), and the constants of the march's limit
+// (vr_ray.cuh, bound_limit): le = L + e rounded up, where e = max(2^-19
+// max|voxel|, 2^-126) covers the float rounding of a sample's own trilinear
+// interpolation (at most 9 * 2^-24 of its largest |corner|, subnormal
+// rounding included), and inv_q = 1 / (delta 2^15) rounded down.  Any
+// non-finite step (no finite voxel, a +inf voxel, a range or scale that
+// overflows) leaves le = +inf: then no sample is ever skipped.
+__global__ void bound_finish_kernel(BoundScale* __restrict__ b)
+{
+    const bool any = b->lo <= b->hi;
+    const float lo = any ? from_ordered(b->lo) : 0.0f, hi = any ? from_ordered(b->hi) : 0.0f;
+    float delta = __fdiv_ru(__fsub_ru(hi, lo), 254.0f);
+    delta = fmaxf(delta, 0x1p-126f);
+    const float inv_q = __frcp_rd(delta * 32768.0f);
+    const float vlim = fmaxf(fabsf(lo), fabsf(hi));
+    const float le = __fadd_ru(lo, fmaxf(vlim * 0x1p-19f, 0x1p-126f));
+    const bool ok = any && !b->inf && isfinite(delta) && isfinite(le) && inv_q > 0.0f &&
+                    isfinite(inv_q);
+    b->L = lo;
+    b->delta = ok ? delta : 1.0f;
+    b->inv_q = ok ? inv_q : 0.0f;
+    b->le = ok ? le : INFINITY;
+    b->vlim = vlim;
+}
+
+// The code of voxel v: a c in [0, 255] with L + c delta >= v in exact
+// arithmetic -- checked with r = v - L rounded up and c delta rounded down,
+// c * delta >= r, which implies it.  NaN and -inf take 0 (a sample with such
+// a corner is NaN or -inf and never raises a maximum), values at or below L
+// too.  A voxel the scale cannot cover (+inf, |v| beyond the magnitude le's
+// rounding term was derived from, or no code reaching it) sets `off`:
+// skipping must then be turned off.
+__device__ __forceinline__ unsigned bound_code(float v, const BoundScale& b, bool& off)
+{
+    if (v != v || v == -INFINITY) return 0u;
+    if (!(fabsf(v) <= b.vlim)) {          // beyond the range le covers (+inf included)
+        off = true;
+        return 255u;
+    }
+    if (!(v > b.L)) return 0u;
+    const float r = __fsub_ru(v, b.L);
+    float c = fmaxf(ceilf(__fdiv_ru(r, b.delta)), 1.0f);
+    if (c <= 255.0f && __fmul_rd(c, b.delta) < r) c += 1.0f;
+    if (!(c <= 255.0f)) {
+        off = true;
+        return 255u;
+    }
+    return (unsigned)c;
+}
+
+// The MIP-bound texel of cell slice sl at (x, y): the codes of planes sl - 1
+// (low byte) and sl (high byte), clamped to the cube.
+__device__ __forceinline__ unsigned short bound_texel(const float* __restrict__ bricks,
+                                                      const VolumeGeom& g, const BoundScale& b,
+                                                      int x, int y, int sl, bool& off)
+{
+    const int za = min(max(sl - 1, 0), g.nz - 1), zb = min(sl, g.nz - 1);
+    const unsigned lo = bound_code(bricks[voxel_index(g, x, y, za)], b, off);
+    const unsigned hi = bound_code(bricks[voxel_index(g, x, y, zb)], b, off);
+    return (unsigned short)(lo | (hi << 8));
+}
+
+// A voxel without a code turns skipping off for good (until the scale is
+// derived again): every sample becomes a candidate.
+__device__ __forceinline__ void bound_disable(bool off, BoundScale* __restrict__ b)
+{
+    if (__syncthreads_or(off) && threadIdx.x == 0) b->le = INFINITY;
+}
+
+// MIP bounds: cell slices [s0, s1) (slice s holds planes s - 1 and s, s in
+// [0, nz]) through a surface, stacked as the FP32 texture's slices.
+__global__ void __launch_bounds__(256) fill_bound_kernel(const float* __restrict__ bricks,
+                                                         VolumeGeom g, cudaSurfaceObject_t surf,
+                                                         int s0, int s1, int shift, int pitch,
+                                                         BoundScale* __restrict__ bs)
+{
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    const BoundScale b = *bs;
+    bool off = false;
     if (x < g.nx && y < g.ny) {
         for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z)
-            write_slice_row(surf, bound_texel(bricks, g, x, y, sl, m), x, y, sl, g.ny, shift,
-                            pitch);
+            write_slice_row(surf, bound_texel(bricks, g, b, x, y, sl, off), x, y, sl, g.ny,
+                            shift, pitch);
     }
-    raise_max(m, vmax);
+    bound_disable(off, bs);
 }
 
 // fill_bound_kernel's slices written linearly: slice s0 + j at dst + j nx ny,
 // x fastest (for a copy into an unstacked bound texture).
 __global__ void __launch_bounds__(256) fill_bound_linear_kernel(
-    const float* __restrict__ bricks, VolumeGeom g, unsigned* __restrict__ dst, int s0, int s1,
-    float* __restrict__ vmax)
+    const float* __restrict__ bricks, VolumeGeom g, unsigned short* __restrict__ dst, int s0,
+    int s1, BoundScale* __restrict__ bs)
 {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    float m = 0.0f;
+    const BoundScale b = *bs;
+    bool off = false;
     if (x < g.nx && y < g.ny) {
         for (int sl = s0 + blockIdx.z; sl < s1; sl += gridDim.z)
-            dst[((size_t)(sl - s0) * g.ny + y) * g.nx + x] = bound_texel(bricks, g, x, y, sl, m);
+            dst[((size_t)(sl - s0) * g.ny + y) * g.nx + x] =
+                bound_texel(bricks, g, b, x, y, sl, off);
     }
-    raise_max(m, vmax);
+    bound_disable(off, bs);
 }
 
 // Pair formats: slices [s0, s1); slice s holds the voxels of planes s - 1 and
@@ -244,31 +341,41 @@ void tex_shape(int cfg, int* bx, int* by, int* px, int* py, int* minb)
     *minb = sh.minb;
 }
 
-// The bound fills' grid: 32 x 8 voxel rows per block, at most 32 blocks along
-// the slices (each block then walks several slices), so that the maximum
-// takes a few thousand atomics on one word rather than one per warp row.
+// The bound kernels' grid: 32 x 8 voxel rows per block, at most 32 blocks
+// along the slices (each block then walks several slices), so that the
+// range reduction takes a few thousand atomics rather than one per warp row.
 static dim3 bound_grid(const Volume& v, int z0, int z1)
 {
     return dim3((unsigned)((v.g.nx + 31) / 32), (unsigned)((v.g.ny + 7) / 8),
-                (unsigned)std::min(z1 - z0, 32));
+                (unsigned)std::max(1, std::min(z1 - z0, 32)));
 }
 
-cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int z0, int z1, float* vmax,
+cudaError_t bound_scale(const Volume& v, cudaStream_t s)
+{
+    bound_reset_kernel<<<1, 1, 0, s>>>(v.bound_scale);
+    bound_range_kernel<<<bound_grid(v, 0, v.g.nz), 256, 0, s>>>((const float*)v.bricks, v.g,
+                                                                v.bound_scale);
+    bound_finish_kernel<<<1, 1, 0, s>>>(v.bound_scale);
+    return cudaGetLastError();
+}
+
+cudaError_t fill_bounds(const Volume& v, cudaSurfaceObject_t surf, int z0, int z1,
                         cudaStream_t s)
 {
     if (z1 <= z0) return cudaSuccess;
     const dim3 grid = bound_grid(v, z0, z1);
     fill_bound_kernel<<<grid, 256, 0, s>>>((const float*)v.bricks, v.g, surf, z0, z1,
-                                           v.stack_shift, v.stack_pitch, vmax);
+                                           v.stack_shift, v.stack_pitch, v.bound_scale);
     return cudaGetLastError();
 }
 
-cudaError_t fill_bounds_linear(const Volume& v, unsigned* dst, int z0, int z1, float* vmax,
+cudaError_t fill_bounds_linear(const Volume& v, unsigned short* dst, int z0, int z1,
                                cudaStream_t s)
 {
     if (z1 <= z0) return cudaSuccess;
     const dim3 grid = bound_grid(v, z0, z1);
-    fill_bound_linear_kernel<<<grid, 256, 0, s>>>((const float*)v.bricks, v.g, dst, z0, z1, vmax);
+    fill_bound_linear_kernel<<<grid, 256, 0, s>>>((const float*)v.bricks, v.g, dst, z0, z1,
+                                                  v.bound_scale);
     return cudaGetLastError();
 }
 

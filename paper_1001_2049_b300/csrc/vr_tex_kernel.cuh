@@ -17,8 +17,8 @@
 // interpolated, which hides the texture latency behind the arithmetic.
 // With empty-space masks attached (SKIP, COMPOSITE), samples whose cell the
 // clip makes transparent are not fetched (vr_ray.cuh, march_tex_win); with
-// MIP bounds attached (SKIP, MIP, FP32) the march reads bfloat16 upper
-// bounds and fetches the FP32 corners only where a sample could raise the
+// MIP bounds attached (SKIP, MIP, FP32) the march reads 8-bit upper-bound
+// codes and fetches the FP32 corners only where a sample could raise the
 // maximum (march_tex_bound).
 #pragma once
 
@@ -87,7 +87,7 @@ cudaError_t launch_c(const MarchParams& p, const TexParams& t, cudaStream_t s)
 {
     // SKIP: COMPOSITE with empty-space masks (cells the clip makes
     // transparent are not fetched); MIP on FP32 storage with MIP bounds (the
-    // march reads the bfloat16 bounds and fetches the FP32 corners only of
+    // march reads the 8-bit bound codes and fetches the FP32 corners only of
     // samples that could raise the maximum).  Passing over MIP samples by
     // their cells' corner maxima would not pay: on noise about a quarter of
     // the cells have a corner above a ray's running maximum, so nearly every

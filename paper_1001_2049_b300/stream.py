@@ -142,8 +142,8 @@ class PartStream:
         self.dtype, self.pair = dtype, bool(pair)
         n_vols = min(max(2, int(cache_parts)), len(self.parts))
         from .api import volume_bytes
-        # zeroed: the MIP bounds' rounding margin follows the largest |voxel|
-        # their fills have seen, from the first (empty) fill on
+        # zeroed: the part volumes' first bound fills read defined values (each
+        # part load derives the MIP bounds' scale again from its planes)
         self.bricks = torch.zeros(volume_bytes((nx, ny, self.planes), dtype), dtype=torch.uint8,
                                   device=self.device)
         self.bounds = bool(bounds) and dtype == "f32" and not pair
@@ -179,7 +179,7 @@ class PartStream:
         if self.pair:
             tex_slices, texel = self.planes + 1, 2 * texel
         staging = nx * ny * self.planes * 4
-        bounds = nx * ny * (self.planes + 2) * 2 if self.bounds else 0
+        bounds = nx * ny * (self.planes + 1) * 2 if self.bounds else 0
         masks = self.vols[0].mask_bytes() if self.masks else 0
         return (self.bricks.numel() + staging
                 + len(self.vols) * (nx * ny * tex_slices * texel + bounds + masks))

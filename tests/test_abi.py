@@ -103,8 +103,9 @@ def test_batch_shapes_and_config_host_only():
 def test_library_storage_byte_queries_host_only():
     # what the library would allocate for texture storage and MIP bounds:
     # one texel per voxel of every slice (planes plus the two repeated edge
-    # planes; pair texels one per cell plane), int8 decode records, bfloat16
-    # bound pairs (4 bytes per cell slice texel) plus the maximum word
+    # planes; pair texels one per cell plane), int8 decode records, 8-bit
+    # bound code pairs (2 bytes per cell slice texel) plus the 32-byte scale
+    # record
     from paper_1001_2049_b300 import mip_bounds_bytes, texture_bytes
     nx, ny, nz = 40, 36, 50
     assert texture_bytes((nx, ny, nz), "f32") == nx * ny * (nz + 2) * 4
@@ -112,7 +113,7 @@ def test_library_storage_byte_queries_host_only():
     assert texture_bytes((nx, ny, nz), "i8") == nx * ny * (nz + 2) + (nz + 2) * 8
     assert texture_bytes((nx, ny, nz), "f16", pair=True) == nx * ny * (nz + 1) * 4
     assert texture_bytes((nx, ny, nz), "i8", pair=True) == nx * ny * (nz + 1) * 2 + (nz + 1) * 16
-    assert mip_bounds_bytes((nx, ny, nz)) == nx * ny * (nz + 1) * 4 + 4
+    assert mip_bounds_bytes((nx, ny, nz)) == nx * ny * (nz + 1) * 2 + 32
     # deep cubes stack slices into at most 2048 layers (a power of two per
     # layer), each slice with a copy of its first and last rows: 4002 slices
     # -> 2 per layer, 4098 -> 4 per layer

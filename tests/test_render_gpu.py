@@ -756,7 +756,7 @@ def test_masks_ragged_cubes(dims, step, dtype):
 
 
 # ---------------------------------------------------------------------------
-# MIP bounds: bfloat16 upper bounds decide which samples read the FP32 texels
+# MIP bounds: 8-bit upper-bound codes decide which samples read the FP32 texels
 # ---------------------------------------------------------------------------
 def _mip_with_and_without_bounds(vol, cams, w, h, step):
     outs = []
@@ -807,8 +807,8 @@ def test_mip_bounds_with_extreme_values():
     vol.attach_texture()
     (a, _), (b, _) = _mip_with_and_without_bounds(vol, cams, 29, 19, 0.5)
     assert torch.equal(a, b)
-    # the largest finite floats (their bfloat16 bound rounds up to +inf, or
-    # stays finite for -FLT_MAX) beside ordinary noise
+    # the largest finite floats beside ordinary noise (a range that overflows:
+    # no code scale, every sample a candidate)
     big, _ = _skip_cases(dims, 78)
     fb = big.reshape(-1)
     fmax = np.finfo(np.float32).max
@@ -821,9 +821,9 @@ def test_mip_bounds_with_extreme_values():
 
 
 def test_mip_bounds_on_negative_cubes():
-    # every voxel negative, so every ray's maximum is negative and the bounds
-    # of the upper planes are the ones stored one bfloat16 step higher (read
-    # back as a whole texel); values with low bits set in every magnitude
+    # every voxel negative, so every ray's maximum is negative (the limit of
+    # the running maximum is then below the codes' origin until the maximum
+    # passes it); values with low bits set in every magnitude
     dims = (29, 23, 37)
     cube, cams = _skip_cases(dims, 79)
     for shift, scale in ((-40.0, 1.0), (-1.0e-3, 1.0e-4), (-3.0e5, 7.0e3)):
@@ -861,7 +861,7 @@ def test_mip_bounds_follow_uploads_and_survive_dropping_bricks():
     ref = Volume(torch.from_numpy(cube).cuda(), "f32")
     ref.attach_texture()
     assert torch.equal(vol.render(cams, 21, 21, "mip", 0.5), ref.render(cams, 21, 21, "mip", 0.5))
-    # new planes with a larger maximum: the bounds and their margin follow
+    # new planes beyond the cube's range: skipping is turned off, images stay
     cube2 = cube.copy()
     cube2[20:30] = cube2[20:30] * 40.0 + 3.0
     for v in (vol, ref):
