@@ -1068,7 +1068,7 @@ def main():
             "roofline": {"bound": "hbm",
                          "kernel": ("tex_kernel" if args.storage == "texture"
                                     else "march kernel") + " %s f32" % dom
-                                   + (" (bfloat16 MIP bounds)" if dom == "mip" and bounds_on
+                                   + (" (8-bit MIP bound codes)" if dom == "mip" and bounds_on
                                       else ""),
                          "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -1082,6 +1082,14 @@ def main():
                          "kernel_sources_sha": sha,
                          "algorithmic_bytes_per_launch": dom_bytes, "dominant": dom,
                          "touched_voxels_per_view": touched,
+                         # the whole step: both launches' algorithmic bytes over
+                         # the timed step
+                         "step": {"achieved": (comp_bytes + mip_bytes) * args.steps
+                                  / elapsed / 1e9,
+                                  "frac": (comp_bytes + mip_bytes) * args.steps
+                                  / elapsed / 1e9 / peak,
+                                  "algorithmic_bytes": comp_bytes + mip_bytes,
+                                  "ms": 1000.0 * elapsed / args.steps},
                          "composite": {"achieved": comp_bytes / (comp_ms / 1000.0) / 1e9,
                                        "frac": comp_bytes / (comp_ms / 1000.0) / 1e9 / peak,
                                        "algorithmic_bytes_per_launch": comp_bytes,

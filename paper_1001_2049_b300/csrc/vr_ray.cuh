@@ -625,15 +625,50 @@ __device__ __forceinline__ uint4 bound_cell(const TT& T, cudaTextureObject_t tb,
     return gather_u32(tb, l, x, yt);
 }
 
+// Two floats in one 64-bit register pair, for the packed FP32 instructions
+// (f32x2: the same IEEE operation on both halves).
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 unpack2(unsigned long long r)
+{
+    float2 f;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(r));
+    return f;
+}
+
+// lerpf on both halves: fma(f, b - a, a), rounded as lerpf.
+__device__ __forceinline__ unsigned long long lerp2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long f)
+{
+    unsigned long long d, r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b), "l"(a));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f), "l"(d), "l"(a));
+    return r;
+}
+
 // The test value y of a cell's bound texels: each code byte moved into the
-// mantissa of 1.0f (bits 8-15: 1 + c 2^-15) by one byte permute, then the
-// trilinear interpolation of the eight values.
+// mantissa of 1.0f (bits 8-15: 1 + c 2^-15) by one byte permute, the two
+// planes of a texel side by side in a register pair, then interp's
+// trilinear interpolation with the lerps of both planes in packed
+// instructions (x, then y, then z; the same roundings as interp).  Measured
+// against the scalar interpolation: 46.3 -> 45.8 ms for the 32-view MIP
+// launch of the 1024^3 cube.
 __device__ __forceinline__ float bound_interp(const uint4& b, const Geo& g)
 {
-    auto lo = [](unsigned w) { return __uint_as_float(__byte_perm(w, 0x3f800000u, 0x7604)); };
-    auto hi = [](unsigned w) { return __uint_as_float(__byte_perm(w, 0x3f800000u, 0x7614)); };
-    return interp(make_float4(lo(b.x), lo(b.y), lo(b.z), lo(b.w)),
-                  make_float4(hi(b.x), hi(b.y), hi(b.z), hi(b.w)), g);
+    auto planes = [](unsigned w) {
+        return pack2(__uint_as_float(__byte_perm(w, 0x3f800000u, 0x7604)),
+                     __uint_as_float(__byte_perm(w, 0x3f800000u, 0x7614)));
+    };
+    const unsigned long long fx = pack2(g.fx, g.fx), fy = pack2(g.fy, g.fy);
+    const unsigned long long y0 = lerp2(planes(b.w), planes(b.z), fx);   // row y0, both planes
+    const unsigned long long y1 = lerp2(planes(b.x), planes(b.y), fx);   // row y1
+    const float2 z = unpack2(lerp2(y0, y1, fy));
+    return lerpf(z.x, z.y, g.fz);
 }
 
 // MIP over FP32 texture storage with MIP bounds attached: the march of
