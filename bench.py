@@ -124,13 +124,13 @@ class Clocks:
 # of every CUDA/C++ source of the library (kernel_sources_sha); when the
 # sources differ the bench reports no traffic rather than a stale one.
 TRAFFIC_CAPTURE = {
-    "capture": "prof_tex_windowed: bench.py --cube-edge 512 --views 4 --steps 1 --warmup 1 "
-               "--shapes 7,3 (ncu --set full; profiles/tex_kernel_f32_cube1024_orbit32.md)",
-    "kernel_sha": "be9a99cfac7cf410",
-    # MIP with bfloat16 bounds, shape 3: (2.404920 + 0.011666) GB over 2.130716 GB
-    "mip_bounds": (2.404920e9 + 0.011666e9) / 2.130716e9,
-    # composite with masks, windowed march, shape 7: (0.372862 + 0.033953) GB over 2.153293 GB
-    "composite_masks": (0.372862e9 + 0.033953e9) / 2.153293e9,
+    "capture": "prof_final: bench.py --cube-edge 512 --views 4 --steps 1 --warmup 1 "
+               "--shapes 7,4 (ncu --set full; profiles/tex_kernel_f32_cube1024_orbit32.md)",
+    "kernel_sha": "1217debf4a9e41a4",
+    # MIP with 8-bit bound codes, shape 4: (1.468586 + 0.016431) GB over 2.130716 GB
+    "mip_bounds": (1.468586e9 + 0.016431e9) / 2.130716e9,
+    # composite with masks, windowed march, shape 7: (0.365928 + 0.033382) GB over 2.153293 GB
+    "composite_masks": (0.365928e9 + 0.033382e9) / 2.153293e9,
 }
 
 
