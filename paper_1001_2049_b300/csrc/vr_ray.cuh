@@ -689,9 +689,20 @@ __device__ __forceinline__ float bound_interp(const uint4& b, const Geo& g)
 // running maximum (bound_limit), i.e. when it could raise the maximum.  Every
 // sample that can change the maximum is evaluated with march_tex's
 // arithmetic, so the result and the sample count are march_tex's bit for
-// bit.  (Gathering every sample, even in the same cell, measured faster than
-// testing for a change of cell and keeping the held texels: the test and
-// the selects cost more issue slots than the gather.)
+// bit.  The gathers of the next two samples are in flight while a sample is
+// tested (three register sets in rotation); a pending sample keeps only its
+// fractions and gather result, and a candidate's gather coordinates are
+// computed again from its index (geo is deterministic), which keeps the
+// march at 48 registers (1024^3, 32 views at 1080p: 45.8 -> 44.1 ms against
+// one gather ahead; three ahead 46.1 ms).  (Gathering every sample, even in
+// the same cell, measured faster than testing for a change of cell and
+// keeping the held texels: the test and the selects cost more issue slots
+// than the gather.)
+struct BoundSample {
+    float fx, fy, fz;   // the sample's fractions (geo)
+    uint4 u;            // its cell's bound texels
+};
+
 template <bool STACK, typename PP, typename TT>
 __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const Ray& r,
                                                Acc<VR_MIP>& acc)
@@ -701,30 +712,47 @@ __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const R
     const float Kf = (float)r.K;
     const float2 q = bound_consts(T);
     float lim = bound_limit(acc.m, q);
-    auto take = [&](const Geo& g, const uint4& u) {
-        if (!(bound_interp(u, g) < lim)) {
+    // gather the bounds of sample kf (positions past the ray's end stay
+    // within a few voxels of the box: the texture clamps their coordinates)
+    auto issue = [&](float kf, BoundSample& b) {
+        const Geo g = geo(P, r, kf);
+        b.fx = g.fx;
+        b.fy = g.fy;
+        b.fz = g.fz;
+        b.u = bound_cell<STACK>(T, tb, g.iz, g.gx, g.gy);
+    };
+    auto take = [&](const BoundSample& b, float kf) {
+        Geo h;
+        h.fx = b.fx;
+        h.fy = b.fy;
+        h.fz = b.fz;
+        if (!(bound_interp(b.u, h) < lim)) {
+            const Geo g = geo(P, r, kf);
             float4 e0, e1;
             cell<VR_F32, STACK>(T, tf, g.iz, g.gx, g.gy, e0, e1);
             acc.m = fmaxf(acc.m, interp(e0, e1, g));
             lim = bound_limit(acc.m, q);
         }
     };
-    Geo ga = geo(P, r, 0.0f), gb;
-    uint4 a = bound_cell<STACK>(T, tb, ga.iz, ga.gx, ga.gy), b;
-    float kf = 1.0f;
+    BoundSample sa, sb, sc;
+    issue(0.0f, sa);
+    issue(1.0f, sb);
+    float k = 0.0f;             // the sample taken next
     for (;;) {
-        gb = geo(P, r, kf);
-        b = bound_cell<STACK>(T, tb, gb.iz, gb.gx, gb.gy);
-        take(ga, a);
-        if (kf >= Kf) break;
-        kf += 1.0f;
-        ga = geo(P, r, kf);
-        a = bound_cell<STACK>(T, tb, ga.iz, ga.gx, ga.gy);
-        take(gb, b);
-        if (kf >= Kf) break;
-        kf += 1.0f;
+        issue(k + 2.0f, sc);
+        take(sa, k);
+        if (k + 1.0f >= Kf) break;
+        k += 1.0f;
+        issue(k + 2.0f, sa);
+        take(sb, k);
+        if (k + 1.0f >= Kf) break;
+        k += 1.0f;
+        issue(k + 2.0f, sb);
+        take(sc, k);
+        if (k + 1.0f >= Kf) break;
+        k += 1.0f;
     }
-    return (int)kf;
+    return (int)(k + 1.0f);
 }
 
 // ---- rendering a cube part by part ----
