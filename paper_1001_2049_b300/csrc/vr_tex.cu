@@ -241,11 +241,14 @@ __global__ void __launch_bounds__(256) fill_bound_linear_kernel(
 }
 
 // Pair formats: slices [s0, s1); slice s holds the voxels of planes s - 1 and
-// s (clamped to the cube) packed in one texel, low bits plane s - 1.
+// s (clamped to the cube) packed in one texel, low bits plane s - 1.  `flip`
+// is XORed into the packed texel: int8 codes are stored as q + 128 (each
+// byte's sign bit flipped), which the march turns back into q exactly
+// (vr_ray.cuh, code_lo).
 template <typename T, typename W>
 __global__ void __launch_bounds__(256) fill_pair_kernel(const T* __restrict__ bricks, VolumeGeom g,
                                                         cudaSurfaceObject_t surf, int s0, int s1,
-                                                        int shift, int pitch)
+                                                        int shift, int pitch, W flip)
 {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -257,9 +260,9 @@ __global__ void __launch_bounds__(256) fill_pair_kernel(const T* __restrict__ br
         const int za = min(max(sl - 1, 0), g.nz - 1), zb = min(sl, g.nz - 1);
         const T lo = bricks[(size_t)(za >> kBrickShift) * slab + row + ((za & 31) << 10)];
         const T hi = bricks[(size_t)(zb >> kBrickShift) * slab + row + ((zb & 31) << 10)];
-        const W packed = (W)((W)(unsigned)(typename std::make_unsigned<T>::type)lo |
-                             ((W)(unsigned)(typename std::make_unsigned<T>::type)hi
-                              << (8 * sizeof(T))));
+        const W packed = (W)(((W)(unsigned)(typename std::make_unsigned<T>::type)lo |
+                              ((W)(unsigned)(typename std::make_unsigned<T>::type)hi
+                               << (8 * sizeof(T)))) ^ flip);
         write_slice_row(surf, packed, x, y, sl, g.ny, shift, pitch);
     }
 }
@@ -387,12 +390,12 @@ cudaError_t fill_texture(const Volume& v, cudaSurfaceObject_t surf, int z0, int 
     const int sh = v.stack_shift, pt = v.stack_pitch;
     if (v.tex_format == kF16Pair) {
         fill_pair_kernel<unsigned short, unsigned int><<<grid, 256, 0, s>>>(
-            (const unsigned short*)v.bricks, v.g, surf, z0, z1, sh, pt);
+            (const unsigned short*)v.bricks, v.g, surf, z0, z1, sh, pt, 0u);
         return cudaGetLastError();
     }
     if (v.tex_format == kI8Pair) {
         fill_pair_kernel<signed char, unsigned short><<<grid, 256, 0, s>>>(
-            (const signed char*)v.bricks, v.g, surf, z0, z1, sh, pt);
+            (const signed char*)v.bricks, v.g, surf, z0, z1, sh, pt, (unsigned short)0x8080u);
         return cudaGetLastError();
     }
     switch (v.dtype) {
