@@ -274,7 +274,7 @@ int vr_volume_attach_texture(vr_volume vol, void* stream);
 
 /* Texture storage in pair format, for VR_F16 and VR_I8 volumes: each texel
  * packs a voxel with its neighbour in the next frequency plane (two binary16
- * values in 32 bits, or two int8 codes in 16 bits), one 2-D slice per cell
+ * values in 32 bits, or two int8 codes, each plus 128, in 16 bits), one 2-D slice per cell
  * plane (nz - 1 of them, stacked as in vr_volume_attach_texture), so one
  * four-texel gather returns all eight corners of a cell.  About twice the
  * bytes of vr_volume_attach_texture; replaces a plain texture storage if one

@@ -20,7 +20,8 @@ constexpr int kMaxLayers = 2048;                  // layers of a layered texture
 // kernels are specialised on: the plain storage types (VR_F32, VR_F16, VR_I8:
 // one voxel per texel) and the pair formats, where a texel packs a voxel with
 // its neighbour in the next frequency plane (two binary16 in 32 bits, or two
-// int8 codes in 16 bits), so one gather returns all eight corners of a cell.
+// int8 codes, each plus 128, in 16 bits), so one gather returns all eight
+// corners of a cell.
 constexpr int kF16Pair = 3;
 constexpr int kI8Pair = 4;
 // Empty-space masks: per macrocell of 4 x 4 x 4 cells, a 64-bit mask of the

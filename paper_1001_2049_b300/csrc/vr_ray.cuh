@@ -584,6 +584,40 @@ __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4*
                                          const Ray& r, Acc<MODE>& acc)
 {
     if (r.K <= 0) return 0;
+    if constexpr ((DT == kF16Pair || DT == kI8Pair) && !KEEP_PAIR) {
+        // pair texels gathered every sample: the gathers of the next two
+        // samples in flight while one is interpolated (three register sets
+        // in rotation; 1024^3 FP16 pair MIP, 32 views at 1080p: 44.4 -> 43.3
+        // ms, int8 pair unchanged); the same samples, in the same order,
+        // with the same arithmetic as the loop below
+        const cudaTextureObject_t t0 = T.tex;
+        const float Kf = (float)r.K;
+        Geo ga = geo(P, r, 0.0f), gb = geo(P, r, 1.0f), gc;
+        fetch_dec<DT>(T, ga);
+        fetch_dec<DT>(T, gb);
+        float4 a0, a1, b0, b1, c0, c1;
+        cell<DT, STACK>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
+        cell<DT, STACK>(T, t0, gb.iz, gb.gx, gb.gy, b0, b1);
+        float k = 0.0f;             // the sample evaluated next
+        for (;;) {
+            gc = geo(P, r, k + 2.0f);
+            fetch_dec<DT>(T, gc);
+            cell<DT, STACK>(T, t0, gc.iz, gc.gx, gc.gy, c0, c1);
+            if (acc.add(P, lut, interp_t<DT, true>(T, a0, a1, ga)) || k + 1.0f >= Kf) break;
+            k += 1.0f;
+            ga = geo(P, r, k + 2.0f);
+            fetch_dec<DT>(T, ga);
+            cell<DT, STACK>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
+            if (acc.add(P, lut, interp_t<DT, true>(T, b0, b1, gb)) || k + 1.0f >= Kf) break;
+            k += 1.0f;
+            gb = geo(P, r, k + 2.0f);
+            fetch_dec<DT>(T, gb);
+            cell<DT, STACK>(T, t0, gb.iz, gb.gx, gb.gy, b0, b1);
+            if (acc.add(P, lut, interp_t<DT, true>(T, c0, c1, gc)) || k + 1.0f >= Kf) break;
+            k += 1.0f;
+        }
+        return (int)(k + 1.0f);
+    }
     const cudaTextureObject_t t0 = T.tex;
     const float Kf = (float)r.K;
     Geo ga = geo(P, r, 0.0f), gb;
