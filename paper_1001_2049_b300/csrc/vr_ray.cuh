@@ -591,7 +591,7 @@ __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4*
         // ms, int8 pair unchanged); the same samples, in the same order,
         // with the same arithmetic as the loop below
         const cudaTextureObject_t t0 = T.tex;
-        const float Kf = (float)r.K;
+        const float last = (float)(r.K - 1);
         Geo ga = geo(P, r, 0.0f), gb = geo(P, r, 1.0f), gc;
         fetch_dec<DT>(T, ga);
         fetch_dec<DT>(T, gb);
@@ -603,17 +603,17 @@ __device__ __forceinline__ int march_tex(const PP& P, const TT& T, const float4*
             gc = geo(P, r, k + 2.0f);
             fetch_dec<DT>(T, gc);
             cell<DT, STACK>(T, t0, gc.iz, gc.gx, gc.gy, c0, c1);
-            if (acc.add(P, lut, interp_t<DT, true>(T, a0, a1, ga)) || k + 1.0f >= Kf) break;
+            if (acc.add(P, lut, interp_t<DT, true>(T, a0, a1, ga)) || k >= last) break;
             k += 1.0f;
             ga = geo(P, r, k + 2.0f);
             fetch_dec<DT>(T, ga);
             cell<DT, STACK>(T, t0, ga.iz, ga.gx, ga.gy, a0, a1);
-            if (acc.add(P, lut, interp_t<DT, true>(T, b0, b1, gb)) || k + 1.0f >= Kf) break;
+            if (acc.add(P, lut, interp_t<DT, true>(T, b0, b1, gb)) || k >= last) break;
             k += 1.0f;
             gb = geo(P, r, k + 2.0f);
             fetch_dec<DT>(T, gb);
             cell<DT, STACK>(T, t0, gb.iz, gb.gx, gb.gy, b0, b1);
-            if (acc.add(P, lut, interp_t<DT, true>(T, c0, c1, gc)) || k + 1.0f >= Kf) break;
+            if (acc.add(P, lut, interp_t<DT, true>(T, c0, c1, gc)) || k >= last) break;
             k += 1.0f;
         }
         return (int)(k + 1.0f);
@@ -753,7 +753,7 @@ __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const R
 {
     if (r.K <= 0) return 0;
     const cudaTextureObject_t tb = T.bound, tf = T.tex;
-    const float Kf = (float)r.K;
+    const float last = (float)(r.K - 1);     // the last sample's index
     const float2 q = bound_consts(T);
     float lim = bound_limit(acc.m, q);
     // gather the bounds of sample kf (positions past the ray's end stay
@@ -785,15 +785,15 @@ __device__ __forceinline__ int march_tex_bound(const PP& P, const TT& T, const R
     for (;;) {
         issue(k + 2.0f, sc);
         take(sa, k);
-        if (k + 1.0f >= Kf) break;
+        if (k >= last) break;
         k += 1.0f;
         issue(k + 2.0f, sa);
         take(sb, k);
-        if (k + 1.0f >= Kf) break;
+        if (k >= last) break;
         k += 1.0f;
         issue(k + 2.0f, sb);
         take(sc, k);
-        if (k + 1.0f >= Kf) break;
+        if (k >= last) break;
         k += 1.0f;
     }
     return (int)(k + 1.0f);
