@@ -126,11 +126,11 @@ class Clocks:
 TRAFFIC_CAPTURE = {
     "capture": "prof_final: bench.py --cube-edge 512 --views 4 --steps 1 --warmup 1 "
                "--shapes 7,3 (ncu --set full; profiles/tex_kernel_f32_cube1024_orbit32.md)",
-    "kernel_sha": "2509293110775e39",
-    # MIP with 8-bit bound codes, shape 3: (1.530018 + 0.021698) GB over 2.130716 GB
-    "mip_bounds": (1.530018e9 + 0.021698e9) / 2.130716e9,
-    # composite with masks, windowed march, shape 7: (0.365723 + 0.033865) GB over 2.153293 GB
-    "composite_masks": (0.365723e9 + 0.033865e9) / 2.153293e9,
+    "kernel_sha": "9225e2aef61aa938",
+    # MIP with 8-bit bound codes, shape 3: (1.536429 + 0.021723) GB over 2.130716 GB
+    "mip_bounds": (1.536429e9 + 0.021723e9) / 2.130716e9,
+    # composite with masks, windowed march, shape 7: (0.366292 + 0.033590) GB over 2.153293 GB
+    "composite_masks": (0.366292e9 + 0.033590e9) / 2.153293e9,
 }
 
 
