@@ -100,9 +100,9 @@ struct Volume {
 // Texture storage as the texture kernels see it.
 // int8 texture storage decodes with its planes' scales and offsets, read per
 // texture slice from one record: plain int8 slice s -> {scale, offset} of
-// plane s - 1 (clamped); pair slice s -> {scale, offset} of planes s - 1
-// and s (clamped); applied to each plane's bilinear value of the codes
-// (interp_t).
+// plane s - 1 (clamped); pair slice s -> {scale, scale, offset, offset} of
+// planes s - 1 and s (clamped); applied to each plane's bilinear value of
+// the codes (interp_t).
 struct TexParams {
     cudaTextureObject_t tex;
     int stack_shift, stack_pitch;   // see Volume

@@ -55,6 +55,50 @@ __device__ __forceinline__ constexpr bool debug_ok(bool, unsigned) { return true
 
 __device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(f, b - a, a); }
 
+// Two floats in one 64-bit register pair, for the packed FP32 instructions
+// (f32x2: the same IEEE operation on both halves).
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 unpack2(unsigned long long r)
+{
+    float2 f;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(r));
+    return f;
+}
+
+// a - b on both halves, rounded to nearest.
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// fma(a, b, c) on both halves.
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// lerpf on both halves: fma(f, b - a, a), rounded as lerpf.
+__device__ __forceinline__ unsigned long long lerp2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long f)
+{
+    unsigned long long d, r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b), "l"(a));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f), "l"(d), "l"(a));
+    return r;
+}
+
+
 // Four texels around (x, y) of a layer: with x = i + 1, y = j + 1 (texel
 // centres at +0.5) the footprint is texels i..i+1, j..j+1, returned as
 // (i, j+1), (i+1, j+1), (i+1, j), (i, j).
@@ -180,18 +224,10 @@ __device__ __forceinline__ float half_bits(unsigned b)
 // int8 pair texels hold each code q as the byte q + 128 (the fill flips its
 // sign bit).  A byte permute places that byte under the exponent of 2^23, so
 // the float is 2^23 + q + 128 exactly, and subtracting 2^23 + 128 leaves q
-// exactly: the value (float)q, from two full-rate instructions instead of a
-// conversion (1024^3 int8 pair, 32 views at 1080p: MIP 50.7 -> 43.9 ms).
+// exactly: the value (float)q from full-rate instructions instead of a
+// conversion (interp_t; 1024^3 int8 pair, 32 views at 1080p: MIP 50.7 ->
+// 43.9 ms).
 constexpr float kCodeBias = 8388736.0f;   // 2^23 + 128
-
-__device__ __forceinline__ float code_lo(unsigned b)
-{
-    return __uint_as_float(__byte_perm(b, 0x4b000000u, 0x7540)) - kCodeBias;
-}
-__device__ __forceinline__ float code_hi(unsigned b)
-{
-    return __uint_as_float(__byte_perm(b, 0x4b000000u, 0x7541)) - kCodeBias;
-}
 
 // Texture slices.  Plain formats: slice s holds plane s - 1, and slices 0
 // and nz + 1 repeat planes 0 and nz - 1.  Pair formats: slice s holds the
@@ -316,7 +352,8 @@ struct Geo {
     float gx, gy;     // gather coordinates (cell corner + 1)
     float fx, fy, fz;
     int iz;           // texture slice of the cell's lower plane (cell + 1)
-    float2 d0, d1;    // plain int8: the decode records of slices iz, iz + 1
+    float2 d0, d1;    // plain int8: the decode records of slices iz, iz + 1;
+                      // int8 pair: the planes' scales, then their offsets
 };
 
 template <typename PP>
@@ -360,8 +397,8 @@ __device__ __forceinline__ void fetch_dec(const TT& T, Geo& g)
         g.d1 = __ldg(static_cast<const float2*>(T.dec) + g.iz + 1);
     } else if constexpr (DT == kI8Pair) {
         const float4 d = __ldg(static_cast<const float4*>(T.dec) + g.iz);   // both planes
-        g.d0 = make_float2(d.x, d.y);
-        g.d1 = make_float2(d.z, d.w);
+        g.d0 = make_float2(d.x, d.y);   // the planes' scales
+        g.d1 = make_float2(d.z, d.w);   // and offsets
     }
 }
 
@@ -389,28 +426,43 @@ __device__ __forceinline__ float interp_t(const TT& T, const float4& q0, const f
                       g);
     } else if constexpr (DT != VR_I8 && DT != kI8Pair) {
         return interp(q0, q1, g);
-    } else {
+    } else if constexpr (DT == kI8Pair) {
+        // both planes side by side in register pairs: each texel's two codes
+        // unpacked by one packed subtraction (code_lo / code_hi), both
+        // planes' bilinear lerps and decodes in packed instructions (the
+        // same IEEE operations, in the same order, as the plain int8 path:
+        // images identical)
+        float2 sc, of;                       // the two planes' scales and offsets
+        if constexpr (HELD) {
+            sc = g.d0;
+            of = g.d1;
+        } else {
+            const float4 d = __ldg(static_cast<const float4*>(T.dec) + g.iz);
+            sc = make_float2(d.x, d.y);
+            of = make_float2(d.z, d.w);
+        }
+        auto planes = [](float t) {          // q of plane g.iz - 1, q of plane g.iz
+            const unsigned w = __float_as_uint(t);
+            return sub2(pack2(__uint_as_float(__byte_perm(w, 0x4b000000u, 0x7540)),
+                              __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7541))),
+                        pack2(kCodeBias, kCodeBias));
+        };
+        const unsigned long long fx = pack2(g.fx, g.fx), fy = pack2(g.fy, g.fy);
+        const unsigned long long y0 = lerp2(planes(q0.w), planes(q0.z), fx);
+        const unsigned long long y1 = lerp2(planes(q0.x), planes(q0.y), fx);
+        const float2 v = unpack2(fma2(lerp2(y0, y1, fy), pack2(sc.x, sc.y), pack2(of.x, of.y)));
+        return lerpf(v.x, v.y, g.fz);
+    } else {                                  // plain int8: the two planes' codes
         float2 d0, d1;
         if constexpr (HELD) {
             d0 = g.d0;
             d1 = g.d1;
-        } else if constexpr (DT == VR_I8) {
+        } else {
             d0 = __ldg(static_cast<const float2*>(T.dec) + g.iz);   // {scale, offset}
             d1 = __ldg(static_cast<const float2*>(T.dec) + g.iz + 1);
-        } else {
-            const float4 d = __ldg(static_cast<const float4*>(T.dec) + g.iz);   // both planes
-            d0 = make_float2(d.x, d.y);
-            d1 = make_float2(d.z, d.w);
         }
-        float4 c0 = q0, c1 = q1;             // plain int8: the two planes' codes
-        if constexpr (DT == kI8Pair) {       // packed: plane g.iz - 1 in the low bytes
-            const unsigned px = __float_as_uint(q0.x), py = __float_as_uint(q0.y),
-                           pz = __float_as_uint(q0.z), pw = __float_as_uint(q0.w);
-            c0 = make_float4(code_lo(px), code_lo(py), code_lo(pz), code_lo(pw));
-            c1 = make_float4(code_hi(px), code_hi(py), code_hi(pz), code_hi(pw));
-        }
-        const float b0 = lerpf(lerpf(c0.w, c0.z, g.fx), lerpf(c0.x, c0.y, g.fx), g.fy);
-        const float b1 = lerpf(lerpf(c1.w, c1.z, g.fx), lerpf(c1.x, c1.y, g.fx), g.fy);
+        const float b0 = lerpf(lerpf(q0.w, q0.z, g.fx), lerpf(q0.x, q0.y, g.fx), g.fy);
+        const float b1 = lerpf(lerpf(q1.w, q1.z, g.fx), lerpf(q1.x, q1.y, g.fx), g.fy);
         return lerpf(fmaf(b0, d0.x, d0.y), fmaf(b1, d1.x, d1.y), g.fz);
     }
 }
@@ -678,32 +730,6 @@ __device__ __forceinline__ uint4 bound_cell(const TT& T, cudaTextureObject_t tb,
     float yt;
     const int l = plane_layer<STACK>(T, z, y, yt);
     return gather_u32(tb, l, x, yt);
-}
-
-// Two floats in one 64-bit register pair, for the packed FP32 instructions
-// (f32x2: the same IEEE operation on both halves).
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
-{
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-
-__device__ __forceinline__ float2 unpack2(unsigned long long r)
-{
-    float2 f;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(r));
-    return f;
-}
-
-// lerpf on both halves: fma(f, b - a, a), rounded as lerpf.
-__device__ __forceinline__ unsigned long long lerp2(unsigned long long a, unsigned long long b,
-                                                    unsigned long long f)
-{
-    unsigned long long d, r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b), "l"(a));
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f), "l"(d), "l"(a));
-    return r;
 }
 
 // The test value y of a cell's bound texels: each code byte moved into the

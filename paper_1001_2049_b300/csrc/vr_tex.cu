@@ -302,8 +302,8 @@ __global__ void __launch_bounds__(256) dec_kernel(const float* __restrict__ scal
     const int sl = blockIdx.x * blockDim.x + threadIdx.x;
     if (sl >= n) return;
     const int z0 = min(max(sl - 1, 0), nz - 1), z1 = min(sl, nz - 1);
-    if (pair)
-        static_cast<float4*>(out)[sl] = make_float4(scale[z0], offset[z0], scale[z1], offset[z1]);
+    if (pair)   // {scale, scale, offset, offset} of planes sl - 1 and sl
+        static_cast<float4*>(out)[sl] = make_float4(scale[z0], scale[z1], offset[z0], offset[z1]);
     else
         static_cast<float2*>(out)[sl] = make_float2(scale[z0], offset[z0]);
 }
