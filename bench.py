@@ -126,11 +126,11 @@ class Clocks:
 TRAFFIC_CAPTURE = {
     "capture": "prof_final: bench.py --cube-edge 512 --views 4 --steps 1 --warmup 1 "
                "--shapes 7,3 (ncu --set full; profiles/tex_kernel_f32_cube1024_orbit32.md)",
-    "kernel_sha": "9225e2aef61aa938",
-    # MIP with 8-bit bound codes, shape 3: (1.536429 + 0.021723) GB over 2.130716 GB
-    "mip_bounds": (1.536429e9 + 0.021723e9) / 2.130716e9,
-    # composite with masks, windowed march, shape 7: (0.366292 + 0.033590) GB over 2.153293 GB
-    "composite_masks": (0.366292e9 + 0.033590e9) / 2.153293e9,
+    "kernel_sha": "96a7a1cab272c21e",
+    # MIP with 8-bit bound codes, shape 3: (1.534231 + 0.021571) GB over 2.130716 GB
+    "mip_bounds": (1.534231e9 + 0.021571e9) / 2.130716e9,
+    # composite with masks, windowed march, shape 7: (0.366143 + 0.033616) GB over 2.153293 GB
+    "composite_masks": (0.366143e9 + 0.033616e9) / 2.153293e9,
 }
 
 
