@@ -820,6 +820,31 @@ def test_mip_bounds_with_extreme_values():
     assert torch.equal(a, b) and na == nb
 
 
+def test_mip_bounds_on_degenerate_ranges():
+    # the code scale's edge cases: a constant cube (range 0: every sample a
+    # candidate), a cube of NaN but one plane, a range far below one code
+    # step of a normal scale (subnormal differences) and one that overflows
+    # a float (no scale: skipping off); images and counts as without bounds
+    dims = (21, 18, 26)
+    _, cams = _skip_cases(dims, 80)
+    rng = np.random.default_rng(9)
+    cases = {
+        "constant": np.full(dims[::-1], 2.5, np.float32),
+        "nan": np.full(dims[::-1], np.nan, np.float32),
+        "tiny range": (np.float32(1.0) + rng.integers(0, 3, dims[::-1]).astype(np.float32)
+                       * np.float32(2.0 ** -23)),
+        "overflowing range": np.clip(rng.standard_normal(dims[::-1]) * 1e38, -3e38,
+                                     3e38).astype(np.float32),
+    }
+    cases["nan"][5] = rng.standard_normal(dims[1::-1]).astype(np.float32)
+    for name, cube in cases.items():
+        vol = Volume(torch.from_numpy(np.ascontiguousarray(cube)).cuda(), "f32")
+        vol.attach_texture()
+        (a, na), (b, nb) = _mip_with_and_without_bounds(vol, cams, 29, 19, 0.41)
+        assert torch.equal(torch.nan_to_num(a), torch.nan_to_num(b)), name
+        assert na == nb, name
+
+
 def test_mip_bounds_on_negative_cubes():
     # every voxel negative, so every ray's maximum is negative (the limit of
     # the running maximum is then below the codes' origin until the maximum
